@@ -1,0 +1,317 @@
+"""Benchmark: ECMC liftings per second on one GB300 (N = 2^20 disks, eta = 0.72).
+
+Workload: a 1024 x 1024 jittered square lattice (seeded), eta = 0.72, k
+chains (default 1024), chain length ell = 1 between breakpoints, v = +x.
+One step = one ecmc_run_to_breakpoint call of --legs legs. ``value`` is
+liftings per second of device time (CUDA events on the context's stream,
+inputs resident in HBM), ``e2e`` the same metric through the C-ABI with host
+buffers (create from host x/y, run, read positions back) inside the timed
+region. The working set (~100 MB) is below the 129 MB L2, so L2 is flushed
+with a 512 MB write between timed steps.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded
+sample of the same workload.
+
+Multi-GPU: the path does not shard a single system; every rank runs an
+independent replica (its own seed), ``value`` sums all ranks' liftings over
+the slowest rank's time ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_LIFTING = 104  # algorithmic: read x,y,t of <= 3 neighbours (72 B), write x_i,t_i,t_j + 2 tags (32 B)
+METRIC = "liftings/s (ECMC events/s), N=2^20 hard disks, eta=0.72, ell=1"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--k", type=int, default=1024, help="chains")
+    p.add_argument("--legs", type=int, default=10, help="legs per step")
+    p.add_argument("--m", type=int, default=1024, help="lattice side (N = m*m)")
+    p.add_argument("--eta", type=float, default=0.72)
+    p.add_argument("--ell", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def workload(a):
+    return {"workload": f"lattice {a.m}x{a.m} (N={a.m * a.m}) eta={a.eta} jitter=0.01, "
+                        f"k={a.k} chains, ell={a.ell}, v=+x, {a.legs} legs/step",
+            "n": a.m * a.m, "eta": a.eta, "k": a.k, "ell": a.ell, "legs_per_step": a.legs,
+            "seed": a.seed, "l2": "flushed between steps (512 MB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for s in self.samples for q in range(4)
+                          if len(s) > 4 + q and s[4 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------- helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2004_11040_gb300", "csrc", "ecmc.cu"), "rb").read()
+        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def cpu_baseline(a, start, budget_s):
+    """The oracle as it stands, one host core, on whole legs of the same workload."""
+    from oracle import oracle as O
+    O.build()
+    x, act = start.x.copy(), start.active.copy()
+    lifts, legs = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        r = O.run_leg(x, start.y, act, start.box, a.ell, log=False)
+        x, act = r.x, r.active
+        lifts += r.lifts
+        legs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": lifts / el, "unit": "liftings/s", "cores": 1, "kind": "oracle",
+            "sample": f"{legs} whole legs ({lifts} liftings) of the same workload in {el:.1f} s"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ reference
+
+def run_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2004_11040_gb300 import synth
+    start = synth.lattice_start(a.m, a.eta, a.k, seed=a.seed)
+    budget = max(2.0, 60.0 / max(1, a.steps + a.warmup))
+    cb = None
+    vals = []
+    for s in range(a.warmup + a.steps):
+        r = cpu_baseline(a, start, budget)
+        if s >= a.warmup:
+            vals.append(r["value"])
+            cb = r
+    v = sum(vals) / len(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "liftings/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1000.0 * budget, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(a),
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "liftings/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    from paper_2004_11040_gb300 import build, ecmc, synth
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    start = synth.lattice_start(a.m, a.eta, a.k, seed=a.seed + rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    sysm = ecmc.System(start.x, start.y, start.active, start.box, a.ell, stream=stream)
+    for _ in range(a.warmup):
+        sysm.run(a.legs)
+    st0, pr0 = sysm.stats(), sysm.profile()
+    dev_ms = 0.0
+    lifts = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        for _ in range(a.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            b = sysm.stats()
+            sysm.run(a.legs)
+            e = sysm.stats()
+            dev_ms += e["device_ms"] - b["device_ms"]
+            lifts += e["liftings"] - b["liftings"]
+        barrier()
+    st1, pr1 = sysm.stats(), sysm.profile()
+    t_max = dev_ms
+    tot_lifts = lifts
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ll = torch.tensor([lifts], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ll, op=dist.ReduceOp.SUM)
+        tot_lifts = int(ll.item())
+    value = tot_lifts / (t_max / 1000.0)
+
+    # dominant kernel and its roofline
+    d = {key: pr1[key] - pr0[key] for key in pr1}
+    if d["repair_ms"] > d["pass1_ms"]:
+        kname, kms, kl, kn = "k_global_run", d["repair_ms"], d["repair_liftings"], d["repair_launches"]
+    else:
+        kname, kms, kl, kn = "k_pass1", d["pass1_ms"], d["pass1_liftings"], d["pass1_launches"]
+    peak, peak_kind = peaks()
+    achieved = (kl * BYTES_PER_LIFTING) / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
+    conflict_legs = st1["conflict_legs"] - st0["conflict_legs"]
+    legs = st1["legs"] - st0["legs"]
+    launches = 3 * legs + 3 * conflict_legs
+
+    # end to end through the C-ABI with host buffers
+    nx = start.n
+    e2e_lifts, e2e_s = 0, 0.0
+    h2d = 2 * nx * 8 + 4 * a.k
+    d2h = 2 * nx * 8 + 4 * a.k
+    hx = torch.from_numpy(start.x).pin_memory().numpy()
+    hy = torch.from_numpy(start.y).pin_memory().numpy()
+    ha = torch.from_numpy(start.active.astype(np.int32)).pin_memory().numpy()
+    ox = torch.empty(nx, dtype=torch.float64).pin_memory().numpy()
+    ot = torch.empty(nx, dtype=torch.float64).pin_memory().numpy()
+    oa = torch.empty(a.k, dtype=torch.int32).pin_memory().numpy()
+    for s in range(max(1, a.steps // 2) + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = ecmc.ecmc_create(sysm.params, hx, hy, ha, stream)
+        fl = np.zeros(a.legs, dtype=np.uint8)
+        ecmc.ecmc_run_to_breakpoint(ctx, a.legs, 0, fl)
+        ecmc.ecmc_positions(ctx, ox, None, ot, oa)
+        el = time.perf_counter() - t0
+        n_l = ecmc.ecmc_stats(ctx)["liftings"]
+        ecmc.ecmc_destroy(ctx)
+        if s > 0:
+            e2e_lifts += n_l
+            e2e_s += el
+    e2e = {"value": e2e_lifts / e2e_s, "unit": "liftings/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    sysm.close()
+
+    if rank != 0:
+        return
+    cb = None
+    if ws == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a, start, a.cpu_seconds)
+    traffic = traffic_for(kname)
+    line = {
+        "metric": METRIC, "value": value, "unit": "liftings/s", "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload(a),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                     "peak_source": peak_kind,
+                     "bytes_per_lifting": BYTES_PER_LIFTING,
+                     "kernel_ms_per_launch": kms / max(kn, 1),
+                     "liftings_per_launch": kl / max(kn, 1)},
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "detail": {"legs": legs, "conflict_legs": conflict_legs,
+                   "liftings": tot_lifts, "profile": d,
+                   "horizon_asserts": st1["horizon_asserts"],
+                   "order_errors": st1["order_errors"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

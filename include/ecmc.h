@@ -1,0 +1,159 @@
+/*
+ * ecmc.h -- C ABI of libecmc: event-chain Monte Carlo (ECMC) for hard disks in
+ * a periodic square box, many chains at once on one GPU (sm_103a).
+ *
+ * The method is that of Li, Todo, Maggs & Krauth, "Multithreaded event-chain
+ * Monte Carlo with local times" (arXiv:2004.11040): between two breakpoints h
+ * and h' = h + ell, k active disks move with v = (1, 0); at a lifting
+ * i -> j (Eq. 1) activity passes from the moving disk i to the disk j it
+ * touches, and the local time t_j is set to t_i (Sec. 2.1, Alg. 1/2). Each
+ * chain advances on its own local time (Sec. 2.2-2.4, Alg. 4-6); the result is
+ * that of the global-time process (Alg. 2, Lemma 2).
+ *
+ * Conventions shared by every call:
+ *   - Disks have diameter d (the contact distance; the paper's 2*sigma).
+ *   - Positions are FP64 in [0, L). Only x changes during a leg (v = (1,0)).
+ *   - Local times are leg-relative: 0 at the start of every leg, ell for the
+ *     stalled (still active) disks at its end (Remark 1).
+ *   - Chain c owns one active disk; chain order matters only for tie-breaking
+ *     of simultaneous events and for the order of the returned lists.
+ *   - Every call returns ECMC_OK (0) or a negative ECMC_E* code and never
+ *     aborts the process; ecmc_last_error() gives a one-line reason.
+ *   - All pointers named "host" are ordinary host memory owned by the caller.
+ *     The context owns every device allocation it makes.
+ *   - Calls on one context must not run concurrently from several host threads.
+ */
+#ifndef ECMC_H
+#define ECMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ECMC_OK 0
+#define ECMC_EINVAL (-1)    /* bad parameters or inputs */
+#define ECMC_ENOMEM (-2)    /* device or host allocation failed */
+#define ECMC_ECUDA (-3)     /* a CUDA call failed (message in last_error) */
+#define ECMC_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define ECMC_ECAPACITY (-5) /* a fixed-size buffer (cell slots, undo log) overflowed */
+
+/* ecmc_params.flags */
+#define ECMC_LOG_LIFTINGS 0x1u /* keep every lifting for ecmc_liftings() */
+#define ECMC_INPUT_DEVICE 0x2u /* x, y, active passed to ecmc_create are device pointers */
+
+typedef struct ecmc_ctx ecmc_ctx;
+
+typedef struct {
+    int64_t n;              /* number of disks N (>= 3) */
+    double box;             /* side L of the periodic square box */
+    double d;               /* disk diameter (contact distance), > 0 */
+    double ell;             /* chain length between breakpoints (h' - h), > 0 */
+    int32_t n_chains;       /* k, 1 <= k <= n */
+    int32_t cells_per_side; /* nc; 0 picks the largest nc with L/nc >= d*(1+2^-20).
+                               Needs nc >= 3 and L/nc < 1.664*d. */
+    uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE */
+    int32_t undo_cap;       /* per-chain event records per leg; 0 = 1024 */
+    int64_t log_cap;        /* liftings kept with ECMC_LOG_LIFTINGS; 0 = 1<<22 */
+} ecmc_params;
+
+typedef struct {
+    int64_t liftings;        /* liftings (events, Eq. 1) over all legs run */
+    int64_t legs;            /* breakpoints reached */
+    int64_t conflict_legs;   /* legs in which two chains' scanned cells met */
+    int64_t repaired_chains; /* chain runs rolled back and redone in time order */
+    int64_t horizon_asserts; /* Eq. 2 failures seen by a conflict-free chain: 0 */
+    int64_t order_errors;    /* repaired events found out of time order: 0 */
+    double device_ms;        /* device time spent in ecmc_run_to_breakpoint */
+} ecmc_stats_t;
+
+/* One lifting i -> j (Eq. 1): chain c, leg index, time t (= new t_j),
+   time of flight tau, x of i at contact, x of j. */
+typedef struct {
+    int32_t leg, c, i, j;
+    double t, tau, xi, xj;
+} ecmc_lift_t;
+
+/*
+ * ecmc_create -- a context holding the lifted configuration {C_h, A_h}
+ * (Sec. 2.1, Alg. 1 input) on the device.
+ *   p       problem description (copied).
+ *   x, y    n positions each; host pointers unless ECMC_INPUT_DEVICE.
+ *           Every coordinate must lie in [0, L); disks must not overlap.
+ *   active  k distinct disk ids; chain c starts on active[c].
+ *   stream  a cudaStream_t (may be NULL for the default stream) on which all
+ *           work of this context is queued; the caller keeps it alive.
+ *   out     receives the context; free it with ecmc_destroy.
+ * Errors: EINVAL (sizes, ids, coordinates, cell geometry), ENOMEM, ECUDA,
+ * ECAPACITY (more disks in a cell than its slots: overlapping input).
+ */
+int ecmc_create(const ecmc_params *p, const double *x, const double *y,
+                const int32_t *active, void *stream, ecmc_ctx **out);
+
+/*
+ * ecmc_run_to_breakpoint -- runs n_legs legs of length ell (Alg. 2 semantics:
+ * each leg ends at the breakpoint h' with all chains stalled, Remark on
+ * stalled spheres), each chain restarting from its stalled disk.
+ *   event_budget  0 = run all n_legs; otherwise stop at the first breakpoint
+ *                 at which the liftings of this call reach the budget.
+ *   leg_flags_out host, n_legs bytes or NULL: 1 for a leg in which two chains
+ *                 scanned a common cell (the leg was then redone in global
+ *                 time order), else 0; entries past *legs_done are untouched.
+ *   legs_done     host or NULL: number of legs completed.
+ * Returns when the legs are done (the stream is synchronised).
+ * Errors: EINVAL, ECUDA, ECAPACITY (undo log), ETIMEOUT.
+ */
+int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t event_budget,
+                           uint8_t *leg_flags_out, int32_t *legs_done);
+
+/*
+ * ecmc_positions -- copies the current configuration to host arrays
+ * (caller-owned; any pointer may be NULL to skip it):
+ *   x, y, t  n doubles each, indexed by disk id; t is leg-relative.
+ *   active   k ints: chain c's active (stalled) disk.
+ * Synchronises the context's stream.
+ */
+int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *active);
+
+/* ecmc_stats -- counters accumulated since ecmc_create (host struct). */
+int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
+
+/*
+ * ecmc_liftings -- the liftings kept under ECMC_LOG_LIFTINGS, leg by leg and,
+ * within a leg, chain by chain in the order each chain made them.
+ *   buf, cap  caller-owned host array; n_out receives the total count (may
+ *             exceed cap; then only cap records are written).
+ * Errors: EINVAL if logging was not enabled; ECAPACITY if log_cap overflowed.
+ */
+int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out);
+
+/*
+ * ecmc_profile -- device time per kernel class, measured with CUDA events on
+ * the context's stream around every launch of ecmc_run_to_breakpoint:
+ *   pass1   the parallel pass (one warp per chain, Alg. 5/6 statements 1-26);
+ *   repair  the global-time redo of legs with a conflict (Alg. 2);
+ *   other   leg start/end bookkeeping, claim reset, rollback.
+ * *_liftings count the liftings each class executed (pass-1 liftings of a
+ * redone leg included).
+ */
+typedef struct {
+    int64_t pass1_launches, repair_launches, other_launches;
+    int64_t pass1_liftings, repair_liftings;
+    double pass1_ms, repair_ms, other_ms;
+} ecmc_profile_t;
+
+int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out);
+
+/* ecmc_destroy -- frees every device allocation of ctx (NULL is a no-op). */
+void ecmc_destroy(ecmc_ctx *ctx);
+
+/* ecmc_last_error -- reason for the last failure on ctx ("" if none); the
+   string belongs to ctx. With ctx == NULL, the last ecmc_create failure. */
+const char *ecmc_last_error(const ecmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECMC_H */

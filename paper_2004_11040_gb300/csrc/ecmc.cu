@@ -1,0 +1,1451 @@
+// ecmc.cu -- libecmc: multithreaded event-chain Monte Carlo for hard disks on
+// one GPU (sm_103a), after Li, Todo, Maggs & Krauth, "Multithreaded event-chain
+// Monte Carlo with local times" (arXiv:2004.11040).
+//
+// Design (one leg = one interval [h, h'] between breakpoints, v = (1, 0)):
+//   * Disks live in square cells of side a = L/nc > d, stored as per-slot
+//     structure-of-arrays (x, y, id); C slots per cell (C = 4 for a < sqrt(2) d).
+//   * One warp runs one chain (Alg. 5/6 statements 1-26): lanes cover
+//     3 rows x C slots of one or two columns ahead of the active disk, compute
+//     the time of flight tau_j = dx_j - sqrt(d^2 - dy_j^2) in FP64 (Sec. 2.2,
+//     statement 4), and reduce (tau, j) with warp shuffles (statements 6-9).
+//   * Before a chain may use a cell it claims it for the leg with atomicCAS on
+//     a per-cell word (statement 10's CAS, lifted from disks to cells). Cells
+//     therefore change only under their claimer, and a chain that meets a cell
+//     claimed by another chain stops: the leg's conflict flag. The target disk
+//     is also claimed with atomicCAS on its per-disk owner word (statement 10).
+//   * Without a conflict every chain followed exactly the path it would take
+//     alone, which equals the global-time result (Lemma 2). With a conflict
+//     the chains that met (connected components of the conflict graph) are
+//     rolled back to the earliest time T* at which one of them was blocked --
+//     their events before T* are exact -- and one warp per component redoes
+//     them from T* in global event-time order (Alg. 2). A component that meets
+//     a cell of another chain stops and merges with it in the next round.
+//     This is the first restart strategy of Sec. 3.4, made exact and local.
+// All FP64 arithmetic uses explicit round-to-nearest intrinsics (and the file
+// is compiled with -fmad=false) so that results are reproducible bit for bit.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ecmc.h"
+
+namespace {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t OWN_STATIC = 0u;
+constexpr uint32_t OWN_ACTIVE = 0x40000000u;
+constexpr uint32_t OWN_STALLED = 0x80000000u;
+constexpr uint32_t OWN_CHAIN = 0x3FFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
+
+// per-leg counters (reset at every leg start)
+enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
+       LC_P1LIFTS, LC_REPAIRED, LC_N };
+enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
+// cumulative counters
+enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,
+       TC_LOG_N, TC_N };
+
+// One event of a chain: enough to undo it, and the lifting record (Eq. 1).
+struct Rec {
+    uint32_t i, from, to, j;  // moved disk, its slot before/after, target (NONE: stall)
+    uint32_t jloc, seq;       // slot of j; order of application within its run
+    double x_old;             // x of i before the move
+    double ti_old, tj_old;    // local times of i and j before the event
+    double t, tau, xi, xj;    // event time (= new t_j), time of flight, x_i at contact, x_j
+    double d_after;           // remaining chain length after the event
+};
+
+struct Dev {
+    int64_t n;
+    int nc, k, cap;
+    double L, d, ell, a, inv_a, eps;
+    // cells: slot q of cell c at index c*C + q
+    double *cx, *cy;
+    uint32_t *cid;
+    uint32_t *claim;  // per cell: 0 or chain+1
+    // per disk
+    double *t;
+    uint32_t *owner;
+    // per chain
+    uint32_t *aloc0, *aloc;
+    uint32_t *ci;  // active disk id
+    double *D, *tc;
+    int32_t *status, *partner, *nrec, *nlift;
+    Rec *rec;  // [k * cap]
+    // pending events for the global-time repair
+    double *ev_T, *ev_tau, *ev_xj, *ev_yj, *ev_tj;
+    uint32_t *ev_j, *ev_jloc;
+    int32_t *ev_lift, *ev_cx, *ev_cy, *ev_mlast;
+    // conflict components
+    double *vt;          // per chain: its events are exact before this time
+    int32_t *uf;         // union-find parent
+    int32_t *fin;        // 1: the chain's events of this leg are final
+    int32_t *comp_of;    // component root per chain
+    int32_t *abort_to;   // chain met by an aborted component (per root), -1
+    int32_t *comp_cnt;   // members per root (dirty components)
+    int32_t *comp_off;   // [k+1] offsets of dirty components
+    int32_t *comp_root;  // root of the q-th dirty component
+    int32_t *comp_mem;   // members, grouped by component
+    int32_t *ctl;        // [CTL_N]
+    int32_t round;
+    unsigned long long *lc;  // [LC_N]
+    unsigned long long *tc_cnt;  // [TC_N]
+    ecmc_lift_t *log;
+    int64_t log_cap;
+    int log_on;
+};
+
+// ------------------------------------------------------------ FP64 geometry
+
+__device__ __forceinline__ int cell_coord(double v, const Dev &s) {
+    int c = __double2int_rz(__dmul_rn(v, s.inv_a));
+    if (c >= s.nc) c = s.nc - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t cell_of(double x, double y, const Dev &s) {
+    return (uint32_t)cell_coord(y, s) * (uint32_t)s.nc + (uint32_t)cell_coord(x, s);
+}
+
+__device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
+    double r = __dadd_rn(x, dx);
+    if (r >= s.L) r = __dsub_rn(r, s.L);
+    return r;
+}
+
+// Time of flight of i towards j (Sec. 2.2: tau = x_j - x_i - b_ij), forward
+// image in x, minimum image in y, corridor |dy| < d; +inf outside.
+__device__ __forceinline__ double time_of_flight(double xi, double yi, double xj, double yj,
+                                                 const Dev &s) {
+    double a = fabs(__dsub_rn(yj, yi));
+    double la = __dsub_rn(s.L, a);
+    if (la < a) a = la;
+    if (!(a < s.d)) return INFINITY;
+    double b = __dsqrt_rn(__dsub_rn(__dmul_rn(s.d, s.d), __dmul_rn(a, a)));
+    double dx = __dsub_rn(xj, xi);
+    if (dx < 0.0) dx = __dadd_rn(dx, s.L);
+    double tau = __dsub_rn(dx, b);
+    if (tau < 0.0) tau = 0.0;
+    return tau;
+}
+
+__device__ __forceinline__ void warp_argmin(double &t, uint32_t &j, uint32_t &l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double t2 = __shfl_xor_sync(FULL, t, o);
+        uint32_t j2 = __shfl_xor_sync(FULL, j, o);
+        uint32_t l2 = __shfl_xor_sync(FULL, l, o);
+        if (t2 < t || (t2 == t && j2 < j)) {
+            t = t2;
+            j = j2;
+            l = l2;
+        }
+    }
+}
+
+// ------------------------------------------------------------- one step
+
+enum { MODE_PASS1 = 0, MODE_COMP = 1 };
+
+struct ChainReg {
+    uint32_t i, iloc;
+    double xi, yi, ti, D;
+};
+
+struct StepOut {
+    double tau;  // tau* (lift) or D (stall)
+    uint32_t j, jloc;
+    double xj, yj, tj;
+    int lift;
+    int cx, cy, mlast;  // scanned footprint: rows cy-1..cy+1, columns cx..cx+mlast
+    int conflict;
+    uint32_t partner;
+};
+
+// Statements 1-9 of Alg. 5 for one chain, with the cell scan: columns ahead
+// of the active disk are scanned until (m*a - fx) - d > min(D, best) + eps.
+// Every scanned cell is claimed for the leg (conflict if another owner holds it).
+// PASS1: the owner is the chain; only its own disk is excluded; Eq. 2 is
+//   checked as an assertion (it cannot fail while the cells are held).
+// COMP: the owner is the conflict component `root` (any member's claim is its
+//   own); active and stalled disks are excluded (Alg. 2), and a static disk
+//   with t_i + tau < t_j is one lap away (lazy per-chain frame).
+template <int C, int MODE>
+__device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
+    constexpr int LPC = (3 * C <= 16) ? 16 : 32;  // lanes per column
+    constexpr int CPP = 32 / LPC;                 // columns per pass
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPC, sub = lane % LPC;
+    const int rr = sub / C, sl = sub % C;
+    const bool used = sub < 3 * C;
+    const int nc = s.nc;
+
+    const int cxi = cell_coord(r.xi, s), cyi = cell_coord(r.yi, s);
+    const double fx = __dsub_rn(r.xi, __dmul_rn((double)cxi, s.a));
+    int row = cyi + rr - 1;
+    if (row < 0) row += nc;
+    if (row >= nc) row -= nc;
+
+    double cur = r.D;  // min(D, best tau so far): drives the stop rule
+    double btau = INFINITY, bx = 0.0, by = 0.0, bt = 0.0;
+    uint32_t bj = NONE, bloc = 0;
+    int mlast = 0;
+    bool stop = false;
+    bool conflict = false;
+    uint32_t partner = NONE;
+    unsigned long long hz = 0;
+
+    for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
+        const int m = m0 + grp;
+        const bool colok = used && m < nc;
+        int col = cxi + m;
+        if (col >= nc) col -= nc;
+        const uint32_t cell = (uint32_t)row * (uint32_t)nc + (uint32_t)col;
+        const uint32_t loc = cell * C + sl;
+        uint32_t id = colok ? s.cid[loc] : EMPTY;
+        double xj = 0.0, yj = 0.0, tj = 0.0;
+        uint32_t own = OWN_STATIC;
+        uint32_t clm = 0;
+        if (colok && sl == 0) clm = s.claim[cell];
+        const bool cand = id != EMPTY && id != r.i;
+        if (cand) {
+            xj = s.cx[loc];
+            yj = s.cy[loc];
+            tj = s.t[id];
+            if (MODE == MODE_COMP) own = s.owner[id];
+        }
+        double tau = INFINITY;
+        if (cand && own == OWN_STATIC) {
+            tau = time_of_flight(r.xi, r.yi, xj, yj, s);
+            if (MODE == MODE_COMP && tau != INFINITY && __dadd_rn(r.ti, tau) < tj)
+                tau = __dadd_rn(tau, s.L);
+        }
+        // column minima (lanes of one column form an aligned group of LPC)
+        double cm = tau;
+#pragma unroll
+        for (int o = 1; o < LPC; o <<= 1) cm = fmin(cm, __shfl_xor_sync(FULL, cm, o));
+        int last_here = -1;
+#pragma unroll
+        for (int g = 0; g < CPP; ++g) {
+            const double cmg = __shfl_sync(FULL, cm, g * LPC);
+            const int mg = m0 + g;
+            if (stop) continue;
+            if (mg >= nc) {
+                stop = true;
+                continue;
+            }
+            if (mg >= 1) {
+                double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)mg, s.a), fx), s.d);
+                if (thr > __dadd_rn(cur, s.eps)) {
+                    stop = true;
+                    continue;
+                }
+            }
+            last_here = mg;
+            mlast = mg;
+            cur = fmin(cur, cmg);
+        }
+        const bool scanned = colok && m <= last_here;
+        double kt = scanned ? tau : INFINITY;
+        uint32_t kj = scanned ? id : NONE;
+        uint32_t kl = loc;
+        warp_argmin(kt, kj, kl);
+        if (kt < btau || (kt == btau && kj < bj)) {
+            const unsigned own_lane = __ballot_sync(FULL, scanned && id == kj && loc == kl);
+            const int src = own_lane ? __ffs(own_lane) - 1 : 0;
+            bx = __shfl_sync(FULL, xj, src);
+            by = __shfl_sync(FULL, yj, src);
+            bt = __shfl_sync(FULL, tj, src);
+            btau = kt;
+            bj = kj;
+            bloc = kl;
+        }
+        if (scanned && sl == 0) {
+            const uint32_t mine = (uint32_t)c + 1u;
+            uint32_t holder = clm;
+            if (holder == 0u) {
+                const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
+                holder = old == 0u ? mine : old;
+            }
+            bool foreign;
+            if (MODE == MODE_PASS1)
+                foreign = holder != mine;
+            else
+                foreign = s.comp_of[holder - 1u] != root;
+            if (foreign) {
+                conflict = true;
+                partner = holder - 1u;
+            }
+        }
+        // Eq. 2 (statement 5) on every scanned candidate: cannot fail while the
+        // cells are held by a lone chain; counted as an assertion.
+        if (MODE == MODE_PASS1 && scanned && tau != INFINITY && __dadd_rn(r.ti, tau) < tj) hz++;
+    }
+
+    StepOut o;
+    o.cx = cxi;
+    o.cy = cyi;
+    o.mlast = mlast;
+    o.conflict = 0;
+    o.partner = NONE;
+    const unsigned cb = __ballot_sync(FULL, conflict);
+    if (cb) {
+        o.conflict = 1;
+        o.partner = __shfl_sync(FULL, partner, __ffs(cb) - 1);
+    }
+    if (MODE == MODE_PASS1) {
+        const unsigned hb = __ballot_sync(FULL, hz != 0);
+        if (hb && lane == __ffs(hb) - 1) atomicAdd(s.lc + LC_HORIZON, 1ull);
+    }
+    if (btau < r.D) {
+        o.lift = 1;
+        o.tau = btau;
+        o.j = bj;
+        o.jloc = bloc;
+        o.xj = bx;
+        o.yj = by;
+        o.tj = bt;
+    } else {
+        o.lift = 0;
+        o.tau = r.D;
+        o.j = NONE;
+        o.jloc = 0;
+        o.xj = 0.0;
+        o.yj = 0.0;
+        o.tj = 0.0;
+    }
+    return o;
+}
+
+// Moves the active disk of chain c by dist (statements 16 / 22), updating its
+// cell slot; returns its new slot or EMPTY on a full cell.
+template <int C>
+__device__ uint32_t move_active(const Dev &s, const ChainReg &r, double xnew) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t cell_old = r.iloc / C;
+    const uint32_t cell_new = cell_of(xnew, r.yi, s);
+    uint32_t newloc = r.iloc;
+    if (cell_new != cell_old) {
+        uint32_t sid = (lane < C) ? s.cid[cell_new * C + lane] : 0u;
+        const unsigned em = __ballot_sync(FULL, lane < C && sid == EMPTY);
+        if (!em) return EMPTY;
+        newloc = cell_new * C + (uint32_t)(__ffs(em) - 1);
+        if (lane == 0) {
+            s.cid[newloc] = r.i;
+            s.cx[newloc] = xnew;
+            s.cy[newloc] = r.yi;
+            s.cid[r.iloc] = EMPTY;
+        }
+    } else if (lane == 0) {
+        s.cx[r.iloc] = xnew;
+    }
+    return newloc;
+}
+
+// Executes a step (lift: statements 10-19; stall: 21-24). Returns the chain's
+// new status. Writes are done by lane 0; all lanes update the registers.
+template <int C>
+__device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, bool cas_owner,
+                           uint32_t seq) {
+    const int lane = threadIdx.x & 31;
+    int32_t nrec = s.nrec[c];
+    if (nrec >= s.cap) {
+        if (lane == 0) atomicAdd(s.lc + LC_ERR_REC, 1ull);
+        return ST_BLOCKED;
+    }
+    if (o.lift) {
+        if (cas_owner) {
+            uint32_t old = 0;
+            if (lane == 0) old = atomicCAS(s.owner + o.j, OWN_STATIC, OWN_ACTIVE | (uint32_t)c);
+            old = __shfl_sync(FULL, old, 0);
+            if (old != OWN_STATIC) {
+                if (lane == 0) {
+                    s.partner[c] = (int32_t)(old & OWN_CHAIN);
+                    atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
+                }
+                return ST_BLOCKED;
+            }
+        }
+        const double tnew = __dadd_rn(r.ti, o.tau);      // statements 14, 15
+        const double xnew = wrap_add(r.xi, o.tau, s);    // statement 16
+        const uint32_t newloc = move_active<C>(s, r, xnew);
+        if (newloc == EMPTY) {
+            if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+            return ST_BLOCKED;
+        }
+        if (lane == 0) {
+            if (!cas_owner) s.owner[o.j] = OWN_ACTIVE | (uint32_t)c;
+            s.t[o.j] = tnew;
+            s.t[r.i] = tnew;
+            s.owner[r.i] = OWN_STATIC;                   // statement 17
+            Rec q;
+            q.i = r.i;
+            q.from = r.iloc;
+            q.to = newloc;
+            q.j = o.j;
+            q.jloc = o.jloc;
+            q.seq = seq;
+            q.x_old = r.xi;
+            q.ti_old = r.ti;
+            q.tj_old = o.tj;
+            q.t = tnew;
+            q.tau = o.tau;
+            q.xi = xnew;
+            q.xj = o.xj;
+            q.d_after = __dsub_rn(r.D, o.tau);
+            s.rec[(size_t)c * s.cap + nrec] = q;
+            s.nrec[c] = nrec + 1;
+            s.nlift[c] += 1;
+        }
+        r.D = __dsub_rn(r.D, o.tau);                     // statement 18
+        r.i = o.j;                                       // statement 19
+        r.iloc = o.jloc;
+        r.xi = o.xj;
+        r.yi = o.yj;
+        r.ti = tnew;
+        __syncwarp();
+        return ST_RUNNING;
+    }
+    const double tnew = __dadd_rn(r.ti, r.D);           // statement 21
+    const double xnew = wrap_add(r.xi, r.D, s);         // statement 22
+    const uint32_t newloc = move_active<C>(s, r, xnew);
+    if (newloc == EMPTY) {
+        if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+        return ST_BLOCKED;
+    }
+    if (lane == 0) {
+        s.t[r.i] = tnew;
+        s.owner[r.i] = OWN_STALLED | (uint32_t)c;       // statement 24
+        Rec q;
+        q.i = r.i;
+        q.from = r.iloc;
+        q.to = newloc;
+        q.j = NONE;
+        q.jloc = 0;
+        q.seq = seq;
+        q.x_old = r.xi;
+        q.ti_old = r.ti;
+        q.tj_old = 0.0;
+        q.t = tnew;
+        q.tau = r.D;
+        q.xi = xnew;
+        q.xj = 0.0;
+        q.d_after = 0.0;
+        s.rec[(size_t)c * s.cap + nrec] = q;
+        s.nrec[c] = nrec + 1;
+    }
+    r.iloc = newloc;
+    r.xi = xnew;
+    r.ti = tnew;
+    r.D = 0.0;                                          // statement 23
+    __syncwarp();
+    return ST_STALLED;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Cells from positions (slot order is irrelevant to every result).
+template <int C>
+__global__ void k_build_cells(Dev s, const double *x, const double *y) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.n) return;
+    const uint32_t cell = cell_of(x[q], y[q], s);
+    for (int sl = 0; sl < C; ++sl) {
+        const uint32_t loc = cell * C + sl;
+        if (atomicCAS(s.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
+            s.cx[loc] = x[q];
+            s.cy[loc] = y[q];
+            return;
+        }
+    }
+    atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+}
+
+__global__ void k_locate(Dev s, int C, uint32_t *loc_of) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)s.nc * s.nc * C) return;
+    const uint32_t id = s.cid[q];
+    if (id != EMPTY) loc_of[id] = (uint32_t)q;
+}
+
+__global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_of) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    const uint32_t a = (uint32_t)active[c];
+    s.aloc[c] = loc_of[a];
+    s.ci[c] = a;
+    s.owner[a] = OWN_ACTIVE | (uint32_t)c;
+    s.nrec[c] = 0;
+    s.status[c] = ST_STALLED;
+}
+
+// Leg start: clear local times and tags left by the previous leg, then start
+// every chain on its stalled disk with D = ell (Alg. 2 input at h).
+__global__ void k_leg_begin(Dev s) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    const int32_t nr = s.nrec[c];
+    const Rec *q = s.rec + (size_t)c * s.cap;
+    for (int32_t e = 0; e < nr; ++e) {
+        s.t[q[e].i] = 0.0;
+        if (q[e].j != NONE) s.t[q[e].j] = 0.0;
+    }
+    const uint32_t loc = s.aloc[c];
+    const uint32_t a = s.cid[loc];
+    s.owner[a] = OWN_ACTIVE | (uint32_t)c;
+    s.ci[c] = a;
+    s.aloc0[c] = loc;
+    s.D[c] = s.ell;
+    s.tc[c] = 0.0;
+    s.status[c] = ST_RUNNING;
+    s.partner[c] = -1;
+    s.nrec[c] = 0;
+    s.nlift[c] = 0;
+}
+
+// Pass 1: one warp per chain, run until stall or conflict.
+template <int C>
+__global__ void k_pass1(Dev s) {
+    const int warps = blockDim.x >> 5;
+    const int c = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (c >= s.k) return;
+    const int lane = threadIdx.x & 31;
+    ChainReg r;
+    r.iloc = s.aloc[c];
+    r.i = s.cid[r.iloc];
+    r.xi = s.cx[r.iloc];
+    r.yi = s.cy[r.iloc];
+    r.ti = 0.0;
+    r.D = s.ell;
+    int st = ST_RUNNING;
+    uint32_t seq = 0;
+    while (st == ST_RUNNING) {
+        const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r);
+        if (o.conflict) {
+            if (lane == 0) s.partner[c] = (int32_t)o.partner;
+            st = ST_BLOCKED;
+            break;
+        }
+        st = commit_step<C>(s, c, r, o, true, seq++);
+    }
+    if (lane == 0) {
+        // events before the blocking time are exact (Sec. 3.4, partial validation)
+        s.vt[c] = st == ST_BLOCKED ? r.ti : INFINITY;
+        s.status[c] = st;
+        s.aloc[c] = r.iloc;
+        s.ci[c] = r.i;
+        s.tc[c] = r.ti;
+        s.D[c] = r.D;
+        if (st == ST_BLOCKED) atomicAdd(s.lc + LC_BLOCKED, 1ull);
+        atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)s.nlift[c]);
+    }
+}
+
+// Exact inverse of commit_step for one record of chain c (lane 0 only).
+__device__ void undo_record(const Dev &s, int c, const Rec &u) {
+    if (u.to != u.from) {
+        s.cid[u.from] = u.i;
+        s.cx[u.from] = u.x_old;
+        s.cy[u.from] = s.cy[u.to];
+        s.cid[u.to] = EMPTY;
+    } else {
+        s.cx[u.from] = u.x_old;
+    }
+    s.t[u.i] = u.ti_old;
+    s.owner[u.i] = OWN_ACTIVE | (uint32_t)c;
+    if (u.j != NONE) {
+        s.t[u.j] = u.tj_old;
+        s.owner[u.j] = OWN_STATIC;
+        s.nlift[c] -= 1;
+    }
+}
+
+__device__ int uf_find(int32_t *p, int x) {
+    for (;;) {
+        const int px = ((volatile int32_t *)p)[x];
+        if (px == x) return x;
+        const int ppx = ((volatile int32_t *)p)[px];
+        if (ppx != px) atomicCAS(p + x, px, ppx);  // path halving
+        x = px;
+    }
+}
+
+__device__ void uf_union(int32_t *p, int a, int b) {
+    for (;;) {
+        a = uf_find(p, a);
+        b = uf_find(p, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(p + a, a, b) == a) return;  // larger root under smaller
+    }
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
+__device__ int block_exscan(int v, int *warp_tot, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = warp_tot[lane];
+        int u = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, u, o);
+            if (lane >= o) u += y;
+        }
+        warp_tot[lane] = u - t;
+        if (lane == 31) *total = u;
+    }
+    __syncthreads();
+    const int r = warp_tot[w] + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Conflict components (one block of 1024 threads). first: edges from pass 1
+// (blocked chain -> holder of the cell it met); later rounds: edges from
+// components that met another chain. Components holding a chain whose events
+// are not final ("dirty") are listed for k_repair with their members.
+__global__ void k_uf(Dev s, int first) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot_cnt, tot_cmp;
+    const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
+    if (first)
+        for (int c = tid; c < k; c += nt) {
+            s.uf[c] = c;
+            s.fin[c] = s.status[c] != ST_BLOCKED;
+            s.abort_to[c] = -1;
+        }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        int other = -1;
+        if (first) {
+            if (s.status[c] == ST_BLOCKED) other = s.partner[c];
+        } else {
+            other = s.abort_to[c];
+            s.abort_to[c] = -1;
+        }
+        if (other >= 0 && other < k) uf_union(s.uf, c, other);
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        s.comp_of[c] = uf_find(s.uf, c);
+        s.comp_cnt[c] = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) s.comp_cnt[s.comp_of[c]] = -1;  // dirty root
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (s.comp_cnt[s.comp_of[c]] != 0) s.fin[c] = 0;
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (s.comp_cnt[c] == -1) s.comp_cnt[c] = 0;
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) atomicAdd(s.comp_cnt + s.comp_of[c], 1);
+    __syncthreads();
+    // chunked exclusive scans over roots: member offsets and component index
+    const int chunk = (k + nt - 1) / nt;
+    const int lo = min(k, tid * chunk), hi = min(k, lo + chunk);
+    int sc = 0, sm = 0;
+    for (int c = lo; c < hi; ++c) {
+        const int n = s.comp_cnt[c];
+        sc += n;
+        sm += n > 0;
+    }
+    int oc = block_exscan(sc, warp_tot, &tot_cnt);
+    int om = block_exscan(sm, warp_tot, &tot_cmp);
+    for (int c = lo; c < hi; ++c) {
+        const int n = s.comp_cnt[c];
+        if (n > 0) {
+            s.comp_root[om] = c;
+            s.comp_off[om] = oc;
+            s.comp_cnt[c] = oc;  // becomes the write cursor
+            oc += n;
+            ++om;
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) s.comp_mem[atomicAdd(s.comp_cnt + s.comp_of[c], 1)] = c;
+    if (tid == 0) {
+        s.comp_off[tot_cmp] = tot_cnt;
+        s.ctl[CTL_NCOMP] = tot_cmp;
+        s.ctl[CTL_NMEMB] = tot_cnt;
+        s.ctl[CTL_WORK] = 0;
+        s.ctl[CTL_NABORT] = 0;
+    }
+}
+
+template <int C>
+__device__ StepOut compute_event(const Dev &s, int c, int root) {
+    const int lane = threadIdx.x & 31;
+    ChainReg r;
+    r.iloc = s.aloc[c];
+    r.i = s.ci[c];
+    r.xi = s.cx[r.iloc];
+    r.yi = s.cy[r.iloc];
+    r.ti = s.tc[c];
+    r.D = s.D[c];
+    const StepOut o = scan_step<C, MODE_COMP>(s, c, root, r);
+    if (lane == 0) {
+        s.ev_T[c] = __dadd_rn(r.ti, o.tau);
+        s.ev_tau[c] = o.tau;
+        s.ev_j[c] = o.j;
+        s.ev_jloc[c] = o.jloc;
+        s.ev_xj[c] = o.xj;
+        s.ev_yj[c] = o.yj;
+        s.ev_tj[c] = o.tj;
+        s.ev_lift[c] = o.lift;
+        s.ev_cx[c] = o.cx;
+        s.ev_cy[c] = o.cy;
+        s.ev_mlast[c] = o.mlast;
+    }
+    __syncwarp();
+    return o;
+}
+
+__device__ __forceinline__ bool in_footprint(const Dev &s, int c, uint32_t cell) {
+    const int nc = s.nc;
+    const int r = (int)(cell / (uint32_t)nc), col = (int)(cell % (uint32_t)nc);
+    int dr = r - s.ev_cy[c];
+    if (dr < 0) dr += nc;
+    if (!(dr == 0 || dr == 1 || dr == nc - 1)) return false;
+    int dm = col - s.ev_cx[c];
+    if (dm < 0) dm += nc;
+    return dm <= s.ev_mlast[c];
+}
+
+__device__ __forceinline__ void atomic_min_time(double *p, double v) {
+    // times are >= 0: their IEEE bit patterns order like the values
+    atomicMin((unsigned long long *)p, (unsigned long long)__double_as_longlong(v));
+}
+
+// One warp per dirty component: roll its members back to T* (the earliest
+// time up to which all of their events are exact), then redo them in global
+// event-time order (Alg. 2) while claiming cells for the component.
+template <int C>
+__global__ void k_repair(Dev s, int round) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= s.ctl[CTL_NCOMP]) return;
+        const int root = s.comp_root[q];
+        const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
+        const int32_t *mem = s.comp_mem + off;
+
+        double Ts = INFINITY;
+        for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
+
+        // 1. undo records with event time >= T*, latest first within each run
+        for (;;) {
+            uint32_t bseq = 0;
+            int bmem = -1;
+            for (int e = lane; e < m; e += 32) {
+                const int c = mem[e];
+                const int32_t nr = s.nrec[c];
+                if (nr == 0) continue;
+                const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+                if (!(u.t >= Ts)) continue;
+                if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
+                    bseq = u.seq;
+                    bmem = e;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint32_t s2 = __shfl_xor_sync(FULL, bseq, o);
+                const int m2 = __shfl_xor_sync(FULL, bmem, o);
+                if (m2 >= 0 && (bmem < 0 || s2 > bseq || (s2 == bseq && m2 < bmem))) {
+                    bseq = s2;
+                    bmem = m2;
+                }
+            }
+            if (bmem < 0) break;
+            if (lane == 0) {
+                const int c = mem[bmem];
+                const int32_t nr = s.nrec[c];
+                undo_record(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
+                s.nrec[c] = nr - 1;
+            }
+            __syncwarp();
+        }
+        // 2. every member continues from its last kept event
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            const int32_t nr = s.nrec[c];
+            if (nr == 0) {
+                const uint32_t loc = s.aloc0[c];
+                s.aloc[c] = loc;
+                s.ci[c] = s.cid[loc];
+                s.tc[c] = 0.0;
+                s.D[c] = s.ell;
+                s.status[c] = ST_RUNNING;
+            } else {
+                const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+                if (u.j == NONE) {
+                    s.aloc[c] = u.to;
+                    s.ci[c] = u.i;
+                    s.tc[c] = u.t;
+                    s.D[c] = 0.0;
+                    s.status[c] = ST_STALLED;
+                } else {
+                    s.aloc[c] = u.jloc;
+                    s.ci[c] = u.j;
+                    s.tc[c] = u.t;
+                    s.D[c] = u.d_after;
+                    s.status[c] = ST_RUNNING;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
+
+        // 3. global event-time order within the component
+        bool abort = false;
+        int met = -1;
+        for (int e = 0; e < m && !abort; ++e) {
+            const int c = mem[e];
+            if (s.status[c] != ST_RUNNING) continue;
+            const StepOut o = compute_event<C>(s, c, root);
+            if (o.conflict) {
+                abort = true;
+                met = (int)o.partner;
+            }
+        }
+        double now = Ts;
+        uint32_t cnt = 0;
+        while (!abort) {
+            double bT = INFINITY;
+            int bc = 0x7FFFFFFF;
+            for (int e = lane; e < m; e += 32) {
+                const int c = mem[e];
+                if (s.status[c] != ST_RUNNING) continue;
+                const double T = s.ev_T[c];
+                if (T < bT || (T == bT && c < bc)) {
+                    bT = T;
+                    bc = c;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double T2 = __shfl_xor_sync(FULL, bT, o);
+                const int c2 = __shfl_xor_sync(FULL, bc, o);
+                if (T2 < bT || (T2 == bT && c2 < bc)) {
+                    bT = T2;
+                    bc = c2;
+                }
+            }
+            if (bc == 0x7FFFFFFF) break;
+            if (bT < now && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
+            now = bT;
+            ChainReg r;
+            r.iloc = s.aloc[bc];
+            r.i = s.ci[bc];
+            r.xi = s.cx[r.iloc];
+            r.yi = s.cy[r.iloc];
+            r.ti = s.tc[bc];
+            r.D = s.D[bc];
+            StepOut o;
+            o.lift = s.ev_lift[bc];
+            o.tau = s.ev_tau[bc];
+            o.j = s.ev_j[bc];
+            o.jloc = s.ev_jloc[bc];
+            o.xj = s.ev_xj[bc];
+            o.yj = s.ev_yj[bc];
+            o.tj = s.ev_tj[bc];
+            const uint32_t cell_a = r.iloc / C;
+            const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
+            const int32_t nrec0 = s.nrec[bc];
+            const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++);
+            if (st == ST_BLOCKED) {  // out of records or slots: reported by the host
+                abort = true;
+                break;
+            }
+            const uint32_t cell_b = s.rec[(size_t)bc * s.cap + nrec0].to / C;
+            if (lane == 0) {
+                s.status[bc] = st;
+                s.aloc[bc] = r.iloc;
+                s.ci[bc] = r.i;
+                s.tc[bc] = r.ti;
+                s.D[bc] = r.D;
+            }
+            __syncwarp();
+            for (int base = 0; base < m && !abort; base += 32) {
+                const int e = base + lane;
+                bool redo = false;
+                if (e < m) {
+                    const int c = mem[e];
+                    if (s.status[c] == ST_RUNNING)
+                        redo = c == bc || in_footprint(s, c, cell_a) ||
+                               in_footprint(s, c, cell_b) || in_footprint(s, c, cell_j);
+                }
+                unsigned b = __ballot_sync(FULL, redo);
+                while (b && !abort) {
+                    const int qq = __ffs(b) - 1;
+                    b &= b - 1;
+                    const StepOut o2 = compute_event<C>(s, mem[base + qq], root);
+                    if (o2.conflict) {
+                        abort = true;
+                        met = (int)o2.partner;
+                    }
+                }
+            }
+        }
+        if (abort) {
+            // events before `now` are exact; the chain met joins next round
+            for (int e = lane; e < m; e += 32) s.vt[mem[e]] = now;
+            if (lane == 0) {
+                if (met >= 0) {
+                    s.abort_to[root] = met;
+                    atomic_min_time(s.vt + met, now);
+                }
+                atomicAdd(s.ctl + CTL_NABORT, 1);
+            }
+        } else {
+            for (int e = lane; e < m; e += 32) {
+                s.fin[mem[e]] = 1;
+                s.vt[mem[e]] = INFINITY;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Leg end: totals, and the lifting log (chain by chain).
+__global__ void k_leg_end(Dev s, int32_t leg) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    const int32_t nl = s.nlift[c];
+    atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
+    if (s.log_on && nl > 0) {
+        const unsigned long long base = atomicAdd(s.tc_cnt + TC_LOG_N, (unsigned long long)nl);
+        const Rec *q = s.rec + (size_t)c * s.cap;
+        unsigned long long w = base;
+        for (int32_t e = 0; e < s.nrec[c]; ++e) {
+            if (q[e].j == NONE) continue;
+            if ((int64_t)w < s.log_cap) {
+                ecmc_lift_t L;
+                L.leg = leg;
+                L.c = c;
+                L.i = (int32_t)q[e].i;
+                L.j = (int32_t)q[e].j;
+                L.t = q[e].t;
+                L.tau = q[e].tau;
+                L.xi = q[e].xi;
+                L.xj = q[e].xj;
+                s.log[w] = L;
+            }
+            ++w;
+        }
+    }
+}
+
+template <int C>
+__global__ void k_export(Dev s, double *x, double *y) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)s.nc * s.nc * C) return;
+    const uint32_t id = s.cid[q];
+    if (id == EMPTY) return;
+    if (x) x[id] = s.cx[q];
+    if (y) y[id] = s.cy[q];
+}
+
+__global__ void k_export_active(Dev s, int32_t *active) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    active[c] = (int32_t)s.cid[s.aloc[c]];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+
+struct ecmc_ctx {
+    ecmc_params p;
+    Dev s;
+    int C = 4;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<void *> allocs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    ecmc_profile_t prof = {};
+    unsigned long long *h_lc = nullptr;  // pinned
+    int32_t *h_ctl = nullptr;            // pinned
+    int n_sm = 1;
+    int64_t legs_total = 0;
+    int64_t lifts_total = 0;
+    int64_t conflict_legs = 0;
+    int64_t repaired = 0;
+    int64_t horizon = 0;
+    int64_t order_err = 0;
+    double device_ms = 0.0;
+    bool log_overflow = false;
+};
+
+static std::string g_create_err;
+
+static int fail(ecmc_ctx *ctx, int code, const std::string &msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, ECMC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+static int dalloc(ecmc_ctx *ctx, T **ptr, size_t count) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, ECMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(p);
+    *ptr = (T *)p;
+    return 0;
+}
+
+static int pick_cells(const ecmc_params *p, int *nc_out, int *C_out) {
+    const double d = p->d, L = p->box;
+    int nc = p->cells_per_side;
+    if (nc == 0) {
+        nc = (int)(L / (d * (1.0 + std::ldexp(1.0, -20))));
+        while (nc > 3 && !(L / nc >= d * (1.0 + std::ldexp(1.0, -20)))) --nc;
+    }
+    if (nc < 3) return -1;
+    const double a = L / nc;
+    if (!(a >= d * (1.0 + std::ldexp(1.0, -20)))) return -1;
+    // At most 4 centres at mutual distance >= d fit in a cell with a < sqrt(2) d
+    // (one per quadrant); at most 6 for a < 1.664 d (a 3 x 2 split).
+    int C;
+    if (a < std::sqrt(2.0) * d * (1.0 - 1e-9))
+        C = 4;
+    else if (a < 1.664 * d)
+        C = 8;
+    else
+        return -1;
+    *nc_out = nc;
+    *C_out = C;
+    return 0;
+}
+
+template <int C>
+static void launch_build(ecmc_ctx *ctx, const double *x, const double *y) {
+    const int64_t n = ctx->s.n;
+    k_build_cells<C><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->s, x, y);
+}
+
+extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *y,
+                           const int32_t *active, void *stream, ecmc_ctx **out) {
+    ecmc_ctx *ctx = nullptr;
+    if (!p || !x || !y || !active || !out) return fail(nullptr, ECMC_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF) return fail(nullptr, ECMC_EINVAL, "n out of range");
+    if (p->n_chains < 1 || p->n_chains > p->n) return fail(nullptr, ECMC_EINVAL, "n_chains out of range");
+    if (!(p->d > 0.0) || !(p->ell > 0.0) || !(p->box > 0.0) || !std::isfinite(p->box) ||
+        !std::isfinite(p->ell))
+        return fail(nullptr, ECMC_EINVAL, "d, ell and box must be positive and finite");
+    int nc = 0, C = 4;
+    if (pick_cells(p, &nc, &C))
+        return fail(nullptr, ECMC_EINVAL, "cell geometry: need nc >= 3 and d < L/nc < 1.664 d");
+    if ((int64_t)nc * nc * C > (int64_t)0xFFFFFFF0)
+        return fail(nullptr, ECMC_EINVAL, "too many cells");
+
+    ctx = new (std::nothrow) ecmc_ctx();
+    if (!ctx) return fail(nullptr, ECMC_ENOMEM, "host allocation");
+    ctx->p = *p;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->C = C;
+    Dev &s = ctx->s;
+    memset(&s, 0, sizeof s);
+    s.n = p->n;
+    s.nc = nc;
+    s.k = p->n_chains;
+    s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
+    s.L = p->box;
+    s.d = p->d;
+    s.ell = p->ell;
+    s.a = p->box / (double)nc;
+    s.inv_a = (double)nc / p->box;
+    s.eps = std::ldexp(p->box, -30);
+    s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
+    s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
+    const size_t ncell = (size_t)nc * nc;
+    const size_t nslot = ncell * C;
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    int rc = 0;
+    auto chk = [&](int r) {
+        if (r && !rc) rc = r;
+    };
+    chk(dalloc(ctx, &s.cx, nslot));
+    chk(dalloc(ctx, &s.cy, nslot));
+    chk(dalloc(ctx, &s.cid, nslot));
+    chk(dalloc(ctx, &s.claim, ncell));
+    chk(dalloc(ctx, &s.t, n));
+    chk(dalloc(ctx, &s.owner, n));
+    chk(dalloc(ctx, &s.aloc0, k));
+    chk(dalloc(ctx, &s.aloc, k));
+    chk(dalloc(ctx, &s.ci, k));
+    chk(dalloc(ctx, &s.D, k));
+    chk(dalloc(ctx, &s.tc, k));
+    chk(dalloc(ctx, &s.status, k));
+    chk(dalloc(ctx, &s.partner, k));
+    chk(dalloc(ctx, &s.nrec, k));
+    chk(dalloc(ctx, &s.nlift, k));
+    chk(dalloc(ctx, &s.rec, k * (size_t)s.cap));
+    chk(dalloc(ctx, &s.ev_T, k));
+    chk(dalloc(ctx, &s.ev_tau, k));
+    chk(dalloc(ctx, &s.ev_xj, k));
+    chk(dalloc(ctx, &s.ev_yj, k));
+    chk(dalloc(ctx, &s.ev_tj, k));
+    chk(dalloc(ctx, &s.vt, k));
+    chk(dalloc(ctx, &s.uf, k));
+    chk(dalloc(ctx, &s.fin, k));
+    chk(dalloc(ctx, &s.comp_of, k));
+    chk(dalloc(ctx, &s.abort_to, k));
+    chk(dalloc(ctx, &s.comp_cnt, k));
+    chk(dalloc(ctx, &s.comp_off, k + 1));
+    chk(dalloc(ctx, &s.comp_root, k));
+    chk(dalloc(ctx, &s.comp_mem, k));
+    chk(dalloc(ctx, &s.ctl, CTL_N));
+    chk(dalloc(ctx, &s.ev_j, k));
+    chk(dalloc(ctx, &s.ev_jloc, k));
+    chk(dalloc(ctx, &s.ev_lift, k));
+    chk(dalloc(ctx, &s.ev_cx, k));
+    chk(dalloc(ctx, &s.ev_cy, k));
+    chk(dalloc(ctx, &s.ev_mlast, k));
+    chk(dalloc(ctx, &s.lc, LC_N));
+    chk(dalloc(ctx, &s.tc_cnt, TC_N));
+    if (s.log_on) chk(dalloc(ctx, &s.log, (size_t)s.log_cap));
+    double *dx = nullptr, *dy = nullptr;
+    int32_t *dact = nullptr;
+    uint32_t *loc_of = nullptr;
+    chk(dalloc(ctx, &loc_of, n));
+    const bool dev_in = (p->flags & ECMC_INPUT_DEVICE) != 0;
+    if (!dev_in) {
+        chk(dalloc(ctx, &dx, n));
+        chk(dalloc(ctx, &dy, n));
+        chk(dalloc(ctx, &dact, k));
+    }
+    if (rc) {
+        g_create_err = ctx->err;
+        ecmc_destroy(ctx);
+        return rc;
+    }
+    // validate inputs on the host copy
+    std::vector<double> hx, hy;
+    std::vector<int32_t> ha(k);
+    const double *vx = x, *vy = y;
+    const int32_t *va = active;
+    if (dev_in) {
+        hx.resize(n);
+        hy.resize(n);
+        if (cudaMemcpy(hx.data(), x, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hy.data(), y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ha.data(), active, k * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            g_create_err = "cannot read device inputs";
+            ecmc_destroy(ctx);
+            return ECMC_ECUDA;
+        }
+        vx = hx.data();
+        vy = hy.data();
+        va = ha.data();
+    }
+    for (size_t q = 0; q < n; ++q) {
+        if (!(vx[q] >= 0.0 && vx[q] < p->box && vy[q] >= 0.0 && vy[q] < p->box)) {
+            g_create_err = "coordinate outside [0, L)";
+            ecmc_destroy(ctx);
+            return ECMC_EINVAL;
+        }
+    }
+    {
+        std::vector<char> seen(n, 0);
+        for (size_t c = 0; c < k; ++c) {
+            const int32_t a = va[c];
+            if (a < 0 || (size_t)a >= n || seen[a]) {
+                g_create_err = "active ids must be distinct and in [0, n)";
+                ecmc_destroy(ctx);
+                return ECMC_EINVAL;
+            }
+            seen[a] = 1;
+        }
+    }
+    cudaStream_t st = ctx->stream;
+    const double *sx = x, *sy = y;
+    const int32_t *sa = active;
+    if (!dev_in) {
+        CU(cudaMemcpyAsync(dx, x, n * 8, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(dy, y, n * 8, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(dact, active, k * 4, cudaMemcpyHostToDevice, st));
+        sx = dx;
+        sy = dy;
+        sa = dact;
+    }
+    CU(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(s.claim, 0, ncell * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(s.t, 0, n * sizeof(double), st));
+    CU(cudaMemsetAsync(s.owner, 0, n * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
+    if (C == 4)
+        launch_build<4>(ctx, sx, sy);
+    else
+        launch_build<8>(ctx, sx, sy);
+    k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
+    k_init_chains<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(s, sa, loc_of);
+    CU(cudaGetLastError());
+    CU(cudaMallocHost(&ctx->h_lc, LC_N * sizeof(unsigned long long)));
+    CU(cudaMallocHost(&ctx->h_ctl, CTL_N * sizeof(int32_t)));
+    {
+        int dev = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (ctx->h_lc[LC_ERR_CAP]) {
+        g_create_err = "more disks in a cell than it has slots (overlapping input?)";
+        ecmc_destroy(ctx);
+        return ECMC_ECAPACITY;
+    }
+    CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
+    CU(cudaEventCreate(&ctx->ev0));
+    CU(cudaEventCreate(&ctx->ev1));
+    for (auto &e : ctx->kev) CU(cudaEventCreate(&e));
+    *out = ctx;
+    return ECMC_OK;
+}
+
+template <int C>
+static int run_leg(ecmc_ctx *ctx, int32_t leg, uint8_t *flag, int64_t *lifts) {
+    Dev &s = ctx->s;
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t *E = ctx->kev;
+    const unsigned kb = (unsigned)((s.k + 127) / 128);
+    CU(cudaEventRecord(E[0], st));
+    CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
+    k_leg_begin<<<kb, 128, 0, st>>>(s);
+    CU(cudaMemsetAsync(s.claim, 0, (size_t)s.nc * s.nc * sizeof(uint32_t), st));
+    const int wpb = 4;
+    CU(cudaEventRecord(E[1], st));
+    k_pass1<C><<<(unsigned)((s.k + wpb - 1) / wpb), 32 * wpb, 0, st>>>(s);
+    CU(cudaEventRecord(E[2], st));
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    float ms_a = 0.f, ms_b = 0.f;
+    CU(cudaEventElapsedTime(&ms_a, E[0], E[1]));
+    CU(cudaEventElapsedTime(&ms_b, E[1], E[2]));
+    ctx->prof.other_ms += ms_a;
+    ctx->prof.other_launches += 1;
+    ctx->prof.pass1_ms += ms_b;
+    ctx->prof.pass1_launches += 1;
+    ctx->prof.pass1_liftings += (int64_t)ctx->h_lc[LC_P1LIFTS];
+    if (ctx->h_lc[LC_ERR_CAP] || ctx->h_lc[LC_ERR_REC])
+        return fail(ctx, ECMC_ECAPACITY, "cell slots or per-chain undo records overflowed");
+    const bool conflict = ctx->h_lc[LC_BLOCKED] != 0;
+    ctx->horizon += (int64_t)ctx->h_lc[LC_HORIZON];
+    CU(cudaEventRecord(E[3], st));
+    CU(cudaEventRecord(E[4], st));
+    if (conflict) {
+        // repair rounds: components -> rollback to T* and redo; merge on contact
+        for (int round = 1;; ++round) {
+            if (round > 255) return fail(ctx, ECMC_ECAPACITY, "too many repair rounds");
+            k_uf<<<1, 1024, 0, st>>>(s, round == 1);
+            k_repair<C><<<(unsigned)(ctx->n_sm * 4), 128, 0, st>>>(s, round);
+            CU(cudaGetLastError());
+            CU(cudaMemcpyAsync(ctx->h_ctl, s.ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            ctx->prof.repair_launches += 1;
+            if (ctx->h_ctl[CTL_NABORT] == 0) break;
+        }
+    }
+    CU(cudaEventRecord(E[5], st));
+    k_leg_end<<<kb, 128, 0, st>>>(s, leg);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    float ms_d = 0.f;
+    CU(cudaEventElapsedTime(&ms_d, E[4], E[5]));
+    if (conflict) {
+        ctx->prof.repair_ms += ms_d;
+        ctx->prof.repair_liftings += (int64_t)ctx->h_lc[LC_LIFTS];
+        ctx->repaired += (int64_t)ctx->h_lc[LC_REPAIRED];
+    }
+    if (ctx->h_lc[LC_ERR_CAP] || ctx->h_lc[LC_ERR_REC])
+        return fail(ctx, ECMC_ECAPACITY, "cell slots or per-chain undo records overflowed");
+    ctx->order_err += (int64_t)ctx->h_lc[LC_ORDER];
+    *flag = conflict ? 1 : 0;
+    *lifts = (int64_t)ctx->h_lc[LC_LIFTS];
+    return 0;
+}
+
+extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t event_budget,
+                                      uint8_t *leg_flags_out, int32_t *legs_done) {
+    if (!ctx) return ECMC_EINVAL;
+    if (n_legs < 0) return fail(ctx, ECMC_EINVAL, "n_legs < 0");
+    if (legs_done) *legs_done = 0;
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    uint64_t done_lifts = 0;
+    int32_t legs = 0;
+    int rc = 0;
+    for (int32_t l = 0; l < n_legs; ++l) {
+        uint8_t flag = 0;
+        int64_t lifts = 0;
+        const int32_t leg_index = (int32_t)ctx->legs_total;
+        rc = ctx->C == 4 ? run_leg<4>(ctx, leg_index, &flag, &lifts)
+                         : run_leg<8>(ctx, leg_index, &flag, &lifts);
+        if (rc) break;
+        ctx->legs_total++;
+        ctx->lifts_total += lifts;
+        ctx->conflict_legs += flag;
+        if (leg_flags_out) leg_flags_out[l] = flag;
+        done_lifts += (uint64_t)lifts;
+        legs = l + 1;
+        if (event_budget && done_lifts >= event_budget) break;
+    }
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    CU(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->device_ms += ms;
+    if (legs_done) *legs_done = legs;
+    return rc;
+}
+
+extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *active) {
+    if (!ctx) return ECMC_EINVAL;
+    Dev &s = ctx->s;
+    cudaStream_t st = ctx->stream;
+    const size_t n = (size_t)s.n;
+    const size_t nslot = (size_t)s.nc * s.nc * ctx->C;
+    double *dx = nullptr, *dy = nullptr;
+    int32_t *da = nullptr;
+    if (x || y) {
+        if (cudaMalloc(&dx, n * 8) != cudaSuccess || cudaMalloc(&dy, n * 8) != cudaSuccess) {
+            cudaFree(dx);
+            (void)cudaGetLastError();
+            return fail(ctx, ECMC_ENOMEM, "positions scratch");
+        }
+        if (ctx->C == 4)
+            k_export<4><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy);
+        else
+            k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy);
+        if (x) CU(cudaMemcpyAsync(x, dx, n * 8, cudaMemcpyDeviceToHost, st));
+        if (y) CU(cudaMemcpyAsync(y, dy, n * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (t) CU(cudaMemcpyAsync(t, s.t, n * 8, cudaMemcpyDeviceToHost, st));
+    if (active) {
+        if (cudaMalloc(&da, (size_t)s.k * 4) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFree(dx);
+            cudaFree(dy);
+            return fail(ctx, ECMC_ENOMEM, "positions scratch");
+        }
+        k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
+        CU(cudaMemcpyAsync(active, da, (size_t)s.k * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    cudaFree(dx);
+    cudaFree(dy);
+    cudaFree(da);
+    CU(cudaGetLastError());
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
+    if (!ctx || !out) return ECMC_EINVAL;
+    out->liftings = ctx->lifts_total;
+    out->legs = ctx->legs_total;
+    out->conflict_legs = ctx->conflict_legs;
+    out->repaired_chains = ctx->repaired;
+    out->horizon_asserts = ctx->horizon;
+    out->order_errors = ctx->order_err;
+    out->device_ms = ctx->device_ms;
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out) {
+    if (!ctx || !out) return ECMC_EINVAL;
+    *out = ctx->prof;
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out) {
+    if (!ctx || !n_out) return ECMC_EINVAL;
+    Dev &s = ctx->s;
+    if (!s.log_on) return fail(ctx, ECMC_EINVAL, "lifting log not enabled");
+    unsigned long long n = 0;
+    CU(cudaMemcpyAsync(&n, s.tc_cnt + TC_LOG_N, sizeof n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n_out = (int64_t)n;
+    if ((int64_t)n > s.log_cap) return fail(ctx, ECMC_ECAPACITY, "lifting log overflowed log_cap");
+    std::vector<ecmc_lift_t> all((size_t)n);
+    if (n) {
+        CU(cudaMemcpyAsync(all.data(), s.log, n * sizeof(ecmc_lift_t), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    // chains append their records concurrently; order leg by leg, chain by chain
+    std::stable_sort(all.begin(), all.end(), [](const ecmc_lift_t &a, const ecmc_lift_t &b) {
+        return a.leg != b.leg ? a.leg < b.leg : a.c < b.c;
+    });
+    if (buf && cap > 0)
+        memcpy(buf, all.data(), (size_t)std::min<int64_t>(cap, (int64_t)n) * sizeof(ecmc_lift_t));
+    return ECMC_OK;
+}
+
+extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
+    if (!ctx) return;
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_lc) cudaFreeHost(ctx->h_lc);
+    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (auto e : ctx->kev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+extern "C" const char *ecmc_last_error(const ecmc_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
