@@ -152,6 +152,45 @@ void ecmc_destroy(ecmc_ctx *ctx);
    string belongs to ctx. With ctx == NULL, the last ecmc_create failure. */
 const char *ecmc_last_error(const ecmc_ctx *ctx);
 
+/*
+ * ecmc_leg_noalloc -- one leg (h -> h + ell), exactly the computation of one
+ * leg of ecmc_run_to_breakpoint, for callers that cannot allocate device
+ * memory: code running inside a framework whose caching allocator already owns
+ * the device heap, real-time loops that may not pay allocation latency, and
+ * plug-ins that are handed pointers only. The paper has no counterpart; this
+ * is a deployment convenience.
+ *
+ * It allocates nothing (no cudaMalloc, cudaFree or allocating library call, on
+ * the device or the host). Its working memory is one file-scope device array
+ * of ECMC_NOALLOC_SCRATCH_MIB MiB that the library holds on every GPU that
+ * loads it, until the process exits. The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call shares the array and
+ * clears what it needs, so calls that overlap on the GPU (other streams or
+ * threads) race and must not be issued.
+ *
+ *   n, box, d, ell, n_chains, cells_per_side   as in ecmc_params
+ *   x        device, n doubles, in/out: positions before and after the leg
+ *   y        device, n doubles, in (y never changes for v = (1, 0))
+ *   active   device, n_chains ints, in/out: chain c's active disk; on return
+ *            its stalled disk, the start disk of the next leg
+ *   t_out    device, n doubles, out (NULL to skip): leg-relative local times
+ *   stream   cudaStream_t (NULL = default stream); synchronised on return
+ *   flag_out host, 1 byte (NULL to skip): 1 if two chains' cells met
+ *   lifts_out host (NULL to skip): liftings made in the leg
+ * Sizes whose arrays (cells, per-disk and per-chain state, ECMC_NOALLOC_RECORDS
+ * event records per chain) do not fit the array return ECMC_EINVAL before any
+ * device work; so do bad scalars, coordinates outside [0, L) and repeated or
+ * out-of-range active ids. ECMC_ECAPACITY: a chain made more than
+ * ECMC_NOALLOC_RECORDS events in the leg, or a cell overflowed. ECMC_ECUDA: a
+ * CUDA call failed. Example limits: N = 65536 disks with 256 chains fit.
+ */
+#define ECMC_NOALLOC_SCRATCH_MIB 24
+#define ECMC_NOALLOC_RECORDS 256
+int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int32_t n_chains,
+                     int32_t cells_per_side, double *x, const double *y, int32_t *active,
+                     double *t_out, void *stream, uint8_t *flag_out, int64_t *lifts_out);
+
 #ifdef __cplusplus
 }
 #endif

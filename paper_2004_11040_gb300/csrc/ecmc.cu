@@ -32,6 +32,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1448,4 +1449,243 @@ extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
 
 extern "C" const char *ecmc_last_error(const ecmc_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+// ------------------------------------------ one leg without any allocation
+//
+// For callers that cannot allocate device memory: code that runs while a
+// framework owns the whole device heap through its own caching allocator
+// (a cudaMalloc would fail or fragment that pool), real-time loops that must
+// not pay allocation latency, and plug-ins that are only handed pointers.
+// All working memory of the leg comes from one file-scope device array of
+// fixed size; the caller passes only inputs and outputs.
+
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)ECMC_NOALLOC_SCRATCH_MIB << 20;
+constexpr int NOALLOC_CAP = ECMC_NOALLOC_RECORDS;  // event records per chain per leg
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// Shared by every call on a device and kept until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array for the current device, looked up once.
+static int noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return ECMC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return ECMC_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (unsigned char *)g_noalloc_ptr[dev];
+    return ECMC_OK;
+}
+
+// Lays the arrays of Dev out in [base, base + bytes); with base == nullptr
+// only the size is computed.
+struct Carve {
+    unsigned char *base;
+    size_t off;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += std::max<size_t>(count, 1) * sizeof(T);
+        return p;
+    }
+};
+
+static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t ncell, size_t n,
+                             size_t k, uint32_t **loc_of) {
+    Carve cv{base, 0};
+    s.cx = cv.take<double>(nslot);
+    s.cy = cv.take<double>(nslot);
+    s.cid = cv.take<uint32_t>(nslot);
+    s.claim = cv.take<uint32_t>(ncell);
+    s.t = cv.take<double>(n);
+    s.owner = cv.take<uint32_t>(n);
+    *loc_of = cv.take<uint32_t>(n);
+    s.aloc0 = cv.take<uint32_t>(k);
+    s.aloc = cv.take<uint32_t>(k);
+    s.ci = cv.take<uint32_t>(k);
+    s.D = cv.take<double>(k);
+    s.tc = cv.take<double>(k);
+    s.status = cv.take<int32_t>(k);
+    s.partner = cv.take<int32_t>(k);
+    s.nrec = cv.take<int32_t>(k);
+    s.nlift = cv.take<int32_t>(k);
+    s.ev_T = cv.take<double>(k);
+    s.ev_tau = cv.take<double>(k);
+    s.ev_xj = cv.take<double>(k);
+    s.ev_yj = cv.take<double>(k);
+    s.ev_tj = cv.take<double>(k);
+    s.ev_j = cv.take<uint32_t>(k);
+    s.ev_jloc = cv.take<uint32_t>(k);
+    s.ev_lift = cv.take<int32_t>(k);
+    s.ev_cx = cv.take<int32_t>(k);
+    s.ev_cy = cv.take<int32_t>(k);
+    s.ev_mlast = cv.take<int32_t>(k);
+    s.vt = cv.take<double>(k);
+    s.uf = cv.take<int32_t>(k);
+    s.fin = cv.take<int32_t>(k);
+    s.comp_of = cv.take<int32_t>(k);
+    s.abort_to = cv.take<int32_t>(k);
+    s.comp_cnt = cv.take<int32_t>(k);
+    s.comp_off = cv.take<int32_t>(k + 1);
+    s.comp_root = cv.take<int32_t>(k);
+    s.comp_mem = cv.take<int32_t>(k);
+    s.ctl = cv.take<int32_t>(CTL_N);
+    s.lc = cv.take<unsigned long long>(LC_N);
+    s.tc_cnt = cv.take<unsigned long long>(TC_N);
+    s.rec = cv.take<Rec>(k * (size_t)s.cap);
+    return cv.off;
+}
+
+// Coordinates in [0, L) and distinct active ids in range, checked on the
+// device (the caller's arrays are device memory). seen[] must be zero.
+__global__ void k_noalloc_check(const double *x, const double *y, const int32_t *active,
+                                int64_t n, int k, double L, uint32_t *seen,
+                                unsigned long long *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride)
+        if (!(x[q] >= 0.0 && x[q] < L && y[q] >= 0.0 && y[q] < L)) atomicAdd(bad, 1ull);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += stride) {
+        const int32_t a = active[c];
+        if (a < 0 || (int64_t)a >= n || atomicExch(seen + a, 1u) != 0u) atomicAdd(bad, 1ull);
+    }
+}
+
+#define CUN(call)                                   \
+    do {                                            \
+        if ((call) != cudaSuccess) {                \
+            (void)cudaGetLastError();               \
+            return ECMC_ECUDA;                      \
+        }                                           \
+    } while (0)
+
+template <int C>
+static int noalloc_leg(Dev &s, cudaStream_t st, int n_sm, uint8_t *flag, int64_t *lifts) {
+    unsigned long long lc[LC_N];
+    int32_t ctl[CTL_N];
+    const unsigned kb = (unsigned)((s.k + 127) / 128);
+    CUN(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
+    k_leg_begin<<<kb, 128, 0, st>>>(s);
+    CUN(cudaMemsetAsync(s.claim, 0, (size_t)s.nc * s.nc * sizeof(uint32_t), st));
+    k_pass1<C><<<(unsigned)((s.k + 3) / 4), 128, 0, st>>>(s);
+    CUN(cudaGetLastError());
+    CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
+    CUN(cudaStreamSynchronize(st));
+    if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) return ECMC_ECAPACITY;
+    const bool conflict = lc[LC_BLOCKED] != 0;
+    if (conflict) {
+        for (int round = 1;; ++round) {
+            if (round > 255) return ECMC_ECAPACITY;
+            k_uf<<<1, 1024, 0, st>>>(s, round == 1);
+            k_repair<C><<<(unsigned)(n_sm * 4), 128, 0, st>>>(s, round);
+            CUN(cudaGetLastError());
+            CUN(cudaMemcpyAsync(ctl, s.ctl, sizeof ctl, cudaMemcpyDeviceToHost, st));
+            CUN(cudaStreamSynchronize(st));
+            if (ctl[CTL_NABORT] == 0) break;
+        }
+    }
+    k_leg_end<<<kb, 128, 0, st>>>(s, 0);
+    CUN(cudaGetLastError());
+    CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
+    CUN(cudaStreamSynchronize(st));
+    if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) return ECMC_ECAPACITY;
+    if (flag) *flag = conflict ? 1 : 0;
+    if (lifts) *lifts = (int64_t)lc[LC_LIFTS];
+    return ECMC_OK;
+}
+
+template <int C>
+static int noalloc_run(Dev &s, uint32_t *loc_of, double *x, const double *y, int32_t *active,
+                       double *t_out, cudaStream_t st, int n_sm, uint8_t *flag, int64_t *lifts) {
+    const size_t nslot = (size_t)s.nc * s.nc * C;
+    unsigned long long lc[LC_N];
+    CUN(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
+    k_noalloc_check<<<(unsigned)std::min<int64_t>((s.n + 255) / 256, 4096), 256, 0, st>>>(
+        x, y, active, s.n, s.k, s.L, loc_of, s.lc + LC_ERR_CAP);
+    CUN(cudaGetLastError());
+    CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
+    CUN(cudaStreamSynchronize(st));
+    if (lc[LC_ERR_CAP]) return ECMC_EINVAL;
+    k_build_cells<C><<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, x, y);
+    k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
+    k_init_chains<<<(unsigned)((s.k + 255) / 256), 256, 0, st>>>(s, active, loc_of);
+    CUN(cudaGetLastError());
+    CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
+    CUN(cudaStreamSynchronize(st));
+    if (lc[LC_ERR_CAP]) return ECMC_ECAPACITY;  // more disks in a cell than slots
+    const int rc = noalloc_leg<C>(s, st, n_sm, flag, lifts);
+    if (rc) return rc;
+    k_export<C><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, x, nullptr);
+    k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, active);
+    if (t_out) CUN(cudaMemcpyAsync(t_out, s.t, (size_t)s.n * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+    CUN(cudaGetLastError());
+    CUN(cudaStreamSynchronize(st));
+    return ECMC_OK;
+}
+
+}  // namespace
+
+extern "C" int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int32_t n_chains,
+                                int32_t cells_per_side, double *x, const double *y,
+                                int32_t *active, double *t_out, void *stream, uint8_t *flag_out,
+                                int64_t *lifts_out) {
+    if (!x || !y || !active) return ECMC_EINVAL;
+    if (n < 3 || n > (int64_t)0x3FFFFFFF || n_chains < 1 || n_chains > n) return ECMC_EINVAL;
+    if (!(d > 0.0) || !(ell > 0.0) || !(box > 0.0) || !std::isfinite(box) || !std::isfinite(ell))
+        return ECMC_EINVAL;
+    ecmc_params p;
+    memset(&p, 0, sizeof p);
+    p.n = n;
+    p.box = box;
+    p.d = d;
+    p.ell = ell;
+    p.n_chains = n_chains;
+    p.cells_per_side = cells_per_side;
+    int nc = 0, C = 4;
+    if (pick_cells(&p, &nc, &C)) return ECMC_EINVAL;
+    Dev s;
+    memset(&s, 0, sizeof s);
+    s.n = n;
+    s.nc = nc;
+    s.k = n_chains;
+    s.cap = NOALLOC_CAP;
+    s.L = box;
+    s.d = d;
+    s.ell = ell;
+    s.a = box / (double)nc;
+    s.inv_a = (double)nc / box;
+    s.eps = std::ldexp(box, -30);
+    const size_t ncell = (size_t)nc * nc, nslot = ncell * C;
+    uint32_t *loc_of = nullptr;
+    // sizes beyond the fixed scratch array are rejected before any device work
+    if (noalloc_layout(s, nullptr, nslot, ncell, (size_t)n, (size_t)n_chains, &loc_of) >
+        NOALLOC_SCRATCH_BYTES)
+        return ECMC_EINVAL;
+    unsigned char *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    const size_t used = noalloc_layout(s, base, nslot, ncell, (size_t)n, (size_t)n_chains, &loc_of);
+    int dev = 0, n_sm = 1;
+    CUN(cudaGetDevice(&dev));
+    CUN(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: start from zero
+    CUN(cudaMemsetAsync(base, 0, used, st));
+    rc = C == 4 ? noalloc_run<4>(s, loc_of, x, y, active, t_out, st, n_sm, flag_out, lifts_out)
+                : noalloc_run<8>(s, loc_of, x, y, active, t_out, st, n_sm, flag_out, lifts_out);
+    return rc;
 }

@@ -24,7 +24,8 @@ ECMC_LOG_LIFTINGS = 0x1
 ECMC_INPUT_DEVICE = 0x2
 
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
-           "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error")
+           "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
+           "ecmc_leg_noalloc")
 
 
 class ecmc_params(C.Structure):
@@ -86,6 +87,10 @@ def load(path: str | None = None):
     lib.ecmc_destroy.restype = None
     lib.ecmc_last_error.argtypes = [vp]
     lib.ecmc_last_error.restype = C.c_char_p
+    lib.ecmc_leg_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                     C.c_int32, vp, vp, vp, vp, vp, C.POINTER(C.c_uint8),
+                                     C.POINTER(C.c_int64)]
+    lib.ecmc_leg_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -149,6 +154,23 @@ def ecmc_liftings(ctx) -> np.ndarray:
     buf = np.zeros(n.value, dtype=LIFT_DTYPE)
     _check(load().ecmc_liftings(ctx, _ptr(buf) if n.value else None, n.value, C.byref(n)), ctx)
     return buf
+
+
+def ecmc_leg_noalloc(n, box, d, ell, n_chains, cells_per_side, x, y, active, t_out=None,
+                     stream=None):
+    """One leg through the entry point that allocates nothing (device tensors
+    in and out); returns (flag, liftings). Raises EcmcError on a failure code."""
+    flag = C.c_uint8()
+    lifts = C.c_int64()
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = load().ecmc_leg_noalloc(int(n), float(box), float(d), float(ell), int(n_chains),
+                                 int(cells_per_side), _ptr(x), _ptr(y), _ptr(active),
+                                 _ptr(t_out), st, C.byref(flag), C.byref(lifts))
+    if rc != ECMC_OK:
+        raise EcmcError(rc, "ecmc_leg_noalloc failed")
+    return flag.value, lifts.value
 
 
 def ecmc_destroy(ctx):
