@@ -48,6 +48,7 @@ constexpr uint32_t OWN_ACTIVE = 0x40000000u;
 constexpr uint32_t OWN_STALLED = 0x80000000u;
 constexpr uint32_t OWN_CHAIN = 0x3FFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;  // +inf
 
 constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
 
@@ -59,10 +60,13 @@ enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
 enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,
        TC_LOG_N, TC_N };
 
-// One event of a chain: enough to undo it, and the lifting record (Eq. 1).
+constexpr uint32_t REC_NO_OWNER = 1u;  // the target's owner word was not taken
+
+// One event of a chain: enough to undo it exactly, and the lifting (Eq. 1).
 struct Rec {
     uint32_t i, from, to, j;  // moved disk, its slot before/after, target (NONE: stall)
     uint32_t jloc, seq;       // slot of j; order of application within its run
+    uint32_t flags, pad;
     double x_old;             // x of i before the move
     double ti_old, tj_old;    // local times of i and j before the event
     double t, tau, xi, xj;    // event time (= new t_j), time of flight, x_i at contact, x_j
@@ -72,21 +76,19 @@ struct Rec {
 struct Dev {
     int64_t n;
     int nc, k, cap;
-    double L, d, ell, a, inv_a, eps;
-    // cells: slot q of cell c at index c*C + q
-    double *cx, *cy;
-    uint32_t *cid;
+    double L, d, d2, ell, a, inv_a, eps;
+    // cells: slot q of cell c at index c*C + q; a disk's x, y, local time and
+    // owner word live in its slot and move with it
+    double *cx, *cy, *ct;
+    uint32_t *cid, *cown;
     uint32_t *claim;  // per cell: 0 or chain+1
-    // per disk
-    double *t;
-    uint32_t *owner;
     // per chain
     uint32_t *aloc0, *aloc;
     uint32_t *ci;  // active disk id
     double *D, *tc;
     int32_t *status, *partner, *nrec, *nlift;
     Rec *rec;  // [k * cap]
-    // pending events for the global-time repair
+    // pending events for the global-time repair of large components
     double *ev_T, *ev_tau, *ev_xj, *ev_yj, *ev_tj;
     uint32_t *ev_j, *ev_jloc;
     int32_t *ev_lift, *ev_cx, *ev_cy, *ev_mlast;
@@ -101,8 +103,7 @@ struct Dev {
     int32_t *comp_root;  // root of the q-th dirty component
     int32_t *comp_mem;   // members, grouped by component
     int32_t *ctl;        // [CTL_N]
-    int32_t round;
-    unsigned long long *lc;  // [LC_N]
+    unsigned long long *lc;      // [LC_N]
     unsigned long long *tc_cnt;  // [TC_N]
     ecmc_lift_t *log;
     int64_t log_cap;
@@ -110,6 +111,16 @@ struct Dev {
 };
 
 // ------------------------------------------------------------ FP64 geometry
+
+// Non-negative doubles (and +inf) order like their bit patterns; comparisons
+// of such values run on the integer pipe.
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+// v < 0 for a value that is not -0.0 (subtractions of finite doubles never give -0.0)
+__device__ __forceinline__ bool dneg(double v) {
+    return __double_as_longlong(v) < 0 && dbits(v) != 0x8000000000000000ull;
+}
 
 __device__ __forceinline__ int cell_coord(double v, const Dev &s) {
     int c = __double2int_rz(__dmul_rn(v, s.inv_a));
@@ -124,7 +135,7 @@ __device__ __forceinline__ uint32_t cell_of(double x, double y, const Dev &s) {
 
 __device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
     double r = __dadd_rn(x, dx);
-    if (r >= s.L) r = __dsub_rn(r, s.L);
+    if (dbits(r) >= dbits(s.L)) r = __dsub_rn(r, s.L);  // r >= 0
     return r;
 }
 
@@ -133,23 +144,32 @@ __device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
 __device__ __forceinline__ double time_of_flight(double xi, double yi, double xj, double yj,
                                                  const Dev &s) {
     double a = fabs(__dsub_rn(yj, yi));
-    double la = __dsub_rn(s.L, a);
-    if (la < a) a = la;
-    if (!(a < s.d)) return INFINITY;
-    double b = __dsqrt_rn(__dsub_rn(__dmul_rn(s.d, s.d), __dmul_rn(a, a)));
+    const double la = __dsub_rn(s.L, a);
+    if (dbits(la) < dbits(a)) a = la;
+    if (!(dbits(a) < dbits(s.d))) return INFINITY;
+    const double b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(a, a)));
     double dx = __dsub_rn(xj, xi);
-    if (dx < 0.0) dx = __dadd_rn(dx, s.L);
+    if (dneg(dx)) dx = __dadd_rn(dx, s.L);
     double tau = __dsub_rn(dx, b);
-    if (tau < 0.0) tau = 0.0;
+    if (dneg(tau)) tau = 0.0;
     return tau;
 }
 
-__device__ __forceinline__ void warp_argmin(double &t, uint32_t &j, uint32_t &l) {
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
+    return (unsigned long long)__shfl_xor_sync(FULL, (long long)v, o);
+}
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
+    return (unsigned long long)__shfl_sync(FULL, (long long)v, src);
+}
+
+// lexicographic (tau, j) minimum over the warp; tau given by its bits
+__device__ __forceinline__ void warp_argmin(unsigned long long &t, uint32_t &j, uint32_t &l) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double t2 = __shfl_xor_sync(FULL, t, o);
-        uint32_t j2 = __shfl_xor_sync(FULL, j, o);
-        uint32_t l2 = __shfl_xor_sync(FULL, l, o);
+        const unsigned long long t2 = shfl_xor_u64(t, o);
+        const uint32_t j2 = __shfl_xor_sync(FULL, j, o);
+        const uint32_t l2 = __shfl_xor_sync(FULL, l, o);
         if (t2 < t || (t2 == t && j2 < j)) {
             t = t2;
             j = j2;
@@ -179,7 +199,9 @@ struct StepOut {
 
 // Statements 1-9 of Alg. 5 for one chain, with the cell scan: columns ahead
 // of the active disk are scanned until (m*a - fx) - d > min(D, best) + eps.
-// Every scanned cell is claimed for the leg (conflict if another owner holds it).
+// Every scanned cell is claimed for the leg (conflict if another owner holds
+// it). A column whose threshold is <= eps is scanned whatever the candidates,
+// so its cells are claimed together with their load.
 // PASS1: the owner is the chain; only its own disk is excluded; Eq. 2 is
 //   checked as an assertion (it cannot fail while the cells are held).
 // COMP: the owner is the conflict component `root` (any member's claim is its
@@ -194,6 +216,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
     const int rr = sub / C, sl = sub % C;
     const bool used = sub < 3 * C;
     const int nc = s.nc;
+    const uint32_t mine = (uint32_t)c + 1u;
 
     const int cxi = cell_coord(r.xi, s), cyi = cell_coord(r.yi, s);
     const double fx = __dsub_rn(r.xi, __dmul_rn((double)cxi, s.a));
@@ -201,14 +224,16 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
     if (row < 0) row += nc;
     if (row >= nc) row -= nc;
 
-    double cur = r.D;  // min(D, best tau so far): drives the stop rule
-    double btau = INFINITY, bx = 0.0, by = 0.0, bt = 0.0;
+    unsigned long long cur = dbits(r.D);  // min(D, best tau so far): drives the stop rule
+    unsigned long long cur_eps = dbits(__dadd_rn(r.D, s.eps));
+    unsigned long long btau = INF_BITS;
+    double bx = 0.0, by = 0.0, bt = 0.0;
     uint32_t bj = NONE, bloc = 0;
     int mlast = 0;
     bool stop = false;
     bool conflict = false;
     uint32_t partner = NONE;
-    unsigned long long hz = 0;
+    bool hz = false;
 
     for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
         const int m = m0 + grp;
@@ -217,51 +242,66 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
         if (col >= nc) col -= nc;
         const uint32_t cell = (uint32_t)row * (uint32_t)nc + (uint32_t)col;
         const uint32_t loc = cell * C + sl;
-        uint32_t id = colok ? s.cid[loc] : EMPTY;
+        // threshold of this lane's column; <= eps means "scanned in any case"
+        const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, s.a), fx), s.d);
+        const bool certain = m == 0 || dneg(thr) || dbits(thr) <= dbits(s.eps);
+        uint32_t holder = 0;
+        bool claimed_early = false;
+        if (colok && sl == 0 && certain) {
+            const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
+            holder = old == 0u ? mine : old;
+            claimed_early = true;
+        } else if (colok && sl == 0) {
+            holder = s.claim[cell];
+        }
+        const uint32_t id = colok ? s.cid[loc] : EMPTY;
         double xj = 0.0, yj = 0.0, tj = 0.0;
         uint32_t own = OWN_STATIC;
-        uint32_t clm = 0;
-        if (colok && sl == 0) clm = s.claim[cell];
         const bool cand = id != EMPTY && id != r.i;
         if (cand) {
             xj = s.cx[loc];
             yj = s.cy[loc];
-            tj = s.t[id];
-            if (MODE == MODE_COMP) own = s.owner[id];
+            tj = s.ct[loc];
+            if (MODE == MODE_COMP) own = s.cown[loc];
         }
         double tau = INFINITY;
         if (cand && own == OWN_STATIC) {
             tau = time_of_flight(r.xi, r.yi, xj, yj, s);
-            if (MODE == MODE_COMP && tau != INFINITY && __dadd_rn(r.ti, tau) < tj)
+            if (MODE == MODE_COMP && tau != INFINITY && dbits(__dadd_rn(r.ti, tau)) < dbits(tj))
                 tau = __dadd_rn(tau, s.L);
         }
+        const unsigned long long tb = dbits(tau);
         // column minima (lanes of one column form an aligned group of LPC)
-        double cm = tau;
+        unsigned long long cm = tb;
 #pragma unroll
-        for (int o = 1; o < LPC; o <<= 1) cm = fmin(cm, __shfl_xor_sync(FULL, cm, o));
+        for (int o = 1; o < LPC; o <<= 1) {
+            const unsigned long long v = shfl_xor_u64(cm, o);
+            cm = v < cm ? v : cm;
+        }
         int last_here = -1;
 #pragma unroll
         for (int g = 0; g < CPP; ++g) {
-            const double cmg = __shfl_sync(FULL, cm, g * LPC);
+            const unsigned long long cmg = shfl_u64(cm, g * LPC);
+            const double thg = __shfl_sync(FULL, thr, g * LPC);
             const int mg = m0 + g;
             if (stop) continue;
             if (mg >= nc) {
                 stop = true;
                 continue;
             }
-            if (mg >= 1) {
-                double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)mg, s.a), fx), s.d);
-                if (thr > __dadd_rn(cur, s.eps)) {
-                    stop = true;
-                    continue;
-                }
+            if (mg >= 1 && !dneg(thg) && dbits(thg) > cur_eps) {
+                stop = true;
+                continue;
             }
             last_here = mg;
             mlast = mg;
-            cur = fmin(cur, cmg);
+            if (cmg < cur) {
+                cur = cmg;
+                cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+            }
         }
         const bool scanned = colok && m <= last_here;
-        double kt = scanned ? tau : INFINITY;
+        unsigned long long kt = scanned ? tb : INF_BITS;
         uint32_t kj = scanned ? id : NONE;
         uint32_t kl = loc;
         warp_argmin(kt, kj, kl);
@@ -276,9 +316,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
             bloc = kl;
         }
         if (scanned && sl == 0) {
-            const uint32_t mine = (uint32_t)c + 1u;
-            uint32_t holder = clm;
-            if (holder == 0u) {
+            if (!claimed_early && holder == 0u) {
                 const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
                 holder = old == 0u ? mine : old;
             }
@@ -294,7 +332,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
         }
         // Eq. 2 (statement 5) on every scanned candidate: cannot fail while the
         // cells are held by a lone chain; counted as an assertion.
-        if (MODE == MODE_PASS1 && scanned && tau != INFINITY && __dadd_rn(r.ti, tau) < tj) hz++;
+        if (MODE == MODE_PASS1 && scanned && tau != INFINITY &&
+            dbits(__dadd_rn(r.ti, tau)) < dbits(tj))
+            hz = true;
     }
 
     StepOut o;
@@ -309,12 +349,12 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
         o.partner = __shfl_sync(FULL, partner, __ffs(cb) - 1);
     }
     if (MODE == MODE_PASS1) {
-        const unsigned hb = __ballot_sync(FULL, hz != 0);
+        const unsigned hb = __ballot_sync(FULL, hz);
         if (hb && lane == __ffs(hb) - 1) atomicAdd(s.lc + LC_HORIZON, 1ull);
     }
-    if (btau < r.D) {
+    if (btau < dbits(r.D)) {
         o.lift = 1;
-        o.tau = btau;
+        o.tau = __longlong_as_double((long long)btau);
         o.j = bj;
         o.jloc = bloc;
         o.xj = bx;
@@ -332,67 +372,66 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
     return o;
 }
 
-// Moves the active disk of chain c by dist (statements 16 / 22), updating its
-// cell slot; returns its new slot or EMPTY on a full cell.
+// Moves the active disk (statements 16 / 22) with its local time and owner
+// word; returns its new slot or EMPTY on a full cell.
 template <int C>
-__device__ uint32_t move_active(const Dev &s, const ChainReg &r, double xnew) {
+__device__ uint32_t move_active(const Dev &s, const ChainReg &r, double xnew, double tnew,
+                                uint32_t own_new) {
     const int lane = threadIdx.x & 31;
     const uint32_t cell_old = r.iloc / C;
     const uint32_t cell_new = cell_of(xnew, r.yi, s);
     uint32_t newloc = r.iloc;
     if (cell_new != cell_old) {
-        uint32_t sid = (lane < C) ? s.cid[cell_new * C + lane] : 0u;
+        const uint32_t sid = (lane < C) ? s.cid[cell_new * C + lane] : 0u;
         const unsigned em = __ballot_sync(FULL, lane < C && sid == EMPTY);
         if (!em) return EMPTY;
         newloc = cell_new * C + (uint32_t)(__ffs(em) - 1);
         if (lane == 0) {
-            s.cid[newloc] = r.i;
             s.cx[newloc] = xnew;
             s.cy[newloc] = r.yi;
+            s.ct[newloc] = tnew;
+            s.cown[newloc] = own_new;
+            s.cid[newloc] = r.i;
             s.cid[r.iloc] = EMPTY;
         }
     } else if (lane == 0) {
         s.cx[r.iloc] = xnew;
+        s.ct[r.iloc] = tnew;
+        s.cown[r.iloc] = own_new;
     }
     return newloc;
 }
 
-// Executes a step (lift: statements 10-19; stall: 21-24). Returns the chain's
-// new status. Writes are done by lane 0; all lanes update the registers.
+// Executes a step (lift: statements 10-19; stall: 21-24) and returns the
+// chain's new status; *newloc receives the moved disk's slot. Writes are done
+// by lane 0; all lanes update the registers. In pass 1 the owner word of the
+// target is taken with atomicCAS whose result (*cas_old, lane 0) the caller
+// checks later; in repair the component owns every cell it touches.
 template <int C>
-__device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, bool cas_owner,
-                           uint32_t seq) {
+__device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, bool pass1,
+                           uint32_t seq, uint32_t *newloc_out, uint32_t *cas_old) {
     const int lane = threadIdx.x & 31;
-    int32_t nrec = s.nrec[c];
+    const int32_t nrec = s.nrec[c];
     if (nrec >= s.cap) {
         if (lane == 0) atomicAdd(s.lc + LC_ERR_REC, 1ull);
         return ST_BLOCKED;
     }
     if (o.lift) {
-        if (cas_owner) {
-            uint32_t old = 0;
-            if (lane == 0) old = atomicCAS(s.owner + o.j, OWN_STATIC, OWN_ACTIVE | (uint32_t)c);
-            old = __shfl_sync(FULL, old, 0);
-            if (old != OWN_STATIC) {
-                if (lane == 0) {
-                    s.partner[c] = (int32_t)(old & OWN_CHAIN);
-                    atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
-                }
-                return ST_BLOCKED;
-            }
-        }
         const double tnew = __dadd_rn(r.ti, o.tau);      // statements 14, 15
         const double xnew = wrap_add(r.xi, o.tau, s);    // statement 16
-        const uint32_t newloc = move_active<C>(s, r, xnew);
+        if (lane == 0) {
+            if (pass1)
+                *cas_old = atomicCAS(s.cown + o.jloc, OWN_STATIC, OWN_ACTIVE | (uint32_t)c);
+            else
+                s.cown[o.jloc] = OWN_ACTIVE | (uint32_t)c;
+            s.ct[o.jloc] = tnew;
+        }
+        const uint32_t newloc = move_active<C>(s, r, xnew, tnew, OWN_STATIC);  // statement 17
         if (newloc == EMPTY) {
             if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
             return ST_BLOCKED;
         }
         if (lane == 0) {
-            if (!cas_owner) s.owner[o.j] = OWN_ACTIVE | (uint32_t)c;
-            s.t[o.j] = tnew;
-            s.t[r.i] = tnew;
-            s.owner[r.i] = OWN_STATIC;                   // statement 17
             Rec q;
             q.i = r.i;
             q.from = r.iloc;
@@ -400,6 +439,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
             q.j = o.j;
             q.jloc = o.jloc;
             q.seq = seq;
+            q.flags = 0;
+            q.pad = 0;
             q.x_old = r.xi;
             q.ti_old = r.ti;
             q.tj_old = o.tj;
@@ -412,6 +453,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
             s.nrec[c] = nrec + 1;
             s.nlift[c] += 1;
         }
+        *newloc_out = newloc;
         r.D = __dsub_rn(r.D, o.tau);                     // statement 18
         r.i = o.j;                                       // statement 19
         r.iloc = o.jloc;
@@ -423,14 +465,12 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
     }
     const double tnew = __dadd_rn(r.ti, r.D);           // statement 21
     const double xnew = wrap_add(r.xi, r.D, s);         // statement 22
-    const uint32_t newloc = move_active<C>(s, r, xnew);
+    const uint32_t newloc = move_active<C>(s, r, xnew, tnew, OWN_STALLED | (uint32_t)c);
     if (newloc == EMPTY) {
         if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
         return ST_BLOCKED;
     }
     if (lane == 0) {
-        s.t[r.i] = tnew;
-        s.owner[r.i] = OWN_STALLED | (uint32_t)c;       // statement 24
         Rec q;
         q.i = r.i;
         q.from = r.iloc;
@@ -438,6 +478,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         q.j = NONE;
         q.jloc = 0;
         q.seq = seq;
+        q.flags = 0;
+        q.pad = 0;
         q.x_old = r.xi;
         q.ti_old = r.ti;
         q.tj_old = 0.0;
@@ -449,6 +491,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         s.rec[(size_t)c * s.cap + nrec] = q;
         s.nrec[c] = nrec + 1;
     }
+    *newloc_out = newloc;
     r.iloc = newloc;
     r.xi = xnew;
     r.ti = tnew;
@@ -470,6 +513,8 @@ __global__ void k_build_cells(Dev s, const double *x, const double *y) {
         if (atomicCAS(s.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
             s.cx[loc] = x[q];
             s.cy[loc] = y[q];
+            s.ct[loc] = 0.0;
+            s.cown[loc] = OWN_STATIC;
             return;
         }
     }
@@ -487,28 +532,29 @@ __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= s.k) return;
     const uint32_t a = (uint32_t)active[c];
-    s.aloc[c] = loc_of[a];
+    const uint32_t loc = loc_of[a];
+    s.aloc[c] = loc;
     s.ci[c] = a;
-    s.owner[a] = OWN_ACTIVE | (uint32_t)c;
+    s.cown[loc] = OWN_ACTIVE | (uint32_t)c;
     s.nrec[c] = 0;
     s.status[c] = ST_STALLED;
 }
 
-// Leg start: clear local times and tags left by the previous leg, then start
-// every chain on its stalled disk with D = ell (Alg. 2 input at h).
+// Leg start: clear local times left by the previous leg (every slot a record
+// names), then start every chain on its stalled disk with D = ell (Alg. 2
+// input at h).
 __global__ void k_leg_begin(Dev s) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= s.k) return;
     const int32_t nr = s.nrec[c];
     const Rec *q = s.rec + (size_t)c * s.cap;
     for (int32_t e = 0; e < nr; ++e) {
-        s.t[q[e].i] = 0.0;
-        if (q[e].j != NONE) s.t[q[e].j] = 0.0;
+        s.ct[q[e].to] = 0.0;
+        if (q[e].j != NONE) s.ct[q[e].jloc] = 0.0;
     }
     const uint32_t loc = s.aloc[c];
-    const uint32_t a = s.cid[loc];
-    s.owner[a] = OWN_ACTIVE | (uint32_t)c;
-    s.ci[c] = a;
+    s.cown[loc] = OWN_ACTIVE | (uint32_t)c;
+    s.ci[c] = s.cid[loc];
     s.aloc0[c] = loc;
     s.D[c] = s.ell;
     s.tc[c] = 0.0;
@@ -534,17 +580,37 @@ __global__ void k_pass1(Dev s) {
     r.D = s.ell;
     int st = ST_RUNNING;
     uint32_t seq = 0;
+    uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
+    int32_t cas_rec = -1;           // record of that lift, while unchecked
     while (st == ST_RUNNING) {
         const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r);
+        if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
+            const uint32_t old = __shfl_sync(FULL, cas_old, 0);
+            if (old != OWN_STATIC) {
+                // the target was another chain's start disk: its cell is held by
+                // this chain, so that chain meets a conflict as well
+                if (lane == 0) {
+                    s.rec[(size_t)c * s.cap + cas_rec].flags |= REC_NO_OWNER;
+                    s.partner[c] = (int32_t)(old & OWN_CHAIN);
+                    atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
+                }
+                st = ST_BLOCKED;
+                break;
+            }
+            cas_rec = -1;
+        }
         if (o.conflict) {
             if (lane == 0) s.partner[c] = (int32_t)o.partner;
             st = ST_BLOCKED;
             break;
         }
-        st = commit_step<C>(s, c, r, o, true, seq++);
+        uint32_t nl;
+        const int32_t nrec0 = s.nrec[c];
+        st = commit_step<C>(s, c, r, o, true, seq++, &nl, &cas_old);
+        if (st == ST_RUNNING) cas_rec = nrec0;
     }
     if (lane == 0) {
-        // events before the blocking time are exact (Sec. 3.4, partial validation)
+        // events before the blocking time are exact (Remark 6)
         s.vt[c] = st == ST_BLOCKED ? r.ti : INFINITY;
         s.status[c] = st;
         s.aloc[c] = r.iloc;
@@ -559,18 +625,18 @@ __global__ void k_pass1(Dev s) {
 // Exact inverse of commit_step for one record of chain c (lane 0 only).
 __device__ void undo_record(const Dev &s, int c, const Rec &u) {
     if (u.to != u.from) {
-        s.cid[u.from] = u.i;
         s.cx[u.from] = u.x_old;
         s.cy[u.from] = s.cy[u.to];
+        s.cid[u.from] = u.i;
         s.cid[u.to] = EMPTY;
     } else {
         s.cx[u.from] = u.x_old;
     }
-    s.t[u.i] = u.ti_old;
-    s.owner[u.i] = OWN_ACTIVE | (uint32_t)c;
+    s.ct[u.from] = u.ti_old;
+    s.cown[u.from] = OWN_ACTIVE | (uint32_t)c;
     if (u.j != NONE) {
-        s.t[u.j] = u.tj_old;
-        s.owner[u.j] = OWN_STATIC;
+        s.ct[u.jloc] = u.tj_old;
+        if (!(u.flags & REC_NO_OWNER)) s.cown[u.jloc] = OWN_STATIC;
         s.nlift[c] -= 1;
     }
 }
@@ -611,7 +677,7 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
     if (lane == 31) warp_tot[w] = x;
     __syncthreads();
     if (w == 0) {
-        int t = warp_tot[lane];
+        const int t = warp_tot[lane];
         int u = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -628,9 +694,9 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
 }
 
 // Conflict components (one block of 1024 threads). first: edges from pass 1
-// (blocked chain -> holder of the cell it met); later rounds: edges from
-// components that met another chain. Components holding a chain whose events
-// are not final ("dirty") are listed for k_repair with their members.
+// (blocked chain -> holder of the cell or owner word it met); later rounds:
+// edges from components that met another chain. Components holding a chain
+// whose events are not final ("dirty") are listed for k_repair.
 __global__ void k_uf(Dev s, int first) {
     __shared__ int warp_tot[32];
     __shared__ int tot_cnt, tot_cmp;
@@ -703,8 +769,246 @@ __global__ void k_uf(Dev s, int first) {
     }
 }
 
+__device__ __forceinline__ bool footprint_has(int fcx, int fcy, int fm, uint32_t cell, int nc) {
+    const int r = (int)(cell / (uint32_t)nc), col = (int)(cell % (uint32_t)nc);
+    int dr = r - fcy;
+    if (dr < 0) dr += nc;
+    if (!(dr == 0 || dr == 1 || dr == nc - 1)) return false;
+    int dm = col - fcx;
+    if (dm < 0) dm += nc;
+    return dm <= fm;
+}
+
+__device__ __forceinline__ void atomic_min_time(double *p, double v) {
+    // times are >= 0: their IEEE bit patterns order like the values
+    atomicMin((unsigned long long *)p, (unsigned long long)__double_as_longlong(v));
+}
+
+// Rolls the members of a component back to T* (their events before T* are
+// exact): records with event time >= T* are undone, latest first within each
+// run (runs of different components touch different cells).
+__device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double Ts) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t bseq = 0;
+        int bmem = -1;
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            const int32_t nr = s.nrec[c];
+            if (nr == 0) continue;
+            const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+            if (!(u.t >= Ts)) continue;
+            if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
+                bseq = u.seq;
+                bmem = e;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t s2 = __shfl_xor_sync(FULL, bseq, o);
+            const int m2 = __shfl_xor_sync(FULL, bmem, o);
+            if (m2 >= 0 && (bmem < 0 || s2 > bseq || (s2 == bseq && m2 < bmem))) {
+                bseq = s2;
+                bmem = m2;
+            }
+        }
+        if (bmem < 0) break;
+        if (lane == 0) {
+            const int c = mem[bmem];
+            const int32_t nr = s.nrec[c];
+            undo_record(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
+            s.nrec[c] = nr - 1;
+        }
+        __syncwarp();
+    }
+}
+
+// State of chain c after its last kept record (or at the leg start).
+__device__ void resume_state(const Dev &s, int c, uint32_t &loc, uint32_t &id, double &t,
+                             double &D, int &st) {
+    const int32_t nr = s.nrec[c];
+    if (nr == 0) {
+        loc = s.aloc0[c];
+        id = s.cid[loc];
+        t = 0.0;
+        D = s.ell;
+        st = ST_RUNNING;
+        return;
+    }
+    const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+    if (u.j == NONE) {
+        loc = u.to;
+        id = u.i;
+        t = u.t;
+        D = 0.0;
+        st = ST_STALLED;
+    } else {
+        loc = u.jloc;
+        id = u.j;
+        t = u.t;
+        D = u.d_after;
+        st = ST_RUNNING;
+    }
+}
+
+// After a component's redo: record abort or success for the next round.
+__device__ void finish_component(const Dev &s, const int32_t *mem, int m, int root, bool abort,
+                                 int met, double now) {
+    const int lane = threadIdx.x & 31;
+    if (abort) {
+        // events before `now` are exact; the chain met joins next round
+        for (int e = lane; e < m; e += 32) s.vt[mem[e]] = now;
+        if (lane == 0) {
+            if (met >= 0) {
+                s.abort_to[root] = met;
+                atomic_min_time(s.vt + met, now);
+            }
+            atomicAdd(s.ctl + CTL_NABORT, 1);
+        }
+    } else {
+        for (int e = lane; e < m; e += 32) {
+            s.fin[mem[e]] = 1;
+            s.vt[mem[e]] = INFINITY;
+        }
+    }
+    __syncwarp();
+}
+
+// Redo of a component with at most 32 members: member e's state and pending
+// event live in the registers of lane e.
 template <int C>
-__device__ StepOut compute_event(const Dev &s, int c, int root) {
+__device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, double Ts,
+                             int round) {
+    const int lane = threadIdx.x & 31;
+    const bool has = lane < m;
+    const int my_c = has ? mem[lane] : 0x7FFFFFFF;
+    uint32_t my_loc = 0, my_id = 0;
+    double my_x = 0.0, my_y = 0.0, my_t = 0.0, my_D = 0.0;
+    int my_st = ST_STALLED;
+    if (has) {
+        resume_state(s, my_c, my_loc, my_id, my_t, my_D, my_st);
+        my_x = s.cx[my_loc];
+        my_y = s.cy[my_loc];
+    }
+    // pending event
+    unsigned long long ev_T = INF_BITS;
+    StepOut ev;
+    ev.lift = 0;
+    ev.tau = 0.0;
+    ev.j = NONE;
+    ev.jloc = 0;
+    ev.xj = ev.yj = ev.tj = 0.0;
+    ev.cx = ev.cy = 0;
+    ev.mlast = -1;
+    bool abort = false;
+    int met = -1;
+    // computes member q's next event into lane q's registers
+    auto compute = [&](int q) {
+        ChainReg r;
+        r.i = __shfl_sync(FULL, my_id, q);
+        r.iloc = __shfl_sync(FULL, my_loc, q);
+        r.xi = __shfl_sync(FULL, my_x, q);
+        r.yi = __shfl_sync(FULL, my_y, q);
+        r.ti = __shfl_sync(FULL, my_t, q);
+        r.D = __shfl_sync(FULL, my_D, q);
+        const int cq = __shfl_sync(FULL, my_c, q);
+        const StepOut o = scan_step<C, MODE_COMP>(s, cq, root, r);
+        if (o.conflict) {
+            abort = true;
+            met = (int)o.partner;
+        }
+        if (lane == q) {
+            ev = o;
+            ev_T = dbits(__dadd_rn(r.ti, o.tau));
+        }
+    };
+    {
+        unsigned b = __ballot_sync(FULL, has && my_st == ST_RUNNING);
+        while (b && !abort) {
+            const int q = __ffs(b) - 1;
+            b &= b - 1;
+            compute(q);
+        }
+    }
+    double now = Ts;
+    uint32_t cnt = 0;
+    while (!abort) {
+        unsigned long long bT = (has && my_st == ST_RUNNING) ? ev_T : ~0ull;
+        int bc = (has && my_st == ST_RUNNING) ? my_c : 0x7FFFFFFF;
+        int bq = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long T2 = shfl_xor_u64(bT, o);
+            const int c2 = __shfl_xor_sync(FULL, bc, o);
+            const int q2 = __shfl_xor_sync(FULL, bq, o);
+            if (T2 < bT || (T2 == bT && c2 < bc)) {
+                bT = T2;
+                bc = c2;
+                bq = q2;
+            }
+        }
+        if (bc == 0x7FFFFFFF) break;
+        const double Tn = __longlong_as_double((long long)bT);
+        if (dbits(Tn) < dbits(now) && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
+        now = Tn;
+        ChainReg r;
+        r.i = __shfl_sync(FULL, my_id, bq);
+        r.iloc = __shfl_sync(FULL, my_loc, bq);
+        r.xi = __shfl_sync(FULL, my_x, bq);
+        r.yi = __shfl_sync(FULL, my_y, bq);
+        r.ti = __shfl_sync(FULL, my_t, bq);
+        r.D = __shfl_sync(FULL, my_D, bq);
+        StepOut o;
+        o.lift = __shfl_sync(FULL, ev.lift, bq);
+        o.tau = __shfl_sync(FULL, ev.tau, bq);
+        o.j = __shfl_sync(FULL, ev.j, bq);
+        o.jloc = __shfl_sync(FULL, ev.jloc, bq);
+        o.xj = __shfl_sync(FULL, ev.xj, bq);
+        o.yj = __shfl_sync(FULL, ev.yj, bq);
+        o.tj = __shfl_sync(FULL, ev.tj, bq);
+        const uint32_t cell_a = r.iloc / C;
+        const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
+        uint32_t nl = 0, dummy = 0;
+        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
+                                      &dummy);
+        if (st == ST_BLOCKED) {  // out of records or slots: reported by the host
+            abort = true;
+            break;
+        }
+        const uint32_t cell_b = nl / C;
+        if (lane == bq) {
+            my_st = st;
+            my_loc = r.iloc;
+            my_id = r.i;
+            my_x = r.xi;
+            my_y = r.yi;
+            my_t = r.ti;
+            my_D = r.D;
+        }
+        const bool redo = has && my_st == ST_RUNNING &&
+                          (lane == bq || footprint_has(ev.cx, ev.cy, ev.mlast, cell_a, s.nc) ||
+                           footprint_has(ev.cx, ev.cy, ev.mlast, cell_b, s.nc) ||
+                           footprint_has(ev.cx, ev.cy, ev.mlast, cell_j, s.nc));
+        unsigned b = __ballot_sync(FULL, redo);
+        while (b && !abort) {
+            const int q = __ffs(b) - 1;
+            b &= b - 1;
+            compute(q);
+        }
+    }
+    if (has) {
+        s.status[my_c] = my_st;
+        s.aloc[my_c] = my_loc;
+        s.ci[my_c] = my_id;
+        s.tc[my_c] = my_t;
+        s.D[my_c] = my_D;
+    }
+    __syncwarp();
+    finish_component(s, mem, m, root, abort, met, now);
+}
+
+template <int C>
+__device__ StepOut compute_event_global(const Dev &s, int c, int root) {
     const int lane = threadIdx.x & 31;
     ChainReg r;
     r.iloc = s.aloc[c];
@@ -731,25 +1035,122 @@ __device__ StepOut compute_event(const Dev &s, int c, int root) {
     return o;
 }
 
-__device__ __forceinline__ bool in_footprint(const Dev &s, int c, uint32_t cell) {
-    const int nc = s.nc;
-    const int r = (int)(cell / (uint32_t)nc), col = (int)(cell % (uint32_t)nc);
-    int dr = r - s.ev_cy[c];
-    if (dr < 0) dr += nc;
-    if (!(dr == 0 || dr == 1 || dr == nc - 1)) return false;
-    int dm = col - s.ev_cx[c];
-    if (dm < 0) dm += nc;
-    return dm <= s.ev_mlast[c];
+// Redo of a component with more than 32 members: state in global memory.
+template <int C>
+__device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, double Ts,
+                             int round) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < m; e += 32) {
+        const int c = mem[e];
+        uint32_t loc, id;
+        double t, D;
+        int st;
+        resume_state(s, c, loc, id, t, D, st);
+        s.aloc[c] = loc;
+        s.ci[c] = id;
+        s.tc[c] = t;
+        s.D[c] = D;
+        s.status[c] = st;
+    }
+    __syncwarp();
+    bool abort = false;
+    int met = -1;
+    for (int e = 0; e < m && !abort; ++e) {
+        const int c = mem[e];
+        if (s.status[c] != ST_RUNNING) continue;
+        const StepOut o = compute_event_global<C>(s, c, root);
+        if (o.conflict) {
+            abort = true;
+            met = (int)o.partner;
+        }
+    }
+    double now = Ts;
+    uint32_t cnt = 0;
+    while (!abort) {
+        double bT = INFINITY;
+        int bc = 0x7FFFFFFF;
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            if (s.status[c] != ST_RUNNING) continue;
+            const double T = s.ev_T[c];
+            if (T < bT || (T == bT && c < bc)) {
+                bT = T;
+                bc = c;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double T2 = __shfl_xor_sync(FULL, bT, o);
+            const int c2 = __shfl_xor_sync(FULL, bc, o);
+            if (T2 < bT || (T2 == bT && c2 < bc)) {
+                bT = T2;
+                bc = c2;
+            }
+        }
+        if (bc == 0x7FFFFFFF) break;
+        if (bT < now && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
+        now = bT;
+        ChainReg r;
+        r.iloc = s.aloc[bc];
+        r.i = s.ci[bc];
+        r.xi = s.cx[r.iloc];
+        r.yi = s.cy[r.iloc];
+        r.ti = s.tc[bc];
+        r.D = s.D[bc];
+        StepOut o;
+        o.lift = s.ev_lift[bc];
+        o.tau = s.ev_tau[bc];
+        o.j = s.ev_j[bc];
+        o.jloc = s.ev_jloc[bc];
+        o.xj = s.ev_xj[bc];
+        o.yj = s.ev_yj[bc];
+        o.tj = s.ev_tj[bc];
+        const uint32_t cell_a = r.iloc / C;
+        const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
+        uint32_t nl = 0, dummy = 0;
+        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
+                                      &dummy);
+        if (st == ST_BLOCKED) {
+            abort = true;
+            break;
+        }
+        const uint32_t cell_b = nl / C;
+        if (lane == 0) {
+            s.status[bc] = st;
+            s.aloc[bc] = r.iloc;
+            s.ci[bc] = r.i;
+            s.tc[bc] = r.ti;
+            s.D[bc] = r.D;
+        }
+        __syncwarp();
+        for (int base = 0; base < m && !abort; base += 32) {
+            const int e = base + lane;
+            bool redo = false;
+            if (e < m) {
+                const int c = mem[e];
+                if (s.status[c] == ST_RUNNING)
+                    redo = c == bc ||
+                           footprint_has(s.ev_cx[c], s.ev_cy[c], s.ev_mlast[c], cell_a, s.nc) ||
+                           footprint_has(s.ev_cx[c], s.ev_cy[c], s.ev_mlast[c], cell_b, s.nc) ||
+                           footprint_has(s.ev_cx[c], s.ev_cy[c], s.ev_mlast[c], cell_j, s.nc);
+            }
+            unsigned b = __ballot_sync(FULL, redo);
+            while (b && !abort) {
+                const int q = __ffs(b) - 1;
+                b &= b - 1;
+                const StepOut o2 = compute_event_global<C>(s, mem[base + q], root);
+                if (o2.conflict) {
+                    abort = true;
+                    met = (int)o2.partner;
+                }
+            }
+        }
+    }
+    finish_component(s, mem, m, root, abort, met, now);
 }
 
-__device__ __forceinline__ void atomic_min_time(double *p, double v) {
-    // times are >= 0: their IEEE bit patterns order like the values
-    atomicMin((unsigned long long *)p, (unsigned long long)__double_as_longlong(v));
-}
-
-// One warp per dirty component: roll its members back to T* (the earliest
-// time up to which all of their events are exact), then redo them in global
-// event-time order (Alg. 2) while claiming cells for the component.
+// One warp per dirty component: roll its members back to T*, then redo them
+// in global event-time order (Alg. 2) while claiming cells for the component.
 template <int C>
 __global__ void k_repair(Dev s, int round) {
     const int lane = threadIdx.x & 31;
@@ -761,184 +1162,16 @@ __global__ void k_repair(Dev s, int round) {
         const int root = s.comp_root[q];
         const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
         const int32_t *mem = s.comp_mem + off;
-
         double Ts = INFINITY;
         for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
-
-        // 1. undo records with event time >= T*, latest first within each run
-        for (;;) {
-            uint32_t bseq = 0;
-            int bmem = -1;
-            for (int e = lane; e < m; e += 32) {
-                const int c = mem[e];
-                const int32_t nr = s.nrec[c];
-                if (nr == 0) continue;
-                const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
-                if (!(u.t >= Ts)) continue;
-                if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
-                    bseq = u.seq;
-                    bmem = e;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint32_t s2 = __shfl_xor_sync(FULL, bseq, o);
-                const int m2 = __shfl_xor_sync(FULL, bmem, o);
-                if (m2 >= 0 && (bmem < 0 || s2 > bseq || (s2 == bseq && m2 < bmem))) {
-                    bseq = s2;
-                    bmem = m2;
-                }
-            }
-            if (bmem < 0) break;
-            if (lane == 0) {
-                const int c = mem[bmem];
-                const int32_t nr = s.nrec[c];
-                undo_record(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
-                s.nrec[c] = nr - 1;
-            }
-            __syncwarp();
-        }
-        // 2. every member continues from its last kept event
-        for (int e = lane; e < m; e += 32) {
-            const int c = mem[e];
-            const int32_t nr = s.nrec[c];
-            if (nr == 0) {
-                const uint32_t loc = s.aloc0[c];
-                s.aloc[c] = loc;
-                s.ci[c] = s.cid[loc];
-                s.tc[c] = 0.0;
-                s.D[c] = s.ell;
-                s.status[c] = ST_RUNNING;
-            } else {
-                const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
-                if (u.j == NONE) {
-                    s.aloc[c] = u.to;
-                    s.ci[c] = u.i;
-                    s.tc[c] = u.t;
-                    s.D[c] = 0.0;
-                    s.status[c] = ST_STALLED;
-                } else {
-                    s.aloc[c] = u.jloc;
-                    s.ci[c] = u.j;
-                    s.tc[c] = u.t;
-                    s.D[c] = u.d_after;
-                    s.status[c] = ST_RUNNING;
-                }
-            }
-        }
-        __syncwarp();
+        rollback_members(s, mem, m, Ts);
         if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
-
-        // 3. global event-time order within the component
-        bool abort = false;
-        int met = -1;
-        for (int e = 0; e < m && !abort; ++e) {
-            const int c = mem[e];
-            if (s.status[c] != ST_RUNNING) continue;
-            const StepOut o = compute_event<C>(s, c, root);
-            if (o.conflict) {
-                abort = true;
-                met = (int)o.partner;
-            }
-        }
-        double now = Ts;
-        uint32_t cnt = 0;
-        while (!abort) {
-            double bT = INFINITY;
-            int bc = 0x7FFFFFFF;
-            for (int e = lane; e < m; e += 32) {
-                const int c = mem[e];
-                if (s.status[c] != ST_RUNNING) continue;
-                const double T = s.ev_T[c];
-                if (T < bT || (T == bT && c < bc)) {
-                    bT = T;
-                    bc = c;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double T2 = __shfl_xor_sync(FULL, bT, o);
-                const int c2 = __shfl_xor_sync(FULL, bc, o);
-                if (T2 < bT || (T2 == bT && c2 < bc)) {
-                    bT = T2;
-                    bc = c2;
-                }
-            }
-            if (bc == 0x7FFFFFFF) break;
-            if (bT < now && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
-            now = bT;
-            ChainReg r;
-            r.iloc = s.aloc[bc];
-            r.i = s.ci[bc];
-            r.xi = s.cx[r.iloc];
-            r.yi = s.cy[r.iloc];
-            r.ti = s.tc[bc];
-            r.D = s.D[bc];
-            StepOut o;
-            o.lift = s.ev_lift[bc];
-            o.tau = s.ev_tau[bc];
-            o.j = s.ev_j[bc];
-            o.jloc = s.ev_jloc[bc];
-            o.xj = s.ev_xj[bc];
-            o.yj = s.ev_yj[bc];
-            o.tj = s.ev_tj[bc];
-            const uint32_t cell_a = r.iloc / C;
-            const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
-            const int32_t nrec0 = s.nrec[bc];
-            const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++);
-            if (st == ST_BLOCKED) {  // out of records or slots: reported by the host
-                abort = true;
-                break;
-            }
-            const uint32_t cell_b = s.rec[(size_t)bc * s.cap + nrec0].to / C;
-            if (lane == 0) {
-                s.status[bc] = st;
-                s.aloc[bc] = r.iloc;
-                s.ci[bc] = r.i;
-                s.tc[bc] = r.ti;
-                s.D[bc] = r.D;
-            }
-            __syncwarp();
-            for (int base = 0; base < m && !abort; base += 32) {
-                const int e = base + lane;
-                bool redo = false;
-                if (e < m) {
-                    const int c = mem[e];
-                    if (s.status[c] == ST_RUNNING)
-                        redo = c == bc || in_footprint(s, c, cell_a) ||
-                               in_footprint(s, c, cell_b) || in_footprint(s, c, cell_j);
-                }
-                unsigned b = __ballot_sync(FULL, redo);
-                while (b && !abort) {
-                    const int qq = __ffs(b) - 1;
-                    b &= b - 1;
-                    const StepOut o2 = compute_event<C>(s, mem[base + qq], root);
-                    if (o2.conflict) {
-                        abort = true;
-                        met = (int)o2.partner;
-                    }
-                }
-            }
-        }
-        if (abort) {
-            // events before `now` are exact; the chain met joins next round
-            for (int e = lane; e < m; e += 32) s.vt[mem[e]] = now;
-            if (lane == 0) {
-                if (met >= 0) {
-                    s.abort_to[root] = met;
-                    atomic_min_time(s.vt + met, now);
-                }
-                atomicAdd(s.ctl + CTL_NABORT, 1);
-            }
-        } else {
-            for (int e = lane; e < m; e += 32) {
-                s.fin[mem[e]] = 1;
-                s.vt[mem[e]] = INFINITY;
-            }
-        }
-        __syncwarp();
+        if (m <= 32)
+            repair_small<C>(s, mem, m, root, Ts, round);
+        else
+            repair_large<C>(s, mem, m, root, Ts, round);
     }
 }
 
@@ -972,13 +1205,14 @@ __global__ void k_leg_end(Dev s, int32_t leg) {
 }
 
 template <int C>
-__global__ void k_export(Dev s, double *x, double *y) {
+__global__ void k_export(Dev s, double *x, double *y, double *t) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)s.nc * s.nc * C) return;
     const uint32_t id = s.cid[q];
     if (id == EMPTY) return;
     if (x) x[id] = s.cx[q];
     if (y) y[id] = s.cy[q];
+    if (t) t[id] = s.ct[q];
 }
 
 __global__ void k_export_active(Dev s, int32_t *active) {
@@ -1103,6 +1337,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
     s.L = p->box;
     s.d = p->d;
+    s.d2 = p->d * p->d;
     s.ell = p->ell;
     s.a = p->box / (double)nc;
     s.inv_a = (double)nc / p->box;
@@ -1118,10 +1353,10 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     };
     chk(dalloc(ctx, &s.cx, nslot));
     chk(dalloc(ctx, &s.cy, nslot));
+    chk(dalloc(ctx, &s.ct, nslot));
     chk(dalloc(ctx, &s.cid, nslot));
+    chk(dalloc(ctx, &s.cown, nslot));
     chk(dalloc(ctx, &s.claim, ncell));
-    chk(dalloc(ctx, &s.t, n));
-    chk(dalloc(ctx, &s.owner, n));
     chk(dalloc(ctx, &s.aloc0, k));
     chk(dalloc(ctx, &s.aloc, k));
     chk(dalloc(ctx, &s.ci, k));
@@ -1222,8 +1457,6 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     }
     CU(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.claim, 0, ncell * sizeof(uint32_t), st));
-    CU(cudaMemsetAsync(s.t, 0, n * sizeof(double), st));
-    CU(cudaMemsetAsync(s.owner, 0, n * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
@@ -1359,37 +1592,37 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
     cudaStream_t st = ctx->stream;
     const size_t n = (size_t)s.n;
     const size_t nslot = (size_t)s.nc * s.nc * ctx->C;
-    double *dx = nullptr, *dy = nullptr;
+    double *dx = nullptr, *dy = nullptr, *dt = nullptr;
     int32_t *da = nullptr;
-    if (x || y) {
-        if (cudaMalloc(&dx, n * 8) != cudaSuccess || cudaMalloc(&dy, n * 8) != cudaSuccess) {
-            cudaFree(dx);
-            (void)cudaGetLastError();
-            return fail(ctx, ECMC_ENOMEM, "positions scratch");
-        }
+    auto release = [&]() {
+        cudaFree(dx);
+        cudaFree(dy);
+        cudaFree(dt);
+        cudaFree(da);
+    };
+    if ((x && cudaMalloc(&dx, n * 8) != cudaSuccess) || (y && cudaMalloc(&dy, n * 8) != cudaSuccess) ||
+        (t && cudaMalloc(&dt, n * 8) != cudaSuccess) ||
+        (active && cudaMalloc(&da, (size_t)s.k * 4) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        release();
+        return fail(ctx, ECMC_ENOMEM, "positions scratch");
+    }
+    if (x || y || t) {
         if (ctx->C == 4)
-            k_export<4><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy);
+            k_export<4><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy, dt);
         else
-            k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy);
-        if (x) CU(cudaMemcpyAsync(x, dx, n * 8, cudaMemcpyDeviceToHost, st));
-        if (y) CU(cudaMemcpyAsync(y, dy, n * 8, cudaMemcpyDeviceToHost, st));
+            k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy, dt);
     }
-    if (t) CU(cudaMemcpyAsync(t, s.t, n * 8, cudaMemcpyDeviceToHost, st));
-    if (active) {
-        if (cudaMalloc(&da, (size_t)s.k * 4) != cudaSuccess) {
-            (void)cudaGetLastError();
-            cudaFree(dx);
-            cudaFree(dy);
-            return fail(ctx, ECMC_ENOMEM, "positions scratch");
-        }
-        k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
-        CU(cudaMemcpyAsync(active, da, (size_t)s.k * 4, cudaMemcpyDeviceToHost, st));
-    }
-    CU(cudaStreamSynchronize(st));
-    cudaFree(dx);
-    cudaFree(dy);
-    cudaFree(da);
-    CU(cudaGetLastError());
+    if (active) k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && y) e = cudaMemcpyAsync(y, dy, n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && t) e = cudaMemcpyAsync(t, dt, n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && active)
+        e = cudaMemcpyAsync(active, da, (size_t)s.k * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("positions: ") + cudaGetErrorString(e));
     return ECMC_OK;
 }
 
@@ -1509,10 +1742,10 @@ static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t n
     Carve cv{base, 0};
     s.cx = cv.take<double>(nslot);
     s.cy = cv.take<double>(nslot);
+    s.ct = cv.take<double>(nslot);
     s.cid = cv.take<uint32_t>(nslot);
+    s.cown = cv.take<uint32_t>(nslot);
     s.claim = cv.take<uint32_t>(ncell);
-    s.t = cv.take<double>(n);
-    s.owner = cv.take<uint32_t>(n);
     *loc_of = cv.take<uint32_t>(n);
     s.aloc0 = cv.take<uint32_t>(k);
     s.aloc = cv.take<uint32_t>(k);
@@ -1628,10 +1861,8 @@ static int noalloc_run(Dev &s, uint32_t *loc_of, double *x, const double *y, int
     if (lc[LC_ERR_CAP]) return ECMC_ECAPACITY;  // more disks in a cell than slots
     const int rc = noalloc_leg<C>(s, st, n_sm, flag, lifts);
     if (rc) return rc;
-    k_export<C><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, x, nullptr);
+    k_export<C><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, x, nullptr, t_out);
     k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, active);
-    if (t_out) CUN(cudaMemcpyAsync(t_out, s.t, (size_t)s.n * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, st));
     CUN(cudaGetLastError());
     CUN(cudaStreamSynchronize(st));
     return ECMC_OK;
@@ -1665,6 +1896,7 @@ extern "C" int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int
     s.cap = NOALLOC_CAP;
     s.L = box;
     s.d = d;
+    s.d2 = d * d;
     s.ell = ell;
     s.a = box / (double)nc;
     s.inv_a = (double)nc / box;
