@@ -101,8 +101,10 @@ int ecmc_create(const ecmc_params *p, const double *x, const double *y,
  *                 scanned a common cell (the leg was then redone in global
  *                 time order), else 0; entries past *legs_done are untouched.
  *   legs_done     host or NULL: number of legs completed.
- * Returns when the legs are done (the stream is synchronised).
- * Errors: EINVAL, ECUDA, ECAPACITY (undo log), ETIMEOUT.
+ * All legs run in one persistent cooperative launch; returns when they are
+ * done (the stream is synchronised).
+ * Errors: EINVAL, ECUDA, ECAPACITY (undo log), ETIMEOUT (a grid barrier wait
+ * passed its 60 s limit).
  */
 int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t event_budget,
                            uint8_t *leg_flags_out, int32_t *legs_done);
@@ -129,13 +131,15 @@ int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
 int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out);
 
 /*
- * ecmc_profile -- device time per kernel class, measured with CUDA events on
- * the context's stream around every launch of ecmc_run_to_breakpoint:
+ * ecmc_profile -- device time per phase of the persistent kernel, read from
+ * the device clock at the phase boundaries of every ecmc_run_to_breakpoint:
  *   pass1   the parallel pass (one warp per chain, Alg. 5/6 statements 1-26);
- *   repair  the global-time redo of legs with a conflict (Alg. 2);
- *   other   leg start/end bookkeeping, claim reset, rollback.
- * *_liftings count the liftings each class executed (pass-1 liftings of a
- * redone leg included).
+ *   repair  component rollback and global-time redo (Alg. 2), with its
+ *           union-find rounds;
+ *   other   leg start (claims, chain table) and leg end (totals, log).
+ * *_launches count legs (pass1, other) and legs with a repair (repair);
+ * pass1_liftings counts liftings of the parallel pass (redone ones included),
+ * repair_liftings the liftings of legs that needed a repair.
  */
 typedef struct {
     int64_t pass1_launches, repair_launches, other_launches;
@@ -144,6 +148,32 @@ typedef struct {
 } ecmc_profile_t;
 
 int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out);
+
+/*
+ * Batches: several independent systems (contexts) advanced together by one
+ * persistent launch on the device, each leg of each system exactly as
+ * ecmc_run_to_breakpoint would compute it (the systems share no state).
+ *
+ * ecmc_batch_create -- launch scratch for batches, queued on `stream`.
+ * ecmc_batch_run    -- runs up to max_legs legs of each of the n_ctx contexts
+ *   (distinct, same cell slots C; their streams are synchronised first).
+ *   budgets       host, n_ctx liftings or NULL: a context stops at the first
+ *                 breakpoint at which its liftings in this call reach its
+ *                 budget (0 = no budget); the launch ends when all stopped.
+ *   liftings_out, legs_out  host, n_ctx each or NULL: per-context results.
+ *   device_ms_out host or NULL: duration of the launch (CUDA events).
+ *   Errors: EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT (a grid barrier wait
+ *   passed its 60 s limit; the launch returned instead of waiting).
+ * ecmc_batch_last_error -- reason of the last failure of b.
+ * ecmc_batch_destroy    -- frees the scratch (the contexts stay valid).
+ */
+typedef struct ecmc_batch ecmc_batch;
+int ecmc_batch_create(void *stream, ecmc_batch **out);
+int ecmc_batch_run(ecmc_batch *b, ecmc_ctx *const *ctxs, int32_t n_ctx, int32_t max_legs,
+                   const uint64_t *budgets, int64_t *liftings_out, int32_t *legs_out,
+                   double *device_ms_out);
+const char *ecmc_batch_last_error(const ecmc_batch *b);
+void ecmc_batch_destroy(ecmc_batch *b);
 
 /* ecmc_destroy -- frees every device allocation of ctx (NULL is a no-op). */
 void ecmc_destroy(ecmc_ctx *ctx);

@@ -543,9 +543,7 @@ __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_
 // Leg start: clear local times left by the previous leg (every slot a record
 // names), then start every chain on its stalled disk with D = ell (Alg. 2
 // input at h).
-__global__ void k_leg_begin(Dev s) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.k) return;
+__device__ void leg_begin_chain(const Dev &s, int c) {
     const int32_t nr = s.nrec[c];
     const Rec *q = s.rec + (size_t)c * s.cap;
     for (int32_t e = 0; e < nr; ++e) {
@@ -564,12 +562,14 @@ __global__ void k_leg_begin(Dev s) {
     s.nlift[c] = 0;
 }
 
-// Pass 1: one warp per chain, run until stall or conflict.
+__global__ void k_leg_begin(Dev s) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s.k) leg_begin_chain(s, c);
+}
+
+// Pass 1: one warp runs chain c until it stalls or meets a conflict.
 template <int C>
-__global__ void k_pass1(Dev s) {
-    const int warps = blockDim.x >> 5;
-    const int c = blockIdx.x * warps + (threadIdx.x >> 5);
-    if (c >= s.k) return;
+__device__ void pass1_chain(const Dev &s, int c) {
     const int lane = threadIdx.x & 31;
     ChainReg r;
     r.iloc = s.aloc[c];
@@ -605,9 +605,9 @@ __global__ void k_pass1(Dev s) {
             break;
         }
         uint32_t nl;
-        const int32_t nrec0 = s.nrec[c];
-        st = commit_step<C>(s, c, r, o, true, seq++, &nl, &cas_old);
-        if (st == ST_RUNNING) cas_rec = nrec0;
+        st = commit_step<C>(s, c, r, o, true, seq, &nl, &cas_old);
+        if (st == ST_RUNNING) cas_rec = (int32_t)seq;
+        ++seq;
     }
     if (lane == 0) {
         // events before the blocking time are exact (Remark 6)
@@ -620,6 +620,14 @@ __global__ void k_pass1(Dev s) {
         if (st == ST_BLOCKED) atomicAdd(s.lc + LC_BLOCKED, 1ull);
         atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)s.nlift[c]);
     }
+    __syncwarp();
+}
+
+template <int C>
+__global__ void k_pass1(Dev s) {
+    const int warps = blockDim.x >> 5;
+    const int c = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (c < s.k) pass1_chain<C>(s, c);
 }
 
 // Exact inverse of commit_step for one record of chain c (lane 0 only).
@@ -665,9 +673,11 @@ __device__ void uf_union(int32_t *p, int a, int b) {
     }
 }
 
-// Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
+// Block-wide exclusive scan of one int per thread (blockDim.x a multiple of 32,
+// at most 1024).
 __device__ int block_exscan(int v, int *warp_tot, int *total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -677,14 +687,14 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
     if (lane == 31) warp_tot[w] = x;
     __syncthreads();
     if (w == 0) {
-        const int t = warp_tot[lane];
+        const int t = lane < nw ? warp_tot[lane] : 0;
         int u = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, u, o);
             if (lane >= o) u += y;
         }
-        warp_tot[lane] = u - t;
+        if (lane < nw) warp_tot[lane] = u - t;
         if (lane == 31) *total = u;
     }
     __syncthreads();
@@ -693,13 +703,11 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
     return r;
 }
 
-// Conflict components (one block of 1024 threads). first: edges from pass 1
-// (blocked chain -> holder of the cell or owner word it met); later rounds:
-// edges from components that met another chain. Components holding a chain
-// whose events are not final ("dirty") are listed for k_repair.
-__global__ void k_uf(Dev s, int first) {
-    __shared__ int warp_tot[32];
-    __shared__ int tot_cnt, tot_cmp;
+// Conflict components (one block). first: edges from pass 1 (blocked chain ->
+// holder of the cell or owner word it met); later rounds: edges from
+// components that met another chain. Components holding a chain whose events
+// are not final ("dirty") are listed for the repair with their members.
+__device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot) {
     const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
     if (first)
         for (int c = tid; c < k; c += nt) {
@@ -745,8 +753,8 @@ __global__ void k_uf(Dev s, int first) {
         sc += n;
         sm += n > 0;
     }
-    int oc = block_exscan(sc, warp_tot, &tot_cnt);
-    int om = block_exscan(sm, warp_tot, &tot_cmp);
+    int oc = block_exscan(sc, warp_tot, tot);
+    int om = block_exscan(sm, warp_tot, tot + 1);
     for (int c = lo; c < hi; ++c) {
         const int n = s.comp_cnt[c];
         if (n > 0) {
@@ -761,12 +769,19 @@ __global__ void k_uf(Dev s, int first) {
     for (int c = tid; c < k; c += nt)
         if (!s.fin[c]) s.comp_mem[atomicAdd(s.comp_cnt + s.comp_of[c], 1)] = c;
     if (tid == 0) {
-        s.comp_off[tot_cmp] = tot_cnt;
-        s.ctl[CTL_NCOMP] = tot_cmp;
-        s.ctl[CTL_NMEMB] = tot_cnt;
+        s.comp_off[tot[1]] = tot[0];
+        s.ctl[CTL_NCOMP] = tot[1];
+        s.ctl[CTL_NMEMB] = tot[0];
         s.ctl[CTL_WORK] = 0;
         s.ctl[CTL_NABORT] = 0;
     }
+    __syncthreads();
+}
+
+__global__ void k_uf(Dev s, int first) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    uf_block(s, first, warp_tot, tot);
 }
 
 __device__ __forceinline__ bool footprint_has(int fcx, int fcy, int fm, uint32_t cell, int nc) {
@@ -1149,8 +1164,27 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
     finish_component(s, mem, m, root, abort, met, now);
 }
 
-// One warp per dirty component: roll its members back to T*, then redo them
-// in global event-time order (Alg. 2) while claiming cells for the component.
+// Component q of the current round: roll its members back to T*, then redo
+// them in global event-time order (Alg. 2) while claiming cells for the
+// component (one warp).
+template <int C>
+__device__ void repair_component(const Dev &s, int q, int round) {
+    const int lane = threadIdx.x & 31;
+    const int root = s.comp_root[q];
+    const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
+    const int32_t *mem = s.comp_mem + off;
+    double Ts = INFINITY;
+    for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
+    rollback_members(s, mem, m, Ts);
+    if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
+    if (m <= 32)
+        repair_small<C>(s, mem, m, root, Ts, round);
+    else
+        repair_large<C>(s, mem, m, root, Ts, round);
+}
+
 template <int C>
 __global__ void k_repair(Dev s, int round) {
     const int lane = threadIdx.x & 31;
@@ -1159,26 +1193,12 @@ __global__ void k_repair(Dev s, int round) {
         if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
         q = __shfl_sync(FULL, q, 0);
         if (q >= s.ctl[CTL_NCOMP]) return;
-        const int root = s.comp_root[q];
-        const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
-        const int32_t *mem = s.comp_mem + off;
-        double Ts = INFINITY;
-        for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
-        rollback_members(s, mem, m, Ts);
-        if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
-        if (m <= 32)
-            repair_small<C>(s, mem, m, root, Ts, round);
-        else
-            repair_large<C>(s, mem, m, root, Ts, round);
+        repair_component<C>(s, q, round);
     }
 }
 
 // Leg end: totals, and the lifting log (chain by chain).
-__global__ void k_leg_end(Dev s, int32_t leg) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.k) return;
+__device__ void leg_end_chain(const Dev &s, int c, int32_t leg) {
     const int32_t nl = s.nlift[c];
     atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
     if (s.log_on && nl > 0) {
@@ -1204,6 +1224,11 @@ __global__ void k_leg_end(Dev s, int32_t leg) {
     }
 }
 
+__global__ void k_leg_end(Dev s, int32_t leg) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s.k) leg_end_chain(s, c, leg);
+}
+
 template <int C>
 __global__ void k_export(Dev s, double *x, double *y, double *t) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1221,13 +1246,261 @@ __global__ void k_export_active(Dev s, int32_t *active) {
     active[c] = (int32_t)s.cid[s.aloc[c]];
 }
 
+// ------------------------------------------- persistent multi-leg kernel
+//
+// One cooperative launch runs up to max_legs legs of every live replica
+// (independent systems, each with its own Dev). The phases of a leg are
+// separated by grid barriers; a replica leaves once it has made its budget of
+// liftings. Every barrier wait is bounded by the device clock: past the limit
+// the kernel records ECMC_ETIMEOUT and returns instead of waiting on.
+
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 60ull * 1000 * 1000 * 1000;
+
+struct RepCtl {
+    int64_t budget;         // liftings for this run (0: none)
+    int64_t lifts;          // liftings made in this run
+    int64_t legs;           // legs completed in this run
+    int64_t conflict_legs;
+    int64_t repaired;
+    int64_t horizon;
+    int64_t order_err;
+    int64_t leg_index0;     // leg index of this run's first leg (lifting log)
+    int64_t p1_lifts;       // liftings made by the parallel pass (redone ones included)
+    int64_t repair_lifts;   // liftings of legs that needed a repair
+    uint8_t *flags;         // per-leg conflict flags (device) or null
+    int32_t flags_cap;
+    int32_t live;           // takes part in this run
+    int32_t done;           // budget reached or error
+    int32_t err;            // LC_ERR_* seen
+};
+
+enum { G_WORK = 0, G_ANY, G_ERR, G_REMAIN0, G_REMAIN1, G_N };
+enum { PH_BEGIN = 0, PH_PASS1, PH_REPAIR, PH_END, PH_N };
+
+struct Batch {
+    Dev *reps;                    // [R]
+    RepCtl *ctl;                  // [R]
+    int32_t *chain_base;          // [R+1] prefix of k over replicas
+    int32_t *comp_base;           // [R+1] prefix of this round's component counts
+    unsigned int *bar;            // [2] grid barrier: arrivals, generation
+    int32_t *g;                   // [G_N]
+    unsigned long long *phase_ns; // [PH_N] device time per phase (block 0 clock)
+    int32_t R;
+    int32_t max_legs;
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(const Batch &b, int *sflag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = b.bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(b.bar, 1u) == gridDim.x - 1) {
+            atomicExch(b.bar, 0u);
+            __threadfence();
+            atomicAdd(b.bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            while (*gen == g0) {
+                if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
+                    ok = 0;
+                    atomicExch(b.g + G_ERR, ECMC_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *sflag = ok && *(volatile int32_t *)(b.g + G_ERR) == 0;
+    }
+    __syncthreads();
+    return *sflag != 0;
+}
+
+// replica of flattened item w, with base[r] <= w < base[r+1]
+__device__ __forceinline__ int find_rep(const int32_t *base, int R, int w) {
+    int lo = 0, hi = R;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= w)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool rep_on(const Batch &b, int r) {
+    return b.ctl[r].live && !b.ctl[r].done;
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_run(Batch b) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    __shared__ int sflag;
+    const int lane = threadIdx.x & 31;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const int gw = gt >> 5, nwarps = nthreads >> 5;
+    const int R = b.R;
+    const int total_chains = b.chain_base[R];
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = timer ? gtimer() : 0ull;
+    auto mark = [&](int ph) {
+        if (timer) {
+            const unsigned long long t = gtimer();
+            b.phase_ns[ph] += t - t_prev;
+            t_prev = t;
+        }
+    };
+    for (int leg = 0; leg < b.max_legs; ++leg) {
+        // leg start: chain table, local times, claims, per-leg counters
+        for (int w = gt; w < total_chains; w += nthreads) {
+            const int r = find_rep(b.chain_base, R, w);
+            if (rep_on(b, r)) leg_begin_chain(b.reps[r], w - b.chain_base[r]);
+        }
+        for (int r = 0; r < R; ++r) {
+            if (!rep_on(b, r)) continue;
+            const Dev &s = b.reps[r];
+            const int64_t ncell = (int64_t)s.nc * s.nc;
+            for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
+            if (gt < LC_N) s.lc[gt] = 0ull;
+        }
+        if (!grid_barrier(b, &sflag)) return;
+        mark(PH_BEGIN);
+        if (gt == 0) b.g[G_REMAIN0 + ((leg + 1) & 1)] = 0;
+        // parallel pass: one warp per chain
+        for (int w = gw; w < total_chains; w += nwarps) {
+            const int r = find_rep(b.chain_base, R, w);
+            if (rep_on(b, r)) pass1_chain<C>(b.reps[r], w - b.chain_base[r]);
+        }
+        if (!grid_barrier(b, &sflag)) return;
+        mark(PH_PASS1);
+        // repair rounds
+        for (int round = 1;; ++round) {
+            for (int r = blockIdx.x; r < R; r += gridDim.x) {
+                const Dev &s = b.reps[r];
+                bool need = false;
+                if (rep_on(b, r))
+                    need = round == 1 ? s.lc[LC_BLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
+                if (need && round <= 255) {
+                    uf_block(s, round == 1, warp_tot, tot);
+                } else if (threadIdx.x == 0) {
+                    s.ctl[CTL_NCOMP] = 0;
+                    s.ctl[CTL_NABORT] = 0;
+                    if (need) b.ctl[r].err = 1;  // too many rounds
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(b, &sflag)) return;
+            if (blockIdx.x == 0) {
+                // prefix of component counts over replicas
+                const int chunk = (R + blockDim.x - 1) / blockDim.x;
+                const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
+                int sum = 0;
+                for (int r = lo; r < hi; ++r) sum += b.reps[r].ctl[CTL_NCOMP];
+                int off = block_exscan(sum, warp_tot, tot);
+                for (int r = lo; r < hi; ++r) {
+                    b.comp_base[r] = off;
+                    off += b.reps[r].ctl[CTL_NCOMP];
+                }
+                if (threadIdx.x == 0) {
+                    b.comp_base[R] = tot[0];
+                    b.g[G_WORK] = 0;
+                    b.g[G_ANY] = tot[0];
+                }
+            }
+            if (!grid_barrier(b, &sflag)) return;
+            const int ncomp = b.g[G_ANY];
+            if (ncomp == 0) break;
+            for (;;) {
+                int q = 0;
+                if (lane == 0) q = atomicAdd(b.g + G_WORK, 1);
+                q = __shfl_sync(FULL, q, 0);
+                if (q >= ncomp) break;
+                const int r = find_rep(b.comp_base, R, q);
+                repair_component<C>(b.reps[r], q - b.comp_base[r], round);
+            }
+            if (!grid_barrier(b, &sflag)) return;
+        }
+        mark(PH_REPAIR);
+        // leg end: liftings and the log, then per-replica totals and budgets
+        for (int w = gt; w < total_chains; w += nthreads) {
+            const int r = find_rep(b.chain_base, R, w);
+            if (rep_on(b, r))
+                leg_end_chain(b.reps[r], w - b.chain_base[r],
+                              (int32_t)(b.ctl[r].leg_index0 + b.ctl[r].legs));
+        }
+        if (!grid_barrier(b, &sflag)) return;
+        for (int r = gt; r < R; r += nthreads) {
+            RepCtl &c = b.ctl[r];
+            if (!(c.live && !c.done)) continue;
+            const Dev &s = b.reps[r];
+            const unsigned long long *lc = s.lc;
+            const int flag = lc[LC_BLOCKED] != 0ull;
+            if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
+            c.lifts += (int64_t)lc[LC_LIFTS];
+            c.p1_lifts += (int64_t)lc[LC_P1LIFTS];
+            if (flag) c.repair_lifts += (int64_t)lc[LC_LIFTS];
+            c.legs += 1;
+            c.conflict_legs += flag;
+            c.repaired += (int64_t)lc[LC_REPAIRED];
+            c.horizon += (int64_t)lc[LC_HORIZON];
+            c.order_err += (int64_t)lc[LC_ORDER];
+            if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) c.err = 1;
+            if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
+            if (!c.done) atomicAdd(b.g + G_REMAIN0 + (leg & 1), 1);
+        }
+        if (!grid_barrier(b, &sflag)) return;
+        mark(PH_END);
+        if (b.g[G_REMAIN0 + (leg & 1)] == 0) break;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
 
+// Launch scratch of the persistent kernel (reps, barrier, counters).
+struct Runner {
+    int cap = 0;
+    Dev *d_reps = nullptr;
+    RepCtl *d_ctl = nullptr;
+    int32_t *d_chain_base = nullptr, *d_comp_base = nullptr;
+    unsigned int *d_bar = nullptr;
+    int32_t *d_g = nullptr;
+    unsigned long long *d_phase = nullptr;
+    int grid4 = 0, grid8 = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static void runner_free(Runner &rn) {
+    cudaFree(rn.d_reps);
+    cudaFree(rn.d_ctl);
+    cudaFree(rn.d_chain_base);
+    cudaFree(rn.d_comp_base);
+    cudaFree(rn.d_bar);
+    cudaFree(rn.d_g);
+    cudaFree(rn.d_phase);
+    if (rn.ev0) cudaEventDestroy(rn.ev0);
+    if (rn.ev1) cudaEventDestroy(rn.ev1);
+    rn = Runner();
+}
+
 struct ecmc_ctx {
     ecmc_params p;
     Dev s;
+    Runner run;
+    uint8_t *d_flags = nullptr;
+    int32_t flags_cap = 0;
     int C = 4;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -1489,67 +1762,169 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     return ECMC_OK;
 }
 
-template <int C>
-static int run_leg(ecmc_ctx *ctx, int32_t leg, uint8_t *flag, int64_t *lifts) {
-    Dev &s = ctx->s;
-    cudaStream_t st = ctx->stream;
-    cudaEvent_t *E = ctx->kev;
-    const unsigned kb = (unsigned)((s.k + 127) / 128);
-    CU(cudaEventRecord(E[0], st));
-    CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
-    k_leg_begin<<<kb, 128, 0, st>>>(s);
-    CU(cudaMemsetAsync(s.claim, 0, (size_t)s.nc * s.nc * sizeof(uint32_t), st));
-    const int wpb = 4;
-    CU(cudaEventRecord(E[1], st));
-    k_pass1<C><<<(unsigned)((s.k + wpb - 1) / wpb), 32 * wpb, 0, st>>>(s);
-    CU(cudaEventRecord(E[2], st));
-    CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    float ms_a = 0.f, ms_b = 0.f;
-    CU(cudaEventElapsedTime(&ms_a, E[0], E[1]));
-    CU(cudaEventElapsedTime(&ms_b, E[1], E[2]));
-    ctx->prof.other_ms += ms_a;
-    ctx->prof.other_launches += 1;
-    ctx->prof.pass1_ms += ms_b;
-    ctx->prof.pass1_launches += 1;
-    ctx->prof.pass1_liftings += (int64_t)ctx->h_lc[LC_P1LIFTS];
-    if (ctx->h_lc[LC_ERR_CAP] || ctx->h_lc[LC_ERR_REC])
-        return fail(ctx, ECMC_ECAPACITY, "cell slots or per-chain undo records overflowed");
-    const bool conflict = ctx->h_lc[LC_BLOCKED] != 0;
-    ctx->horizon += (int64_t)ctx->h_lc[LC_HORIZON];
-    CU(cudaEventRecord(E[3], st));
-    CU(cudaEventRecord(E[4], st));
-    if (conflict) {
-        // repair rounds: components -> rollback to T* and redo; merge on contact
-        for (int round = 1;; ++round) {
-            if (round > 255) return fail(ctx, ECMC_ECAPACITY, "too many repair rounds");
-            k_uf<<<1, 1024, 0, st>>>(s, round == 1);
-            k_repair<C><<<(unsigned)(ctx->n_sm * 4), 128, 0, st>>>(s, round);
-            CU(cudaGetLastError());
-            CU(cudaMemcpyAsync(ctx->h_ctl, s.ctl, CTL_N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            CU(cudaStreamSynchronize(st));
-            ctx->prof.repair_launches += 1;
-            if (ctx->h_ctl[CTL_NABORT] == 0) break;
+static int runner_reserve(Runner &rn, int R, std::string &err) {
+    if (rn.cap >= R && rn.d_reps) return 0;
+    runner_free(rn);
+    const int cap = std::max(R, 1);
+    if (cudaMalloc(&rn.d_reps, cap * sizeof(Dev)) != cudaSuccess ||
+        cudaMalloc(&rn.d_ctl, cap * sizeof(RepCtl)) != cudaSuccess ||
+        cudaMalloc(&rn.d_chain_base, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&rn.d_comp_base, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&rn.d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&rn.d_g, G_N * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&rn.d_phase, PH_N * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaEventCreate(&rn.ev0) != cudaSuccess || cudaEventCreate(&rn.ev1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        runner_free(rn);
+        err = "runner allocation failed";
+        return ECMC_ENOMEM;
+    }
+    int dev = 0, n_sm = 1, b4 = 0, b8 = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, 256, 0) != cudaSuccess ||
+        !coop || b4 < 1 || b8 < 1) {
+        (void)cudaGetLastError();
+        runner_free(rn);
+        err = "cooperative launch unavailable";
+        return ECMC_ECUDA;
+    }
+    rn.grid4 = n_sm * b4;
+    rn.grid8 = n_sm * b8;
+    rn.cap = cap;
+    return 0;
+}
+
+// Runs up to max_legs legs of every context in one persistent launch on
+// `st`; per-context totals are folded into each context's host counters.
+static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R, int32_t max_legs,
+                      const uint64_t *budgets, int64_t *lifts_out, int32_t *legs_out,
+                      std::string &err, double *ms_out) {
+    if (R < 1 || max_legs < 0) {
+        err = "bad batch size or leg count";
+        return ECMC_EINVAL;
+    }
+    const int C = ctxs[0]->C;
+    for (int r = 0; r < R; ++r) {
+        if (!ctxs[r] || ctxs[r]->C != C) {
+            err = "all contexts of a batch need the same cell slots (cell size)";
+            return ECMC_EINVAL;
         }
+        for (int q = 0; q < r; ++q)
+            if (ctxs[q] == ctxs[r]) {
+                err = "a context appears twice in a batch";
+                return ECMC_EINVAL;
+            }
     }
-    CU(cudaEventRecord(E[5], st));
-    k_leg_end<<<kb, 128, 0, st>>>(s, leg);
-    CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    float ms_d = 0.f;
-    CU(cudaEventElapsedTime(&ms_d, E[4], E[5]));
-    if (conflict) {
-        ctx->prof.repair_ms += ms_d;
-        ctx->prof.repair_liftings += (int64_t)ctx->h_lc[LC_LIFTS];
-        ctx->repaired += (int64_t)ctx->h_lc[LC_REPAIRED];
+    int rc = runner_reserve(rn, R, err);
+    if (rc) return rc;
+    if (max_legs == 0) return 0;
+    std::vector<Dev> reps(R);
+    std::vector<RepCtl> ctl(R);
+    std::vector<int32_t> base(R + 1, 0);
+    for (int r = 0; r < R; ++r) {
+        ecmc_ctx *c = ctxs[r];
+        if (c->stream != st && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            err = "context stream";
+            return ECMC_ECUDA;
+        }
+        if (c->flags_cap < max_legs) {
+            cudaFree(c->d_flags);
+            c->d_flags = nullptr;
+            c->flags_cap = 0;
+            if (cudaMalloc(&c->d_flags, (size_t)max_legs) != cudaSuccess) {
+                (void)cudaGetLastError();
+                err = "flags allocation";
+                return ECMC_ENOMEM;
+            }
+            c->flags_cap = max_legs;
+        }
+        reps[r] = c->s;
+        memset(&ctl[r], 0, sizeof(RepCtl));
+        ctl[r].budget = budgets ? (int64_t)budgets[r] : 0;
+        ctl[r].leg_index0 = c->legs_total;
+        ctl[r].flags = c->d_flags;
+        ctl[r].flags_cap = c->flags_cap;
+        ctl[r].live = 1;
+        base[r + 1] = base[r] + c->s.k;
     }
-    if (ctx->h_lc[LC_ERR_CAP] || ctx->h_lc[LC_ERR_REC])
-        return fail(ctx, ECMC_ECAPACITY, "cell slots or per-chain undo records overflowed");
-    ctx->order_err += (int64_t)ctx->h_lc[LC_ORDER];
-    *flag = conflict ? 1 : 0;
-    *lifts = (int64_t)ctx->h_lc[LC_LIFTS];
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !rc) {
+            (void)cudaGetLastError();
+            err = std::string(what) + ": " + cudaGetErrorString(e);
+            rc = ECMC_ECUDA;
+        }
+    };
+    cu(cudaMemcpyAsync(rn.d_reps, reps.data(), R * sizeof(Dev), cudaMemcpyHostToDevice, st), "reps");
+    cu(cudaMemcpyAsync(rn.d_ctl, ctl.data(), R * sizeof(RepCtl), cudaMemcpyHostToDevice, st), "ctl");
+    cu(cudaMemcpyAsync(rn.d_chain_base, base.data(), (R + 1) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, st), "base");
+    cu(cudaMemsetAsync(rn.d_bar, 0, 2 * sizeof(unsigned int), st), "bar");
+    cu(cudaMemsetAsync(rn.d_g, 0, G_N * sizeof(int32_t), st), "g");
+    cu(cudaMemsetAsync(rn.d_phase, 0, PH_N * sizeof(unsigned long long), st), "phase");
+    if (rc) return rc;
+    Batch b;
+    b.reps = rn.d_reps;
+    b.ctl = rn.d_ctl;
+    b.chain_base = rn.d_chain_base;
+    b.comp_base = rn.d_comp_base;
+    b.bar = rn.d_bar;
+    b.g = rn.d_g;
+    b.phase_ns = rn.d_phase;
+    b.R = R;
+    b.max_legs = max_legs;
+    void *args[] = {&b};
+    cu(cudaEventRecord(rn.ev0, st), "event");
+    if (C == 4)
+        cu(cudaLaunchCooperativeKernel((void *)k_run<4>, rn.grid4, 256, args, 0, st), "launch");
+    else
+        cu(cudaLaunchCooperativeKernel((void *)k_run<8>, rn.grid8, 256, args, 0, st), "launch");
+    cu(cudaEventRecord(rn.ev1, st), "event");
+    int32_t g[G_N];
+    unsigned long long ph[PH_N];
+    cu(cudaMemcpyAsync(ctl.data(), rn.d_ctl, R * sizeof(RepCtl), cudaMemcpyDeviceToHost, st), "ctl");
+    cu(cudaMemcpyAsync(g, rn.d_g, sizeof g, cudaMemcpyDeviceToHost, st), "g");
+    cu(cudaMemcpyAsync(ph, rn.d_phase, sizeof ph, cudaMemcpyDeviceToHost, st), "phase");
+    cu(cudaStreamSynchronize(st), "run");
+    if (rc) return rc;
+    float ms = 0.f;
+    cu(cudaEventElapsedTime(&ms, rn.ev0, rn.ev1), "elapsed");
+    if (ms_out) *ms_out = ms;
+    bool cap_err = false;
+    for (int r = 0; r < R; ++r) {
+        ecmc_ctx *c = ctxs[r];
+        const RepCtl &q = ctl[r];
+        c->legs_total += q.legs;
+        c->lifts_total += q.lifts;
+        c->conflict_legs += q.conflict_legs;
+        c->repaired += q.repaired;
+        c->horizon += q.horizon;
+        c->order_err += q.order_err;
+        c->prof.pass1_launches += q.legs;
+        c->prof.other_launches += q.legs;
+        c->prof.repair_launches += q.conflict_legs;
+        c->prof.pass1_liftings += q.p1_lifts;
+        c->prof.repair_liftings += q.repair_lifts;
+        if (R == 1) {
+            c->prof.pass1_ms += ph[PH_PASS1] * 1e-6;
+            c->prof.repair_ms += ph[PH_REPAIR] * 1e-6;
+            c->prof.other_ms += (ph[PH_BEGIN] + ph[PH_END]) * 1e-6;
+            c->device_ms += ms;
+        }
+        if (lifts_out) lifts_out[r] = q.lifts;
+        if (legs_out) legs_out[r] = (int32_t)q.legs;
+        if (q.err) cap_err = true;
+    }
+    if (g[G_ERR] == ECMC_ETIMEOUT) {
+        err = "a grid barrier wait passed its time limit";
+        return ECMC_ETIMEOUT;
+    }
+    if (cap_err) {
+        err = "cell slots, undo records or repair rounds overflowed";
+        return ECMC_ECAPACITY;
+    }
     return 0;
 }
 
@@ -1558,32 +1933,58 @@ extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t ev
     if (!ctx) return ECMC_EINVAL;
     if (n_legs < 0) return fail(ctx, ECMC_EINVAL, "n_legs < 0");
     if (legs_done) *legs_done = 0;
-    CU(cudaEventRecord(ctx->ev0, ctx->stream));
-    uint64_t done_lifts = 0;
+    if (n_legs == 0) return ECMC_OK;
+    ecmc_ctx *one[1] = {ctx};
     int32_t legs = 0;
-    int rc = 0;
-    for (int32_t l = 0; l < n_legs; ++l) {
-        uint8_t flag = 0;
-        int64_t lifts = 0;
-        const int32_t leg_index = (int32_t)ctx->legs_total;
-        rc = ctx->C == 4 ? run_leg<4>(ctx, leg_index, &flag, &lifts)
-                         : run_leg<8>(ctx, leg_index, &flag, &lifts);
-        if (rc) break;
-        ctx->legs_total++;
-        ctx->lifts_total += lifts;
-        ctx->conflict_legs += flag;
-        if (leg_flags_out) leg_flags_out[l] = flag;
-        done_lifts += (uint64_t)lifts;
-        legs = l + 1;
-        if (event_budget && done_lifts >= event_budget) break;
-    }
-    CU(cudaEventRecord(ctx->ev1, ctx->stream));
-    CU(cudaEventSynchronize(ctx->ev1));
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-    ctx->device_ms += ms;
+    std::string err;
+    const int rc = runner_run(ctx->run, ctx->stream, one, 1, n_legs, &event_budget, nullptr, &legs,
+                              err, nullptr);
     if (legs_done) *legs_done = legs;
+    if (leg_flags_out && legs > 0) {
+        CU(cudaMemcpyAsync(leg_flags_out, ctx->d_flags, (size_t)legs, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    if (rc) return fail(ctx, rc, err);
+    return ECMC_OK;
+}
+
+struct ecmc_batch {
+    Runner run;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    double device_ms = 0.0;
+};
+
+extern "C" int ecmc_batch_create(void *stream, ecmc_batch **out) {
+    if (!out) return ECMC_EINVAL;
+    ecmc_batch *b = new (std::nothrow) ecmc_batch();
+    if (!b) return ECMC_ENOMEM;
+    b->stream = (cudaStream_t)stream;
+    *out = b;
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_batch_run(ecmc_batch *b, ecmc_ctx *const *ctxs, int32_t n_ctx,
+                              int32_t max_legs, const uint64_t *budgets, int64_t *liftings_out,
+                              int32_t *legs_out, double *device_ms_out) {
+    if (!b || !ctxs || n_ctx < 1) return ECMC_EINVAL;
+    double ms = 0.0;
+    const int rc = runner_run(b->run, b->stream, ctxs, n_ctx, max_legs, budgets, liftings_out,
+                              legs_out, b->err, &ms);
+    b->device_ms += ms;
+    if (device_ms_out) *device_ms_out = ms;
     return rc;
+}
+
+extern "C" const char *ecmc_batch_last_error(const ecmc_batch *b) {
+    return b ? b->err.c_str() : "";
+}
+
+extern "C" void ecmc_batch_destroy(ecmc_batch *b) {
+    if (!b) return;
+    runner_free(b->run);
+    delete b;
 }
 
 extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *active) {
@@ -1670,6 +2071,8 @@ extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64
 
 extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
     if (!ctx) return;
+    runner_free(ctx->run);
+    cudaFree(ctx->d_flags);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_lc) cudaFreeHost(ctx->h_lc);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);

@@ -25,7 +25,8 @@ ECMC_INPUT_DEVICE = 0x2
 
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
-           "ecmc_leg_noalloc")
+           "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
+           "ecmc_batch_destroy", "ecmc_leg_noalloc")
 
 
 class ecmc_params(C.Structure):
@@ -87,6 +88,15 @@ def load(path: str | None = None):
     lib.ecmc_destroy.restype = None
     lib.ecmc_last_error.argtypes = [vp]
     lib.ecmc_last_error.restype = C.c_char_p
+    lib.ecmc_batch_create.argtypes = [vp, C.POINTER(vp)]
+    lib.ecmc_batch_create.restype = C.c_int
+    lib.ecmc_batch_run.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp,
+                                   C.POINTER(C.c_double)]
+    lib.ecmc_batch_run.restype = C.c_int
+    lib.ecmc_batch_last_error.argtypes = [vp]
+    lib.ecmc_batch_last_error.restype = C.c_char_p
+    lib.ecmc_batch_destroy.argtypes = [vp]
+    lib.ecmc_batch_destroy.restype = None
     lib.ecmc_leg_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int32,
                                      C.c_int32, vp, vp, vp, vp, vp, C.POINTER(C.c_uint8),
                                      C.POINTER(C.c_int64)]
@@ -179,6 +189,40 @@ def ecmc_destroy(ctx):
 
 def ecmc_last_error(ctx=None) -> str:
     return (load().ecmc_last_error(ctx) or b"").decode()
+
+
+def ecmc_batch_create(stream=None):
+    out = C.c_void_p()
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = load().ecmc_batch_create(st, C.byref(out))
+    if rc != ECMC_OK:
+        raise EcmcError(rc, "ecmc_batch_create failed")
+    return out
+
+
+def ecmc_batch_run(batch, ctxs, max_legs, budgets=None):
+    """One persistent launch over the contexts; returns (liftings, legs, ms)."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    bud = None
+    if budgets is not None:
+        bud = np.ascontiguousarray(budgets, dtype=np.uint64)
+    lifts = np.zeros(n, dtype=np.int64)
+    legs = np.zeros(n, dtype=np.int32)
+    ms = C.c_double()
+    rc = load().ecmc_batch_run(batch, C.cast(arr, C.c_void_p), n, int(max_legs),
+                               _ptr(bud) if bud is not None else None, _ptr(lifts), _ptr(legs),
+                               C.byref(ms))
+    if rc != ECMC_OK:
+        msg = (load().ecmc_batch_last_error(batch) or b"").decode()
+        raise EcmcError(rc, msg)
+    return lifts, legs, ms.value
+
+
+def ecmc_batch_destroy(batch):
+    load().ecmc_batch_destroy(batch)
 
 
 class System:
