@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--k", type=int, default=1024, help="chains")
     p.add_argument("--legs", type=int, default=10, help="legs per step")
+    p.add_argument("--windows", type=int, default=1, help="claim windows per leg")
     p.add_argument("--m", type=int, default=1024, help="lattice side (N = m*m)")
     p.add_argument("--eta", type=float, default=0.72)
     p.add_argument("--ell", type=float, default=1.0)
@@ -56,6 +57,7 @@ def workload(a):
     return {"workload": f"lattice {a.m}x{a.m} (N={a.m * a.m}) eta={a.eta} jitter=0.01, "
                         f"k={a.k} chains, ell={a.ell}, v=+x, {a.legs} legs/step",
             "n": a.m * a.m, "eta": a.eta, "k": a.k, "ell": a.ell, "legs_per_step": a.legs,
+            "claim_windows_per_leg": a.windows,
             "seed": a.seed, "l2": "flushed between steps (512 MB write)"}
 
 
@@ -211,7 +213,8 @@ def run_ours(a):
             dist.barrier()
             torch.cuda.synchronize()
 
-    sysm = ecmc.System(start.x, start.y, start.active, start.box, a.ell, stream=stream)
+    sysm = ecmc.System(start.x, start.y, start.active, start.box, a.ell, stream=stream,
+                       windows=a.windows)
     for _ in range(a.warmup):
         sysm.run(a.legs)
     st0, pr0 = sysm.stats(), sysm.profile()

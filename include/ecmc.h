@@ -56,6 +56,11 @@ typedef struct {
     uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE */
     int32_t undo_cap;       /* per-chain event records per leg; 0 = 1024 */
     int64_t log_cap;        /* liftings kept with ECMC_LOG_LIFTINGS; 0 = 1<<22 */
+    int32_t windows;        /* claim windows per leg, 1..4096; 0 = 1. A leg is run as W
+                               windows of global time [w ell/W, (w+1) ell/W): chains pause
+                               (without moving) at a window's end. Results do not depend
+                               on W; the conflict flags and the speed do. */
+    int32_t reserved;       /* must be 0 */
 } ecmc_params;
 
 typedef struct {
@@ -92,14 +97,19 @@ int ecmc_create(const ecmc_params *p, const double *x, const double *y,
                 const int32_t *active, void *stream, ecmc_ctx **out);
 
 /*
+ * Conflicts. Within a claim window every chain claims, with atomicCAS, each
+ * cell it scans; two chains that want one cell "meet". A leg's flag is 1 iff
+ * in some window the cells that two chains would scan, each run alone from the
+ * window's start, overlap; those chains are then rolled back and redone in
+ * global time order, so results are always those of Alg. 2.
+ *
  * ecmc_run_to_breakpoint -- runs n_legs legs of length ell (Alg. 2 semantics:
  * each leg ends at the breakpoint h' with all chains stalled, Remark on
  * stalled spheres), each chain restarting from its stalled disk.
  *   event_budget  0 = run all n_legs; otherwise stop at the first breakpoint
  *                 at which the liftings of this call reach the budget.
- *   leg_flags_out host, n_legs bytes or NULL: 1 for a leg in which two chains
- *                 scanned a common cell (the leg was then redone in global
- *                 time order), else 0; entries past *legs_done are untouched.
+ *   leg_flags_out host, n_legs bytes or NULL: the leg's conflict flag (see
+ *                 above); entries past *legs_done are untouched.
  *   legs_done     host or NULL: number of legs completed.
  * All legs run in one persistent cooperative launch; returns when they are
  * done (the stream is synchronised).

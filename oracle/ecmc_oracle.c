@@ -16,11 +16,15 @@
  *                   v = (1, 0). Events are taken in order of their global time
  *                   T (ties: lower chain index first). Output: C_{h'}, A_{h'},
  *                   the local times and the set of liftings (Eq. 1).
- *                   It also returns the leg's conflict flag: every chain is run
- *                   alone from the leg start (Alg. 4 with a single chain, the
- *                   other chains' start disks counted as static) while the
- *                   cells it scans are recorded; the flag is 1 iff one cell is
- *                   scanned by two chains.
+ *                   It also returns the leg's conflict flag. The leg is cut
+ *                   into W windows of global time, [w ell/W, (w+1) ell/W);
+ *                   at the start of each window every unfinished chain is run
+ *                   alone from the current state (Alg. 4 with a single chain,
+ *                   the other chains' disks counted as static) through its
+ *                   events before the window's end, while the cells it scans
+ *                   are recorded; the flag is 1 iff in some window one cell
+ *                   is scanned by two chains. The windows only decide the
+ *                   flag: the events executed are those of Alg. 2 whatever W.
  *   orc_alg4_leg -- Alg. 4 (single-threaded ECMC with local times): chains
  *                   run one after another on the shared state, the horizon
  *                   condition (Eq. 2, in the strict form of statement 5 of
@@ -75,8 +79,10 @@ typedef struct {
 typedef struct {
     int64_t n;
     double L, d, ell;
-    int32_t nc;     /* cells per side (scan and claims) */
-    int32_t search; /* 0: all pairs (definition), 1: cell scan */
+    int32_t nc;      /* cells per side (scan and claims) */
+    int32_t search;  /* 0: all pairs (definition), 1: cell scan */
+    int32_t windows; /* claim windows per leg (>= 1), see orc_leg */
+    int32_t pad;
 } orc_params;
 
 /* ------------------------------------------------------------------ geometry */
@@ -108,6 +114,12 @@ static double wrap_add(double x, double dx, double L) {
     double r = x + dx;
     if (r >= L) r -= L;
     return r;
+}
+
+/* End of claim window w of W in a leg of length ell (the last one is open). */
+static double window_end(const orc_params *p, int w) {
+    if (w + 1 >= p->windows) return INFINITY;
+    return ((double)(w + 1) * p->ell) / (double)p->windows;
 }
 
 /* ---------------------------------------------------------------- cell lists */
@@ -307,32 +319,46 @@ static void claim_record(int cell, void *vctx) {
 }
 
 /*
- * Runs chain c alone from the current state (its start disk i0, D = ell, no
- * tags: every other disk counts as static), records the cells it scans, then
- * restores x and the cell lists. Returns the number of lifts it made.
+ * Runs one chain alone from the current state -- its disk i0 at local time
+ * t[i0], remaining length D; every other disk counts as static -- through its
+ * events before t_end, recording the cells it scans (the last scan, whose
+ * event lies at or after t_end, included); then restores x, t and the cells.
  */
 static int64_t isolated_chain(const orc_params *p, cells_t *g, double *x,
-                              const double *y, double *t, int i0, claim_ctx_t *cc,
-                              int32_t *undo_i, double *undo_x, int64_t undo_cap,
+                              const double *y, double *t, int i0, double D0,
+                              double t_end, claim_ctx_t *cc, int32_t *undo_i,
+                              double *undo_x, double *undo_t, int64_t undo_cap,
                               int *overflow) {
     int i = i0;
-    double D = p->ell;
+    double D = D0;
     int64_t nu = 0, lifts = 0;
     for (;;) {
         step_t s = step_cells(p, g, x, y, t, NULL, i, D, claim_record, cc);
-        if (nu >= undo_cap) {
+        if (!(t[i] + s.tau < t_end)) break;
+        if (nu + 2 > undo_cap) {
             *overflow = 1;
             break;
         }
         undo_i[nu] = i;
         undo_x[nu] = x[i];
+        undo_t[nu] = t[i];
         ++nu;
+        if (s.lift) {
+            undo_i[nu] = s.j;
+            undo_x[nu] = x[s.j];
+            undo_t[nu] = t[s.j];
+            ++nu;
+        }
+        double tn = t[i] + s.tau;
         double xn = wrap_add(x[i], s.tau, p->L);
         cell_move(g, i, x[i], xn, y[i]);
         x[i] = xn;
-        if (!s.lift) break;
-        t[s.j] = t[i] + s.tau;
-        t[i] = t[i] + s.tau;
+        if (!s.lift) {
+            t[i] = tn;
+            break;
+        }
+        t[s.j] = tn;
+        t[i] = tn;
         D = D - s.tau;
         i = s.j;
         ++lifts;
@@ -341,7 +367,7 @@ static int64_t isolated_chain(const orc_params *p, cells_t *g, double *x,
         int j = undo_i[u];
         cell_move(g, j, x[j], undo_x[u], y[j]);
         x[j] = undo_x[u];
-        t[j] = 0.0;
+        t[j] = undo_t[u];
     }
     return lifts;
 }
@@ -394,33 +420,17 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
     int64_t undo_cap = 1 << 20;
     int32_t *undo_i = (int32_t *)malloc((size_t)undo_cap * sizeof(int32_t));
     double *undo_x = (double *)malloc((size_t)undo_cap * sizeof(double));
+    double *undo_t = (double *)malloc((size_t)undo_cap * sizeof(double));
     int rc = 0;
-    if (!tag || !D || !run || !ev || !owner || !undo_i || !undo_x) {
+    if (!tag || !D || !run || !ev || !owner || !undo_i || !undo_x || !undo_t) {
         rc = -1;
         goto done;
     }
 
-    /* conflict flag: isolated runs from the leg start */
-    {
-        for (int64_t q = 0; q < (int64_t)nc * nc; ++q) owner[q] = -1;
-        claim_ctx_t cc;
-        cc.owner = owner;
-        cc.conflict = 0;
-        int overflow = 0;
-        for (int64_t j = 0; j < n; ++j) t[j] = 0.0;
-        for (int c = 0; c < k; ++c) {
-            cc.c = c;
-            isolated_chain(p, &g, x, y, t, active[c], &cc, undo_i, undo_x, undo_cap,
-                           &overflow);
-        }
-        if (overflow) {
-            rc = -2;
-            goto done;
-        }
-        if (flag) *flag = (uint8_t)cc.conflict;
+    if (p->windows < 1) {
+        rc = -3;
+        goto done;
     }
-
-    /* Alg. 2 */
     for (int64_t j = 0; j < n; ++j) t[j] = 0.0;
     for (int c = 0; c < k; ++c) {
         tag[active[c]] = TAG_ACTIVE;
@@ -432,75 +442,100 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
         compute_event(p, &g, x, y, t, tag, active[c], D[c], &ev[c]);
     int64_t nl = 0;
     double now = 0.0;
-    for (;;) {
-        int cb = -1;
-        for (int c = 0; c < k; ++c) {
-            if (!run[c]) continue;
-            if (cb < 0 || ev[c].T < ev[cb].T) cb = c;
-        }
-        if (cb < 0) break;
-        /* events come in global-time order: nothing recomputed lies in the past */
-        if (ev[cb].T < now) {
-            rc = -6;
-            goto done;
-        }
-        now = ev[cb].T;
-        int i = active[cb];
-        step_t s = ev[cb].s;
-        double x_old = x[i];
-        int changed[3];
-        int nchanged = 0;
-        changed[nchanged++] = cell_of(x_old, y[i], &g);
-        if (s.lift) {
-            int j = s.j;
-            double tnew = t[i] + s.tau;
-            t[j] = tnew;                          /* statement 14 */
-            t[i] = tnew;                          /* statement 15 */
-            double xn = wrap_add(x[i], s.tau, p->L); /* statement 16 */
-            cell_move(&g, i, x[i], xn, y[i]);
-            x[i] = xn;
-            tag[i] = TAG_STATIC;                  /* statement 17 */
-            D[cb] = D[cb] - s.tau;                /* statement 18 */
-            tag[j] = TAG_ACTIVE;
-            active[cb] = j;                       /* statement 19 */
-            changed[nchanged++] = cell_of(xn, y[i], &g);
-            changed[nchanged++] = cell_of(x[j], y[j], &g);
-            if (log) {
-                if (*log_n >= log_cap) {
-                    rc = -2;
-                    goto done;
-                }
-                orc_lift *e = &log[(*log_n)++];
-                e->leg = leg;
-                e->c = cb;
-                e->i = i;
-                e->j = j;
-                e->t = tnew;
-                e->tau = s.tau;
-                e->xi = xn;
-                e->xj = x[j];
+    int any_conflict = 0;
+    for (int w = 0; w < p->windows; ++w) {
+        const double t_end = window_end(p, w);
+        /* conflict flag of the window: isolated runs from the current state */
+        {
+            for (int64_t q = 0; q < (int64_t)nc * nc; ++q) owner[q] = -1;
+            claim_ctx_t cc;
+            cc.owner = owner;
+            cc.conflict = 0;
+            int overflow = 0;
+            for (int c = 0; c < k; ++c) {
+                if (!run[c]) continue;
+                cc.c = c;
+                isolated_chain(p, &g, x, y, t, active[c], D[c], t_end, &cc, undo_i, undo_x,
+                               undo_t, undo_cap, &overflow);
             }
-            ++nl;
-            if (lifts_per_chain) lifts_per_chain[cb] += 1;
-        } else {
-            t[i] = t[i] + D[cb];                  /* statement 21 */
-            double xn = wrap_add(x[i], D[cb], p->L); /* statement 22 */
-            cell_move(&g, i, x[i], xn, y[i]);
-            x[i] = xn;
-            D[cb] = 0.0;                          /* statement 23 */
-            tag[i] = TAG_STALLED;                 /* statement 24 */
-            run[cb] = 0;
-            changed[nchanged++] = cell_of(xn, y[i], &g);
+            if (overflow) {
+                rc = -2;
+                goto done;
+            }
+            any_conflict |= cc.conflict;
         }
-        /* recompute the events that the change can affect */
-        for (int c = 0; c < k; ++c) {
-            if (!run[c]) continue;
-            int redo = (c == cb) || p->search == 0;
-            for (int q = 0; q < nchanged && !redo; ++q)
-                if (in_footprint(&ev[c].s, changed[q], nc)) redo = 1;
-            if (redo) compute_event(p, &g, x, y, t, tag, active[c], D[c], &ev[c]);
+        /* Alg. 2: the events of the window in global-time order */
+        for (;;) {
+            int cb = -1;
+            for (int c = 0; c < k; ++c) {
+                if (!run[c]) continue;
+                if (cb < 0 || ev[c].T < ev[cb].T) cb = c;
+            }
+            if (cb < 0 || !(ev[cb].T < t_end)) break;
+            /* events come in global-time order: nothing recomputed lies in the past */
+            if (ev[cb].T < now) {
+                rc = -6;
+                goto done;
+            }
+            now = ev[cb].T;
+            int i = active[cb];
+            step_t s = ev[cb].s;
+            double x_old = x[i];
+            int changed[3];
+            int nchanged = 0;
+            changed[nchanged++] = cell_of(x_old, y[i], &g);
+            if (s.lift) {
+                int j = s.j;
+                double tnew = t[i] + s.tau;
+                t[j] = tnew;                             /* statement 14 */
+                t[i] = tnew;                             /* statement 15 */
+                double xn = wrap_add(x[i], s.tau, p->L); /* statement 16 */
+                cell_move(&g, i, x[i], xn, y[i]);
+                x[i] = xn;
+                tag[i] = TAG_STATIC;                     /* statement 17 */
+                D[cb] = D[cb] - s.tau;                   /* statement 18 */
+                tag[j] = TAG_ACTIVE;
+                active[cb] = j;                          /* statement 19 */
+                changed[nchanged++] = cell_of(xn, y[i], &g);
+                changed[nchanged++] = cell_of(x[j], y[j], &g);
+                if (log) {
+                    if (*log_n >= log_cap) {
+                        rc = -2;
+                        goto done;
+                    }
+                    orc_lift *e = &log[(*log_n)++];
+                    e->leg = leg;
+                    e->c = cb;
+                    e->i = i;
+                    e->j = j;
+                    e->t = tnew;
+                    e->tau = s.tau;
+                    e->xi = xn;
+                    e->xj = x[j];
+                }
+                ++nl;
+                if (lifts_per_chain) lifts_per_chain[cb] += 1;
+            } else {
+                t[i] = t[i] + D[cb];                     /* statement 21 */
+                double xn = wrap_add(x[i], D[cb], p->L); /* statement 22 */
+                cell_move(&g, i, x[i], xn, y[i]);
+                x[i] = xn;
+                D[cb] = 0.0;                             /* statement 23 */
+                tag[i] = TAG_STALLED;                    /* statement 24 */
+                run[cb] = 0;
+                changed[nchanged++] = cell_of(xn, y[i], &g);
+            }
+            /* recompute the events that the change can affect */
+            for (int c = 0; c < k; ++c) {
+                if (!run[c]) continue;
+                int redo = (c == cb) || p->search == 0;
+                for (int q = 0; q < nchanged && !redo; ++q)
+                    if (in_footprint(&ev[c].s, changed[q], nc)) redo = 1;
+                if (redo) compute_event(p, &g, x, y, t, tag, active[c], D[c], &ev[c]);
+            }
         }
     }
+    if (flag) *flag = (uint8_t)any_conflict;
     if (lifts) *lifts = nl;
 done:
     cells_free(&g);
@@ -511,6 +546,7 @@ done:
     free(owner);
     free(undo_i);
     free(undo_x);
+    free(undo_t);
     return rc;
 }
 

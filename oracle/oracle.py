@@ -48,7 +48,8 @@ LIFT_DTYPE = np.dtype([("leg", np.int32), ("c", np.int32), ("i", np.int32), ("j"
 
 class Params(C.Structure):
     _fields_ = [("n", C.c_int64), ("L", C.c_double), ("d", C.c_double), ("ell", C.c_double),
-                ("nc", C.c_int32), ("search", C.c_int32)]
+                ("nc", C.c_int32), ("search", C.c_int32), ("windows", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 _lib = None
@@ -112,7 +113,7 @@ class OracleError(RuntimeError):
 
 
 def run_leg(x, y, active, L, ell, *, d=1.0, nc=None, search=1, leg=0, log=True,
-            log_cap=None) -> LegResult:
+            log_cap=None, windows=1) -> LegResult:
     """One leg of Alg. 2 (global time) with the conflict flag. Inputs are not modified."""
     x = np.array(x, dtype=np.float64, copy=True)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -120,7 +121,7 @@ def run_leg(x, y, active, L, ell, *, d=1.0, nc=None, search=1, leg=0, log=True,
     n, k = x.shape[0], act.shape[0]
     if nc is None:
         nc = default_cells(L, d)
-    p = Params(n, L, d, ell, nc, search)
+    p = Params(n, L, d, ell, nc, search, windows, 0)
     t = np.zeros(n, dtype=np.float64)
     if log_cap is None:
         log_cap = max(1024, int(64 * k * (ell + 1.0) / 0.01) if log else 0)
@@ -156,7 +157,7 @@ def run_alg4_leg(x, y, active, L, ell, *, d=1.0, leg=0):
     y = np.ascontiguousarray(y, dtype=np.float64)
     act = np.array(active, dtype=np.int32, copy=True)
     n, k = x.shape[0], act.shape[0]
-    p = Params(n, L, d, ell, 3, 0)
+    p = Params(n, L, d, ell, 3, 0, 1, 0)
     t = np.zeros(n, dtype=np.float64)
     cap = 1_000_000
     logbuf = np.zeros(cap, dtype=LIFT_DTYPE)
@@ -172,7 +173,7 @@ def step(x, y, i, D, L, *, d=1.0, nc=None, search=0, tag=None, t=None):
     y = np.ascontiguousarray(y, dtype=np.float64)
     if nc is None:
         nc = default_cells(L, d)
-    p = Params(x.shape[0], L, d, 0.0, nc, search)
+    p = Params(x.shape[0], L, d, 0.0, nc, search, 1, 0)
     lift, j, m = C.c_int32(), C.c_int32(), C.c_int32()
     tau = C.c_double()
     tg = None
@@ -193,7 +194,7 @@ def claim_set(x, y, i0, L, ell, *, d=1.0, nc=None) -> np.ndarray:
     y = np.ascontiguousarray(y, dtype=np.float64)
     if nc is None:
         nc = default_cells(L, d)
-    p = Params(x.shape[0], L, d, ell, nc, 1)
+    p = Params(x.shape[0], L, d, ell, nc, 1, 1, 0)
     cap = nc * nc
     cells = np.zeros(cap, dtype=np.int32)
     n_out = C.c_int64()

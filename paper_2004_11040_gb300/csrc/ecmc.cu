@@ -54,7 +54,7 @@ constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
 
 // per-leg counters (reset at every leg start)
 enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
-       LC_P1LIFTS, LC_REPAIRED, LC_N };
+       LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_N };
 enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
 // cumulative counters
 enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,
@@ -75,7 +75,7 @@ struct Rec {
 
 struct Dev {
     int64_t n;
-    int nc, k, cap;
+    int nc, k, cap, windows;
     double L, d, d2, ell, a, inv_a, eps;
     // cells: slot q of cell c at index c*C + q; a disk's x, y, local time and
     // owner word live in its slot and move with it
@@ -108,6 +108,7 @@ struct Dev {
     ecmc_lift_t *log;
     int64_t log_cap;
     int log_on;
+    double *dbg;  // [16] first failed internal check (diagnostics)
 };
 
 // ------------------------------------------------------------ FP64 geometry
@@ -120,6 +121,20 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 // v < 0 for a value that is not -0.0 (subtractions of finite doubles never give -0.0)
 __device__ __forceinline__ bool dneg(double v) {
     return __double_as_longlong(v) < 0 && dbits(v) != 0x8000000000000000ull;
+}
+
+// Records the first failed internal check: kind, then up to 6 values.
+__device__ void diag(const Dev &s, int kind, double a, double b, double c, double d, double e,
+                     double f) {
+    if (!s.dbg) return;
+    if (atomicCAS((unsigned long long *)s.dbg, 0ull, (unsigned long long)__double_as_longlong((double)kind)) != 0ull)
+        return;
+    s.dbg[1] = a;
+    s.dbg[2] = b;
+    s.dbg[3] = c;
+    s.dbg[4] = d;
+    s.dbg[5] = e;
+    s.dbg[6] = f;
 }
 
 __device__ __forceinline__ int cell_coord(double v, const Dev &s) {
@@ -202,13 +217,19 @@ struct StepOut {
 // Every scanned cell is claimed for the leg (conflict if another owner holds
 // it). A column whose threshold is <= eps is scanned whatever the candidates,
 // so its cells are claimed together with their load.
-// PASS1: the owner is the chain; only its own disk is excluded; Eq. 2 is
-//   checked as an assertion (it cannot fail while the cells are held).
+// In both modes the active and stalled disks of all chains are excluded
+// (Alg. 2), and a static disk with t_i + tau < t_j became static after the
+// chain's disk had passed it (lazy per-chain frame): it is one lap away.
+// Reading the owner word in pass 1 as well keeps every pass-1 event of a
+// claim window at or after the window start: a lift onto another chain's
+// active disk could otherwise land before it (zero flight time from contact).
+// PASS1: the owner is the chain. A disk with t_i + tau < t_j whose t_j lies in
+//   the current window (start tw) would be a horizon violation (Eq. 2); it
+//   cannot occur while the cells are held and is counted as an assertion.
 // COMP: the owner is the conflict component `root` (any member's claim is its
-//   own); active and stalled disks are excluded (Alg. 2), and a static disk
-//   with t_i + tau < t_j is one lap away (lazy per-chain frame).
+//   own).
 template <int C, int MODE>
-__device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
+__device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, double tw) {
     constexpr int LPC = (3 * C <= 16) ? 16 : 32;  // lanes per column
     constexpr int CPP = 32 / LPC;                 // columns per pass
     const int lane = threadIdx.x & 31;
@@ -252,7 +273,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
             holder = old == 0u ? mine : old;
             claimed_early = true;
         } else if (colok && sl == 0) {
-            holder = s.claim[cell];
+            // through L2: claims are reset between windows by other SMs, so an
+            // L1 line from an earlier window could still show this chain's claim
+            holder = __ldcg(s.claim + cell);
         }
         const uint32_t id = colok ? s.cid[loc] : EMPTY;
         double xj = 0.0, yj = 0.0, tj = 0.0;
@@ -262,13 +285,16 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
             xj = s.cx[loc];
             yj = s.cy[loc];
             tj = s.ct[loc];
-            if (MODE == MODE_COMP) own = s.cown[loc];
+            own = s.cown[loc];
         }
         double tau = INFINITY;
+        bool behind = false;
         if (cand && own == OWN_STATIC) {
             tau = time_of_flight(r.xi, r.yi, xj, yj, s);
-            if (MODE == MODE_COMP && tau != INFINITY && dbits(__dadd_rn(r.ti, tau)) < dbits(tj))
+            if (tau != INFINITY && dbits(__dadd_rn(r.ti, tau)) < dbits(tj)) {
+                behind = true;
                 tau = __dadd_rn(tau, s.L);
+            }
         }
         const unsigned long long tb = dbits(tau);
         // column minima (lanes of one column form an aligned group of LPC)
@@ -324,17 +350,15 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r) {
             if (MODE == MODE_PASS1)
                 foreign = holder != mine;
             else
-                foreign = s.comp_of[holder - 1u] != root;
+                foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
             if (foreign) {
                 conflict = true;
                 partner = holder - 1u;
             }
         }
-        // Eq. 2 (statement 5) on every scanned candidate: cannot fail while the
-        // cells are held by a lone chain; counted as an assertion.
-        if (MODE == MODE_PASS1 && scanned && tau != INFINITY &&
-            dbits(__dadd_rn(r.ti, tau)) < dbits(tj))
-            hz = true;
+        // Eq. 2 (statement 5) on every scanned candidate touched in this window:
+        // cannot fail while the cells are held by a lone chain; an assertion.
+        if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
     }
 
     StepOut o;
@@ -567,58 +591,79 @@ __global__ void k_leg_begin(Dev s) {
     if (c < s.k) leg_begin_chain(s, c);
 }
 
-// Pass 1: one warp runs chain c until it stalls or meets a conflict.
+// Pass 1 of a claim window [tw, tend): one warp runs chain c from its current
+// state through its events before tend, until it stalls, pauses at tend or
+// meets a conflict.
 template <int C>
-__device__ void pass1_chain(const Dev &s, int c) {
+__device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
+    if (s.status[c] != ST_RUNNING) return;
     const int lane = threadIdx.x & 31;
     ChainReg r;
     r.iloc = s.aloc[c];
-    r.i = s.cid[r.iloc];
+    r.i = s.ci[c];
+    if (lane == 0 && (s.cid[r.iloc] != r.i || s.cown[r.iloc] != (OWN_ACTIVE | (uint32_t)c)))
+        diag(s, 6, tw, c, r.i, s.cid[r.iloc], s.cown[r.iloc], s.tc[c]);
     r.xi = s.cx[r.iloc];
     r.yi = s.cy[r.iloc];
-    r.ti = 0.0;
-    r.D = s.ell;
+    r.ti = s.tc[c];
+    r.D = s.D[c];
     int st = ST_RUNNING;
-    uint32_t seq = 0;
+    uint32_t seq = (uint32_t)s.nrec[c];
     uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
     int32_t cas_rec = -1;           // record of that lift, while unchecked
+    bool blocked = false;
+    const int32_t lifts0 = s.nlift[c];
     while (st == ST_RUNNING) {
-        const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r);
+        const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r, tw);
         if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
             const uint32_t old = __shfl_sync(FULL, cas_old, 0);
             if (old != OWN_STATIC) {
-                // the target was another chain's start disk: its cell is held by
-                // this chain, so that chain meets a conflict as well
+                // the owner word was read as static in a cell this chain holds,
+                // so no other chain can have taken it: kept as a check that
+                // blocks the chain (and names the owner) should it ever fail
                 if (lane == 0) {
                     s.rec[(size_t)c * s.cap + cas_rec].flags |= REC_NO_OWNER;
                     s.partner[c] = (int32_t)(old & OWN_CHAIN);
                     atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
                 }
-                st = ST_BLOCKED;
+                blocked = true;
                 break;
             }
             cas_rec = -1;
         }
         if (o.conflict) {
             if (lane == 0) s.partner[c] = (int32_t)o.partner;
-            st = ST_BLOCKED;
+            blocked = true;
             break;
         }
+        if (!(dbits(__dadd_rn(r.ti, o.tau)) < dbits(tend))) break;  // pauses at the window end
+        if (dbits(__dadd_rn(r.ti, o.tau)) < dbits(tw) && lane == 0) {
+            // a window's events start at its start time (repairs roll back to it)
+            atomicAdd(s.lc + LC_ORDER, 1ull);
+            diag(s, 9, tw, c, r.i, o.j, r.ti, o.tau);
+        }
+        if (lane == 0 && s.cid[r.iloc] != r.i) diag(s, 7, tw, c, r.i, s.cid[r.iloc], r.iloc, r.ti);
+        if (lane == 0 && o.lift && s.cid[o.jloc] != o.j)
+            diag(s, 8, tw, c, o.j, s.cid[o.jloc], o.jloc, r.ti);
         uint32_t nl;
         st = commit_step<C>(s, c, r, o, true, seq, &nl, &cas_old);
         if (st == ST_RUNNING) cas_rec = (int32_t)seq;
         ++seq;
     }
+    if (blocked) st = ST_BLOCKED;
     if (lane == 0) {
-        // events before the blocking time are exact (Remark 6)
-        s.vt[c] = st == ST_BLOCKED ? r.ti : INFINITY;
+        // events before the blocking time, and all before the window, are exact
+        s.vt[c] = blocked ? fmax(r.ti, tw) : INFINITY;
         s.status[c] = st;
         s.aloc[c] = r.iloc;
         s.ci[c] = r.i;
         s.tc[c] = r.ti;
         s.D[c] = r.D;
-        if (st == ST_BLOCKED) atomicAdd(s.lc + LC_BLOCKED, 1ull);
-        atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)s.nlift[c]);
+        if (blocked) {
+            atomicAdd(s.lc + LC_BLOCKED, 1ull);
+            atomicAdd(s.lc + LC_WBLOCKED, 1ull);
+        }
+        atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)(s.nlift[c] - lifts0));
     }
     __syncwarp();
 }
@@ -627,7 +672,7 @@ template <int C>
 __global__ void k_pass1(Dev s) {
     const int warps = blockDim.x >> 5;
     const int c = blockIdx.x * warps + (threadIdx.x >> 5);
-    if (c < s.k) pass1_chain<C>(s, c);
+    if (c < s.k) pass1_chain<C>(s, c, 0.0, INFINITY);
 }
 
 // Exact inverse of commit_step for one record of chain c (lane 0 only).
@@ -893,7 +938,7 @@ __device__ void finish_component(const Dev &s, const int32_t *mem, int m, int ro
 // event live in the registers of lane e.
 template <int C>
 __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, double Ts,
-                             int round) {
+                             int round, double tend) {
     const int lane = threadIdx.x & 31;
     const bool has = lane < m;
     const int my_c = has ? mem[lane] : 0x7FFFFFFF;
@@ -904,6 +949,11 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         resume_state(s, my_c, my_loc, my_id, my_t, my_D, my_st);
         my_x = s.cx[my_loc];
         my_y = s.cy[my_loc];
+        if (s.cid[my_loc] != my_id) {
+            const int32_t nr = s.nrec[my_c];
+            diag(s, 1, round, my_c, my_loc, my_id, s.cid[my_loc],
+                 nr > 0 ? (double)s.rec[(size_t)my_c * s.cap + nr - 1].seq : -1.0);
+        }
     }
     // pending event
     unsigned long long ev_T = INF_BITS;
@@ -927,7 +977,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         r.ti = __shfl_sync(FULL, my_t, q);
         r.D = __shfl_sync(FULL, my_D, q);
         const int cq = __shfl_sync(FULL, my_c, q);
-        const StepOut o = scan_step<C, MODE_COMP>(s, cq, root, r);
+        const StepOut o = scan_step<C, MODE_COMP>(s, cq, root, r, 0.0);
         if (o.conflict) {
             abort = true;
             met = (int)o.partner;
@@ -963,8 +1013,12 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
             }
         }
         if (bc == 0x7FFFFFFF) break;
+        if (!(bT < dbits(tend))) break;  // the rest lies in a later window
         const double Tn = __longlong_as_double((long long)bT);
-        if (dbits(Tn) < dbits(now) && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
+        if (dbits(Tn) < dbits(now) && lane == 0) {
+            atomicAdd(s.lc + LC_ORDER, 1ull);
+            diag(s, 2, round, bc, Tn, now, Ts, m);
+        }
         now = Tn;
         ChainReg r;
         r.i = __shfl_sync(FULL, my_id, bq);
@@ -983,6 +1037,9 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         o.tj = __shfl_sync(FULL, ev.tj, bq);
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
+        if (o.lift && (s.cid[o.jloc] != o.j || s.cown[o.jloc] != OWN_STATIC) && lane == 0)
+            diag(s, 4, round, bc, o.j, s.cid[o.jloc], s.cown[o.jloc], Tn);
+        if (s.cid[r.iloc] != r.i && lane == 0) diag(s, 5, round, bc, r.i, s.cid[r.iloc], r.iloc, Tn);
         uint32_t nl = 0, dummy = 0;
         const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
                                       &dummy);
@@ -1032,7 +1089,7 @@ __device__ StepOut compute_event_global(const Dev &s, int c, int root) {
     r.yi = s.cy[r.iloc];
     r.ti = s.tc[c];
     r.D = s.D[c];
-    const StepOut o = scan_step<C, MODE_COMP>(s, c, root, r);
+    const StepOut o = scan_step<C, MODE_COMP>(s, c, root, r, 0.0);
     if (lane == 0) {
         s.ev_T[c] = __dadd_rn(r.ti, o.tau);
         s.ev_tau[c] = o.tau;
@@ -1053,7 +1110,7 @@ __device__ StepOut compute_event_global(const Dev &s, int c, int root) {
 // Redo of a component with more than 32 members: state in global memory.
 template <int C>
 __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, double Ts,
-                             int round) {
+                             int round, double tend) {
     const int lane = threadIdx.x & 31;
     for (int e = lane; e < m; e += 32) {
         const int c = mem[e];
@@ -1061,6 +1118,11 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         double t, D;
         int st;
         resume_state(s, c, loc, id, t, D, st);
+        if (s.cid[loc] != id) {
+            const int32_t nr = s.nrec[c];
+            diag(s, 11, round, c, loc, id, s.cid[loc],
+                 nr > 0 ? (double)s.rec[(size_t)c * s.cap + nr - 1].seq : -1.0);
+        }
         s.aloc[c] = loc;
         s.ci[c] = id;
         s.tc[c] = t;
@@ -1103,6 +1165,7 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
             }
         }
         if (bc == 0x7FFFFFFF) break;
+        if (!(bT < tend)) break;  // the rest lies in a later window
         if (bT < now && lane == 0) atomicAdd(s.lc + LC_ORDER, 1ull);
         now = bT;
         ChainReg r;
@@ -1122,6 +1185,9 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         o.tj = s.ev_tj[bc];
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
+        if (o.lift && (s.cid[o.jloc] != o.j || s.cown[o.jloc] != OWN_STATIC) && lane == 0)
+            diag(s, 14, round, bc, o.j, s.cid[o.jloc], s.cown[o.jloc], bT);
+        if (s.cid[r.iloc] != r.i && lane == 0) diag(s, 15, round, bc, r.i, s.cid[r.iloc], r.iloc, bT);
         uint32_t nl = 0, dummy = 0;
         const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
                                       &dummy);
@@ -1168,7 +1234,7 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
 // them in global event-time order (Alg. 2) while claiming cells for the
 // component (one warp).
 template <int C>
-__device__ void repair_component(const Dev &s, int q, int round) {
+__device__ void repair_component(const Dev &s, int q, int round, double tend) {
     const int lane = threadIdx.x & 31;
     const int root = s.comp_root[q];
     const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
@@ -1180,9 +1246,9 @@ __device__ void repair_component(const Dev &s, int q, int round) {
     rollback_members(s, mem, m, Ts);
     if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
     if (m <= 32)
-        repair_small<C>(s, mem, m, root, Ts, round);
+        repair_small<C>(s, mem, m, root, Ts, round, tend);
     else
-        repair_large<C>(s, mem, m, root, Ts, round);
+        repair_large<C>(s, mem, m, root, Ts, round, tend);
 }
 
 template <int C>
@@ -1193,7 +1259,7 @@ __global__ void k_repair(Dev s, int round) {
         if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
         q = __shfl_sync(FULL, q, 0);
         if (q >= s.ctl[CTL_NCOMP]) return;
-        repair_component<C>(s, q, round);
+        repair_component<C>(s, q, round, INFINITY);
     }
 }
 
@@ -1272,6 +1338,10 @@ struct RepCtl {
     int32_t live;           // takes part in this run
     int32_t done;           // budget reached or error
     int32_t err;            // LC_ERR_* seen
+    int32_t incons;         // chain-table checks that failed (must stay 0)
+    int32_t bad_where;      // first failure: leg * 65536 + window * 16 + phase
+    int32_t bad_chain;
+    int32_t pad2;
 };
 
 enum { G_WORK = 0, G_ANY, G_ERR, G_REMAIN0, G_REMAIN1, G_N };
@@ -1287,7 +1357,17 @@ struct Batch {
     unsigned long long *phase_ns; // [PH_N] device time per phase (block 0 clock)
     int32_t R;
     int32_t max_legs;
+    int32_t windows;  // claim windows per leg (all replicas of a launch)
 };
+
+__device__ __forceinline__ double window_start(const Dev &s, int w) {
+    return w == 0 ? 0.0 : __ddiv_rn(__dmul_rn((double)w, s.ell), (double)s.windows);
+}
+
+__device__ __forceinline__ double window_end(const Dev &s, int w) {
+    return w + 1 >= s.windows ? INFINITY
+                              : __ddiv_rn(__dmul_rn((double)(w + 1), s.ell), (double)s.windows);
+}
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -1321,6 +1401,8 @@ __device__ bool grid_barrier(const Batch &b, int *sflag) {
         *sflag = ok && *(volatile int32_t *)(b.g + G_ERR) == 0;
     }
     __syncthreads();
+    // every thread orders its later loads after the barrier (acquire)
+    __threadfence();
     return *sflag != 0;
 }
 
@@ -1339,6 +1421,23 @@ __device__ __forceinline__ int find_rep(const int32_t *base, int R, int w) {
 
 __device__ __forceinline__ bool rep_on(const Batch &b, int r) {
     return b.ctl[r].live && !b.ctl[r].done;
+}
+
+// Invariant: a running or stalled chain's table slot holds its active disk.
+__device__ void check_chains(const Batch &b, int gt, int nthreads, int total_chains, int where) {
+    for (int w = gt; w < total_chains; w += nthreads) {
+        const int r = find_rep(b.chain_base, b.R, w);
+        if (!rep_on(b, r)) continue;
+        const Dev &s = b.reps[r];
+        const int c = w - b.chain_base[r];
+        if (s.status[c] == ST_BLOCKED) continue;
+        if (s.cid[s.aloc[c]] != s.ci[c]) {
+            if (atomicAdd(&b.ctl[r].incons, 1) == 0) {
+                b.ctl[r].bad_where = where;
+                b.ctl[r].bad_chain = c;
+            }
+        }
+    }
 }
 
 template <int C>
@@ -1377,61 +1476,82 @@ __global__ void __launch_bounds__(256) k_run(Batch b) {
         if (!grid_barrier(b, &sflag)) return;
         mark(PH_BEGIN);
         if (gt == 0) b.g[G_REMAIN0 + ((leg + 1) & 1)] = 0;
-        // parallel pass: one warp per chain
-        for (int w = gw; w < total_chains; w += nwarps) {
-            const int r = find_rep(b.chain_base, R, w);
-            if (rep_on(b, r)) pass1_chain<C>(b.reps[r], w - b.chain_base[r]);
-        }
-        if (!grid_barrier(b, &sflag)) return;
-        mark(PH_PASS1);
-        // repair rounds
-        for (int round = 1;; ++round) {
-            for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        for (int w = 0; w < b.windows; ++w) {
+            if (w > 0) {
+                // new claim window: claims and the window's blocked count
+                for (int r = 0; r < R; ++r) {
+                    if (!rep_on(b, r)) continue;
+                    const Dev &s = b.reps[r];
+                    const int64_t ncell = (int64_t)s.nc * s.nc;
+                    for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
+                    if (gt == 0) s.lc[LC_WBLOCKED] = 0ull;
+                }
+                if (!grid_barrier(b, &sflag)) return;
+            }
+            // parallel pass: one warp per chain, chains spread over the blocks
+            const int lw = threadIdx.x >> 5;
+            for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
+                const int r = find_rep(b.chain_base, R, w2);
+                if (!rep_on(b, r)) continue;
                 const Dev &s = b.reps[r];
-                bool need = false;
-                if (rep_on(b, r))
-                    need = round == 1 ? s.lc[LC_BLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
-                if (need && round <= 255) {
-                    uf_block(s, round == 1, warp_tot, tot);
-                } else if (threadIdx.x == 0) {
-                    s.ctl[CTL_NCOMP] = 0;
-                    s.ctl[CTL_NABORT] = 0;
-                    if (need) b.ctl[r].err = 1;  // too many rounds
-                }
-                __syncthreads();
+                const double tw = window_start(s, w), te = window_end(s, w);
+                pass1_chain<C>(s, w2 - b.chain_base[r], tw, te);
             }
             if (!grid_barrier(b, &sflag)) return;
-            if (blockIdx.x == 0) {
-                // prefix of component counts over replicas
-                const int chunk = (R + blockDim.x - 1) / blockDim.x;
-                const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
-                int sum = 0;
-                for (int r = lo; r < hi; ++r) sum += b.reps[r].ctl[CTL_NCOMP];
-                int off = block_exscan(sum, warp_tot, tot);
-                for (int r = lo; r < hi; ++r) {
-                    b.comp_base[r] = off;
-                    off += b.reps[r].ctl[CTL_NCOMP];
+            mark(PH_PASS1);
+            check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 1);
+            // repair rounds
+            for (int round = 1;; ++round) {
+                for (int r = blockIdx.x; r < R; r += gridDim.x) {
+                    const Dev &s = b.reps[r];
+                    bool need = false;
+                    if (rep_on(b, r))
+                        need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
+                    if (need && round == 1 && threadIdx.x == 0) s.lc[LC_CWINDOWS] += 1ull;
+                    if (need && round <= 255) {
+                        uf_block(s, round == 1, warp_tot, tot);
+                    } else if (threadIdx.x == 0) {
+                        s.ctl[CTL_NCOMP] = 0;
+                        s.ctl[CTL_NABORT] = 0;
+                        if (need) b.ctl[r].err = 1;  // too many rounds
+                    }
+                    __syncthreads();
                 }
-                if (threadIdx.x == 0) {
-                    b.comp_base[R] = tot[0];
-                    b.g[G_WORK] = 0;
-                    b.g[G_ANY] = tot[0];
+                if (!grid_barrier(b, &sflag)) return;
+                if (blockIdx.x == 0) {
+                    // prefix of component counts over replicas
+                    const int chunk = (R + blockDim.x - 1) / blockDim.x;
+                    const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
+                    int sum = 0;
+                    for (int r = lo; r < hi; ++r) sum += b.reps[r].ctl[CTL_NCOMP];
+                    int off = block_exscan(sum, warp_tot, tot);
+                    for (int r = lo; r < hi; ++r) {
+                        b.comp_base[r] = off;
+                        off += b.reps[r].ctl[CTL_NCOMP];
+                    }
+                    if (threadIdx.x == 0) {
+                        b.comp_base[R] = tot[0];
+                        b.g[G_WORK] = 0;
+                        b.g[G_ANY] = tot[0];
+                    }
                 }
+                if (!grid_barrier(b, &sflag)) return;
+                const int ncomp = b.g[G_ANY];
+                if (ncomp == 0) break;
+                for (;;) {
+                    int q = 0;
+                    if (lane == 0) q = atomicAdd(b.g + G_WORK, 1);
+                    q = __shfl_sync(FULL, q, 0);
+                    if (q >= ncomp) break;
+                    const int r = find_rep(b.comp_base, R, q);
+                    const Dev &s = b.reps[r];
+                    repair_component<C>(s, q - b.comp_base[r], round, window_end(s, w));
+                }
+                if (!grid_barrier(b, &sflag)) return;
+                check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 2 + round);
             }
-            if (!grid_barrier(b, &sflag)) return;
-            const int ncomp = b.g[G_ANY];
-            if (ncomp == 0) break;
-            for (;;) {
-                int q = 0;
-                if (lane == 0) q = atomicAdd(b.g + G_WORK, 1);
-                q = __shfl_sync(FULL, q, 0);
-                if (q >= ncomp) break;
-                const int r = find_rep(b.comp_base, R, q);
-                repair_component<C>(b.reps[r], q - b.comp_base[r], round);
-            }
-            if (!grid_barrier(b, &sflag)) return;
+            mark(PH_REPAIR);
         }
-        mark(PH_REPAIR);
         // leg end: liftings and the log, then per-replica totals and budgets
         for (int w = gt; w < total_chains; w += nthreads) {
             const int r = find_rep(b.chain_base, R, w);
@@ -1517,6 +1637,7 @@ struct ecmc_ctx {
     int64_t repaired = 0;
     int64_t horizon = 0;
     int64_t order_err = 0;
+    int64_t inconsistent = 0;
     double device_ms = 0.0;
     bool log_overflow = false;
 };
@@ -1588,6 +1709,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     *out = nullptr;
     if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF) return fail(nullptr, ECMC_EINVAL, "n out of range");
     if (p->n_chains < 1 || p->n_chains > p->n) return fail(nullptr, ECMC_EINVAL, "n_chains out of range");
+    if (p->windows < 0 || p->windows > 4096) return fail(nullptr, ECMC_EINVAL, "windows out of range");
     if (!(p->d > 0.0) || !(p->ell > 0.0) || !(p->box > 0.0) || !std::isfinite(p->box) ||
         !std::isfinite(p->ell))
         return fail(nullptr, ECMC_EINVAL, "d, ell and box must be positive and finite");
@@ -1608,6 +1730,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     s.nc = nc;
     s.k = p->n_chains;
     s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
+    s.windows = p->windows > 0 ? p->windows : 1;
     s.L = p->box;
     s.d = p->d;
     s.d2 = p->d * p->d;
@@ -1655,6 +1778,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.comp_root, k));
     chk(dalloc(ctx, &s.comp_mem, k));
     chk(dalloc(ctx, &s.ctl, CTL_N));
+    chk(dalloc(ctx, &s.dbg, 16));
     chk(dalloc(ctx, &s.ev_j, k));
     chk(dalloc(ctx, &s.ev_jloc, k));
     chk(dalloc(ctx, &s.ev_lift, k));
@@ -1733,6 +1857,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
+    CU(cudaMemsetAsync(s.dbg, 0, 16 * sizeof(double), st));
     if (C == 4)
         launch_build<4>(ctx, sx, sy);
     else
@@ -1807,9 +1932,10 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         return ECMC_EINVAL;
     }
     const int C = ctxs[0]->C;
+    const int W = ctxs[0]->s.windows;
     for (int r = 0; r < R; ++r) {
-        if (!ctxs[r] || ctxs[r]->C != C) {
-            err = "all contexts of a batch need the same cell slots (cell size)";
+        if (!ctxs[r] || ctxs[r]->C != C || ctxs[r]->s.windows != W) {
+            err = "all contexts of a batch need the same cell slots (cell size) and windows";
             return ECMC_EINVAL;
         }
         for (int q = 0; q < r; ++q)
@@ -1875,6 +2001,7 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     b.phase_ns = rn.d_phase;
     b.R = R;
     b.max_legs = max_legs;
+    b.windows = W;
     void *args[] = {&b};
     cu(cudaEventRecord(rn.ev0, st), "event");
     if (C == 4)
@@ -1892,7 +2019,8 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     float ms = 0.f;
     cu(cudaEventElapsedTime(&ms, rn.ev0, rn.ev1), "elapsed");
     if (ms_out) *ms_out = ms;
-    bool cap_err = false;
+    bool cap_err = false, incons_err = false;
+    std::string incons_msg;
     for (int r = 0; r < R; ++r) {
         ecmc_ctx *c = ctxs[r];
         const RepCtl &q = ctl[r];
@@ -1916,6 +2044,18 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         if (lifts_out) lifts_out[r] = q.lifts;
         if (legs_out) legs_out[r] = (int32_t)q.legs;
         if (q.err) cap_err = true;
+        if (q.incons) {
+            c->inconsistent += q.incons;
+            if (!incons_err) {
+                char buf[160];
+                snprintf(buf, sizeof buf,
+                         "chain table check failed %d times; first: leg %d window %d phase %d chain %d",
+                         q.incons, q.bad_where / 65536, (q.bad_where % 65536) / 16,
+                         q.bad_where % 16, q.bad_chain);
+                incons_msg = buf;
+            }
+            incons_err = true;
+        }
     }
     if (g[G_ERR] == ECMC_ETIMEOUT) {
         err = "a grid barrier wait passed its time limit";
@@ -1924,6 +2064,22 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     if (cap_err) {
         err = "cell slots, undo records or repair rounds overflowed";
         return ECMC_ECAPACITY;
+    }
+    for (int r = 0; r < R; ++r) {
+        double dg[7];
+        if (ctxs[r]->s.dbg &&
+            cudaMemcpy(dg, ctxs[r]->s.dbg, sizeof dg, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            dg[0] != 0.0) {
+            char buf[240];
+            snprintf(buf, sizeof buf, "internal check %g failed: %.17g %.17g %.17g %.17g %.17g %.17g",
+                     dg[0], dg[1], dg[2], dg[3], dg[4], dg[5], dg[6]);
+            err = buf;
+            return ECMC_ECUDA;
+        }
+    }
+    if (incons_err) {
+        err = incons_msg;
+        return ECMC_ECUDA;
     }
     return 0;
 }
@@ -2297,6 +2453,7 @@ extern "C" int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int
     s.nc = nc;
     s.k = n_chains;
     s.cap = NOALLOC_CAP;
+    s.windows = 1;
     s.L = box;
     s.d = d;
     s.d2 = d * d;

@@ -32,7 +32,8 @@ EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stat
 class ecmc_params(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double), ("d", C.c_double), ("ell", C.c_double),
                 ("n_chains", C.c_int32), ("cells_per_side", C.c_int32), ("flags", C.c_uint32),
-                ("undo_cap", C.c_int32), ("log_cap", C.c_int64)]
+                ("undo_cap", C.c_int32), ("log_cap", C.c_int64), ("windows", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ecmc_stats_t(C.Structure):
@@ -229,7 +230,7 @@ class System:
     """One ECMC system on the GPU: a thin owner of an ecmc_ctx handle."""
 
     def __init__(self, x, y, active, box, ell, *, d=1.0, cells_per_side=0, log=False,
-                 undo_cap=0, log_cap=0, stream=None, device_input=False):
+                 undo_cap=0, log_cap=0, stream=None, device_input=False, windows=1):
         x = x if device_input else np.ascontiguousarray(x, dtype=np.float64)
         y = y if device_input else np.ascontiguousarray(y, dtype=np.float64)
         active = active if device_input else np.ascontiguousarray(active, dtype=np.int32)
@@ -237,7 +238,8 @@ class System:
         self.k = int(active.shape[0])
         flags = (ECMC_LOG_LIFTINGS if log else 0) | (ECMC_INPUT_DEVICE if device_input else 0)
         self.params = ecmc_params(self.n, float(box), float(d), float(ell), self.k,
-                                  int(cells_per_side), flags, int(undo_cap), int(log_cap))
+                                  int(cells_per_side), flags, int(undo_cap), int(log_cap),
+                                  int(windows), 0)
         self.ctx = ecmc_create(self.params, x, y, active, stream)
 
     def run(self, n_legs, event_budget=0):

@@ -14,10 +14,10 @@ from paper_2004_11040_gb300 import ecmc, synth
 pytestmark = pytest.mark.gpu
 
 
-def run_gpu(start, ell, n_legs, nc=0, log=True, undo_cap=0):
+def run_gpu(start, ell, n_legs, nc=0, log=True, undo_cap=0, windows=1):
     sysm = ecmc.System(start.x, start.y, start.active, start.box, ell, d=start.d,
                        cells_per_side=nc, log=log, undo_cap=undo_cap,
-                       log_cap=max(1 << 16, 64 * start.k * n_legs * 64))
+                       log_cap=max(1 << 16, 64 * start.k * n_legs * 64), windows=windows)
     flags, done = sysm.run(n_legs)
     assert done == n_legs
     x, y, t, a = sysm.positions()
@@ -27,10 +27,10 @@ def run_gpu(start, ell, n_legs, nc=0, log=True, undo_cap=0):
     return flags, x, y, t, a, logs, st
 
 
-def run_oracle(start, ell, n_legs, nc=0):
+def run_oracle(start, ell, n_legs, nc=0, windows=1):
     ncell = nc or O.default_cells(start.box, start.d)
     last, legs = O.run_legs(start.x, start.y, start.active, start.box, ell, n_legs,
-                            d=start.d, nc=ncell)
+                            d=start.d, nc=ncell, windows=windows)
     flags = np.array([r.flag for r in legs], dtype=np.uint8)
     log = np.concatenate([r.log for r in legs]) if legs else np.zeros(0, O.LIFT_DTYPE)
     return flags, last, log
@@ -42,9 +42,9 @@ def chain_order(log):
     return log[idx]
 
 
-def assert_parity(start, ell, n_legs, nc=0):
-    gf, gx, gy, gt, ga, glog, st = run_gpu(start, ell, n_legs, nc)
-    of, last, olog = run_oracle(start, ell, n_legs, nc)
+def assert_parity(start, ell, n_legs, nc=0, windows=1):
+    gf, gx, gy, gt, ga, glog, st = run_gpu(start, ell, n_legs, nc, windows=windows)
+    of, last, olog = run_oracle(start, ell, n_legs, nc, windows=windows)
     assert np.array_equal(gy, start.y)
     assert np.array_equal(gf, of), (gf, of)
     assert np.array_equal(ga, last.active)
@@ -155,3 +155,30 @@ def test_dense_random_2d_components(seed):
     s = synth.rsa_start(400, 0.5, 40, seed=seed)
     flags, st = assert_parity(s, 1.5, 3)
     assert flags.all()
+
+
+@pytest.mark.parametrize("windows", [2, 5, 16])
+@pytest.mark.parametrize("seed", [0, 3])
+def test_claim_windows_config1(windows, seed):
+    """Claim windows: same liftings and positions as one window, flags equal to
+    the oracle's windowed flags."""
+    s = synth.lattice_start(16, 0.70, 4, seed=seed)
+    assert_parity(s, 0.5, 8, windows=windows)
+
+
+@pytest.mark.parametrize("windows", [4, 32])
+def test_claim_windows_dense_components(windows):
+    s = synth.lattice_start(32, 0.70, 200, seed=2)
+    assert_parity(s, 1.0, 3, windows=windows)
+
+
+def test_claim_windows_config2_and_random():
+    s = synth.lattice_start(128, 0.708, 128, seed=7)
+    assert_parity(s, 1.0, 2, windows=8)
+    r = synth.rsa_start(400, 0.5, 40, seed=21)
+    assert_parity(r, 1.5, 3, windows=6)
+
+
+def test_claim_windows_config3_one_leg():
+    s = synth.lattice_start(1024, 0.72, 4096, seed=3)
+    assert_parity(s, 1.0, 1, windows=16)

@@ -370,3 +370,19 @@ def test_literal_global_time_algorithm(seed):
     dx = np.abs(pos - g.x)
     assert np.minimum(dx, L - dx).max() < 1e-12
     assert act == g.active.tolist()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_claim_windows_only_change_the_flag(seed):
+    """Cutting a leg into claim windows is scheduling only: the liftings,
+    positions and local times of Alg. 2 are the same for every W."""
+    s = synth.lattice_start(24, 0.70, 12, seed=seed)
+    base = O.run_leg(s.x, s.y, s.active, s.box, 1.0, windows=1)
+    for w in (2, 3, 8, 32):
+        r = O.run_leg(s.x, s.y, s.active, s.box, 1.0, windows=w)
+        assert np.array_equal(r.x, base.x) and np.array_equal(r.t, base.t)
+        assert np.array_equal(r.active, base.active)
+        assert np.array_equal(r.log, base.log)
+    # chains far apart in time no longer meet once the leg is cut finely
+    flags = [O.run_leg(s.x, s.y, s.active, s.box, 1.0, windows=w).flag for w in (1, 64)]
+    assert flags[0] == 1
