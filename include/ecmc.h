@@ -54,7 +54,7 @@ typedef struct {
     int32_t cells_per_side; /* nc; 0 picks the largest nc with L/nc >= d*(1+2^-20).
                                Needs nc >= 3 and L/nc < 1.664*d. */
     uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE */
-    int32_t undo_cap;       /* per-chain event records per leg; 0 = 1024 */
+    int32_t undo_cap;       /* per-chain event records per leg, < 2^24; 0 = 1024 */
     int64_t log_cap;        /* liftings kept with ECMC_LOG_LIFTINGS; 0 = 1<<22 */
     int32_t windows;        /* claim windows per leg, 1..4096; 0 = 1. A leg is run as W
                                windows of global time [w ell/W, (w+1) ell/W): chains pause

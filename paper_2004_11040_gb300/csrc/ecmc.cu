@@ -228,8 +228,11 @@ struct StepOut {
 //   cannot occur while the cells are held and is counted as an assertion.
 // COMP: the owner is the conflict component `root` (any member's claim is its
 //   own).
+// nm > 0 (COMP): the component's members are the chains my_member of lanes
+// 0..nm-1, so a claim's holder is tested with shuffles instead of a load.
 template <int C, int MODE>
-__device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, double tw) {
+__device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, double tw,
+                             int nm = 0, int my_member = -1) {
     constexpr int LPC = (3 * C <= 16) ? 16 : 32;  // lanes per column
     constexpr int CPP = 32 / LPC;                 // columns per pass
     const int lane = threadIdx.x & 31;
@@ -257,6 +260,11 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool hz = false;
 
     for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
+        if (m0 >= 1) {
+            // the stop rule for the pass's first column, before its loads
+            const double t0 = __dsub_rn(__dsub_rn(__dmul_rn((double)m0, s.a), fx), s.d);
+            if (!dneg(t0) && dbits(t0) > cur_eps) break;
+        }
         const int m = m0 + grp;
         const bool colok = used && m < nc;
         int col = cxi + m;
@@ -277,16 +285,18 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             // L1 line from an earlier window could still show this chain's claim
             holder = __ldcg(s.claim + cell);
         }
-        const uint32_t id = colok ? s.cid[loc] : EMPTY;
+        // all loads of the slot at once (an empty slot's values are ignored;
+        // they share the cell's sectors with the occupied ones)
+        uint32_t id = EMPTY, own = OWN_STATIC;
         double xj = 0.0, yj = 0.0, tj = 0.0;
-        uint32_t own = OWN_STATIC;
-        const bool cand = id != EMPTY && id != r.i;
-        if (cand) {
+        if (colok) {
+            id = s.cid[loc];
             xj = s.cx[loc];
             yj = s.cy[loc];
             tj = s.ct[loc];
             own = s.cown[loc];
         }
+        const bool cand = id != EMPTY && id != r.i;
         double tau = INFINITY;
         bool behind = false;
         if (cand && own == OWN_STATIC) {
@@ -341,20 +351,24 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             bj = kj;
             bloc = kl;
         }
-        if (scanned && sl == 0) {
-            if (!claimed_early && holder == 0u) {
-                const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
-                holder = old == 0u ? mine : old;
-            }
-            bool foreign;
-            if (MODE == MODE_PASS1)
-                foreign = holder != mine;
-            else
-                foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
-            if (foreign) {
-                conflict = true;
-                partner = holder - 1u;
-            }
+        if (scanned && sl == 0 && !claimed_early && holder == 0u) {
+            const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
+            holder = old == 0u ? mine : old;
+        }
+        bool foreign = false;
+        if (MODE == MODE_PASS1) {
+            foreign = scanned && sl == 0 && holder != mine;
+        } else if (nm > 0) {
+            const int hq = (scanned && sl == 0) ? (int)(holder - 1u) : -1;
+            bool member = hq < 0;
+            for (int q = 0; q < nm; ++q) member |= __shfl_sync(FULL, my_member, q) == hq;
+            foreign = !member;
+        } else if (scanned && sl == 0) {
+            foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
+        }
+        if (foreign) {
+            conflict = true;
+            partner = holder - 1u;
         }
         // Eq. 2 (statement 5) on every scanned candidate touched in this window:
         // cannot fail while the cells are held by a lone chain; an assertion.
@@ -433,9 +447,8 @@ __device__ uint32_t move_active(const Dev &s, const ChainReg &r, double xnew, do
 // checks later; in repair the component owns every cell it touches.
 template <int C>
 __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, bool pass1,
-                           uint32_t seq, uint32_t *newloc_out, uint32_t *cas_old) {
+                           uint32_t seq, int32_t nrec, uint32_t *newloc_out, uint32_t *cas_old) {
     const int lane = threadIdx.x & 31;
-    const int32_t nrec = s.nrec[c];
     if (nrec >= s.cap) {
         if (lane == 0) atomicAdd(s.lc + LC_ERR_REC, 1ull);
         return ST_BLOCKED;
@@ -475,7 +488,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
             q.d_after = __dsub_rn(r.D, o.tau);
             s.rec[(size_t)c * s.cap + nrec] = q;
             s.nrec[c] = nrec + 1;
-            s.nlift[c] += 1;
+            atomicAdd(s.nlift + c, 1);
         }
         *newloc_out = newloc;
         r.D = __dsub_rn(r.D, o.tau);                     // statement 18
@@ -612,7 +625,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
     int32_t cas_rec = -1;           // record of that lift, while unchecked
     bool blocked = false;
-    const int32_t lifts0 = s.nlift[c];
+    uint32_t lifts = 0;
     while (st == ST_RUNNING) {
         const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r, tw);
         if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
@@ -642,12 +655,12 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
             atomicAdd(s.lc + LC_ORDER, 1ull);
             diag(s, 9, tw, c, r.i, o.j, r.ti, o.tau);
         }
-        if (lane == 0 && s.cid[r.iloc] != r.i) diag(s, 7, tw, c, r.i, s.cid[r.iloc], r.iloc, r.ti);
-        if (lane == 0 && o.lift && s.cid[o.jloc] != o.j)
-            diag(s, 8, tw, c, o.j, s.cid[o.jloc], o.jloc, r.ti);
         uint32_t nl;
-        st = commit_step<C>(s, c, r, o, true, seq, &nl, &cas_old);
-        if (st == ST_RUNNING) cas_rec = (int32_t)seq;
+        st = commit_step<C>(s, c, r, o, true, seq, (int32_t)seq, &nl, &cas_old);
+        if (st == ST_RUNNING) {
+            cas_rec = (int32_t)seq;
+            ++lifts;
+        }
         ++seq;
     }
     if (blocked) st = ST_BLOCKED;
@@ -663,7 +676,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
             atomicAdd(s.lc + LC_BLOCKED, 1ull);
             atomicAdd(s.lc + LC_WBLOCKED, 1ull);
         }
-        atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)(s.nlift[c] - lifts0));
+        atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)lifts);
     }
     __syncwarp();
 }
@@ -675,7 +688,7 @@ __global__ void k_pass1(Dev s) {
     if (c < s.k) pass1_chain<C>(s, c, 0.0, INFINITY);
 }
 
-// Exact inverse of commit_step for one record of chain c (lane 0 only).
+// Exact inverse of commit_step for one record of chain c (one lane).
 __device__ void undo_record(const Dev &s, int c, const Rec &u) {
     if (u.to != u.from) {
         s.cx[u.from] = u.x_old;
@@ -690,7 +703,7 @@ __device__ void undo_record(const Dev &s, int c, const Rec &u) {
     if (u.j != NONE) {
         s.ct[u.jloc] = u.tj_old;
         if (!(u.flags & REC_NO_OWNER)) s.cown[u.jloc] = OWN_STATIC;
-        s.nlift[c] -= 1;
+        atomicSub(s.nlift + c, 1);
     }
 }
 
@@ -845,8 +858,13 @@ __device__ __forceinline__ void atomic_min_time(double *p, double v) {
 }
 
 // Rolls the members of a component back to T* (their events before T* are
-// exact): records with event time >= T* are undone, latest first within each
-// run (runs of different components touch different cells).
+// exact): records with event time >= T* are undone, latest first. Records of
+// repair rounds (seq >= REPAIR_SEQ0) can share slots across members and are
+// undone one at a time in descending seq; beneath them, the records of the
+// window's pass 1 lie in cells claimed by their own chain only, so each
+// member undoes its own in parallel.
+constexpr uint32_t REPAIR_SEQ0 = 1u << 24;
+
 __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double Ts) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -857,7 +875,7 @@ __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double
             const int32_t nr = s.nrec[c];
             if (nr == 0) continue;
             const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
-            if (!(u.t >= Ts)) continue;
+            if (!(u.t >= Ts) || u.seq < REPAIR_SEQ0) continue;
             if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
                 bseq = u.seq;
                 bmem = e;
@@ -881,6 +899,18 @@ __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double
         }
         __syncwarp();
     }
+    for (int e = lane; e < m; e += 32) {
+        const int c = mem[e];
+        int32_t nr = s.nrec[c];
+        while (nr > 0) {
+            const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+            if (!(u.t >= Ts)) break;
+            undo_record(s, c, u);
+            --nr;
+        }
+        s.nrec[c] = nr;
+    }
+    __syncwarp();
 }
 
 // State of chain c after its last kept record (or at the leg start).
@@ -945,8 +975,10 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
     uint32_t my_loc = 0, my_id = 0;
     double my_x = 0.0, my_y = 0.0, my_t = 0.0, my_D = 0.0;
     int my_st = ST_STALLED;
+    int32_t my_nrec = 0;
     if (has) {
         resume_state(s, my_c, my_loc, my_id, my_t, my_D, my_st);
+        my_nrec = s.nrec[my_c];
         my_x = s.cx[my_loc];
         my_y = s.cy[my_loc];
         if (s.cid[my_loc] != my_id) {
@@ -977,7 +1009,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         r.ti = __shfl_sync(FULL, my_t, q);
         r.D = __shfl_sync(FULL, my_D, q);
         const int cq = __shfl_sync(FULL, my_c, q);
-        const StepOut o = scan_step<C, MODE_COMP>(s, cq, root, r, 0.0);
+        const StepOut o = scan_step<C, MODE_COMP>(s, cq, root, r, 0.0, m, my_c);
         if (o.conflict) {
             abort = true;
             met = (int)o.partner;
@@ -1037,18 +1069,16 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         o.tj = __shfl_sync(FULL, ev.tj, bq);
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
-        if (o.lift && (s.cid[o.jloc] != o.j || s.cown[o.jloc] != OWN_STATIC) && lane == 0)
-            diag(s, 4, round, bc, o.j, s.cid[o.jloc], s.cown[o.jloc], Tn);
-        if (s.cid[r.iloc] != r.i && lane == 0) diag(s, 5, round, bc, r.i, s.cid[r.iloc], r.iloc, Tn);
         uint32_t nl = 0, dummy = 0;
-        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
-                                      &dummy);
+        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++,
+                                      __shfl_sync(FULL, my_nrec, bq), &nl, &dummy);
         if (st == ST_BLOCKED) {  // out of records or slots: reported by the host
             abort = true;
             break;
         }
         const uint32_t cell_b = nl / C;
         if (lane == bq) {
+            my_nrec += 1;
             my_st = st;
             my_loc = r.iloc;
             my_id = r.i;
@@ -1185,12 +1215,9 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         o.tj = s.ev_tj[bc];
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
-        if (o.lift && (s.cid[o.jloc] != o.j || s.cown[o.jloc] != OWN_STATIC) && lane == 0)
-            diag(s, 14, round, bc, o.j, s.cid[o.jloc], s.cown[o.jloc], bT);
-        if (s.cid[r.iloc] != r.i && lane == 0) diag(s, 15, round, bc, r.i, s.cid[r.iloc], r.iloc, bT);
         uint32_t nl = 0, dummy = 0;
-        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++, &nl,
-                                      &dummy);
+        const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++,
+                                      s.nrec[bc], &nl, &dummy);
         if (st == ST_BLOCKED) {
             abort = true;
             break;
@@ -1710,6 +1737,8 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF) return fail(nullptr, ECMC_EINVAL, "n out of range");
     if (p->n_chains < 1 || p->n_chains > p->n) return fail(nullptr, ECMC_EINVAL, "n_chains out of range");
     if (p->windows < 0 || p->windows > 4096) return fail(nullptr, ECMC_EINVAL, "windows out of range");
+    if (p->undo_cap < 0 || p->undo_cap >= (1 << 24))
+        return fail(nullptr, ECMC_EINVAL, "undo_cap out of range (0 .. 2^24 - 1)");
     if (!(p->d > 0.0) || !(p->ell > 0.0) || !(p->box > 0.0) || !std::isfinite(p->box) ||
         !std::isfinite(p->ell))
         return fail(nullptr, ECMC_EINVAL, "d, ell and box must be positive and finite");
