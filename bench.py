@@ -12,6 +12,12 @@ with a 512 MB write between timed steps.
 --impl reference times the CPU oracle (plain C, one core) on a bounded
 sample of the same workload.
 
+--workload batched: many independent replicas of uneven size (N log-uniform
+in [1024, 65536], eta uniform in [0.60, 0.74], k = sqrt(N), a liftings budget
+each) advanced by one persistent launch per slice, against the same systems
+one at a time. --workload serve: a seeded Poisson stream of whole-ECMC
+requests through the continuous-batching server (p50/p99 latency).
+
 Multi-GPU: the path does not shard a single system; every rank runs an
 independent replica (its own seed), ``value`` sums all ranks' liftings over
 the slowest rank's time ("replicas only").
@@ -43,14 +49,23 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--k", type=int, default=1024, help="chains")
     p.add_argument("--legs", type=int, default=10, help="legs per step")
-    p.add_argument("--windows", type=int, default=1, help="claim windows per leg")
+    p.add_argument("--windows", type=int, default=0,
+                   help="claim windows per leg (0: 2 up to 4096 chains, else 4)")
+    p.add_argument("--workload", default="lattice", choices=["lattice", "batched", "serve"])
+    p.add_argument("--replicas", type=int, default=512)
+    p.add_argument("--budget", type=float, default=1e6, help="liftings per replica (batched)")
+    p.add_argument("--requests", type=int, default=200)
+    p.add_argument("--rate", type=float, default=50.0, help="request arrivals per second")
     p.add_argument("--m", type=int, default=1024, help="lattice side (N = m*m)")
     p.add_argument("--eta", type=float, default=0.72)
     p.add_argument("--ell", type=float, default=1.0)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    return p.parse_args()
+    a = p.parse_args()
+    if a.windows <= 0:
+        a.windows = 2 if a.k <= 4096 else 4
+    return a
 
 
 def workload(a):
@@ -311,9 +326,118 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- batched replicas / serving
+
+def run_batched_bench(a):
+    """Replicas of uneven size to a liftings budget each: one persistent launch
+    per slice for all of them, against the same systems one at a time."""
+    import torch
+
+    from paper_2004_11040_gb300 import batch, build
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    reps = batch.make_replicas(a.replicas, seed=a.seed + rank)
+    choice = batch.autotune(reps, stream=stream, cache=None)
+    systems = batch.create(reps, choice["cell_factor"], stream=stream)
+    try:
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            lifts, ms, launches = batch.run_batched(systems, int(a.budget),
+                                                    choice["legs_per_launch"], stream)
+            wall = time.perf_counter() - t0
+    finally:
+        for q in systems:
+            q.close()
+    sample = min(16, len(reps))
+    plain = batch.create(reps[:sample], choice["cell_factor"], stream=stream)
+    try:
+        p_lifts, p_ms, p_launches = batch.run_plain(plain, int(a.budget), choice["legs_per_launch"])
+    finally:
+        for q in plain:
+            q.close()
+    if rank != 0:
+        return
+    v, pv = lifts / (ms / 1e3), p_lifts / (p_ms / 1e3)
+    print(json.dumps({
+        "metric": "batched liftings/s over all replicas", "value": v, "unit": "liftings/s",
+        "n_gpus": ws, "steps": launches, "warmup": 0, "ms_per_step": ms / max(1, launches),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{a.replicas} replicas, N log-uniform [1024, 65536] (lattice), "
+                               f"eta U[0.60, 0.74], k = sqrt(N), ell = 1, "
+                               f"{int(a.budget)} liftings each", "seed": a.seed},
+        "wall_liftings_per_s": lifts / wall, "autotune": {k: v2 for k, v2 in choice.items()
+                                                          if k != "trials"},
+        "one_at_a_time": {"value": pv, "unit": "liftings/s", "sample_replicas": sample,
+                          "launches": p_launches},
+        "batched_over_one_at_a_time": v / pv, "gpu_launches": launches,
+        "clocks": clk.summary()}), flush=True)
+
+
+def run_serve_bench(a):
+    """A seeded Poisson stream of whole-ECMC requests through the server."""
+    import torch
+
+    from paper_2004_11040_gb300 import build, serve
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    reqs = serve.make_requests(a.requests, seed=a.seed + rank, rate=a.rate,
+                               budget_range=(1e4, max(1e4, a.budget)))
+    serve.prepare(reqs)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(hbm_budget_bytes=int(free * 0.6), stream=stream)
+    try:
+        with ClockSampler(local) as clk:
+            st = srv.serve(reqs)
+    finally:
+        srv.close()
+    # the same requests one at a time (a sample), device time
+    sample = reqs[: min(12, len(reqs))]
+    one_lifts, one_ms = 0, 0.0
+    for r in sample:
+        from paper_2004_11040_gb300 import ecmc
+        q = r.start
+        sysm = ecmc.System(q.x, q.y, q.active, q.box, 1.0, undo_cap=srv.undo_cap, stream=stream)
+        got = 0
+        while got < r.budget:
+            b = sysm.stats()
+            sysm.run(srv.slice_legs, event_budget=r.budget - got)
+            e = sysm.stats()
+            got += e["liftings"] - b["liftings"]
+            one_ms += e["device_ms"] - b["device_ms"]
+        one_lifts += got
+        sysm.close()
+    if rank != 0:
+        return
+    summ = st.summary()
+    one = one_lifts / (one_ms / 1e3)
+    print(json.dumps({
+        "metric": "served liftings/s (device) with p50/p99 request latency",
+        "value": summ["liftings_per_s_device"], "unit": "liftings/s", "n_gpus": ws,
+        "steps": summ["slices"], "warmup": 0,
+        "ms_per_step": summ["device_ms"] / max(1, summ["slices"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{a.requests} requests, Poisson {a.rate}/s, N log-uniform "
+                               f"[4096, 4194304] (lattice), eta U[0.62, 0.72], k = sqrt(N), "
+                               f"budget log-uniform [1e4, {a.budget:g}] liftings",
+                   "seed": a.seed},
+        "serve": summ,
+        "one_at_a_time": {"value": one, "unit": "liftings/s", "sample_requests": len(sample)},
+        "served_over_one_at_a_time": summ["liftings_per_s_device"] / one if one else None,
+        "clocks": clk.summary()}), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched_bench(args)
+    elif args.workload == "serve":
+        run_serve_bench(args)
     else:
         run_ours(args)
