@@ -210,6 +210,9 @@ struct StepOut {
     int cx, cy, mlast;  // scanned footprint: rows cy-1..cy+1, columns cx..cx+mlast
     int conflict;
     uint32_t partner;
+    // empty slots of the middle row (the active disk's row) as scanned: C bits
+    // per column offset m (bit m*C + slot), for the columns with (m+1)*C <= 64
+    unsigned long long emask;
 };
 
 // Statements 1-9 of Alg. 5 for one chain, with the cell scan: columns ahead
@@ -258,13 +261,14 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool conflict = false;
     uint32_t partner = NONE;
     bool hz = false;
+    unsigned long long emask = 0ull;
 
     for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
-        if (m0 >= 1) {
-            // the stop rule for the pass's first column, before its loads
-            const double t0 = __dsub_rn(__dsub_rn(__dmul_rn((double)m0, s.a), fx), s.d);
-            if (!dneg(t0) && dbits(t0) > cur_eps) break;
-        }
+        // the stop rule for the next pass's first column, decided at the end
+        // of this pass before any of the next pass's loads (computed here so
+        // that its latency hides behind this pass)
+        const double thr_next =
+            __dsub_rn(__dsub_rn(__dmul_rn((double)(m0 + CPP), s.a), fx), s.d);
         const int m = m0 + grp;
         const bool colok = used && m < nc;
         int col = cxi + m;
@@ -274,6 +278,21 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // threshold of this lane's column; <= eps means "scanned in any case"
         const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, s.a), fx), s.d);
         const bool certain = m == 0 || dneg(thr) || dbits(thr) <= dbits(s.eps);
+        // all loads of the slot at once (an empty slot's values are ignored;
+        // they share the cell's sectors with the occupied ones). They are
+        // issued before the claim so that both round trips overlap: a cell
+        // read before its claim succeeds was not written in this window
+        // (claims are taken before writes and never released in a window),
+        // and a failed claim discards what was read.
+        uint32_t id = EMPTY, own = OWN_STATIC;
+        double xj = 0.0, yj = 0.0, tj = 0.0;
+        if (colok) {
+            id = s.cid[loc];
+            xj = s.cx[loc];
+            yj = s.cy[loc];
+            tj = s.ct[loc];
+            own = s.cown[loc];
+        }
         uint32_t holder = 0;
         bool claimed_early = false;
         if (colok && sl == 0 && certain) {
@@ -285,18 +304,17 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             // L1 line from an earlier window could still show this chain's claim
             holder = __ldcg(s.claim + cell);
         }
-        // all loads of the slot at once (an empty slot's values are ignored;
-        // they share the cell's sectors with the occupied ones)
-        uint32_t id = EMPTY, own = OWN_STATIC;
-        double xj = 0.0, yj = 0.0, tj = 0.0;
-        if (colok) {
-            id = s.cid[loc];
-            xj = s.cx[loc];
-            yj = s.cy[loc];
-            tj = s.ct[loc];
-            own = s.cown[loc];
-        }
         const bool cand = id != EMPTY && id != r.i;
+        {
+            const unsigned eb = __ballot_sync(FULL, colok && rr == 1 && id == EMPTY);
+#pragma unroll
+            for (int g = 0; g < CPP; ++g) {
+                const int mc = m0 + g;
+                if ((mc + 1) * C <= 64)
+                    emask |= (unsigned long long)((eb >> (g * LPC + C)) & ((1u << C) - 1u))
+                             << (mc * C);
+            }
+        }
         double tau = INFINITY;
         bool behind = false;
         if (cand && own == OWN_STATIC) {
@@ -373,12 +391,14 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // Eq. 2 (statement 5) on every scanned candidate touched in this window:
         // cannot fail while the cells are held by a lone chain; an assertion.
         if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
+        if (!dneg(thr_next) && dbits(thr_next) > cur_eps) break;
     }
 
     StepOut o;
     o.cx = cxi;
     o.cy = cyi;
     o.mlast = mlast;
+    o.emask = emask;
     o.conflict = 0;
     o.partner = NONE;
     const unsigned cb = __ballot_sync(FULL, conflict);
@@ -413,15 +433,24 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
 // Moves the active disk (statements 16 / 22) with its local time and owner
 // word; returns its new slot or EMPTY on a full cell.
 template <int C>
-__device__ uint32_t move_active(const Dev &s, const ChainReg &r, double xnew, double tnew,
-                                uint32_t own_new) {
+__device__ uint32_t move_active(const Dev &s, const ChainReg &r, const StepOut &o, double xnew,
+                                double tnew, uint32_t own_new) {
     const int lane = threadIdx.x & 31;
     const uint32_t cell_old = r.iloc / C;
     const uint32_t cell_new = cell_of(xnew, r.yi, s);
     uint32_t newloc = r.iloc;
     if (cell_new != cell_old) {
-        const uint32_t sid = (lane < C) ? s.cid[cell_new * C + lane] : 0u;
-        const unsigned em = __ballot_sync(FULL, lane < C && sid == EMPTY);
+        // the new cell lies in the active disk's row of the scanned footprint,
+        // whose empty slots the scan recorded (else they are read here)
+        int mc = (int)(cell_new % (uint32_t)s.nc) - o.cx;
+        if (mc < 0) mc += s.nc;
+        unsigned em;
+        if (mc <= o.mlast && (mc + 1) * C <= 64) {
+            em = (unsigned)(o.emask >> (mc * C)) & ((1u << C) - 1u);
+        } else {
+            const uint32_t sid = (lane < C) ? s.cid[cell_new * C + lane] : 0u;
+            em = __ballot_sync(FULL, lane < C && sid == EMPTY);
+        }
         if (!em) return EMPTY;
         newloc = cell_new * C + (uint32_t)(__ffs(em) - 1);
         if (lane == 0) {
@@ -463,7 +492,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
                 s.cown[o.jloc] = OWN_ACTIVE | (uint32_t)c;
             s.ct[o.jloc] = tnew;
         }
-        const uint32_t newloc = move_active<C>(s, r, xnew, tnew, OWN_STATIC);  // statement 17
+        const uint32_t newloc = move_active<C>(s, r, o, xnew, tnew, OWN_STATIC);  // statement 17
         if (newloc == EMPTY) {
             if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
             return ST_BLOCKED;
@@ -502,7 +531,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
     }
     const double tnew = __dadd_rn(r.ti, r.D);           // statement 21
     const double xnew = wrap_add(r.xi, r.D, s);         // statement 22
-    const uint32_t newloc = move_active<C>(s, r, xnew, tnew, OWN_STALLED | (uint32_t)c);
+    const uint32_t newloc = move_active<C>(s, r, o, xnew, tnew, OWN_STALLED | (uint32_t)c);
     if (newloc == EMPTY) {
         if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
         return ST_BLOCKED;
@@ -765,7 +794,9 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
 // holder of the cell or owner word it met); later rounds: edges from
 // components that met another chain. Components holding a chain whose events
 // are not final ("dirty") are listed for the repair with their members.
-__device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot) {
+// reset_abort: clear the abort count here (the persistent kernel clears it in
+// its prefix phase instead, after every block has read it).
+__device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot, bool reset_abort) {
     const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
     if (first)
         for (int c = tid; c < k; c += nt) {
@@ -831,7 +862,7 @@ __device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot) {
         s.ctl[CTL_NCOMP] = tot[1];
         s.ctl[CTL_NMEMB] = tot[0];
         s.ctl[CTL_WORK] = 0;
-        s.ctl[CTL_NABORT] = 0;
+        if (reset_abort) s.ctl[CTL_NABORT] = 0;
     }
     __syncthreads();
 }
@@ -839,7 +870,7 @@ __device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot) {
 __global__ void k_uf(Dev s, int first) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
-    uf_block(s, first, warp_tot, tot);
+    uf_block(s, first, warp_tot, tot, true);
 }
 
 __device__ __forceinline__ bool footprint_has(int fcx, int fcy, int fm, uint32_t cell, int nc) {
@@ -997,6 +1028,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
     ev.xj = ev.yj = ev.tj = 0.0;
     ev.cx = ev.cy = 0;
     ev.mlast = -1;
+    ev.emask = 0ull;
     bool abort = false;
     int met = -1;
     // computes member q's next event into lane q's registers
@@ -1067,6 +1099,9 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         o.xj = __shfl_sync(FULL, ev.xj, bq);
         o.yj = __shfl_sync(FULL, ev.yj, bq);
         o.tj = __shfl_sync(FULL, ev.tj, bq);
+        o.cx = __shfl_sync(FULL, ev.cx, bq);
+        o.mlast = __shfl_sync(FULL, ev.mlast, bq);
+        o.emask = shfl_u64(ev.emask, bq);
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
         uint32_t nl = 0, dummy = 0;
@@ -1213,6 +1248,9 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         o.xj = s.ev_xj[bc];
         o.yj = s.ev_yj[bc];
         o.tj = s.ev_tj[bc];
+        o.cx = 0;
+        o.mlast = -1;  // no recorded empty slots: move_active reads the new cell
+        o.emask = 0ull;
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
         uint32_t nl = 0, dummy = 0;
@@ -1467,8 +1505,15 @@ __device__ void check_chains(const Batch &b, int gt, int nthreads, int total_cha
     }
 }
 
+// Block shape of the persistent kernel: 8 warps per block, 2 blocks per SM
+// (16 warps per SM, 128 registers). Fewer, larger register files (3 blocks of
+// 4 warps, no spills) measured slower: the passes want warps more than
+// registers.
+constexpr int RUN_THREADS = 256;
+constexpr int RUN_MIN_BLOCKS = 2;
+
 template <int C>
-__global__ void __launch_bounds__(256) k_run(Batch b) {
+__global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
     __shared__ int sflag;
@@ -1536,10 +1581,9 @@ __global__ void __launch_bounds__(256) k_run(Batch b) {
                         need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
                     if (need && round == 1 && threadIdx.x == 0) s.lc[LC_CWINDOWS] += 1ull;
                     if (need && round <= 255) {
-                        uf_block(s, round == 1, warp_tot, tot);
+                        uf_block(s, round == 1, warp_tot, tot, false);
                     } else if (threadIdx.x == 0) {
                         s.ctl[CTL_NCOMP] = 0;
-                        s.ctl[CTL_NABORT] = 0;
                         if (need) b.ctl[r].err = 1;  // too many rounds
                     }
                     __syncthreads();
@@ -1555,6 +1599,8 @@ __global__ void __launch_bounds__(256) k_run(Batch b) {
                     for (int r = lo; r < hi; ++r) {
                         b.comp_base[r] = off;
                         off += b.reps[r].ctl[CTL_NCOMP];
+                        // every block read the abort counts before the barrier above
+                        b.reps[r].ctl[CTL_NABORT] = 0;
                     }
                     if (threadIdx.x == 0) {
                         b.comp_base[R] = tot[0];
@@ -1576,6 +1622,11 @@ __global__ void __launch_bounds__(256) k_run(Batch b) {
                 }
                 if (!grid_barrier(b, &sflag)) return;
                 check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 2 + round);
+                // no component met another chain: the window is repaired
+                int aborted = 0;
+                for (int r = threadIdx.x; r < R; r += blockDim.x)
+                    if (rep_on(b, r) && b.reps[r].ctl[CTL_NABORT] != 0) aborted = 1;
+                if (!__syncthreads_or(aborted)) break;
             }
             mark(PH_REPAIR);
         }
@@ -1937,8 +1988,8 @@ static int runner_reserve(Runner &rn, int R, std::string &err) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, 256, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, RUN_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, RUN_THREADS, 0) != cudaSuccess ||
         !coop || b4 < 1 || b8 < 1) {
         (void)cudaGetLastError();
         runner_free(rn);
@@ -2034,9 +2085,9 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     void *args[] = {&b};
     cu(cudaEventRecord(rn.ev0, st), "event");
     if (C == 4)
-        cu(cudaLaunchCooperativeKernel((void *)k_run<4>, rn.grid4, 256, args, 0, st), "launch");
+        cu(cudaLaunchCooperativeKernel((void *)k_run<4>, rn.grid4, RUN_THREADS, args, 0, st), "launch");
     else
-        cu(cudaLaunchCooperativeKernel((void *)k_run<8>, rn.grid8, 256, args, 0, st), "launch");
+        cu(cudaLaunchCooperativeKernel((void *)k_run<8>, rn.grid8, RUN_THREADS, args, 0, st), "launch");
     cu(cudaEventRecord(rn.ev1, st), "event");
     int32_t g[G_N];
     unsigned long long ph[PH_N];
