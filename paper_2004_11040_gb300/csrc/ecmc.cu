@@ -245,7 +245,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     const int nc = s.nc;
     const uint32_t mine = (uint32_t)c + 1u;
 
-    const int cxi = cell_coord(r.xi, s), cyi = cell_coord(r.yi, s);
+    // the active disk's cell is that of its slot (cells always hold the
+    // disks whose coordinates fall in them)
+    const int cxi = (int)((r.iloc / C) % (uint32_t)nc), cyi = (int)((r.iloc / C) / (uint32_t)nc);
     const double fx = __dsub_rn(r.xi, __dmul_rn((double)cxi, s.a));
     int row = cyi + rr - 1;
     if (row < 0) row += nc;
@@ -286,6 +288,10 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // and a failed claim discards what was read.
         uint32_t id = EMPTY, own = OWN_STATIC;
         double xj = 0.0, yj = 0.0, tj = 0.0;
+        // claim word: the raw result of the CAS (claimed_early) or the value
+        // read; turned into the holder only where the conflict test needs it
+        uint32_t claim_w = 0;
+        bool claimed_early = false;
         if (colok) {
             id = s.cid[loc];
             xj = s.cx[loc];
@@ -293,16 +299,16 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             tj = s.ct[loc];
             own = s.cown[loc];
         }
-        uint32_t holder = 0;
-        bool claimed_early = false;
-        if (colok && sl == 0 && certain) {
-            const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
-            holder = old == 0u ? mine : old;
-            claimed_early = true;
-        } else if (colok && sl == 0) {
-            // through L2: claims are reset between windows by other SMs, so an
-            // L1 line from an earlier window could still show this chain's claim
-            holder = __ldcg(s.claim + cell);
+        if (colok && sl == 0) {
+            if (certain) {
+                claim_w = atomicCAS(s.claim + cell, 0u, mine);
+                claimed_early = true;
+            } else {
+                // through L2: claims are reset between windows by other SMs, so
+                // an L1 line from an earlier window could still show this
+                // chain's claim
+                claim_w = __ldcg(s.claim + cell);
+            }
         }
         const bool cand = id != EMPTY && id != r.i;
         {
@@ -369,6 +375,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             bj = kj;
             bloc = kl;
         }
+        uint32_t holder = claimed_early ? (claim_w == 0u ? mine : claim_w) : claim_w;
         if (scanned && sl == 0 && !claimed_early && holder == 0u) {
             const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
             holder = old == 0u ? mine : old;
