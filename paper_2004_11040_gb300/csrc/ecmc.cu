@@ -77,6 +77,8 @@ struct Dev {
     int64_t n;
     int nc, k, cap, windows;
     double L, d, d2, ell, a, inv_a, eps;
+    double far;  // L - 3a: a chain with less than this left never lifts onto a
+                 // disk behind its active disk (that is more than L - 2a ahead)
     // cells: slot q of cell c at index c*C + q; a disk's x, y, local time and
     // owner word live in its slot and move with it
     double *cx, *cy, *ct;
@@ -154,22 +156,6 @@ __device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
     return r;
 }
 
-// Time of flight of i towards j (Sec. 2.2: tau = x_j - x_i - b_ij), forward
-// image in x, minimum image in y, corridor |dy| < d; +inf outside.
-__device__ __forceinline__ double time_of_flight(double xi, double yi, double xj, double yj,
-                                                 const Dev &s) {
-    double a = fabs(__dsub_rn(yj, yi));
-    const double la = __dsub_rn(s.L, a);
-    if (dbits(la) < dbits(a)) a = la;
-    if (!(dbits(a) < dbits(s.d))) return INFINITY;
-    const double b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(a, a)));
-    double dx = __dsub_rn(xj, xi);
-    if (dneg(dx)) dx = __dadd_rn(dx, s.L);
-    double tau = __dsub_rn(dx, b);
-    if (dneg(tau)) tau = 0.0;
-    return tau;
-}
-
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
     return (unsigned long long)__shfl_xor_sync(FULL, (long long)v, o);
 }
@@ -179,20 +165,6 @@ __device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int
 }
 
 // lexicographic (tau, j) minimum over the warp; tau given by its bits
-__device__ __forceinline__ void warp_argmin(unsigned long long &t, uint32_t &j, uint32_t &l) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long t2 = shfl_xor_u64(t, o);
-        const uint32_t j2 = __shfl_xor_sync(FULL, j, o);
-        const uint32_t l2 = __shfl_xor_sync(FULL, l, o);
-        if (t2 < t || (t2 == t && j2 < j)) {
-            t = t2;
-            j = j2;
-            l = l2;
-        }
-    }
-}
-
 // ------------------------------------------------------------- one step
 
 enum { MODE_PASS1 = 0, MODE_COMP = 1 };
@@ -253,6 +225,12 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     if (row < 0) row += nc;
     if (row >= nc) row -= nc;
 
+    // warp-uniform skips of arithmetic no lane needs (results unchanged): the
+    // periodic minimum in y only where the scanned rows wrap around the box
+    // (elsewhere |dy| < 2a < L/2), and a disk behind the active disk in its
+    // own column (more than L - 2a ahead) only when D could reach it
+    const bool ywrap = cyi == 0 || cyi == nc - 1 || nc <= 4;
+    const bool near_d = !(dbits(r.D) < dbits(s.far));
     unsigned long long cur = dbits(r.D);  // min(D, best tau so far): drives the stop rule
     unsigned long long cur_eps = dbits(__dadd_rn(r.D, s.eps));
     unsigned long long btau = INF_BITS;
@@ -265,12 +243,15 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool hz = false;
     unsigned long long emask = 0ull;
 
+    double thr_first = 0.0;  // threshold of the pass's first column (column 0: scanned)
     for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
         // the stop rule for the next pass's first column, decided at the end
         // of this pass before any of the next pass's loads (computed here so
         // that its latency hides behind this pass)
         const double thr_next =
             __dsub_rn(__dsub_rn(__dmul_rn((double)(m0 + CPP), s.a), fx), s.d);
+        const double thr_second =
+            CPP == 2 ? __dsub_rn(__dsub_rn(__dmul_rn((double)(m0 + 1), s.a), fx), s.d) : 0.0;
         const int m = m0 + grp;
         const bool colok = used && m < nc;
         int col = cxi + m;
@@ -278,7 +259,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         const uint32_t cell = (uint32_t)row * (uint32_t)nc + (uint32_t)col;
         const uint32_t loc = cell * C + sl;
         // threshold of this lane's column; <= eps means "scanned in any case"
-        const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, s.a), fx), s.d);
+        const double thr = (CPP == 2 && grp == 1) ? thr_second : thr_first;
         const bool certain = m == 0 || dneg(thr) || dbits(thr) <= dbits(s.eps);
         // all loads of the slot at once (an empty slot's values are ignored;
         // they share the cell's sectors with the occupied ones). They are
@@ -321,59 +302,112 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                              << (mc * C);
             }
         }
+        // time of flight of i towards j (statement 4; Sec. 2.2: tau = x_j - x_i
+        // - b_ij with b_ij = sqrt(d^2 - dy^2)): forward image in x, minimum
+        // image in y, corridor |dy| < d, +inf outside, clamped at 0
+        const bool cst = cand && own == OWN_STATIC;
+        double ay = fabs(__dsub_rn(yj, r.yi));
+        if (ywrap) {
+            const double la = __dsub_rn(s.L, ay);
+            if (dbits(la) < dbits(ay)) ay = la;
+        }
+        const bool corr = cst && dbits(ay) < dbits(s.d);
+        double b = 0.0;
+        if (__any_sync(FULL, corr)) b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(ay, ay)));
+        double dx = __dsub_rn(xj, r.xi);
+        const bool neg = dneg(dx);
+        const bool drop = neg && m == 0 && !near_d;
+        const bool needl = corr && neg && !drop;
+        if (__any_sync(FULL, needl) && needl) dx = __dadd_rn(dx, s.L);
         double tau = INFINITY;
+        if (corr && !drop) {
+            tau = __dsub_rn(dx, b);
+            if (dneg(tau)) tau = 0.0;
+        }
+        // lazy frame: a disk that became static after the active disk passed
+        // it (t_i + tau < t_j) is one lap away; t_j = +0 never is
         bool behind = false;
-        if (cand && own == OWN_STATIC) {
-            tau = time_of_flight(r.xi, r.yi, xj, yj, s);
-            if (tau != INFINITY && dbits(__dadd_rn(r.ti, tau)) < dbits(tj)) {
-                behind = true;
-                tau = __dadd_rn(tau, s.L);
-            }
+        const bool tnz = tau != INFINITY && dbits(tj) != 0ull;
+        if (__any_sync(FULL, tnz)) {
+            behind = tnz && dbits(__dadd_rn(r.ti, tau)) < dbits(tj);
+            if (__any_sync(FULL, behind) && behind) tau = __dadd_rn(tau, s.L);
         }
         const unsigned long long tb = dbits(tau);
-        // column minima (lanes of one column form an aligned group of LPC)
-        unsigned long long cm = tb;
+        // (tau, j) minimum of each column (an aligned group of LPC lanes), then
+        // of the pass's other column: every lane ends with both
+        unsigned long long g0t = tb;
+        uint32_t g0j = tb != INF_BITS ? id : NONE, g0l = loc;
 #pragma unroll
         for (int o = 1; o < LPC; o <<= 1) {
-            const unsigned long long v = shfl_xor_u64(cm, o);
-            cm = v < cm ? v : cm;
+            const unsigned long long t2 = shfl_xor_u64(g0t, o);
+            const uint32_t j2 = __shfl_xor_sync(FULL, g0j, o);
+            const uint32_t l2 = __shfl_xor_sync(FULL, g0l, o);
+            if (t2 < g0t || (t2 == g0t && j2 < g0j)) {
+                g0t = t2;
+                g0j = j2;
+                g0l = l2;
+            }
         }
-        int last_here = -1;
-#pragma unroll
-        for (int g = 0; g < CPP; ++g) {
-            const unsigned long long cmg = shfl_u64(cm, g * LPC);
-            const double thg = __shfl_sync(FULL, thr, g * LPC);
-            const int mg = m0 + g;
-            if (stop) continue;
-            if (mg >= nc) {
-                stop = true;
-                continue;
+        unsigned long long g1t = INF_BITS;
+        uint32_t g1j = NONE, g1l = 0;
+        if (CPP == 2) {
+            const unsigned long long t2 = shfl_xor_u64(g0t, LPC);
+            const uint32_t j2 = __shfl_xor_sync(FULL, g0j, LPC);
+            const uint32_t l2 = __shfl_xor_sync(FULL, g0l, LPC);
+            if (grp == 0) {
+                g1t = t2;
+                g1j = j2;
+                g1l = l2;
+            } else {
+                g1t = g0t;
+                g1j = g0j;
+                g1l = g0l;
+                g0t = t2;
+                g0j = j2;
+                g0l = l2;
             }
-            if (mg >= 1 && !dneg(thg) && dbits(thg) > cur_eps) {
+        }
+        // stop rule, uniform: column m0 is scanned (m0 = 0, or the previous
+        // pass found its threshold within reach); the second column if its
+        // threshold is within min(D, best) + eps
+        int last_here = m0;
+        mlast = m0;
+        bool improved = false;
+        if (g0t < btau || (g0t == btau && g0j < bj)) {
+            btau = g0t;
+            bj = g0j;
+            bloc = g0l;
+            improved = true;
+        }
+        if (g0t < cur) {
+            cur = g0t;
+            cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+        }
+        if (CPP == 2) {
+            if (m0 + 1 >= nc || (!dneg(thr_second) && dbits(thr_second) > cur_eps)) {
                 stop = true;
-                continue;
-            }
-            last_here = mg;
-            mlast = mg;
-            if (cmg < cur) {
-                cur = cmg;
-                cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+            } else {
+                last_here = m0 + 1;
+                mlast = m0 + 1;
+                if (g1t < btau || (g1t == btau && g1j < bj)) {
+                    btau = g1t;
+                    bj = g1j;
+                    bloc = g1l;
+                    improved = true;
+                }
+                if (g1t < cur) {
+                    cur = g1t;
+                    cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+                }
             }
         }
         const bool scanned = colok && m <= last_here;
-        unsigned long long kt = scanned ? tb : INF_BITS;
-        uint32_t kj = scanned ? id : NONE;
-        uint32_t kl = loc;
-        warp_argmin(kt, kj, kl);
-        if (kt < btau || (kt == btau && kj < bj)) {
-            const unsigned own_lane = __ballot_sync(FULL, scanned && id == kj && loc == kl);
+        if (improved) {
+            const unsigned own_lane = __ballot_sync(FULL, scanned && id == bj && loc == bloc);
             const int src = own_lane ? __ffs(own_lane) - 1 : 0;
             bx = __shfl_sync(FULL, xj, src);
             by = __shfl_sync(FULL, yj, src);
             bt = __shfl_sync(FULL, tj, src);
-            btau = kt;
-            bj = kj;
-            bloc = kl;
         }
         uint32_t holder = claimed_early ? (claim_w == 0u ? mine : claim_w) : claim_w;
         if (scanned && sl == 0 && !claimed_early && holder == 0u) {
@@ -399,6 +433,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // cannot fail while the cells are held by a lone chain; an assertion.
         if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
         if (!dneg(thr_next) && dbits(thr_next) > cur_eps) break;
+        thr_first = thr_next;
     }
 
     StepOut o;
@@ -413,7 +448,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         o.conflict = 1;
         o.partner = __shfl_sync(FULL, partner, __ffs(cb) - 1);
     }
-    if (MODE == MODE_PASS1) {
+    if (MODE == MODE_PASS1 && !cb) {
+        // only a step whose cells are all held is checked: a conflicting one
+        // may have read a cell while its holder wrote it, and is discarded
         const unsigned hb = __ballot_sync(FULL, hz);
         if (hb && lane == __ffs(hb) - 1) atomicAdd(s.lc + LC_HORIZON, 1ull);
     }
@@ -1527,7 +1564,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     const int lane = threadIdx.x & 31;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
-    const int gw = gt >> 5, nwarps = nthreads >> 5;
+    const int nwarps = nthreads >> 5;
     const int R = b.R;
     const int total_chains = b.chain_base[R];
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1824,6 +1861,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     s.ell = p->ell;
     s.a = p->box / (double)nc;
     s.inv_a = (double)nc / p->box;
+    s.far = s.L - 3.0 * s.a;
     s.eps = std::ldexp(p->box, -30);
     s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
     s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
@@ -2547,6 +2585,7 @@ extern "C" int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int
     s.ell = ell;
     s.a = box / (double)nc;
     s.inv_a = (double)nc / box;
+    s.far = s.L - 3.0 * s.a;
     s.eps = std::ldexp(box, -30);
     const size_t ncell = (size_t)nc * nc, nslot = ncell * C;
     uint32_t *loc_of = nullptr;
