@@ -17,6 +17,11 @@ in [1024, 65536], eta uniform in [0.60, 0.74], k = sqrt(N), a liftings budget
 each) advanced by one persistent launch per slice, against the same systems
 one at a time. --workload serve: a seeded Poisson stream of whole-ECMC
 requests through the continuous-batching server (p50/p99 latency).
+--workload conflicts: the conflict (violation) rate per leg against the
+number of chains, n / sqrt(N): N = 128^2 at eta = 0.708 with 128 chains, and
+N = 2^20 at eta = 0.72 with 256 ... 16384 chains, each run to --target
+liftings; one claim window per leg (the leg-level flag) and the default
+windows (per-window flags, the throughput setting).
 
 Multi-GPU: the path does not shard a single system; every rank runs an
 independent replica (its own seed), ``value`` sums all ranks' liftings over
@@ -51,7 +56,10 @@ def parse():
     p.add_argument("--legs", type=int, default=10, help="legs per step")
     p.add_argument("--windows", type=int, default=0,
                    help="claim windows per leg (0: 2 up to 4096 chains, else 4)")
-    p.add_argument("--workload", default="lattice", choices=["lattice", "batched", "serve"])
+    p.add_argument("--workload", default="lattice",
+                   choices=["lattice", "batched", "serve", "conflicts"])
+    p.add_argument("--target", type=float, default=1e9,
+                   help="liftings per point (conflicts workload)")
     p.add_argument("--replicas", type=int, default=512)
     p.add_argument("--budget", type=float, default=1e6, help="liftings per replica (batched)")
     p.add_argument("--requests", type=int, default=200)
@@ -431,6 +439,52 @@ def run_serve_bench(a):
         "clocks": clk.summary()}), flush=True)
 
 
+def run_conflicts(a):
+    """Conflict rate per leg (flag: claim sets of isolated chains overlap) and
+    the fraction of chains repaired, against n / sqrt(N)."""
+    import torch
+
+    from paper_2004_11040_gb300 import build, ecmc, synth
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    stream = torch.cuda.current_stream()
+    points = [(128, 0.708, 128), (1024, 0.72, 256), (1024, 0.72, 1024), (1024, 0.72, 4096),
+              (1024, 0.72, 16384)]
+    out = []
+    for m, eta, k in points:
+        start = synth.lattice_start(m, eta, k, seed=a.seed)
+        for windows in (1, 2 if k <= 4096 else 4):
+            sysm = ecmc.System(start.x, start.y, start.active, start.box, 1.0, stream=stream,
+                               windows=windows)
+            # the one-window runs of many chains repair for long: bounded sample
+            target = a.target if windows > 1 or k <= 1024 else min(a.target, 2e7)
+            flags = []
+            t0 = time.perf_counter()
+            while sysm.stats()["liftings"] < target:
+                f, _ = sysm.run(50)
+                flags.extend(int(v) for v in f)
+            st = sysm.stats()
+            sysm.close()
+            legs = st["legs"]
+            out.append({"N": m * m, "eta": eta, "k": k, "n_over_sqrtN": k / m,
+                        "claim_windows": windows, "legs": legs, "liftings": st["liftings"],
+                        "conflict_rate_per_leg": st["conflict_legs"] / legs,
+                        "repaired_chains_per_leg_per_chain": st["repaired_chains"] / legs / k,
+                        "liftings_per_s": st["liftings"] / (st["device_ms"] / 1e3),
+                        "horizon_asserts": st["horizon_asserts"],
+                        "order_errors": st["order_errors"],
+                        "wall_s": time.perf_counter() - t0})
+            print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "conflict rate per leg vs n/sqrt(N)", "unit": "fraction",
+                      "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+                      "config": {"workload": "jittered square lattices, ell = 1, v = +x",
+                                 "target_liftings_per_point": a.target, "seed": a.seed},
+                      "points": out}), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
     if args.impl == "reference":
@@ -439,5 +493,7 @@ if __name__ == "__main__":
         run_batched_bench(args)
     elif args.workload == "serve":
         run_serve_bench(args)
+    elif args.workload == "conflicts":
+        run_conflicts(args)
     else:
         run_ours(args)
