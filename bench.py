@@ -177,6 +177,34 @@ def cpu_baseline(a, start, budget_s):
             "sample": f"{legs} whole legs ({lifts} liftings) of the same workload in {el:.1f} s"}
 
 
+def cpu_multicore(a, start, budget_s):
+    """The paper's Alg. 5 (OpenMP threads, atomic CAS on tags) on all host
+    cores, whole legs of the same workload; horizon violations are counted,
+    not repaired (the paper's benchmark mode)."""
+    from oracle import alg5
+    first = alg5.run(start.x, start.y, start.active, start.box, a.ell, 1)
+    legs = max(1, int(budget_s / max(first.seconds, 1e-3)))
+    r = alg5.run(start.x, start.y, start.active, start.box, a.ell, legs)
+    return {"value": r.lifts / r.seconds, "unit": "liftings/s", "cores": r.threads,
+            "kind": "paper Alg. 5 on host threads (OpenMP, atomic CAS on tags)",
+            "sample": f"{legs} whole legs ({r.lifts} liftings) of the same workload in "
+                      f"{r.seconds:.1f} s; {r.violations} horizon violations counted, "
+                      f"not repaired"}
+
+
+def host_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -309,9 +337,10 @@ def run_ours(a):
 
     if rank != 0:
         return
-    cb = None
+    cb = cbm = None
     if ws == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a, start, a.cpu_seconds)
+        cbm = cpu_multicore(a, start, a.cpu_seconds / 2)
     traffic = traffic_for(kname)
     line = {
         "metric": METRIC, "value": value, "unit": "liftings/s", "n_gpus": ws,
@@ -324,7 +353,8 @@ def run_ours(a):
                      "bytes_per_lifting": BYTES_PER_LIFTING,
                      "kernel_ms_per_launch": kms,
                      "liftings_per_launch": kl},
-        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+        "cpu_baseline": cb, "cpu_baseline_multicore": cbm, "host": host_info(),
+        "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
         "detail": {"legs": legs, "conflict_legs": conflict_legs,
                    "liftings": tot_lifts, "profile": d,
