@@ -67,10 +67,12 @@ typedef struct {
     int64_t liftings;        /* liftings (events, Eq. 1) over all legs run */
     int64_t legs;            /* breakpoints reached */
     int64_t conflict_legs;   /* legs in which two chains' scanned cells met */
-    int64_t repaired_chains; /* chain runs rolled back and redone in time order */
+    int64_t repaired_chains; /* chains in conflict components (once per repair round) */
     int64_t horizon_asserts; /* Eq. 2 failures seen by a conflict-free chain: 0 */
     int64_t order_errors;    /* repaired events found out of time order: 0 */
     double device_ms;        /* device time spent in ecmc_run_to_breakpoint */
+    int64_t continued_chains; /* of repaired_chains: in components finished by continuing
+                                 the blocked chains (Lemma 2), nothing redone */
 } ecmc_stats_t;
 
 /* One lifting i -> j (Eq. 1): chain c, leg index, time t (= new t_j),

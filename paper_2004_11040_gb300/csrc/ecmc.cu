@@ -54,6 +54,7 @@ constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
 
 // per-leg counters (reset at every leg start)
 enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
+       LC_CONTINUED,
        LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_N };
 enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
 // cumulative counters
@@ -89,6 +90,7 @@ struct Dev {
     uint32_t *ci;  // active disk id
     double *D, *tc;
     int32_t *status, *partner, *nrec, *nlift;
+    int32_t *nocont;  // pass 1 saw another chain's active or stalled disk in its corridor
     Rec *rec;  // [k * cap]
     // pending events for the global-time repair of large components
     double *ev_T, *ev_tau, *ev_xj, *ev_yj, *ev_tj;
@@ -97,7 +99,8 @@ struct Dev {
     // conflict components
     double *vt;          // per chain: its events are exact before this time
     int32_t *uf;         // union-find parent
-    int32_t *fin;        // 1: the chain's events of this leg are final
+    int32_t *fin;        // 0: in a component to repair; 1: final since the round began;
+                         // 2: made final in this round (by its component's repair)
     int32_t *comp_of;    // component root per chain
     int32_t *abort_to;   // chain met by an aborted component (per root), -1
     int32_t *comp_cnt;   // members per root (dirty components)
@@ -167,7 +170,7 @@ __device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int
 // lexicographic (tau, j) minimum over the warp; tau given by its bits
 // ------------------------------------------------------------- one step
 
-enum { MODE_PASS1 = 0, MODE_COMP = 1 };
+enum { MODE_PASS1 = 0, MODE_COMP = 1, MODE_CONT = 2 };
 
 struct ChainReg {
     uint32_t i, iloc;
@@ -182,6 +185,8 @@ struct StepOut {
     int cx, cy, mlast;  // scanned footprint: rows cy-1..cy+1, columns cx..cx+mlast
     int conflict;
     uint32_t partner;
+    int nonstatic;  // an active or stalled disk of another chain lies in a scanned corridor
+    int viol;       // CONT: a scanned corridor disk fails the horizon condition (Eq. 2)
     // empty slots of the middle row (the active disk's row) as scanned: C bits
     // per column offset m (bit m*C + slot), for the columns with (m+1)*C <= 64
     unsigned long long emask;
@@ -203,8 +208,12 @@ struct StepOut {
 //   cannot occur while the cells are held and is counted as an assertion.
 // COMP: the owner is the conflict component `root` (any member's claim is its
 //   own).
-// nm > 0 (COMP): the component's members are the chains my_member of lanes
-// 0..nm-1, so a claim's holder is tested with shuffles instead of a load.
+__device__ void uf_union(int32_t *p, int a, int b);
+
+// nm > 0 (COMP, CONT): the component's members are the chains my_member of
+// lanes 0..nm-1, so a claim's holder is tested with shuffles instead of a
+// load; nm = 0: by comp_of; nm < 0 (CONT): by comp_of, and a chain that is in
+// no component is taken over by this one.
 template <int C, int MODE>
 __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, double tw,
                              int nm = 0, int my_member = -1) {
@@ -241,6 +250,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool conflict = false;
     uint32_t partner = NONE;
     bool hz = false;
+    bool nonst = false;  // a scanned corridor holds another chain's active or stalled disk
+    bool viol = false;   // CONT: a scanned corridor disk fails Eq. 2
     unsigned long long emask = 0ull;
 
     double thr_first = 0.0;  // threshold of the pass's first column (column 0: scanned)
@@ -312,6 +323,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             if (dbits(la) < dbits(ay)) ay = la;
         }
         const bool corr = cst && dbits(ay) < dbits(s.d);
+        const bool ncs = cand && own != OWN_STATIC && dbits(ay) < dbits(s.d);
         double b = 0.0;
         if (__any_sync(FULL, corr)) b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(ay, ay)));
         double dx = __dsub_rn(xj, r.xi);
@@ -326,10 +338,13 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         }
         // lazy frame: a disk that became static after the active disk passed
         // it (t_i + tau < t_j) is one lap away; t_j = +0 never is
-        bool behind = false;
+        bool behind = false, hzv = false;
         const bool tnz = tau != INFINITY && dbits(tj) != 0ull;
         if (__any_sync(FULL, tnz)) {
-            behind = tnz && dbits(__dadd_rn(r.ti, tau)) < dbits(tj);
+            const double sum = __dadd_rn(r.ti, tau);
+            behind = tnz && dbits(sum) < dbits(tj);
+            // the horizon condition t_i + tau_ij > t_j (Eq. 2, strict)
+            if (MODE == MODE_CONT) hzv = tnz && !(dbits(sum) > dbits(tj));
             if (__any_sync(FULL, behind) && behind) tau = __dadd_rn(tau, s.L);
         }
         const unsigned long long tb = dbits(tau);
@@ -423,7 +438,24 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             for (int q = 0; q < nm; ++q) member |= __shfl_sync(FULL, my_member, q) == hq;
             foreign = !member;
         } else if (scanned && sl == 0) {
-            foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
+            const int h = (int)(holder - 1u);
+            int hc = __ldcg(s.comp_of + h);
+            if (MODE == MODE_CONT && nm < 0 && hc == h && hc != root && __ldcg(s.fin + h) == 1 &&
+                !__ldcg(s.nocont + h)) {
+                // a chain in no component, its pass-1 run final and free of
+                // active disks: the component takes it over (its cells
+                // become the component's; its run stays as it is)
+                const int old = atomicCAS(s.comp_of + h, h, root);
+                if (old == h) {
+                    // its cells now hold this component's events: a later
+                    // merge that reaches it must take the component along
+                    uf_union(s.uf, h, root);
+                    hc = root;
+                } else if (old == root) {
+                    hc = root;
+                }
+            }
+            foreign = hc != root;
         }
         if (foreign) {
             conflict = true;
@@ -432,6 +464,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // Eq. 2 (statement 5) on every scanned candidate touched in this window:
         // cannot fail while the cells are held by a lone chain; an assertion.
         if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
+        if (scanned && ncs) nonst = true;
+        if (MODE == MODE_CONT && scanned && hzv) viol = true;
         if (!dneg(thr_next) && dbits(thr_next) > cur_eps) break;
         thr_first = thr_next;
     }
@@ -441,6 +475,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     o.cy = cyi;
     o.mlast = mlast;
     o.emask = emask;
+    o.nonstatic = __ballot_sync(FULL, nonst) != 0u;
+    o.viol = MODE == MODE_CONT ? __ballot_sync(FULL, viol) != 0u : 0;
     o.conflict = 0;
     o.partner = NONE;
     const unsigned cb = __ballot_sync(FULL, conflict);
@@ -682,8 +718,11 @@ __global__ void k_leg_begin(Dev s) {
 // meets a conflict.
 template <int C>
 __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
-    if (s.status[c] != ST_RUNNING) return;
     const int lane = threadIdx.x & 31;
+    if (s.status[c] != ST_RUNNING) {
+        if (lane == 0) s.nocont[c] = 0;
+        return;
+    }
     ChainReg r;
     r.iloc = s.aloc[c];
     r.i = s.ci[c];
@@ -698,9 +737,11 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
     int32_t cas_rec = -1;           // record of that lift, while unchecked
     bool blocked = false;
+    bool nonstatic = false;  // a scan met another chain's active or stalled disk
     uint32_t lifts = 0;
     while (st == ST_RUNNING) {
         const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r, tw);
+        nonstatic |= o.nonstatic != 0;
         if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
             const uint32_t old = __shfl_sync(FULL, cas_old, 0);
             if (old != OWN_STATIC) {
@@ -712,6 +753,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
                     s.partner[c] = (int32_t)(old & OWN_CHAIN);
                     atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
                 }
+                nonstatic = true;
                 blocked = true;
                 break;
             }
@@ -740,6 +782,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     if (lane == 0) {
         // events before the blocking time, and all before the window, are exact
         s.vt[c] = blocked ? fmax(r.ti, tw) : INFINITY;
+        s.nocont[c] = nonstatic;
         s.status[c] = st;
         s.aloc[c] = r.iloc;
         s.ci[c] = r.i;
@@ -1032,7 +1075,7 @@ __device__ void finish_component(const Dev &s, const int32_t *mem, int m, int ro
         }
     } else {
         for (int e = lane; e < m; e += 32) {
-            s.fin[mem[e]] = 1;
+            s.fin[mem[e]] = 2;
             s.vt[mem[e]] = INFINITY;
         }
     }
@@ -1073,6 +1116,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
     ev.cx = ev.cy = 0;
     ev.mlast = -1;
     ev.emask = 0ull;
+    ev.nonstatic = ev.viol = 0;
     bool abort = false;
     int met = -1;
     // computes member q's next event into lane q's registers
@@ -1295,6 +1339,7 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         o.cx = 0;
         o.mlast = -1;  // no recorded empty slots: move_active reads the new cell
         o.emask = 0ull;
+        o.nonstatic = o.viol = 0;
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
         uint32_t nl = 0, dummy = 0;
@@ -1342,8 +1387,73 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
 // Component q of the current round: roll its members back to T*, then redo
 // them in global event-time order (Alg. 2) while claiming cells for the
 // component (one warp).
+// First repair round of a claim window: the blocked members continue from
+// where they stopped, one after another, over the state the other members
+// left. Pass 1 was a run of Alg. 4 (chains advanced one at a time: each
+// chain's cells were its own) in which every step satisfied the horizon
+// condition; if no member's pass 1 met another chain's active or stalled
+// disk, and every continued step satisfies the horizon condition (Eq. 2) for
+// every scanned corridor disk and meets no active or stalled disk either, the
+// whole run is one of Alg. 4 without a horizon violation, which by Lemma 2
+// ends where Alg. 2 ends: nothing has to be redone. Otherwise the caller
+// rolls the component back to T* and replays it in global order.
+enum { CONT_DONE = 0, CONT_FAIL = 1, CONT_FOREIGN = 2 };
+
 template <int C>
-__device__ void repair_component(const Dev &s, int q, int round, double tend) {
+__device__ int continue_component(const Dev &s, const int32_t *mem, int m, int root, int round,
+                                  double tw, double tend, int *met) {
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    for (int e = lane; e < m; e += 32) bad |= s.nocont[mem[e]] != 0;
+    if (__any_sync(FULL, bad)) return CONT_FAIL;
+    // members by comp_of; up to 32 members the component may take over chains
+    // that are in no component (the replay that a failure falls back to then
+    // tests membership against its own member list, so it leaves them alone)
+    const int nm = m <= 32 ? -1 : 0;
+    const int my_member = lane < m ? mem[lane] : -1;
+    uint32_t cnt = 0;
+    for (int e = 0; e < m; ++e) {
+        const int c = mem[e];
+        if (s.status[c] != ST_BLOCKED) continue;
+        ChainReg r;
+        r.iloc = s.aloc[c];
+        r.i = s.ci[c];
+        r.xi = s.cx[r.iloc];
+        r.yi = s.cy[r.iloc];
+        r.ti = s.tc[c];
+        r.D = s.D[c];
+        int32_t nrec = s.nrec[c];
+        int st = ST_RUNNING;
+        while (st == ST_RUNNING) {
+            const StepOut o = scan_step<C, MODE_CONT>(s, c, root, r, tw, nm, my_member);
+            if (o.conflict) {
+                *met = (int)o.partner;
+                return CONT_FOREIGN;
+            }
+            if (o.viol || o.nonstatic) return CONT_FAIL;
+            const unsigned long long T = dbits(__dadd_rn(r.ti, o.tau));
+            if (!(T < dbits(tend))) break;  // pauses at the window end
+            if (T < dbits(tw)) return CONT_FAIL;
+            uint32_t nl = 0, unused = 0;
+            st = commit_step<C>(s, c, r, o, false, ((uint32_t)round << 24) | cnt++, nrec, &nl,
+                                &unused);
+            if (st == ST_BLOCKED) return CONT_FAIL;  // out of records or slots
+            ++nrec;
+        }
+        if (lane == 0) {
+            s.status[c] = st;
+            s.aloc[c] = r.iloc;
+            s.ci[c] = r.i;
+            s.tc[c] = r.ti;
+            s.D[c] = r.D;
+        }
+        __syncwarp();
+    }
+    return CONT_DONE;
+}
+
+template <int C>
+__device__ void repair_component(const Dev &s, int q, int round, double tw, double tend) {
     const int lane = threadIdx.x & 31;
     const int root = s.comp_root[q];
     const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
@@ -1352,8 +1462,23 @@ __device__ void repair_component(const Dev &s, int q, int round, double tend) {
     for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
-    rollback_members(s, mem, m, Ts);
     if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
+    if (round == 1) {
+        int met = -1;
+        const int how = continue_component<C>(s, mem, m, root, round, tw, tend, &met);
+        if (how == CONT_DONE) {
+            if (lane == 0) atomicAdd(s.lc + LC_CONTINUED, (unsigned long long)m);
+            finish_component(s, mem, m, root, false, -1, Ts);
+            return;
+        }
+        if (how == CONT_FOREIGN) {
+            // the replay of the merged component rolls back to T* (all of
+            // this round's events lie after it)
+            finish_component(s, mem, m, root, true, met, Ts);
+            return;
+        }
+    }
+    rollback_members(s, mem, m, Ts);
     if (m <= 32)
         repair_small<C>(s, mem, m, root, Ts, round, tend);
     else
@@ -1368,7 +1493,7 @@ __global__ void k_repair(Dev s, int round) {
         if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
         q = __shfl_sync(FULL, q, 0);
         if (q >= s.ctl[CTL_NCOMP]) return;
-        repair_component<C>(s, q, round, INFINITY);
+        repair_component<C>(s, q, round, 0.0, INFINITY);
     }
 }
 
@@ -1437,6 +1562,7 @@ struct RepCtl {
     int64_t legs;           // legs completed in this run
     int64_t conflict_legs;
     int64_t repaired;
+    int64_t continued;
     int64_t horizon;
     int64_t order_err;
     int64_t leg_index0;     // leg index of this run's first leg (lifting log)
@@ -1662,7 +1788,8 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                     if (q >= ncomp) break;
                     const int r = find_rep(b.comp_base, R, q);
                     const Dev &s = b.reps[r];
-                    repair_component<C>(s, q - b.comp_base[r], round, window_end(s, w));
+                    repair_component<C>(s, q - b.comp_base[r], round, window_start(s, w),
+                                        window_end(s, w));
                 }
                 if (!grid_barrier(b, &sflag)) return;
                 check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 2 + round);
@@ -1695,6 +1822,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             c.legs += 1;
             c.conflict_legs += flag;
             c.repaired += (int64_t)lc[LC_REPAIRED];
+            c.continued += (int64_t)lc[LC_CONTINUED];
             c.horizon += (int64_t)lc[LC_HORIZON];
             c.order_err += (int64_t)lc[LC_ORDER];
             if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) c.err = 1;
@@ -1757,6 +1885,7 @@ struct ecmc_ctx {
     int64_t lifts_total = 0;
     int64_t conflict_legs = 0;
     int64_t repaired = 0;
+    int64_t continued = 0;
     int64_t horizon = 0;
     int64_t order_err = 0;
     int64_t inconsistent = 0;
@@ -1885,6 +2014,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.tc, k));
     chk(dalloc(ctx, &s.status, k));
     chk(dalloc(ctx, &s.partner, k));
+    chk(dalloc(ctx, &s.nocont, k));
     chk(dalloc(ctx, &s.nrec, k));
     chk(dalloc(ctx, &s.nlift, k));
     chk(dalloc(ctx, &s.rec, k * (size_t)s.cap));
@@ -2153,6 +2283,7 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         c->lifts_total += q.lifts;
         c->conflict_legs += q.conflict_legs;
         c->repaired += q.repaired;
+        c->continued += q.continued;
         c->horizon += q.horizon;
         c->order_err += q.order_err;
         c->prof.pass1_launches += q.legs;
@@ -2314,6 +2445,7 @@ extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
     out->legs = ctx->legs_total;
     out->conflict_legs = ctx->conflict_legs;
     out->repaired_chains = ctx->repaired;
+    out->continued_chains = ctx->continued;
     out->horizon_asserts = ctx->horizon;
     out->order_errors = ctx->order_err;
     out->device_ms = ctx->device_ms;
@@ -2438,6 +2570,7 @@ static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t n
     s.tc = cv.take<double>(k);
     s.status = cv.take<int32_t>(k);
     s.partner = cv.take<int32_t>(k);
+    s.nocont = cv.take<int32_t>(k);
     s.nrec = cv.take<int32_t>(k);
     s.nlift = cv.take<int32_t>(k);
     s.ev_T = cv.take<double>(k);

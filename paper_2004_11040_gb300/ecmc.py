@@ -39,7 +39,8 @@ class ecmc_params(C.Structure):
 class ecmc_stats_t(C.Structure):
     _fields_ = [("liftings", C.c_int64), ("legs", C.c_int64), ("conflict_legs", C.c_int64),
                 ("repaired_chains", C.c_int64), ("horizon_asserts", C.c_int64),
-                ("order_errors", C.c_int64), ("device_ms", C.c_double)]
+                ("order_errors", C.c_int64), ("device_ms", C.c_double),
+                ("continued_chains", C.c_int64)]
 
 
 class ecmc_profile_t(C.Structure):

@@ -182,3 +182,20 @@ def test_claim_windows_config2_and_random():
 def test_claim_windows_config3_one_leg():
     s = synth.lattice_start(1024, 0.72, 4096, seed=3)
     assert_parity(s, 1.0, 1, windows=16)
+
+
+def test_repairs_by_continuation_and_takeover_n1m():
+    """N = 2^20 with 16384 chains: most conflict components are finished by
+    continuing their blocked chains (and taking over chains in no component);
+    the rest by rollback and replay. Bit-exact either way."""
+    s = synth.lattice_start(1024, 0.72, 16384, seed=5)
+    flags, st = assert_parity(s, 1.0, 1, windows=4)
+    assert flags.all()
+    assert 0 < st["continued_chains"] < st["repaired_chains"]
+
+
+def test_repairs_by_continuation_random_2d():
+    """Cross-row liftings: continuation fails where chains really interact."""
+    s = synth.rsa_start(3000, 0.45, 120, seed=13)
+    flags, st = assert_parity(s, 1.5, 3, windows=3)
+    assert st["repaired_chains"] > 0
