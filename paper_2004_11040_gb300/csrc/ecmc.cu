@@ -212,8 +212,9 @@ __device__ void uf_union(int32_t *p, int a, int b);
 
 // nm > 0 (COMP, CONT): the component's members are the chains my_member of
 // lanes 0..nm-1, so a claim's holder is tested with shuffles instead of a
-// load; nm = 0: by comp_of; nm < 0 (CONT): by comp_of, and a chain that is in
-// no component is taken over by this one.
+// load; nm = 0: by comp_of; nm < 0 (CONT): the -nm members in the lanes'
+// registers, then comp_of, and a chain that is in no component is taken
+// over by this one.
 template <int C, int MODE>
 __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, double tw,
                              int nm = 0, int my_member = -1) {
@@ -432,30 +433,31 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         bool foreign = false;
         if (MODE == MODE_PASS1) {
             foreign = scanned && sl == 0 && holder != mine;
-        } else if (nm > 0) {
+        } else if (nm != 0) {
             const int hq = (scanned && sl == 0) ? (int)(holder - 1u) : -1;
             bool member = hq < 0;
-            for (int q = 0; q < nm; ++q) member |= __shfl_sync(FULL, my_member, q) == hq;
+            const int nmem = nm > 0 ? nm : -nm;
+            for (int q = 0; q < nmem; ++q) member |= __shfl_sync(FULL, my_member, q) == hq;
+            if (MODE == MODE_CONT && nm < 0 && !member) {
+                // not a listed member: taken over earlier, or takeable now
+                const int h = hq;
+                int hc = __ldcg(s.comp_of + h);
+                if (hc == h && hc != root && __ldcg(s.fin + h) == 1 && !__ldcg(s.nocont + h)) {
+                    const int old = atomicCAS(s.comp_of + h, h, root);
+                    if (old == h) {
+                        // its cells now hold this component's events: a later
+                        // merge that reaches it must take the component along
+                        uf_union(s.uf, h, root);
+                        hc = root;
+                    } else if (old == root) {
+                        hc = root;
+                    }
+                }
+                member = hc == root;
+            }
             foreign = !member;
         } else if (scanned && sl == 0) {
-            const int h = (int)(holder - 1u);
-            int hc = __ldcg(s.comp_of + h);
-            if (MODE == MODE_CONT && nm < 0 && hc == h && hc != root && __ldcg(s.fin + h) == 1 &&
-                !__ldcg(s.nocont + h)) {
-                // a chain in no component, its pass-1 run final and free of
-                // active disks: the component takes it over (its cells
-                // become the component's; its run stays as it is)
-                const int old = atomicCAS(s.comp_of + h, h, root);
-                if (old == h) {
-                    // its cells now hold this component's events: a later
-                    // merge that reaches it must take the component along
-                    uf_union(s.uf, h, root);
-                    hc = root;
-                } else if (old == root) {
-                    hc = root;
-                }
-            }
-            foreign = hc != root;
+            foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
         }
         if (foreign) {
             conflict = true;
@@ -1060,8 +1062,12 @@ __device__ void resume_state(const Dev &s, int c, uint32_t &loc, uint32_t &id, d
 }
 
 // After a component's redo: record abort or success for the next round.
+// keep_vt (success): the members' vt becomes `now` instead of infinity, so
+// that a later merge rolls them back to `now` or earlier (their slot
+// operations were not applied in time order, so none may stay on top of an
+// undone earlier one).
 __device__ void finish_component(const Dev &s, const int32_t *mem, int m, int root, bool abort,
-                                 int met, double now) {
+                                 int met, double now, bool keep_vt = false) {
     const int lane = threadIdx.x & 31;
     if (abort) {
         // events before `now` are exact; the chain met joins next round
@@ -1076,7 +1082,7 @@ __device__ void finish_component(const Dev &s, const int32_t *mem, int m, int ro
     } else {
         for (int e = lane; e < m; e += 32) {
             s.fin[mem[e]] = 2;
-            s.vt[mem[e]] = INFINITY;
+            s.vt[mem[e]] = keep_vt ? now : INFINITY;
         }
     }
     __syncwarp();
@@ -1406,10 +1412,13 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
     bool bad = false;
     for (int e = lane; e < m; e += 32) bad |= s.nocont[mem[e]] != 0;
     if (__any_sync(FULL, bad)) return CONT_FAIL;
-    // members by comp_of; up to 32 members the component may take over chains
-    // that are in no component (the replay that a failure falls back to then
-    // tests membership against its own member list, so it leaves them alone)
-    const int nm = m <= 32 ? -1 : 0;
+    // up to 32 members: members by the lanes' registers, and the component may
+    // take over chains that are in no component (the replay that a failure
+    // falls back to tests membership against its own member list, so it
+    // leaves them alone); more members: by comp_of, no takeover. A failure
+    // rolls back to T*: the continued events lie after it, and undoing them
+    // all first keeps the slot operations in last-in first-out order.
+    const int nm = m <= 32 ? -m : 0;
     const int my_member = lane < m ? mem[lane] : -1;
     uint32_t cnt = 0;
     for (int e = 0; e < m; ++e) {
@@ -1462,13 +1471,16 @@ __device__ void repair_component(const Dev &s, int q, int round, double tw, doub
     for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
+    Ts = fmax(Ts, tw);  // earlier windows are final
     if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
     if (round == 1) {
         int met = -1;
         const int how = continue_component<C>(s, mem, m, root, round, tw, tend, &met);
         if (how == CONT_DONE) {
             if (lane == 0) atomicAdd(s.lc + LC_CONTINUED, (unsigned long long)m);
-            finish_component(s, mem, m, root, false, -1, Ts);
+            // a later merge must undo all continued events (they were applied
+            // chain by chain, not in time order): it rolls back to T* or earlier
+            finish_component(s, mem, m, root, false, -1, Ts, true);
             return;
         }
         if (how == CONT_FOREIGN) {
