@@ -1199,6 +1199,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         const uint32_t cell_a = r.iloc / C;
         const uint32_t cell_j = o.lift ? o.jloc / C : cell_a;
         uint32_t nl = 0, dummy = 0;
+        const double y_moved = r.yi;  // the moved disk keeps its y
         const int st = commit_step<C>(s, bc, r, o, false, ((uint32_t)round << 24) | cnt++,
                                       __shfl_sync(FULL, my_nrec, bq), &nl, &dummy);
         if (st == ST_BLOCKED) {  // out of records or slots: reported by the host
@@ -1216,10 +1217,32 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
             my_t = r.ti;
             my_D = r.D;
         }
-        const bool redo = has && my_st == ST_RUNNING &&
-                          (lane == bq || footprint_has(ev.cx, ev.cy, ev.mlast, cell_a, s.nc) ||
-                           footprint_has(ev.cx, ev.cy, ev.mlast, cell_b, s.nc) ||
-                           footprint_has(ev.cx, ev.cy, ev.mlast, cell_j, s.nc));
+        // a member's pending event can change only through a disk in its
+        // corridor (|dy| < d from its active disk), or through the empty slots
+        // of its active disk's row (where it will move)
+        auto near = [&](double y) {
+            double a = fabs(__dsub_rn(y, my_y));
+            if (dbits(__dsub_rn(s.L, a)) < dbits(a)) a = __dsub_rn(s.L, a);
+            return dbits(a) < dbits(s.d);
+        };
+        auto in_row = [&](uint32_t cell) {
+            return (int)(cell / (uint32_t)s.nc) == ev.cy &&
+                   footprint_has(ev.cx, ev.cy, ev.mlast, cell, s.nc);
+        };
+        bool redo = false;
+        if (has && my_st == ST_RUNNING) {
+            if (lane == bq) {
+                redo = true;
+            } else {
+                const bool nm = near(y_moved);
+                redo = (footprint_has(ev.cx, ev.cy, ev.mlast, cell_a, s.nc) &&
+                        (nm || in_row(cell_a))) ||
+                       (footprint_has(ev.cx, ev.cy, ev.mlast, cell_b, s.nc) &&
+                        (nm || in_row(cell_b))) ||
+                       (o.lift && footprint_has(ev.cx, ev.cy, ev.mlast, cell_j, s.nc) &&
+                        near(o.yj));
+            }
+        }
         unsigned b = __ballot_sync(FULL, redo);
         while (b && !abort) {
             const int q = __ffs(b) - 1;
