@@ -205,6 +205,21 @@ def host_info():
     return {"nproc": os.cpu_count(), "model": model}
 
 
+def aggregate(dev_ms, lifts, ws, device="cpu"):
+    """Whole-job numbers of a replicas-only run: the slowest rank's time and
+    all ranks' liftings (a rank that exits early simply contributes nothing
+    beyond its own count). With ws == 1 the rank's own numbers."""
+    if ws <= 1:
+        return dev_ms, lifts
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([dev_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ll = torch.tensor([float(lifts)], device=device, dtype=torch.float64)
+    dist.all_reduce(ll, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(ll.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -283,16 +298,7 @@ def run_ours(a):
             lifts += e["liftings"] - b["liftings"]
         barrier()
     st1, pr1 = sysm.stats(), sysm.profile()
-    t_max = dev_ms
-    tot_lifts = lifts
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ll = torch.tensor([lifts], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ll, op=dist.ReduceOp.SUM)
-        tot_lifts = int(ll.item())
+    t_max, tot_lifts = aggregate(dev_ms, lifts, ws, device="cuda")
     value = tot_lifts / (t_max / 1000.0)
 
     # the hot path is one persistent kernel launch (k_run) per step
