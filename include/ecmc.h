@@ -130,6 +130,22 @@ int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t event_budget,
  */
 int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *active);
 
+/*
+ * ecmc_set_direction -- direction of motion for the following legs
+ * (Sec. 1: in the periodic square box the direction must change at some
+ * breakpoints for ECMC to be irreducible; the legs themselves are as in
+ * Alg. 2 with v along that direction).
+ *   direction  0: +x (the state after ecmc_create); 1: +y.
+ * Call between runs (the state is always at a breakpoint then). The context
+ * keeps motion along +x of its own frame and is transposed in place (x and y
+ * swapped, cells (r, c) <-> (c, r)); ecmc_positions returns x and y in the
+ * caller's frame; the xi, xj of ecmc_liftings are along the direction of
+ * motion. Local times are reset to 0 (they are leg-relative), and the lifting
+ * log is kept. Synchronises the context's stream.
+ * Errors: EINVAL (direction not 0 or 1), ECUDA.
+ */
+int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction);
+
 /* ecmc_stats -- counters accumulated since ecmc_create (host struct). */
 int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
 

@@ -1575,6 +1575,50 @@ __global__ void k_export(Dev s, double *x, double *y, double *t) {
     if (t) t[id] = s.ct[q];
 }
 
+// Direction change at a breakpoint (Sec. 1: in the periodic box the direction
+// must change now and then for the algorithm to be irreducible). Motion stays
+// +x in the context's frame; moving along +y of the caller's frame is moving
+// along +x of the transposed frame, so the context is transposed in place:
+// cell (r, c) <-> (c, r), slot for slot, with x and y swapped. Local times are
+// cleared (the next leg starts at 0, and the event records that named the
+// slots to clear are dropped).
+template <int C>
+__global__ void k_transpose(Dev s) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)s.nc * s.nc) return;
+    const int r = (int)(q / s.nc), c = (int)(q % s.nc);
+    if (r > c) return;
+    const uint32_t a = (uint32_t)q, b = (uint32_t)c * (uint32_t)s.nc + (uint32_t)r;
+    for (int sl = 0; sl < C; ++sl) {
+        const uint32_t la = a * C + sl, lb = b * C + sl;
+        const double xa = s.cx[la], ya = s.cy[la], xb = s.cx[lb], yb = s.cy[lb];
+        const uint32_t ia = s.cid[la], ib = s.cid[lb], oa = s.cown[la], ob = s.cown[lb];
+        s.cx[la] = yb;
+        s.cy[la] = xb;
+        s.cid[la] = ib;
+        s.cown[la] = ob;
+        s.ct[la] = 0.0;
+        s.cx[lb] = ya;
+        s.cy[lb] = xa;
+        s.cid[lb] = ia;
+        s.cown[lb] = oa;
+        s.ct[lb] = 0.0;
+    }
+}
+
+template <int C>
+__global__ void k_transpose_chains(Dev s) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    auto tr = [&](uint32_t loc) {
+        const uint32_t cell = loc / C, rr = cell / (uint32_t)s.nc, cc = cell % (uint32_t)s.nc;
+        return (cc * (uint32_t)s.nc + rr) * C + loc % C;
+    };
+    s.aloc[c] = tr(s.aloc[c]);
+    s.aloc0[c] = tr(s.aloc0[c]);
+    s.nrec[c] = 0;
+}
+
 __global__ void k_export_active(Dev s, int32_t *active) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= s.k) return;
@@ -1926,6 +1970,7 @@ struct ecmc_ctx {
     int64_t inconsistent = 0;
     double device_ms = 0.0;
     bool log_overflow = false;
+    int32_t direction = 0;  // 0: +x; 1: +y (the context is stored transposed)
 };
 
 static std::string g_create_err;
@@ -2456,10 +2501,12 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
         return fail(ctx, ECMC_ENOMEM, "positions scratch");
     }
     if (x || y || t) {
+        // in a transposed context the stored x is the caller's y
+        double *ex = ctx->direction ? dy : dx, *ey = ctx->direction ? dx : dy;
         if (ctx->C == 4)
-            k_export<4><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy, dt);
+            k_export<4><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, ex, ey, dt);
         else
-            k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, dx, dy, dt);
+            k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, ex, ey, dt);
     }
     if (active) k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
     cudaError_t e = cudaGetLastError();
@@ -2471,6 +2518,27 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
     if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("positions: ") + cudaGetErrorString(e));
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction) {
+    if (!ctx) return ECMC_EINVAL;
+    if (direction != 0 && direction != 1) return fail(ctx, ECMC_EINVAL, "direction must be 0 (+x) or 1 (+y)");
+    if (direction == ctx->direction) return ECMC_OK;
+    Dev &s = ctx->s;
+    cudaStream_t st = ctx->stream;
+    const int64_t ncell = (int64_t)s.nc * s.nc;
+    if (ctx->C == 4) {
+        k_transpose<4><<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(s);
+        k_transpose_chains<4><<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s);
+    } else {
+        k_transpose<8><<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(s);
+        k_transpose_chains<8><<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("set_direction: ") + cudaGetErrorString(e));
+    ctx->direction = direction;
     return ECMC_OK;
 }
 

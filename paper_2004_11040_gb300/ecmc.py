@@ -26,7 +26,7 @@ ECMC_INPUT_DEVICE = 0x2
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
            "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
-           "ecmc_batch_destroy", "ecmc_leg_noalloc")
+           "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction")
 
 
 class ecmc_params(C.Structure):
@@ -80,6 +80,8 @@ def load(path: str | None = None):
     lib.ecmc_run_to_breakpoint.restype = C.c_int
     lib.ecmc_positions.argtypes = [vp, vp, vp, vp, vp]
     lib.ecmc_positions.restype = C.c_int
+    lib.ecmc_set_direction.argtypes = [vp, C.c_int32]
+    lib.ecmc_set_direction.restype = C.c_int
     lib.ecmc_stats.argtypes = [vp, C.POINTER(ecmc_stats_t)]
     lib.ecmc_stats.restype = C.c_int
     lib.ecmc_profile.argtypes = [vp, C.POINTER(ecmc_profile_t)]
@@ -146,6 +148,11 @@ def ecmc_run_to_breakpoint(ctx, n_legs: int, event_budget: int = 0, leg_flags_ou
 
 def ecmc_positions(ctx, x=None, y=None, t=None, active=None):
     _check(load().ecmc_positions(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(active)), ctx)
+
+
+def ecmc_set_direction(ctx, direction: int):
+    """0: legs move +x (after creation); 1: legs move +y."""
+    _check(load().ecmc_set_direction(ctx, int(direction)), ctx)
 
 
 def ecmc_stats(ctx) -> dict:
@@ -258,6 +265,9 @@ class System:
 
     def stats(self):
         return ecmc_stats(self.ctx)
+
+    def set_direction(self, direction: int):
+        ecmc_set_direction(self.ctx, direction)
 
     def liftings(self):
         return ecmc_liftings(self.ctx)

@@ -199,3 +199,33 @@ def test_repairs_by_continuation_random_2d():
     s = synth.rsa_start(3000, 0.45, 120, seed=13)
     flags, st = assert_parity(s, 1.5, 3, windows=3)
     assert st["repaired_chains"] > 0
+
+
+@pytest.mark.parametrize("kind", ["lattice", "rsa"])
+def test_direction_alternation_equals_oracle_on_swapped_frame(kind):
+    """Legs alternating +x / +y: a +y leg is the oracle's +x leg with x and y
+    exchanged. Positions and active disks bit for bit after every leg."""
+    if kind == "lattice":
+        s = synth.lattice_start(24, 0.70, 12, seed=4)
+        ell = 1.0
+    else:
+        s = synth.rsa_start(500, 0.45, 20, seed=6)
+        ell = 1.5
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, ell)
+    x, y, act = s.x.copy(), s.y.copy(), s.active.copy()
+    for leg in range(6):
+        d = leg % 2
+        sysm.set_direction(d)
+        sysm.run(1)
+        if d == 0:
+            r = O.run_leg(x, y, act, s.box, ell, log=False)
+            x, act = r.x, r.active
+        else:
+            r = O.run_leg(y, x, act, s.box, ell, log=False)
+            y, act = r.x, r.active
+        gx, gy, _, ga = sysm.positions()
+        assert np.array_equal(gx, x) and np.array_equal(gy, y), leg
+        assert np.array_equal(ga, act), leg
+    st = sysm.stats()
+    assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
+    sysm.close()
