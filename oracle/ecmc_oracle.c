@@ -57,6 +57,16 @@
  *     fx = x_i - cx*a and eps = L * 2^-30. The margin makes the cell scan
  *     return the same lifting as the all-pairs definition (tested).
  *   - An "event" is a lifting i -> j; stalls are not events.
+ *   - Constraint graph G(3) (Sec. 3.1): the arrows of disk i are, in each of
+ *     three corridors of the minimum-image dy = y_j - y_i -- centre
+ *     |dy| < d/2, upper d/2 <= dy < d, lower -d < dy <= -d/2 -- the disk of
+ *     least (tau_ij, j) with tau as above (all local times 0: the graph is
+ *     taken from a synchronised configuration, the start of a leg), or none
+ *     if the corridor is empty. Disks closer than d in y cannot pass one
+ *     another under v = (1, 0), so the arrows hold for as long as v does.
+ *     With search == 2 every step takes its candidates from the arrows of the
+ *     active disk alone, and the conflict flag is computed from the disks a
+ *     step reads (the active disk and its arrow targets) instead of cells.
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,7 +90,7 @@ typedef struct {
     int64_t n;
     double L, d, ell;
     int32_t nc;      /* cells per side (scan and claims) */
-    int32_t search;  /* 0: all pairs (definition), 1: cell scan */
+    int32_t search;  /* 0: all pairs (definition), 1: cell scan, 2: constraint graph */
     int32_t windows; /* claim windows per leg (>= 1), see orc_leg */
     int32_t pad;
 } orc_params;
@@ -114,6 +124,26 @@ static double wrap_add(double x, double dx, double L) {
     double r = x + dx;
     if (r >= L) r -= L;
     return r;
+}
+
+/*
+ * Corridor of j as seen from i (Sec. 3.1): 0 for |dy| < d/2, 1 for
+ * d/2 <= dy < d, 2 for -d < dy <= -d/2, -1 for |dy| >= d; dy is the minimum
+ * image of y_j - y_i, and |dy| is computed exactly as in perp_dist.
+ */
+static int corridor(double yj, double yi, double L, double d) {
+    double dy = yj - yi;
+    double a = fabs(dy);
+    int flip = 0;
+    if (L - a < a) {
+        a = L - a;
+        flip = 1;
+    }
+    if (!(a < d)) return -1;
+    if (a < 0.5 * d) return 0;
+    int up = dy > 0.0;
+    if (flip) up = !up;
+    return up ? 1 : 2;
 }
 
 /* End of claim window w of W in a leg of length ell (the last one is open). */
@@ -301,6 +331,120 @@ static int in_footprint(const step_t *s, int cell, int nc) {
     return dm <= s->mlast;
 }
 
+/* ------------------------------------------- constraint graph G(3), Sec. 3.1 */
+
+/* Arrows of i by the definition: every other disk is examined. */
+static void arrows_allpairs(const orc_params *p, const double *x, const double *y, int i,
+                            int32_t out[3]) {
+    double bt[3] = {INFINITY, INFINITY, INFINITY};
+    int bj[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    for (int64_t j = 0; j < p->n; ++j) {
+        if (j == i) continue;
+        int kc = corridor(y[j], y[i], p->L, p->d);
+        if (kc < 0) continue;
+        double tau = time_of_flight(x[i], y[i], x[j], y[j], p->L, p->d);
+        if (better(tau, (int)j, bt[kc], bj[kc])) {
+            bt[kc] = tau;
+            bj[kc] = (int)j;
+        }
+    }
+    for (int kc = 0; kc < 3; ++kc) out[kc] = bt[kc] == INFINITY ? -1 : bj[kc];
+}
+
+/*
+ * Arrows of i by the cell scan: columns cx, cx+1, ... of rows cy-1..cy+1
+ * (|dy| < d keeps j within one row of cells), stopping before column m >= 1
+ * once (m*a - fx) - d exceeds the best tau of every corridor by eps (no disk
+ * of a later column can then do better); a corridor that is still empty
+ * makes the scan go once round the box.
+ */
+static void arrows_cells(const orc_params *p, const cells_t *g, const double *x,
+                         const double *y, int i, int32_t out[3]) {
+    int nc = g->nc;
+    int cx = cell_coord(x[i], g), cy = cell_coord(y[i], g);
+    double fx = x[i] - (double)cx * g->a;
+    int rows[3] = {(cy + nc - 1) % nc, cy, (cy + 1) % nc};
+    double bt[3] = {INFINITY, INFINITY, INFINITY};
+    int bj[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    for (int m = 0; m < nc; ++m) {
+        if (m >= 1) {
+            double worst = bt[0];
+            if (bt[1] > worst) worst = bt[1];
+            if (bt[2] > worst) worst = bt[2];
+            double thr = ((double)m * g->a - fx) - p->d;
+            if (thr > worst + g->eps) break;
+        }
+        int col = (cx + m) % nc;
+        for (int r = 0; r < 3; ++r) {
+            for (int j = g->head[rows[r] * nc + col]; j >= 0; j = g->next[j]) {
+                if (j == i) continue;
+                int kc = corridor(y[j], y[i], p->L, p->d);
+                if (kc < 0) continue;
+                double tau = time_of_flight(x[i], y[i], x[j], y[j], p->L, p->d);
+                if (better(tau, j, bt[kc], bj[kc])) {
+                    bt[kc] = tau;
+                    bj[kc] = j;
+                }
+            }
+        }
+    }
+    for (int kc = 0; kc < 3; ++kc) out[kc] = bt[kc] == INFINITY ? -1 : bj[kc];
+}
+
+/*
+ * The graph as a step needs it: arrows of disk i from the configuration at
+ * the start of the leg (x0 and its cells g0), computed on first use.
+ */
+typedef struct {
+    const double *x0;
+    const cells_t *g0;
+    int32_t *arrow; /* [3n]; -2 = not computed yet */
+} graph_t;
+
+static const int32_t *graph_arrows(const orc_params *p, graph_t *G, const double *y, int i) {
+    int32_t *a = G->arrow + 3 * (int64_t)i;
+    if (a[0] == -2) arrows_cells(p, G->g0, G->x0, y, i, a);
+    return a;
+}
+
+/*
+ * Statements 1-9 with the candidates taken from the arrows of i; every disk
+ * read (i and each arrow target) is passed to claim().
+ */
+static step_t step_graph(const orc_params *p, graph_t *G, const double *x, const double *y,
+                         const double *t, const int8_t *tag, int i, double D,
+                         claim_fn claim, void *claim_ctx) {
+    const int32_t *a = graph_arrows(p, G, y, i);
+    if (claim) claim(i, claim_ctx);
+    double btau = INFINITY;
+    int bj = INT32_MAX;
+    for (int kc = 0; kc < 3; ++kc) {
+        int j = a[kc];
+        if (j < 0) continue;
+        if (claim) claim(j, claim_ctx);
+        if (!is_candidate(j, i, tag)) continue;
+        double tau = lazy_tof(p, x, y, t, i, j);
+        if (tau == INFINITY) continue;
+        if (better(tau, j, btau, bj)) {
+            btau = tau;
+            bj = j;
+        }
+    }
+    step_t s;
+    memset(&s, 0, sizeof s);
+    s.mlast = -1;
+    if (btau < D) {
+        s.lift = 1;
+        s.j = bj;
+        s.tau = btau;
+    } else {
+        s.lift = 0;
+        s.j = -1;
+        s.tau = D;
+    }
+    return s;
+}
+
 /* ------------------------------------------------ isolated runs (the flag) */
 
 typedef struct {
@@ -324,7 +468,7 @@ static void claim_record(int cell, void *vctx) {
  * events before t_end, recording the cells it scans (the last scan, whose
  * event lies at or after t_end, included); then restores x, t and the cells.
  */
-static int64_t isolated_chain(const orc_params *p, cells_t *g, double *x,
+static int64_t isolated_chain(const orc_params *p, cells_t *g, graph_t *G, double *x,
                               const double *y, double *t, int i0, double D0,
                               double t_end, claim_ctx_t *cc, int32_t *undo_i,
                               double *undo_x, double *undo_t, int64_t undo_cap,
@@ -333,7 +477,9 @@ static int64_t isolated_chain(const orc_params *p, cells_t *g, double *x,
     double D = D0;
     int64_t nu = 0, lifts = 0;
     for (;;) {
-        step_t s = step_cells(p, g, x, y, t, NULL, i, D, claim_record, cc);
+        step_t s = p->search == 2
+                       ? step_graph(p, G, x, y, t, NULL, i, D, claim_record, cc)
+                       : step_cells(p, g, x, y, t, NULL, i, D, claim_record, cc);
         if (!(t[i] + s.tau < t_end)) break;
         if (nu + 2 > undo_cap) {
             *overflow = 1;
@@ -379,11 +525,13 @@ typedef struct {
     step_t s;
 } event_t;
 
-static void compute_event(const orc_params *p, const cells_t *g, const double *x,
-                          const double *y, const double *t, const int8_t *tag,
-                          int i, double D, event_t *ev) {
+static void compute_event(const orc_params *p, const cells_t *g, graph_t *G,
+                          const double *x, const double *y, const double *t,
+                          const int8_t *tag, int i, double D, event_t *ev) {
     if (p->search == 0)
         ev->s = step_allpairs(p, x, y, t, tag, i, D);
+    else if (p->search == 2)
+        ev->s = step_graph(p, G, x, y, t, tag, i, D, NULL, NULL);
     else
         ev->s = step_cells(p, g, x, y, t, tag, i, D, NULL, NULL);
     ev->T = t[i] + ev->s.tau;
@@ -396,7 +544,7 @@ static void compute_event(const orc_params *p, const cells_t *g, const double *x
  *   active [k] in/out: chain c's active disk
  *   log    optional lifting log (appended at *log_n, capacity log_cap)
  *   flag   out: 1 iff the isolated claim sets of two chains share a cell
- *          (needs search == 1 or nc > 0; computed before the leg is run)
+ *          (search 0 or 1) or a disk (search 2), computed window by window
  *   lifts  out: number of liftings in this leg
  * Returns 0, or -1 on allocation failure, -2 on log/undo overflow,
  * -3 on bad parameters, -6 if an event was found earlier than the last one
@@ -416,7 +564,14 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
     double *D = (double *)malloc((size_t)k * sizeof(double));
     int8_t *run = (int8_t *)malloc((size_t)k);
     event_t *ev = (event_t *)malloc((size_t)k * sizeof(event_t));
-    int32_t *owner = (int32_t *)malloc((size_t)nc * nc * sizeof(int32_t));
+    /* claim owners: per cell, or per disk with the constraint graph */
+    int64_t n_claim = p->search == 2 ? n : (int64_t)nc * nc;
+    int32_t *owner = (int32_t *)malloc((size_t)n_claim * sizeof(int32_t));
+    /* constraint graph: arrows from the leg-start configuration */
+    graph_t G = {NULL, NULL, NULL};
+    double *x0 = NULL;
+    cells_t g0;
+    int have_g0 = 0;
     int64_t undo_cap = 1 << 20;
     int32_t *undo_i = (int32_t *)malloc((size_t)undo_cap * sizeof(int32_t));
     double *undo_x = (double *)malloc((size_t)undo_cap * sizeof(double));
@@ -431,6 +586,19 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
         rc = -3;
         goto done;
     }
+    if (p->search == 2) {
+        x0 = (double *)malloc((size_t)n * sizeof(double));
+        G.arrow = (int32_t *)malloc((size_t)n * 3 * sizeof(int32_t));
+        if (!x0 || !G.arrow || cells_init(&g0, p, x, y)) {
+            rc = -1;
+            goto done;
+        }
+        have_g0 = 1;
+        memcpy(x0, x, (size_t)n * sizeof(double));
+        for (int64_t q = 0; q < 3 * n; ++q) G.arrow[q] = -2;
+        G.x0 = x0;
+        G.g0 = &g0;
+    }
     for (int64_t j = 0; j < n; ++j) t[j] = 0.0;
     for (int c = 0; c < k; ++c) {
         tag[active[c]] = TAG_ACTIVE;
@@ -439,7 +607,7 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
         if (lifts_per_chain) lifts_per_chain[c] = 0;
     }
     for (int c = 0; c < k; ++c)
-        compute_event(p, &g, x, y, t, tag, active[c], D[c], &ev[c]);
+        compute_event(p, &g, &G, x, y, t, tag, active[c], D[c], &ev[c]);
     int64_t nl = 0;
     double now = 0.0;
     int any_conflict = 0;
@@ -447,7 +615,7 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
         const double t_end = window_end(p, w);
         /* conflict flag of the window: isolated runs from the current state */
         {
-            for (int64_t q = 0; q < (int64_t)nc * nc; ++q) owner[q] = -1;
+            for (int64_t q = 0; q < n_claim; ++q) owner[q] = -1;
             claim_ctx_t cc;
             cc.owner = owner;
             cc.conflict = 0;
@@ -455,8 +623,8 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
             for (int c = 0; c < k; ++c) {
                 if (!run[c]) continue;
                 cc.c = c;
-                isolated_chain(p, &g, x, y, t, active[c], D[c], t_end, &cc, undo_i, undo_x,
-                               undo_t, undo_cap, &overflow);
+                isolated_chain(p, &g, &G, x, y, t, active[c], D[c], t_end, &cc, undo_i,
+                               undo_x, undo_t, undo_cap, &overflow);
             }
             if (overflow) {
                 rc = -2;
@@ -525,13 +693,14 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
                 run[cb] = 0;
                 changed[nchanged++] = cell_of(xn, y[i], &g);
             }
-            /* recompute the events that the change can affect */
+            /* recompute the events that the change can affect (all of them
+               without a cell footprint to test against) */
             for (int c = 0; c < k; ++c) {
                 if (!run[c]) continue;
-                int redo = (c == cb) || p->search == 0;
+                int redo = (c == cb) || p->search != 1;
                 for (int q = 0; q < nchanged && !redo; ++q)
                     if (in_footprint(&ev[c].s, changed[q], nc)) redo = 1;
-                if (redo) compute_event(p, &g, x, y, t, tag, active[c], D[c], &ev[c]);
+                if (redo) compute_event(p, &g, &G, x, y, t, tag, active[c], D[c], &ev[c]);
             }
         }
     }
@@ -539,6 +708,9 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
     if (lifts) *lifts = nl;
 done:
     cells_free(&g);
+    if (have_g0) cells_free(&g0);
+    free(x0);
+    free(G.arrow);
     free(tag);
     free(D);
     free(run);
@@ -756,4 +928,36 @@ int orc_claim_set(const orc_params *p, const double *x_in, const double *y,
     free(t);
     free(seen);
     return cc.n > cap ? -2 : 0;
+}
+
+/*
+ * Arrows of the constraint graph G(3) (Sec. 3.1) for the disks ids[0..m-1]
+ * (for every disk when ids is NULL; m is then ignored): out[3q + kc] is the
+ * target in corridor kc (0 centre, 1 upper, 2 lower) or -1 when the corridor
+ * is empty. search 0: by the definition, every pair; search 1: by the cell
+ * scan that orc_leg uses with search == 2.
+ */
+int orc_graph3(const orc_params *p, const double *x, const double *y, int32_t search,
+               const int32_t *ids, int64_t m, int32_t *out) {
+    if (p->n <= 0 || p->nc < 3 || !(p->L / (double)p->nc > p->d)) return -3;
+    const int64_t cnt = ids ? m : p->n;
+    cells_t g;
+    int have = 0;
+    if (search != 0) {
+        if (cells_init(&g, p, x, y)) return -1;
+        have = 1;
+    }
+    for (int64_t q = 0; q < cnt; ++q) {
+        const int i = ids ? ids[q] : (int)q;
+        if (i < 0 || i >= p->n) {
+            if (have) cells_free(&g);
+            return -3;
+        }
+        if (search == 0)
+            arrows_allpairs(p, x, y, i, out + 3 * q);
+        else
+            arrows_cells(p, &g, x, y, i, out + 3 * q);
+    }
+    if (have) cells_free(&g);
+    return 0;
 }

@@ -5,8 +5,11 @@ baseline of ``bench.py`` use this module. The product path (the CUDA library)
 never imports or links it.
 
 The oracle computes Alg. 2 of the paper (ECMC with global time) between two
-breakpoints, the leg's conflict flag from isolated chain runs, and Alg. 4 for
-the Lemma 2 self-check; see the header of ``ecmc_oracle.c`` for the readings.
+breakpoints, the leg's conflict flag from isolated chain runs, Alg. 4 for the
+Lemma 2 self-check, and the constraint graph G(3) of Sec. 3.1; see the header
+of ``ecmc_oracle.c`` for the readings. ``search`` selects how a step finds its
+candidates: 0 every pair (the definition), 1 the cell scan, 2 the arrows of
+G(3); the events are those of Alg. 2 in every case, the flag depends on it.
 """
 from __future__ import annotations
 
@@ -74,6 +77,9 @@ def lib():
         _lib.orc_claim_set.argtypes = [C.POINTER(Params), dp, dp, C.c_int32, ip, C.c_int64,
                                        C.POINTER(C.c_int64)]
         _lib.orc_claim_set.restype = C.c_int
+        _lib.orc_graph3.argtypes = [C.POINTER(Params), dp, dp, C.c_int32, C.c_void_p, C.c_int64,
+                                    ip]
+        _lib.orc_graph3.restype = C.c_int
     return _lib
 
 
@@ -203,3 +209,26 @@ def claim_set(x, y, i0, L, ell, *, d=1.0, nc=None) -> np.ndarray:
     if rc != 0:
         raise OracleError(f"orc_claim_set failed: {rc}")
     return cells[: n_out.value].copy()
+
+
+def graph3(x, y, L, *, d=1.0, nc=None, search=0, ids=None) -> np.ndarray:
+    """Arrows of G(3) (Sec. 3.1): an int32 array [m, 3] (corridor 0 centre,
+    1 upper, 2 lower; -1 = empty corridor) for the disks ``ids`` (all disks by
+    default). search 0: every pair (the definition); 1: the cell scan."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if nc is None:
+        nc = default_cells(L, d)
+    p = Params(x.shape[0], L, d, 0.0, nc, 1, 1, 0)
+    if ids is None:
+        m = x.shape[0]
+        idp = None
+    else:
+        ida = np.ascontiguousarray(ids, dtype=np.int32)
+        m = ida.shape[0]
+        idp = ida.ctypes.data
+    out = np.zeros((m, 3), dtype=np.int32)
+    rc = lib().orc_graph3(C.byref(p), _dptr(x), _dptr(y), search, idp, m, _iptr(out))
+    if rc != 0:
+        raise OracleError(f"orc_graph3 failed: {rc}")
+    return out
