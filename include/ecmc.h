@@ -42,6 +42,8 @@ extern "C" {
 /* ecmc_params.flags */
 #define ECMC_LOG_LIFTINGS 0x1u /* keep every lifting for ecmc_liftings() */
 #define ECMC_INPUT_DEVICE 0x2u /* x, y, active passed to ecmc_create are device pointers */
+#define ECMC_GRAPH 0x4u        /* find liftings through the constraint graph G(3) (Sec. 3.1)
+                                  instead of the cell scan; see "Constraint-graph mode" */
 
 typedef struct ecmc_ctx ecmc_ctx;
 
@@ -53,7 +55,7 @@ typedef struct {
     int32_t n_chains;       /* k, 1 <= k <= n */
     int32_t cells_per_side; /* nc; 0 picks the largest nc with L/nc >= d*(1+2^-20).
                                Needs nc >= 3 and L/nc < 1.664*d. */
-    uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE */
+    uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE | ECMC_GRAPH */
     int32_t undo_cap;       /* per-chain event records per leg, < 2^24; 0 = 1024 */
     int64_t log_cap;        /* liftings kept with ECMC_LOG_LIFTINGS; 0 = 1<<22 */
     int32_t windows;        /* claim windows per leg, 1..4096; 0 = 1. A leg is run as W
@@ -99,6 +101,21 @@ int ecmc_create(const ecmc_params *p, const double *x, const double *y,
                 const int32_t *active, void *stream, ecmc_ctx **out);
 
 /*
+ * Constraint-graph mode (ECMC_GRAPH). The context builds, at creation and at
+ * every ecmc_set_direction, the constraint graph G(3) of Sec. 3.1: for each
+ * disk i and each of three corridors of dy = y_j - y_i (minimum image) --
+ * centre |dy| < d/2, upper d/2 <= dy < d, lower -d < dy <= -d/2 -- the disk of
+ * least time of flight (tau, then index), or none. While v is fixed disks
+ * closer than d in y cannot pass one another, so the arrows stay valid over
+ * any number of legs, and a step reads only the (at most three) arrow targets
+ * of the active disk. Results (positions, local times, liftings) are those of
+ * the cell scan, i.e. of Alg. 2. Claims are taken on the disks a step reads
+ * (the active disk and its arrow targets) instead of cells, so a leg's flag
+ * is 1 iff in some window the disks that two chains read, each run alone,
+ * overlap. Limits: n_chains <= 2^20 - 2; such contexts cannot be batched
+ * (ecmc_batch_run returns EINVAL). cells_per_side only sets the cell scan
+ * that builds the graph.
+ *
  * Conflicts. Within a claim window every chain claims, with atomicCAS, each
  * cell it scans; two chains that want one cell "meet". A leg's flag is 1 iff
  * in some window the cells that two chains would scan, each run alone from the

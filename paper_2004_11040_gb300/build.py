@@ -1,21 +1,28 @@
-"""Builds libecmc.so in-tree with nvcc for sm_103a (GB300)."""
+"""Builds libecmc.so in-tree with nvcc for sm_103a (GB300).
+
+Two translation units -- the cell-scan path with the C ABI (ecmc.cu) and the
+constraint-graph path (graph.cu) -- are compiled in parallel, then linked.
+"""
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "ecmc.cu")
+CSRC = os.path.join(HERE, "csrc")
+UNITS = [os.path.join(CSRC, "ecmc.cu"), os.path.join(CSRC, "graph.cu")]
 HDR = os.path.join(ROOT, "include", "ecmc.h")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libecmc.so")
 
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [
-    "-gencode", "arch=compute_103a,code=sm_103a",
+    *ARCH,
     "-lineinfo", "-O3", "-std=c++17",
     "-fmad=false",  # no FMA contraction: FP64 results bit-reproducible
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
 ]
 
 
@@ -26,17 +33,36 @@ def nvcc() -> str:
     return "nvcc"
 
 
+def _sources() -> list[str]:
+    return UNITS + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(CSRC, "*.h")) + [HDR, os.path.abspath(__file__)]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR), os.path.getmtime(__file__))
+    newest = max(os.path.getmtime(f) for f in _sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(OUT_DIR, os.path.basename(u)[:-3] + tag + ".o") for u in UNITS]
+    procs = []
+    for u, o in zip(UNITS, objs):
+        cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", u, "-o", o]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append(subprocess.Popen(cmd))
+    codes = [p.wait() for p in procs]
+    try:
+        for u, c in zip(UNITS, codes):
+            if c != 0:
+                raise subprocess.CalledProcessError(c, f"nvcc {os.path.basename(u)}")
+        tmp = LIB + tag
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -1,0 +1,242 @@
+// common.cuh -- device pieces shared by the cell-scan path (ecmc.cu) and the
+// constraint-graph path (graph.cu) of libecmc: owner-word encoding, chain
+// states, counters, bit-level FP64 order, union-find of conflict components,
+// block scans and the bounded grid barrier of the persistent kernels.
+// Everything lives in an unnamed namespace: each translation unit keeps its
+// own copy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ecmc.h"
+
+namespace {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+// owner word of a disk (the paper's tag, Sec. 2.3): static, or active / stalled
+// for chain c in the low 30 bits
+constexpr uint32_t OWN_STATIC = 0u;
+constexpr uint32_t OWN_ACTIVE = 0x40000000u;
+constexpr uint32_t OWN_STALLED = 0x80000000u;
+constexpr uint32_t OWN_CHAIN = 0x3FFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;  // +inf
+
+constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
+
+// per-leg counters (reset at every leg start)
+enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
+       LC_CONTINUED,
+       LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_N };
+enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
+// cumulative counters
+enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,
+       TC_LOG_N, TC_N };
+
+// Event records of repair rounds carry seq = round << 24 | count; those of a
+// window's parallel pass have seq < 2^24.
+constexpr uint32_t REPAIR_SEQ0 = 1u << 24;
+
+// Bound on every grid-barrier wait of the persistent kernels.
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 60ull * 1000 * 1000 * 1000;
+
+// Non-negative doubles (and +inf) order like their bit patterns; comparisons
+// of such values run on the integer pipe.
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+// v < 0 for a value that is not -0.0 (subtractions of finite doubles never give -0.0)
+__device__ __forceinline__ bool dneg(double v) {
+    return __double_as_longlong(v) < 0 && dbits(v) != 0x8000000000000000ull;
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
+    return (unsigned long long)__shfl_xor_sync(FULL, (long long)v, o);
+}
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
+    return (unsigned long long)__shfl_sync(FULL, (long long)v, src);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void atomic_min_time(double *p, double v) {
+    // times are >= 0: their IEEE bit patterns order like the values
+    atomicMin((unsigned long long *)p, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ int uf_find(int32_t *p, int x) {
+    for (;;) {
+        const int px = ((volatile int32_t *)p)[x];
+        if (px == x) return x;
+        const int ppx = ((volatile int32_t *)p)[px];
+        if (ppx != px) atomicCAS(p + x, px, ppx);  // path halving
+        x = px;
+    }
+}
+
+__device__ void uf_union(int32_t *p, int a, int b) {
+    for (;;) {
+        a = uf_find(p, a);
+        b = uf_find(p, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(p + a, a, b) == a) return;  // larger root under smaller
+    }
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x a multiple of 32,
+// at most 1024).
+__device__ int block_exscan(int v, int *warp_tot, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int t = lane < nw ? warp_tot[lane] : 0;
+        int u = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, u, o);
+            if (lane >= o) u += y;
+        }
+        if (lane < nw) warp_tot[lane] = u - t;
+        if (lane == 31) *total = u;
+    }
+    __syncthreads();
+    const int r = warp_tot[w] + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Conflict components (one block). first: edges from the parallel pass
+// (blocked chain -> holder of the claim it met); later rounds: edges from
+// components that met another chain. Components holding a chain whose events
+// are not final ("dirty") are listed for the repair with their members.
+// reset_abort: clear the abort count here (the persistent kernels clear it
+// elsewhere, after every block has read it).
+template <class S>
+__device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool reset_abort) {
+    const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
+    if (first)
+        for (int c = tid; c < k; c += nt) {
+            s.uf[c] = c;
+            s.fin[c] = s.status[c] != ST_BLOCKED;
+            s.abort_to[c] = -1;
+        }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        int other = -1;
+        if (first) {
+            if (s.status[c] == ST_BLOCKED) other = s.partner[c];
+        } else {
+            other = s.abort_to[c];
+            s.abort_to[c] = -1;
+        }
+        if (other >= 0 && other < k) uf_union(s.uf, c, other);
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        s.comp_of[c] = uf_find(s.uf, c);
+        s.comp_cnt[c] = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) s.comp_cnt[s.comp_of[c]] = -1;  // dirty root
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (s.comp_cnt[s.comp_of[c]] != 0) s.fin[c] = 0;
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (s.comp_cnt[c] == -1) s.comp_cnt[c] = 0;
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) atomicAdd(s.comp_cnt + s.comp_of[c], 1);
+    __syncthreads();
+    // chunked exclusive scans over roots: member offsets and component index
+    const int chunk = (k + nt - 1) / nt;
+    const int lo = min(k, tid * chunk), hi = min(k, lo + chunk);
+    int sc = 0, sm = 0;
+    for (int c = lo; c < hi; ++c) {
+        const int n = s.comp_cnt[c];
+        sc += n;
+        sm += n > 0;
+    }
+    int oc = block_exscan(sc, warp_tot, tot);
+    int om = block_exscan(sm, warp_tot, tot + 1);
+    for (int c = lo; c < hi; ++c) {
+        const int n = s.comp_cnt[c];
+        if (n > 0) {
+            s.comp_root[om] = c;
+            s.comp_off[om] = oc;
+            s.comp_cnt[c] = oc;  // becomes the write cursor
+            oc += n;
+            ++om;
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt)
+        if (!s.fin[c]) s.comp_mem[atomicAdd(s.comp_cnt + s.comp_of[c], 1)] = c;
+    if (tid == 0) {
+        s.comp_off[tot[1]] = tot[0];
+        s.ctl[CTL_NCOMP] = tot[1];
+        s.ctl[CTL_NMEMB] = tot[0];
+        s.ctl[CTL_WORK] = 0;
+        if (reset_abort) s.ctl[CTL_NABORT] = 0;
+    }
+    __syncthreads();
+}
+
+// Grid barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the
+// generation. A wait longer than BARRIER_TIMEOUT_NS records ECMC_ETIMEOUT in
+// *err and gives up; the return value is false once *err is set, and the
+// caller then returns.
+__device__ bool grid_sync(unsigned int *bar, int32_t *err, int *sflag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            while (*gen == g0) {
+                if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
+                    ok = 0;
+                    atomicExch(err, ECMC_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *sflag = ok && *(volatile int32_t *)err == 0;
+    }
+    __syncthreads();
+    // every thread orders its later loads after the barrier (acquire)
+    __threadfence();
+    return *sflag != 0;
+}
+
+}  // namespace

@@ -37,29 +37,11 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "ecmc.h"
+#include "graph.h"
 
 namespace {
-
-constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr uint32_t OWN_STATIC = 0u;
-constexpr uint32_t OWN_ACTIVE = 0x40000000u;
-constexpr uint32_t OWN_STALLED = 0x80000000u;
-constexpr uint32_t OWN_CHAIN = 0x3FFFFFFFu;
-constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;  // +inf
-
-constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
-
-// per-leg counters (reset at every leg start)
-enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
-       LC_CONTINUED,
-       LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_N };
-enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
-// cumulative counters
-enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,
-       TC_LOG_N, TC_N };
 
 constexpr uint32_t REC_NO_OWNER = 1u;  // the target's owner word was not taken
 
@@ -118,16 +100,6 @@ struct Dev {
 
 // ------------------------------------------------------------ FP64 geometry
 
-// Non-negative doubles (and +inf) order like their bit patterns; comparisons
-// of such values run on the integer pipe.
-__device__ __forceinline__ unsigned long long dbits(double v) {
-    return (unsigned long long)__double_as_longlong(v);
-}
-// v < 0 for a value that is not -0.0 (subtractions of finite doubles never give -0.0)
-__device__ __forceinline__ bool dneg(double v) {
-    return __double_as_longlong(v) < 0 && dbits(v) != 0x8000000000000000ull;
-}
-
 // Records the first failed internal check: kind, then up to 6 values.
 __device__ void diag(const Dev &s, int kind, double a, double b, double c, double d, double e,
                      double f) {
@@ -159,15 +131,7 @@ __device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
     return r;
 }
 
-__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
-    return (unsigned long long)__shfl_xor_sync(FULL, (long long)v, o);
-}
 
-__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
-    return (unsigned long long)__shfl_sync(FULL, (long long)v, src);
-}
-
-// lexicographic (tau, j) minimum over the warp; tau given by its bits
 // ------------------------------------------------------------- one step
 
 enum { MODE_PASS1 = 0, MODE_COMP = 1, MODE_CONT = 2 };
@@ -825,137 +789,6 @@ __device__ void undo_record(const Dev &s, int c, const Rec &u) {
     }
 }
 
-__device__ int uf_find(int32_t *p, int x) {
-    for (;;) {
-        const int px = ((volatile int32_t *)p)[x];
-        if (px == x) return x;
-        const int ppx = ((volatile int32_t *)p)[px];
-        if (ppx != px) atomicCAS(p + x, px, ppx);  // path halving
-        x = px;
-    }
-}
-
-__device__ void uf_union(int32_t *p, int a, int b) {
-    for (;;) {
-        a = uf_find(p, a);
-        b = uf_find(p, b);
-        if (a == b) return;
-        if (a < b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        if (atomicCAS(p + a, a, b) == a) return;  // larger root under smaller
-    }
-}
-
-// Block-wide exclusive scan of one int per thread (blockDim.x a multiple of 32,
-// at most 1024).
-__device__ int block_exscan(int v, int *warp_tot, int *total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        const int t = lane < nw ? warp_tot[lane] : 0;
-        int u = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, u, o);
-            if (lane >= o) u += y;
-        }
-        if (lane < nw) warp_tot[lane] = u - t;
-        if (lane == 31) *total = u;
-    }
-    __syncthreads();
-    const int r = warp_tot[w] + x - v;
-    __syncthreads();
-    return r;
-}
-
-// Conflict components (one block). first: edges from pass 1 (blocked chain ->
-// holder of the cell or owner word it met); later rounds: edges from
-// components that met another chain. Components holding a chain whose events
-// are not final ("dirty") are listed for the repair with their members.
-// reset_abort: clear the abort count here (the persistent kernel clears it in
-// its prefix phase instead, after every block has read it).
-__device__ void uf_block(const Dev &s, int first, int *warp_tot, int *tot, bool reset_abort) {
-    const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
-    if (first)
-        for (int c = tid; c < k; c += nt) {
-            s.uf[c] = c;
-            s.fin[c] = s.status[c] != ST_BLOCKED;
-            s.abort_to[c] = -1;
-        }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt) {
-        int other = -1;
-        if (first) {
-            if (s.status[c] == ST_BLOCKED) other = s.partner[c];
-        } else {
-            other = s.abort_to[c];
-            s.abort_to[c] = -1;
-        }
-        if (other >= 0 && other < k) uf_union(s.uf, c, other);
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt) {
-        s.comp_of[c] = uf_find(s.uf, c);
-        s.comp_cnt[c] = 0;
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) s.comp_cnt[s.comp_of[c]] = -1;  // dirty root
-    __syncthreads();
-    for (int c = tid; c < k; c += nt)
-        if (s.comp_cnt[s.comp_of[c]] != 0) s.fin[c] = 0;
-    __syncthreads();
-    for (int c = tid; c < k; c += nt)
-        if (s.comp_cnt[c] == -1) s.comp_cnt[c] = 0;
-    __syncthreads();
-    for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) atomicAdd(s.comp_cnt + s.comp_of[c], 1);
-    __syncthreads();
-    // chunked exclusive scans over roots: member offsets and component index
-    const int chunk = (k + nt - 1) / nt;
-    const int lo = min(k, tid * chunk), hi = min(k, lo + chunk);
-    int sc = 0, sm = 0;
-    for (int c = lo; c < hi; ++c) {
-        const int n = s.comp_cnt[c];
-        sc += n;
-        sm += n > 0;
-    }
-    int oc = block_exscan(sc, warp_tot, tot);
-    int om = block_exscan(sm, warp_tot, tot + 1);
-    for (int c = lo; c < hi; ++c) {
-        const int n = s.comp_cnt[c];
-        if (n > 0) {
-            s.comp_root[om] = c;
-            s.comp_off[om] = oc;
-            s.comp_cnt[c] = oc;  // becomes the write cursor
-            oc += n;
-            ++om;
-        }
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) s.comp_mem[atomicAdd(s.comp_cnt + s.comp_of[c], 1)] = c;
-    if (tid == 0) {
-        s.comp_off[tot[1]] = tot[0];
-        s.ctl[CTL_NCOMP] = tot[1];
-        s.ctl[CTL_NMEMB] = tot[0];
-        s.ctl[CTL_WORK] = 0;
-        if (reset_abort) s.ctl[CTL_NABORT] = 0;
-    }
-    __syncthreads();
-}
-
 __global__ void k_uf(Dev s, int first) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
@@ -972,19 +805,12 @@ __device__ __forceinline__ bool footprint_has(int fcx, int fcy, int fm, uint32_t
     return dm <= fm;
 }
 
-__device__ __forceinline__ void atomic_min_time(double *p, double v) {
-    // times are >= 0: their IEEE bit patterns order like the values
-    atomicMin((unsigned long long *)p, (unsigned long long)__double_as_longlong(v));
-}
-
 // Rolls the members of a component back to T* (their events before T* are
 // exact): records with event time >= T* are undone, latest first. Records of
 // repair rounds (seq >= REPAIR_SEQ0) can share slots across members and are
 // undone one at a time in descending seq; beneath them, the records of the
 // window's pass 1 lie in cells claimed by their own chain only, so each
 // member undoes its own in parallel.
-constexpr uint32_t REPAIR_SEQ0 = 1u << 24;
-
 __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double Ts) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -1633,8 +1459,6 @@ __global__ void k_export_active(Dev s, int32_t *active) {
 // liftings. Every barrier wait is bounded by the device clock: past the limit
 // the kernel records ECMC_ETIMEOUT and returns instead of waiting on.
 
-constexpr unsigned long long BARRIER_TIMEOUT_NS = 60ull * 1000 * 1000 * 1000;
-
 struct RepCtl {
     int64_t budget;         // liftings for this run (0: none)
     int64_t lifts;          // liftings made in this run
@@ -1683,41 +1507,8 @@ __device__ __forceinline__ double window_end(const Dev &s, int w) {
                               : __ddiv_rn(__dmul_rn((double)(w + 1), s.ell), (double)s.windows);
 }
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ bool grid_barrier(const Batch &b, int *sflag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *gen = b.bar + 1;
-        const unsigned int g0 = *gen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(b.bar, 1u) == gridDim.x - 1) {
-            atomicExch(b.bar, 0u);
-            __threadfence();
-            atomicAdd(b.bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = gtimer();
-            while (*gen == g0) {
-                if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
-                    ok = 0;
-                    atomicExch(b.g + G_ERR, ECMC_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        *sflag = ok && *(volatile int32_t *)(b.g + G_ERR) == 0;
-    }
-    __syncthreads();
-    // every thread orders its later loads after the barrier (acquire)
-    __threadfence();
-    return *sflag != 0;
+    return grid_sync(b.bar, b.g + G_ERR, sflag);
 }
 
 // replica of flattened item w, with base[r] <= w < base[r+1]
@@ -1971,6 +1762,7 @@ struct ecmc_ctx {
     double device_ms = 0.0;
     bool log_overflow = false;
     int32_t direction = 0;  // 0: +x; 1: +y (the context is stored transposed)
+    GraphCtx *graph = nullptr;  // ECMC_GRAPH: the constraint-graph path holds the state
 };
 
 static std::string g_create_err;
@@ -2027,6 +1819,93 @@ static int pick_cells(const ecmc_params *p, int *nc_out, int *C_out) {
     return 0;
 }
 
+// Inputs checked on a host copy: coordinates in [0, L), active ids distinct
+// and in [0, n). Returns 0 or an error code (message in g_create_err).
+static int check_inputs(const ecmc_params *p, const double *x, const double *y,
+                        const int32_t *active, bool dev_in) {
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    std::vector<double> hx, hy;
+    std::vector<int32_t> ha(k);
+    const double *vx = x, *vy = y;
+    const int32_t *va = active;
+    if (dev_in) {
+        hx.resize(n);
+        hy.resize(n);
+        if (cudaMemcpy(hx.data(), x, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hy.data(), y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ha.data(), active, k * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g_create_err = "cannot read device inputs";
+            return ECMC_ECUDA;
+        }
+        vx = hx.data();
+        vy = hy.data();
+        va = ha.data();
+    }
+    for (size_t q = 0; q < n; ++q) {
+        if (!(vx[q] >= 0.0 && vx[q] < p->box && vy[q] >= 0.0 && vy[q] < p->box)) {
+            g_create_err = "coordinate outside [0, L)";
+            return ECMC_EINVAL;
+        }
+    }
+    std::vector<char> seen(n, 0);
+    for (size_t c = 0; c < k; ++c) {
+        const int32_t a = va[c];
+        if (a < 0 || (size_t)a >= n || seen[a]) {
+            g_create_err = "active ids must be distinct and in [0, n)";
+            return ECMC_EINVAL;
+        }
+        seen[a] = 1;
+    }
+    return 0;
+}
+
+// ECMC_GRAPH: the state lives in the constraint-graph path (graph.cu).
+static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
+                        const int32_t *active) {
+    const ecmc_params *p = &ctx->p;
+    const bool dev_in = (p->flags & ECMC_INPUT_DEVICE) != 0;
+    int rc = check_inputs(p, x, y, active, dev_in);
+    if (rc) return rc;
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    double *dx = nullptr, *dy = nullptr;
+    int32_t *da = nullptr;
+    const double *sx = x, *sy = y;
+    const int32_t *sa = active;
+    auto release = [&]() {
+        cudaFree(dx);
+        cudaFree(dy);
+        cudaFree(da);
+    };
+    if (!dev_in) {
+        if (cudaMalloc(&dx, n * 8) != cudaSuccess || cudaMalloc(&dy, n * 8) != cudaSuccess ||
+            cudaMalloc(&da, k * 4) != cudaSuccess) {
+            (void)cudaGetLastError();
+            release();
+            g_create_err = "cudaMalloc failed (inputs)";
+            return ECMC_ENOMEM;
+        }
+        if (cudaMemcpyAsync(dx, x, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(dy, y, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(da, active, k * 4, cudaMemcpyHostToDevice, ctx->stream) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            release();
+            g_create_err = "input upload";
+            return ECMC_ECUDA;
+        }
+        sx = dx;
+        sy = dy;
+        sa = da;
+    }
+    std::string err;
+    rc = graph_create(p, nc, sx, sy, sa, ctx->stream, &ctx->graph, err);
+    cudaStreamSynchronize(ctx->stream);
+    release();
+    if (rc) g_create_err = err;
+    return rc;
+}
+
 template <int C>
 static void launch_build(ecmc_ctx *ctx, const double *x, const double *y) {
     const int64_t n = ctx->s.n;
@@ -2057,6 +1936,18 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     ctx->p = *p;
     ctx->stream = (cudaStream_t)stream;
     ctx->C = C;
+    if (p->flags & ECMC_GRAPH) {
+        memset(&ctx->s, 0, sizeof ctx->s);
+        ctx->s.n = p->n;
+        ctx->s.k = p->n_chains;
+        const int rc = create_graph(ctx, nc, x, y, active);
+        if (rc) {
+            ecmc_destroy(ctx);
+            return rc;
+        }
+        *out = ctx;
+        return ECMC_OK;
+    }
     Dev &s = ctx->s;
     memset(&s, 0, sizeof s);
     s.n = p->n;
@@ -2138,42 +2029,11 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         ecmc_destroy(ctx);
         return rc;
     }
-    // validate inputs on the host copy
-    std::vector<double> hx, hy;
-    std::vector<int32_t> ha(k);
-    const double *vx = x, *vy = y;
-    const int32_t *va = active;
-    if (dev_in) {
-        hx.resize(n);
-        hy.resize(n);
-        if (cudaMemcpy(hx.data(), x, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(hy.data(), y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(ha.data(), active, k * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
-            g_create_err = "cannot read device inputs";
-            ecmc_destroy(ctx);
-            return ECMC_ECUDA;
-        }
-        vx = hx.data();
-        vy = hy.data();
-        va = ha.data();
-    }
-    for (size_t q = 0; q < n; ++q) {
-        if (!(vx[q] >= 0.0 && vx[q] < p->box && vy[q] >= 0.0 && vy[q] < p->box)) {
-            g_create_err = "coordinate outside [0, L)";
-            ecmc_destroy(ctx);
-            return ECMC_EINVAL;
-        }
-    }
     {
-        std::vector<char> seen(n, 0);
-        for (size_t c = 0; c < k; ++c) {
-            const int32_t a = va[c];
-            if (a < 0 || (size_t)a >= n || seen[a]) {
-                g_create_err = "active ids must be distinct and in [0, n)";
-                ecmc_destroy(ctx);
-                return ECMC_EINVAL;
-            }
-            seen[a] = 1;
+        const int vr = check_inputs(p, x, y, active, dev_in);
+        if (vr) {
+            ecmc_destroy(ctx);
+            return vr;
         }
     }
     cudaStream_t st = ctx->stream;
@@ -2269,6 +2129,10 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     const int C = ctxs[0]->C;
     const int W = ctxs[0]->s.windows;
     for (int r = 0; r < R; ++r) {
+        if (ctxs[r] && ctxs[r]->graph) {
+            err = "constraint-graph contexts run alone (ecmc_run_to_breakpoint)";
+            return ECMC_EINVAL;
+        }
         if (!ctxs[r] || ctxs[r]->C != C || ctxs[r]->s.windows != W) {
             err = "all contexts of a batch need the same cell slots (cell size) and windows";
             return ECMC_EINVAL;
@@ -2426,6 +2290,30 @@ extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t ev
     if (n_legs < 0) return fail(ctx, ECMC_EINVAL, "n_legs < 0");
     if (legs_done) *legs_done = 0;
     if (n_legs == 0) return ECMC_OK;
+    if (ctx->graph) {
+        GraphTotals t;
+        std::string err;
+        int32_t legs = 0;
+        const int rc = graph_run(ctx->graph, n_legs, event_budget, leg_flags_out, &legs, &t, err);
+        if (legs_done) *legs_done = legs;
+        ctx->legs_total += t.legs;
+        ctx->lifts_total += t.lifts;
+        ctx->conflict_legs += t.conflict_legs;
+        ctx->repaired += t.repaired;
+        ctx->horizon += t.horizon;
+        ctx->order_err += t.order_err;
+        ctx->device_ms += t.ms;
+        ctx->prof.pass1_launches += t.legs;
+        ctx->prof.other_launches += t.legs;
+        ctx->prof.repair_launches += t.conflict_legs;
+        ctx->prof.pass1_liftings += t.p1_lifts;
+        ctx->prof.repair_liftings += t.repair_lifts;
+        ctx->prof.pass1_ms += t.pass1_ms;
+        ctx->prof.repair_ms += t.repair_ms;
+        ctx->prof.other_ms += t.other_ms;
+        if (rc) return fail(ctx, rc, err);
+        return ECMC_OK;
+    }
     ecmc_ctx *one[1] = {ctx};
     int32_t legs = 0;
     std::string err;
@@ -2500,7 +2388,13 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
         release();
         return fail(ctx, ECMC_ENOMEM, "positions scratch");
     }
-    if (x || y || t) {
+    if (ctx->graph) {
+        double *ex = ctx->direction ? dy : dx, *ey = ctx->direction ? dx : dy;
+        if (graph_export(ctx->graph, ex, ey, dt, da) != 0) {
+            release();
+            return fail(ctx, ECMC_ECUDA, "positions (graph)");
+        }
+    } else if (x || y || t) {
         // in a transposed context the stored x is the caller's y
         double *ex = ctx->direction ? dy : dx, *ey = ctx->direction ? dx : dy;
         if (ctx->C == 4)
@@ -2508,7 +2402,8 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
         else
             k_export<8><<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, ex, ey, dt);
     }
-    if (active) k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
+    if (active && !ctx->graph)
+        k_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, da);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, n * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && y) e = cudaMemcpyAsync(y, dy, n * 8, cudaMemcpyDeviceToHost, st);
@@ -2525,6 +2420,13 @@ extern "C" int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction) {
     if (!ctx) return ECMC_EINVAL;
     if (direction != 0 && direction != 1) return fail(ctx, ECMC_EINVAL, "direction must be 0 (+x) or 1 (+y)");
     if (direction == ctx->direction) return ECMC_OK;
+    if (ctx->graph) {
+        std::string err;
+        const int rc = graph_transpose(ctx->graph, err);
+        if (rc) return fail(ctx, rc, "set_direction: " + err);
+        ctx->direction = direction;
+        return ECMC_OK;
+    }
     Dev &s = ctx->s;
     cudaStream_t st = ctx->stream;
     const int64_t ncell = (int64_t)s.nc * s.nc;
@@ -2563,6 +2465,11 @@ extern "C" int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out) {
 
 extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out) {
     if (!ctx || !n_out) return ECMC_EINVAL;
+    if (ctx->graph) {
+        std::string err;
+        const int rc = graph_liftings(ctx->graph, buf, cap, n_out, err);
+        return rc ? fail(ctx, rc, err) : ECMC_OK;
+    }
     Dev &s = ctx->s;
     if (!s.log_on) return fail(ctx, ECMC_EINVAL, "lifting log not enabled");
     unsigned long long n = 0;
@@ -2587,6 +2494,7 @@ extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64
 
 extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
     if (!ctx) return;
+    graph_destroy(ctx->graph);
     runner_free(ctx->run);
     cudaFree(ctx->d_flags);
     for (void *p : ctx->allocs) cudaFree(p);

@@ -1,0 +1,1433 @@
+// graph.cu -- libecmc's constraint-graph path (ECMC_GRAPH): the liftings of
+// a chain are found through the arrows of the constraint graph G(3) of
+// Sec. 3.1 instead of a scan of the cells ahead.
+//
+// For v = (1, 0) the arrows of disk i are, in each of three corridors of
+// dy = y_j - y_i (minimum image) -- centre |dy| < d/2, upper d/2 <= dy < d,
+// lower -d < dy <= -d/2 -- the disk of least time of flight (tau, j), if any.
+// Disks closer than d in y cannot pass one another while v holds, so the
+// arrows stay valid across breakpoints (Sec. 3.1) and a step reads at most
+// three target disks; b_ij = sqrt(d^2 - dy^2) is fixed with the arrow and
+// stored beside it, so the step does no square root.
+//
+// Layout: one 64-byte record per disk (x, local time, owner word, claim word,
+// three arrows and their b), y in its own array (it never changes along +x).
+//
+// Conflicts are claims on disks instead of cells: within a claim window a
+// chain claims (atomicCAS on the disk's claim word, tagged with the window's
+// epoch) every disk a step reads -- its active disk and the arrow targets --
+// before using what it read. A disk is therefore written only by its claimer
+// during a window, a chain that meets another chain's claim stops, and
+// without a meeting each chain follows the path it takes alone, which is the
+// global-time result (Lemma 2). The leg's flag is 1 iff the disks that two
+// chains read, each run alone from the window's start, overlap. Chains that
+// met are rolled back to the earliest time one of them stopped and replayed
+// in global event-time order (Alg. 2), one warp per conflict component, as on
+// the cell path.
+//
+// All FP64 arithmetic uses explicit round-to-nearest intrinsics (the file is
+// compiled with -fmad=false) so that results are reproducible bit for bit.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "graph.h"
+
+namespace {
+
+// claim word: epoch (1..EPOCH_MAX) << 20 | chain + 1; 0 or another epoch = free
+constexpr int CLAIM_SHIFT = 20;
+constexpr uint32_t CLAIM_CHAIN = (1u << CLAIM_SHIFT) - 1u;
+constexpr uint32_t EPOCH_MAX = 4095u;
+constexpr int MAX_CHAINS = (int)CLAIM_CHAIN - 1;
+
+struct __align__(64) GDisk {
+    double x, t;    // position along the motion; local time (leg-relative)
+    uint32_t own;   // owner word (static / active / stalled + chain)
+    uint32_t claim; // claim word of the current window
+    uint32_t a[3];  // arrows: centre, upper, lower corridor (NONE: empty)
+    uint32_t pad;
+    double b[3];    // b_ij = sqrt(d^2 - dy^2) of each arrow
+};
+static_assert(sizeof(GDisk) == 64, "one disk record is one 64-byte line");
+
+// One event of a chain: enough to undo it exactly, and the lifting (Eq. 1).
+struct GEv {
+    uint32_t i, j, seq, pad;  // moved disk, target (NONE: stall), application order
+    double x_old;             // x of i before the move
+    double ti_old, tj_old;    // local times of i and j before the event
+    double t, tau, xi, xj;    // event time (= new t_j), time of flight, x_i at contact, x_j
+    double d_after;           // remaining chain length after the event
+};
+
+struct GDev {
+    int64_t n;
+    int k, cap, windows, nc;
+    double L, d, ell;
+    GDisk *g;   // [n]
+    double *y;  // [n]
+    // per chain
+    uint32_t *ci, *ci0;  // active disk now / at the leg start
+    double *D, *tc;
+    int32_t *status, *partner, *nrec, *nlift;
+    GEv *rec;  // [k * cap]
+    // pending events of the replay, and the arrows they were computed from
+    double *ev_T, *ev_tau, *ev_xj, *ev_tj;
+    uint32_t *ev_j, *ev_a;  // ev_a: [3k]
+    int32_t *ev_lift;
+    // conflict components (names as the union-find of common.cuh expects)
+    double *vt;
+    int32_t *uf, *fin, *comp_of, *abort_to, *comp_cnt, *comp_off, *comp_root, *comp_mem, *ctl;
+    int32_t *nabort;  // [2] components that met another chain, by round parity
+    unsigned long long *lc;      // [LC_N]
+    unsigned long long *tc_cnt;  // [TC_N]
+    ecmc_lift_t *log;
+    int64_t log_cap;
+    int log_on;
+    double *dbg;  // [16] first failed internal check
+};
+
+__device__ void gdiag(const GDev &s, int kind, double a, double b, double c, double d,
+                      double e, double f) {
+    if (!s.dbg) return;
+    if (atomicCAS((unsigned long long *)s.dbg, 0ull,
+                  (unsigned long long)__double_as_longlong((double)kind)) != 0ull)
+        return;
+    s.dbg[1] = a;
+    s.dbg[2] = b;
+    s.dbg[3] = c;
+    s.dbg[4] = d;
+    s.dbg[5] = e;
+    s.dbg[6] = f;
+}
+
+__device__ __forceinline__ double wrap_add(double x, double dx, double L) {
+    double r = __dadd_rn(x, dx);
+    if (dbits(r) >= dbits(L)) r = __dsub_rn(r, L);  // r >= 0
+    return r;
+}
+
+// ------------------------------------------------------------ graph build
+
+struct GBuild {
+    int64_t n;
+    int nc, nb;
+    double L, d, d2, a, inv_a, eps, w;  // cells of side a; y bins of width w
+    const double *x, *y;
+    uint32_t *cid;       // [nc*nc*C] disk per slot, EMPTY
+    double *cx, *cy;     // [nc*nc*C]
+    int32_t *bins;       // [nb + 1]: counts, then their exclusive prefix
+    GDisk *g;
+    unsigned long long *err;  // cell overflow count
+};
+
+__device__ __forceinline__ int cell_coord(double v, double inv_a, int nc) {
+    int c = __double2int_rz(__dmul_rn(v, inv_a));
+    if (c >= nc) c = nc - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+template <int C>
+__global__ void k_gb_cells(GBuild b) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= b.n) return;
+    const double x = b.x[q], y = b.y[q];
+    const uint32_t cell = (uint32_t)cell_coord(y, b.inv_a, b.nc) * (uint32_t)b.nc +
+                          (uint32_t)cell_coord(x, b.inv_a, b.nc);
+    int bin = __double2int_rz(__ddiv_rn(y, b.w));
+    if (bin >= b.nb) bin = b.nb - 1;
+    if (bin < 0) bin = 0;
+    atomicAdd(b.bins + bin, 1);
+    for (int sl = 0; sl < C; ++sl) {
+        const uint32_t loc = cell * C + sl;
+        if (atomicCAS(b.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
+            b.cx[loc] = x;
+            b.cy[loc] = y;
+            return;
+        }
+    }
+    atomicAdd(b.err, 1ull);
+}
+
+// Exclusive prefix of the y-bin counts (one block).
+__global__ void k_gb_scan(GBuild b) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int chunk = (b.nb + nt - 1) / nt;
+    const int lo = min(b.nb, tid * chunk), hi = min(b.nb, lo + chunk);
+    int sum = 0;
+    for (int q = lo; q < hi; ++q) sum += b.bins[q];
+    int off = block_exscan(sum, warp_tot, tot);
+    for (int q = lo; q < hi; ++q) {
+        const int v = b.bins[q];
+        b.bins[q] = off;
+        off += v;
+    }
+    if (tid == 0) b.bins[b.nb] = tot[0];
+}
+
+// Disks whose y falls in a bin that meets [lo, hi) (periodic, hi - lo < L):
+// an upper bound on the disks with y in that range.
+__device__ int band_count(const GBuild &b, double lo, double hi) {
+    if (lo < 0.0) {
+        lo = __dadd_rn(lo, b.L);
+        hi = __dadd_rn(hi, b.L);
+    } else if (lo >= b.L) {
+        lo = __dsub_rn(lo, b.L);
+        hi = __dsub_rn(hi, b.L);
+    }
+    auto bin = [&](double v) {
+        int q = __double2int_rz(__ddiv_rn(v, b.w));
+        return min(max(q, 0), b.nb - 1);
+    };
+    const int b0 = bin(lo);
+    if (hi <= b.L) return b.bins[bin(hi) + 1] - b.bins[b0];
+    return (b.bins[b.nb] - b.bins[b0]) + (b.bins[bin(__dsub_rn(hi, b.L)) + 1] - b.bins[0]);
+}
+
+// Arrows of G(3): one warp per disk scans the columns ahead (rows cy-1..cy+1)
+// and keeps, per corridor, the least (tau, j). Before a pass whose first
+// column m >= 1 lies beyond (m a - fx) - d > max over the corridors still in
+// play of their best tau (+ eps), no later column can improve any of them and
+// the scan stops; a corridor that the y bins show empty is not in play, any
+// other one keeps the scan going (once round the box at most).
+template <int C>
+__global__ void k_gb_arrows(GBuild b) {
+    constexpr int LPC = (3 * C <= 16) ? 16 : 32;  // lanes per column
+    constexpr int CPP = 32 / LPC;                 // columns per pass
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPC, sub = lane % LPC;
+    const int rr = sub / C, sl = sub % C;
+    const bool used = sub < 3 * C;
+    const int nc = b.nc;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double half = __dmul_rn(0.5, b.d);
+    for (int64_t i = warp; i < b.n; i += nwarps) {
+        const double xi = b.x[i], yi = b.y[i];
+        const int cxi = cell_coord(xi, b.inv_a, nc), cyi = cell_coord(yi, b.inv_a, nc);
+        const double fx = __dsub_rn(xi, __dmul_rn((double)cxi, b.a));
+        // corridors that may hold a disk (one bin of margin on each side)
+        bool play[3];
+        play[0] = band_count(b, __dsub_rn(__dsub_rn(yi, half), b.w),
+                             __dadd_rn(__dadd_rn(yi, half), b.w)) > 1;  // i itself is there
+        play[1] = band_count(b, __dsub_rn(__dadd_rn(yi, half), b.w),
+                             __dadd_rn(__dadd_rn(yi, b.d), b.w)) > 0;
+        play[2] = band_count(b, __dsub_rn(__dsub_rn(yi, b.d), b.w),
+                             __dadd_rn(__dsub_rn(yi, half), b.w)) > 0;
+        unsigned long long bt[3] = {INF_BITS, INF_BITS, INF_BITS};
+        uint32_t bj[3] = {NONE, NONE, NONE};
+        double bb[3] = {0.0, 0.0, 0.0};
+        int row = cyi + rr - 1;
+        if (row < 0) row += nc;
+        if (row >= nc) row -= nc;
+        for (int m0 = 0; m0 < nc; m0 += CPP) {
+            if (m0 >= 1) {
+                unsigned long long worst = 0ull;
+                bool any = false;
+                for (int kc = 0; kc < 3; ++kc)
+                    if (play[kc]) {
+                        any = true;
+                        if (bt[kc] > worst) worst = bt[kc];
+                    }
+                if (!any) break;
+                if (worst != INF_BITS) {
+                    const double thr =
+                        __dsub_rn(__dsub_rn(__dmul_rn((double)m0, b.a), fx), b.d);
+                    const double lim = __dadd_rn(__longlong_as_double((long long)worst), b.eps);
+                    if (!dneg(thr) && dbits(thr) > dbits(lim)) break;
+                }
+            }
+            const int m = m0 + grp;
+            int col = cxi + m;
+            if (col >= nc) col -= nc;
+            uint32_t id = EMPTY;
+            double xj = 0.0, yj = 0.0;
+            if (used && m < nc) {
+                const uint32_t loc = ((uint32_t)row * (uint32_t)nc + (uint32_t)col) * C + sl;
+                id = b.cid[loc];
+                xj = b.cx[loc];
+                yj = b.cy[loc];
+            }
+            int kc = -1;
+            double tau = 0.0, bv = 0.0;
+            if (id != EMPTY && id != (uint32_t)i) {
+                const double dy = __dsub_rn(yj, yi);
+                double ay = fabs(dy);
+                bool flip = false;
+                const double la = __dsub_rn(b.L, ay);
+                if (dbits(la) < dbits(ay)) {
+                    ay = la;
+                    flip = true;
+                }
+                if (dbits(ay) < dbits(b.d)) {
+                    if (dbits(ay) < dbits(half)) {
+                        kc = 0;
+                    } else {
+                        bool up = !dneg(dy) && dbits(dy) != 0ull;
+                        if (flip) up = !up;
+                        kc = up ? 1 : 2;
+                    }
+                    bv = __dsqrt_rn(__dsub_rn(b.d2, __dmul_rn(ay, ay)));
+                    double dx = __dsub_rn(xj, xi);
+                    if (dneg(dx)) dx = __dadd_rn(dx, b.L);
+                    tau = __dsub_rn(dx, bv);
+                    if (dneg(tau)) tau = 0.0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                unsigned long long kt = kc == q ? dbits(tau) : INF_BITS;
+                uint32_t kj = kc == q ? id : NONE;
+                double kb = bv;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long t2 = shfl_xor_u64(kt, o);
+                    const uint32_t j2 = __shfl_xor_sync(FULL, kj, o);
+                    const double b2 = __shfl_xor_sync(FULL, kb, o);
+                    if (t2 < kt || (t2 == kt && j2 < kj)) {
+                        kt = t2;
+                        kj = j2;
+                        kb = b2;
+                    }
+                }
+                if (kj != NONE && (kt < bt[q] || (kt == bt[q] && kj < bj[q]))) {
+                    bt[q] = kt;
+                    bj[q] = kj;
+                    bb[q] = kb;
+                }
+            }
+        }
+        if (lane == 0) {
+            GDisk &r = b.g[i];
+            r.x = xi;
+            r.t = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                r.a[q] = bj[q];
+                r.b[q] = bj[q] == NONE ? 0.0 : bb[q];
+            }
+            r.pad = 0;
+        }
+    }
+}
+
+// Owner words and claims from scratch: every disk static, then the chains'
+// start disks active.
+__global__ void k_g_init(GDev s) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < s.n) {
+        s.g[q].own = OWN_STATIC;
+        s.g[q].claim = 0u;
+    }
+}
+
+__global__ void k_g_init_chains(GDev s, const int32_t *active) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    const uint32_t a = (uint32_t)active[c];
+    s.ci[c] = a;
+    s.ci0[c] = a;
+    s.g[a].own = OWN_ACTIVE | (uint32_t)c;
+    s.nrec[c] = 0;
+    s.status[c] = ST_STALLED;
+}
+
+
+// --------------------------------------------------------------- one step
+
+__device__ __forceinline__ uint32_t claim_word(uint32_t epoch, int c) {
+    return (epoch << CLAIM_SHIFT) | (uint32_t)(c + 1);
+}
+
+__device__ __forceinline__ bool claim_live(uint32_t w, uint32_t epoch) {
+    return (w >> CLAIM_SHIFT) == epoch;
+}
+
+// What one step found.
+struct GStep {
+    double tau;        // tau* (lift) or D (stall)
+    uint32_t j;        // target (lift)
+    int lift;
+    double xj, tj;     // the target's x and local time as read
+    int conflict;      // a disk read is held by a chain of the other side
+    uint32_t partner;  // that chain
+    int hz;            // PASS1: Eq. 2 failed on a disk touched in this window
+    GDisk jr;          // the target's record as read: its arrows serve the next step
+};
+
+// Statements 1-9 of Alg. 5 for chain c along the arrows a[] (with b[]) of
+// its active disk i at x_i, t_i, with remaining length D. Every disk read is
+// claimed for the window: i itself when claim_i (wi: its claim word as read),
+// and each arrow target. A claim held by another chain is a conflict in
+// PASS1; in a repair only if that chain is not in the component `root`.
+// Candidates are the static targets (Alg. 2: j not active); a target with
+// t_i + tau < t_j became static after chain c's disk had passed it and is one
+// lap away (lazy per-chain frame); ties go to the lower disk index.
+template <bool PASS1>
+__device__ GStep graph_step(const GDev &s, int c, uint32_t epoch, int root, const uint32_t a[3],
+                            const double b[3], uint32_t i, double xi, double ti, double D,
+                            double tw, bool claim_i, uint32_t wi) {
+    const uint32_t mine = claim_word(epoch, c);
+    GDisk r[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (a[q] != NONE) r[q] = s.g[a[q]];
+    GStep o;
+    o.conflict = 0;
+    o.partner = NONE;
+    o.hz = 0;
+    // a claim word held by chain h: is h on this side?
+    auto ours = [&](uint32_t w) {
+        const int h = (int)(w & CLAIM_CHAIN) - 1;
+        if (h == c) return true;
+        if (PASS1 || h < 0 || h >= s.k) return false;
+        return __ldcg(s.comp_of + h) == root;
+    };
+    auto meet = [&](uint32_t w) {
+        if (!o.conflict) {
+            o.conflict = 1;
+            o.partner = (w & CLAIM_CHAIN) - 1u;
+        }
+    };
+    // claims: a word of this window is read as it is; any other is taken
+    uint32_t seen[4], old[4];
+    bool cas[4] = {false, false, false, false};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool have = q < 3 ? a[q] != NONE : claim_i;
+        if (!have) continue;
+        const uint32_t w = q < 3 ? r[q].claim : wi;
+        seen[q] = w;
+        if (claim_live(w, epoch)) {
+            if (!ours(w)) meet(w);
+        } else {
+            GDisk *p = s.g + (q < 3 ? a[q] : i);
+            old[q] = atomicCAS(&p->claim, w, mine);
+            cas[q] = true;
+        }
+    }
+    // time of flight to each static target (statement 4): forward image in x,
+    // b_ij fixed with the arrow, clamped at 0
+    unsigned long long bt = INF_BITS;
+    int bq = -1;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (a[q] == NONE || r[q].own != OWN_STATIC) continue;
+        double dx = __dsub_rn(r[q].x, xi);
+        if (dneg(dx)) dx = __dadd_rn(dx, s.L);
+        double tau = __dsub_rn(dx, b[q]);
+        if (dneg(tau)) tau = 0.0;
+        if (dbits(r[q].t) != 0ull) {
+            const double sum = __dadd_rn(ti, tau);
+            if (dbits(sum) < dbits(r[q].t)) {
+                if (PASS1 && dbits(r[q].t) >= dbits(tw)) o.hz = 1;
+                tau = __dadd_rn(tau, s.L);
+            }
+        }
+        const unsigned long long tb = dbits(tau);
+        if (bq < 0 || tb < bt || (tb == bt && a[q] < a[bq])) {
+            bt = tb;
+            bq = q;
+        }
+    }
+    // the claims taken above: a failed one names the chain that holds the disk
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (cas[q] && old[q] != seen[q] && !ours(old[q])) meet(old[q]);
+    if (bq >= 0 && bt < dbits(D)) {
+        o.lift = 1;
+        o.tau = __longlong_as_double((long long)bt);
+        o.j = a[bq];
+        o.xj = r[bq].x;
+        o.tj = r[bq].t;
+        o.jr = r[bq];
+    } else {
+        o.lift = 0;
+        o.tau = D;
+        o.j = NONE;
+        o.xj = o.tj = 0.0;
+    }
+    return o;
+}
+
+// Executes chain c's step from disk i (statements 10-19 for a lift, 21-24 for
+// a stall) and appends its record. Returns the new status, or ST_BLOCKED when
+// the record log is full (reported to the host).
+__device__ int graph_commit(const GDev &s, int c, uint32_t i, double xi, double ti, double D,
+                            const GStep &o, uint32_t seq) {
+    const int32_t nr = s.nrec[c];
+    if (nr >= s.cap) {
+        atomicAdd(s.lc + LC_ERR_REC, 1ull);
+        return ST_BLOCKED;
+    }
+    GEv u;
+    u.i = i;
+    u.seq = seq;
+    u.pad = 0;
+    u.x_old = xi;
+    u.ti_old = ti;
+    GDisk &ri = s.g[i];
+    if (o.lift) {
+        const double tnew = __dadd_rn(ti, o.tau);     // statements 14, 15
+        const double xnew = wrap_add(xi, o.tau, s.L); // statement 16
+        GDisk &rj = s.g[o.j];
+        rj.own = OWN_ACTIVE | (uint32_t)c;             // statement 10 (the claim holds j)
+        rj.t = tnew;
+        ri.t = tnew;
+        ri.x = xnew;
+        ri.own = OWN_STATIC;                           // statement 17
+        u.j = o.j;
+        u.tj_old = o.tj;
+        u.t = tnew;
+        u.tau = o.tau;
+        u.xi = xnew;
+        u.xj = o.xj;
+        u.d_after = __dsub_rn(D, o.tau);               // statement 18
+        s.rec[(size_t)c * s.cap + nr] = u;
+        s.nrec[c] = nr + 1;
+        s.nlift[c] += 1;
+        return ST_RUNNING;
+    }
+    const double tnew = __dadd_rn(ti, D);             // statement 21
+    const double xnew = wrap_add(xi, D, s.L);         // statement 22
+    ri.x = xnew;
+    ri.t = tnew;
+    ri.own = OWN_STALLED | (uint32_t)c;               // statement 24
+    u.j = NONE;
+    u.tj_old = 0.0;
+    u.t = tnew;
+    u.tau = D;
+    u.xi = xnew;
+    u.xj = 0.0;
+    u.d_after = 0.0;                                  // statement 23
+    s.rec[(size_t)c * s.cap + nr] = u;
+    s.nrec[c] = nr + 1;
+    return ST_STALLED;
+}
+
+// ------------------------------------------------------------------ legs
+
+// Leg start: clear the local times the previous leg wrote (every disk its
+// records name), then start every chain on its stalled disk with D = ell.
+__device__ void g_leg_begin_chain(const GDev &s, int c) {
+    const int32_t nr = s.nrec[c];
+    const GEv *q = s.rec + (size_t)c * s.cap;
+    for (int32_t e = 0; e < nr; ++e) {
+        s.g[q[e].i].t = 0.0;
+        if (q[e].j != NONE) s.g[q[e].j].t = 0.0;
+    }
+    const uint32_t i = s.ci[c];
+    s.g[i].own = OWN_ACTIVE | (uint32_t)c;
+    s.ci0[c] = i;
+    s.D[c] = s.ell;
+    s.tc[c] = 0.0;
+    s.status[c] = ST_RUNNING;
+    s.partner[c] = -1;
+    s.nrec[c] = 0;
+    s.nlift[c] = 0;
+}
+
+// Parallel pass of a claim window [tw, tend): one thread runs chain c from
+// its state through its events before tend, until it stalls, pauses at tend
+// or meets another chain's claim.
+__device__ void g_pass1_chain(const GDev &s, int c, uint32_t epoch, double tw, double tend) {
+    if (s.status[c] != ST_RUNNING) return;
+    uint32_t i = s.ci[c];
+    GDisk ri = s.g[i];
+    if (ri.own != (OWN_ACTIVE | (uint32_t)c)) gdiag(s, 6, tw, c, i, ri.own, 0, 0);
+    uint32_t a[3] = {ri.a[0], ri.a[1], ri.a[2]};
+    double b[3] = {ri.b[0], ri.b[1], ri.b[2]};
+    double xi = ri.x, ti = s.tc[c], D = s.D[c];
+    int st = ST_RUNNING;
+    bool blocked = false, first = true;
+    uint32_t lifts = 0;
+    for (;;) {
+        const GStep o =
+            graph_step<true>(s, c, epoch, c, a, b, i, xi, ti, D, tw, first, ri.claim);
+        first = false;
+        if (o.conflict) {
+            s.partner[c] = o.partner < (uint32_t)s.k ? (int32_t)o.partner : -1;
+            blocked = true;
+            break;
+        }
+        // Eq. 2 (statement 5) on the disks of this window: cannot fail while
+        // they are held by a lone chain; an assertion
+        if (o.hz) atomicAdd(s.lc + LC_HORIZON, 1ull);
+        const double T = __dadd_rn(ti, o.tau);
+        if (!(dbits(T) < dbits(tend))) break;  // pauses at the window end
+        if (dbits(T) < dbits(tw)) {
+            atomicAdd(s.lc + LC_ORDER, 1ull);
+            gdiag(s, 9, tw, c, i, o.j, ti, o.tau);
+        }
+        st = graph_commit(s, c, i, xi, ti, D, o, (uint32_t)s.nrec[c]);
+        if (st != ST_RUNNING) break;
+        ++lifts;
+        i = o.j;
+        xi = o.xj;
+        ti = T;
+        D = __dsub_rn(D, o.tau);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            a[q] = o.jr.a[q];
+            b[q] = o.jr.b[q];
+        }
+    }
+    if (blocked) st = ST_BLOCKED;
+    // events before the blocking time, and all before the window, are exact
+    s.vt[c] = blocked ? fmax(ti, tw) : INFINITY;
+    s.status[c] = st;
+    s.ci[c] = i;
+    s.tc[c] = ti;
+    s.D[c] = D;
+    if (blocked) {
+        atomicAdd(s.lc + LC_BLOCKED, 1ull);
+        atomicAdd(s.lc + LC_WBLOCKED, 1ull);
+    }
+    if (lifts) atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)lifts);
+}
+
+// --------------------------------------------------------------- repairs
+
+// Exact inverse of graph_commit for one record of chain c.
+__device__ void g_undo(const GDev &s, int c, const GEv &u) {
+    GDisk &ri = s.g[u.i];
+    ri.x = u.x_old;
+    ri.t = u.ti_old;
+    ri.own = OWN_ACTIVE | (uint32_t)c;
+    if (u.j != NONE) {
+        GDisk &rj = s.g[u.j];
+        rj.t = u.tj_old;
+        rj.own = OWN_STATIC;
+        s.nlift[c] -= 1;
+    }
+}
+
+// Rolls the members of a component back to T* (their events before T* are
+// exact): records with event time >= T* are undone, latest first. Records of
+// repair rounds (seq >= REPAIR_SEQ0) may touch one disk from several members
+// and are undone one at a time in descending seq; beneath them, the records
+// of the window's parallel pass touch disks claimed by their own chain only,
+// so each member undoes its own in parallel.
+__device__ void g_rollback(const GDev &s, const int32_t *mem, int m, double Ts) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t bseq = 0;
+        int bmem = -1;
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            const int32_t nr = s.nrec[c];
+            if (nr == 0) continue;
+            const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+            if (!(u.t >= Ts) || u.seq < REPAIR_SEQ0) continue;
+            if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
+                bseq = u.seq;
+                bmem = e;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t s2 = __shfl_xor_sync(FULL, bseq, o);
+            const int m2 = __shfl_xor_sync(FULL, bmem, o);
+            if (m2 >= 0 && (bmem < 0 || s2 > bseq || (s2 == bseq && m2 < bmem))) {
+                bseq = s2;
+                bmem = m2;
+            }
+        }
+        if (bmem < 0) break;
+        if (lane == 0) {
+            const int c = mem[bmem];
+            const int32_t nr = s.nrec[c];
+            g_undo(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
+            s.nrec[c] = nr - 1;
+        }
+        __syncwarp();
+    }
+    for (int e = lane; e < m; e += 32) {
+        const int c = mem[e];
+        int32_t nr = s.nrec[c];
+        while (nr > 0) {
+            const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+            if (!(u.t >= Ts)) break;
+            g_undo(s, c, u);
+            --nr;
+        }
+        s.nrec[c] = nr;
+    }
+    __syncwarp();
+}
+
+// State of chain c after its last kept record (or at the leg start).
+__device__ void g_resume(const GDev &s, int c) {
+    const int32_t nr = s.nrec[c];
+    if (nr == 0) {
+        s.ci[c] = s.ci0[c];
+        s.tc[c] = 0.0;
+        s.D[c] = s.ell;
+        s.status[c] = ST_RUNNING;
+        return;
+    }
+    const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+    if (u.j == NONE) {
+        s.ci[c] = u.i;
+        s.tc[c] = u.t;
+        s.D[c] = 0.0;
+        s.status[c] = ST_STALLED;
+    } else {
+        s.ci[c] = u.j;
+        s.tc[c] = u.t;
+        s.D[c] = u.d_after;
+        s.status[c] = ST_RUNNING;
+    }
+}
+
+// Pending event of member c (one thread), kept with the arrows it read.
+__device__ void g_compute(const GDev &s, int c, int root, uint32_t epoch, bool &abort,
+                          int &met) {
+    const uint32_t i = s.ci[c];
+    const GDisk ri = s.g[i];
+    const double ti = s.tc[c], D = s.D[c];
+    const GStep o = graph_step<false>(s, c, epoch, root, ri.a, ri.b, i, ri.x, ti, D, 0.0,
+                                      true, ri.claim);
+    if (o.conflict && !abort) {
+        abort = true;
+        met = (int)o.partner;
+    }
+    s.ev_T[c] = __dadd_rn(ti, o.tau);
+    s.ev_tau[c] = o.tau;
+    s.ev_j[c] = o.j;
+    s.ev_lift[c] = o.lift;
+    s.ev_xj[c] = o.xj;
+    s.ev_tj[c] = o.tj;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s.ev_a[3 * (size_t)c + q] = ri.a[q];
+}
+
+// After a component's replay: record abort or success for the next round.
+__device__ void g_finish(const GDev &s, const int32_t *mem, int m, int root, bool abort,
+                         int met, double now, int round) {
+    const int lane = threadIdx.x & 31;
+    if (abort) {
+        // events before `now` are exact; the chain met joins next round
+        for (int e = lane; e < m; e += 32) s.vt[mem[e]] = now;
+        if (lane == 0) {
+            if (met >= 0 && met < s.k) {
+                s.abort_to[root] = met;
+                atomic_min_time(s.vt + met, now);
+            }
+            atomicAdd(s.nabort + (round & 1), 1);
+        }
+    } else {
+        for (int e = lane; e < m; e += 32) {
+            s.fin[mem[e]] = 2;
+            s.vt[mem[e]] = INFINITY;
+        }
+    }
+    __syncwarp();
+}
+
+// Component q of this round (one warp): roll its members back to T*, then
+// replay them in global event-time order (Alg. 2) up to the window's end.
+// Members are spread over the lanes (member e on lane e mod 32); after each
+// event only the members whose arrows read a disk it changed recompute.
+__device__ void g_repair_component(const GDev &s, int q, int round, uint32_t epoch, double tw,
+                                   double tend) {
+    const int lane = threadIdx.x & 31;
+    const int root = s.comp_root[q];
+    const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
+    const int32_t *mem = s.comp_mem + off;
+    double Ts = INFINITY;
+    for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
+    Ts = fmax(Ts, tw);  // earlier windows are final
+    if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
+    g_rollback(s, mem, m, Ts);
+    for (int e = lane; e < m; e += 32) g_resume(s, mem[e]);
+    __syncwarp();
+    bool abort = false;
+    int met = -1;
+    for (int e = lane; e < m; e += 32)
+        if (s.status[mem[e]] == ST_RUNNING) g_compute(s, mem[e], root, epoch, abort, met);
+    double now = Ts;
+    uint32_t cnt = 0;
+    for (;;) {
+        {
+            const unsigned ab = __ballot_sync(FULL, abort);
+            if (ab) {
+                met = __shfl_sync(FULL, met, __ffs(ab) - 1);
+                abort = true;
+                break;
+            }
+        }
+        unsigned long long bT = ~0ull;
+        int bc = 0x7FFFFFFF, bl = lane;
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            if (s.status[c] != ST_RUNNING) continue;
+            const unsigned long long T = dbits(s.ev_T[c]);
+            if (T < bT || (T == bT && c < bc)) {
+                bT = T;
+                bc = c;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long T2 = shfl_xor_u64(bT, o);
+            const int c2 = __shfl_xor_sync(FULL, bc, o);
+            const int l2 = __shfl_xor_sync(FULL, bl, o);
+            if (T2 < bT || (T2 == bT && c2 < bc)) {
+                bT = T2;
+                bc = c2;
+                bl = l2;
+            }
+        }
+        if (bc == 0x7FFFFFFF) break;
+        if (!(bT < dbits(tend))) break;  // the rest lies in a later window
+        const double Tn = __longlong_as_double((long long)bT);
+        if (dbits(Tn) < dbits(now) && lane == 0) {
+            atomicAdd(s.lc + LC_ORDER, 1ull);
+            gdiag(s, 2, round, bc, Tn, now, Ts, m);
+        }
+        now = Tn;
+        uint32_t ib = NONE, jb = NONE;
+        int st = ST_RUNNING;
+        if (lane == bl) {
+            const uint32_t i = s.ci[bc];
+            const double ti = s.tc[bc], D = s.D[bc];
+            GStep o;
+            o.lift = s.ev_lift[bc];
+            o.tau = s.ev_tau[bc];
+            o.j = s.ev_j[bc];
+            o.xj = s.ev_xj[bc];
+            o.tj = s.ev_tj[bc];
+            const double xi = s.g[i].x;
+            st = graph_commit(s, bc, i, xi, ti, D, o, ((uint32_t)round << 24) | cnt);
+            ib = i;
+            if (st == ST_RUNNING) {
+                jb = o.j;
+                s.ci[bc] = o.j;
+                s.tc[bc] = __dadd_rn(ti, o.tau);
+                s.D[bc] = __dsub_rn(D, o.tau);
+            } else if (st == ST_STALLED) {
+                s.tc[bc] = __dadd_rn(ti, D);
+                s.D[bc] = 0.0;
+                s.status[bc] = ST_STALLED;
+            }
+        }
+        ++cnt;
+        st = __shfl_sync(FULL, st, bl);
+        ib = __shfl_sync(FULL, ib, bl);
+        jb = __shfl_sync(FULL, jb, bl);
+        __syncwarp();
+        if (st == ST_BLOCKED) {  // out of records: reported by the host
+            abort = true;
+            met = -1;
+            break;
+        }
+        for (int e = lane; e < m; e += 32) {
+            const int c = mem[e];
+            if (s.status[c] != ST_RUNNING) continue;
+            bool redo = c == bc;
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) {
+                const uint32_t v = s.ev_a[3 * (size_t)c + k2];
+                redo |= v != NONE && (v == ib || v == jb);
+            }
+            if (redo) g_compute(s, c, root, epoch, abort, met);
+        }
+        __syncwarp();
+    }
+    g_finish(s, mem, m, root, abort, met, now, round);
+}
+
+// Leg end: totals, and the lifting log (chain by chain).
+__device__ void g_leg_end_chain(const GDev &s, int c, int32_t leg) {
+    const int32_t nl = s.nlift[c];
+    atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
+    if (s.log_on && nl > 0) {
+        const unsigned long long base = atomicAdd(s.tc_cnt + TC_LOG_N, (unsigned long long)nl);
+        const GEv *q = s.rec + (size_t)c * s.cap;
+        unsigned long long w = base;
+        for (int32_t e = 0; e < s.nrec[c]; ++e) {
+            if (q[e].j == NONE) continue;
+            if ((int64_t)w < s.log_cap) {
+                ecmc_lift_t L;
+                L.leg = leg;
+                L.c = c;
+                L.i = (int32_t)q[e].i;
+                L.j = (int32_t)q[e].j;
+                L.t = q[e].t;
+                L.tau = q[e].tau;
+                L.xi = q[e].xi;
+                L.xj = q[e].xj;
+                s.log[w] = L;
+            }
+            ++w;
+        }
+    }
+}
+
+// ------------------------------------------- persistent multi-leg kernel
+
+struct GCtl {
+    int64_t budget;  // liftings for this run (0: none)
+    int64_t lifts, legs, conflict_legs, repaired, horizon, order_err, p1_lifts, repair_lifts;
+    uint8_t *flags;  // per-leg conflict flags (device) or null
+    int32_t flags_cap;
+    int32_t done;    // budget reached or error
+    int32_t err;     // LC_ERR_* seen, or too many repair rounds
+    int32_t pad;
+};
+
+enum { GPH_BEGIN = 0, GPH_PASS1, GPH_REPAIR, GPH_END, GPH_N };
+
+struct GRun {
+    GDev s;
+    GCtl *ctl;
+    unsigned int *bar;               // [2] grid barrier
+    int32_t *err;                    // ECMC_ETIMEOUT from a barrier
+    unsigned long long *phase_ns;    // [GPH_N] device time per phase (block 0 clock)
+    int32_t max_legs;
+    uint32_t win0;                   // claim windows run before this launch, mod EPOCH_MAX
+    int64_t leg0;                    // legs run before this launch (lifting log)
+};
+
+__device__ __forceinline__ double g_window_start(const GDev &s, int w) {
+    return w == 0 ? 0.0 : __ddiv_rn(__dmul_rn((double)w, s.ell), (double)s.windows);
+}
+
+__device__ __forceinline__ double g_window_end(const GDev &s, int w) {
+    return w + 1 >= s.windows ? INFINITY
+                              : __ddiv_rn(__dmul_rn((double)(w + 1), s.ell), (double)s.windows);
+}
+
+constexpr int GRUN_THREADS = 256;
+constexpr int GRUN_MIN_BLOCKS = 2;
+
+// One cooperative launch runs up to max_legs legs. Per leg and claim window:
+// the parallel pass (one thread per chain), then repair rounds (conflict
+// components by one block, their replays by one warp each) until no component
+// met another chain. Phases are separated by grid barriers whose waits are
+// bounded (ECMC_ETIMEOUT).
+__global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRun R) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    __shared__ int sflag;
+    const GDev &s = R.s;
+    const int lane = threadIdx.x & 31;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = timer ? gtimer() : 0ull;
+    auto mark = [&](int ph) {
+        if (timer) {
+            const unsigned long long t = gtimer();
+            R.phase_ns[ph] += t - t_prev;
+            t_prev = t;
+        }
+    };
+    for (int leg = 0; leg < R.max_legs; ++leg) {
+        for (int c = gt; c < s.k; c += nthreads) g_leg_begin_chain(s, c);
+        if (gt < LC_N) s.lc[gt] = 0ull;
+        if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
+        if (!grid_sync(R.bar, R.err, &sflag)) return;
+        mark(GPH_BEGIN);
+        for (int w = 0; w < s.windows; ++w) {
+            const uint32_t epoch =
+                (uint32_t)(((uint64_t)R.win0 + (uint64_t)leg * s.windows + w) % EPOCH_MAX) + 1u;
+            if (epoch == 1u) {
+                // the epochs wrapped: no claim word may look like one of this window
+                for (int64_t q = gt; q < s.n; q += nthreads) s.g[q].claim = 0u;
+                if (!grid_sync(R.bar, R.err, &sflag)) return;
+            }
+            const double tw = g_window_start(s, w), te = g_window_end(s, w);
+            for (int c = gt; c < s.k; c += nthreads) g_pass1_chain(s, c, epoch, tw, te);
+            if (!grid_sync(R.bar, R.err, &sflag)) return;
+            mark(GPH_PASS1);
+            if (gt == 0) s.nabort[1] = 0;  // the first round's abort count
+            for (int round = 1;; ++round) {
+                if (blockIdx.x == 0) {
+                    const bool need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull
+                                                 : s.nabort[(round - 1) & 1] != 0;
+                    __syncthreads();
+                    if (round == 1 && threadIdx.x == 0) {
+                        s.lc[LC_WBLOCKED] = 0ull;
+                        if (need) s.lc[LC_CWINDOWS] += 1ull;
+                    }
+                    if (need && round <= 255) {
+                        uf_block(s, round == 1, warp_tot, tot, false);
+                    } else if (threadIdx.x == 0) {
+                        s.ctl[CTL_NCOMP] = 0;
+                        if (need) R.ctl->err = 1;  // too many rounds
+                    }
+                    __syncthreads();
+                }
+                if (!grid_sync(R.bar, R.err, &sflag)) return;
+                // every block has read the previous round's abort count
+                if (gt == 0) s.nabort[(round + 1) & 1] = 0;
+                const int ncomp = s.ctl[CTL_NCOMP];
+                if (ncomp == 0) break;
+                for (;;) {
+                    int q = 0;
+                    if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
+                    q = __shfl_sync(FULL, q, 0);
+                    if (q >= ncomp) break;
+                    g_repair_component(s, q, round, epoch, tw, te);
+                }
+                if (!grid_sync(R.bar, R.err, &sflag)) return;
+                // no component met another chain: the window is repaired
+                if (*(volatile int32_t *)(s.nabort + (round & 1)) == 0) break;
+            }
+            mark(GPH_REPAIR);
+        }
+        // leg end: liftings and the log, then totals and the budget
+        for (int c = gt; c < s.k; c += nthreads)
+            g_leg_end_chain(s, c, (int32_t)(R.leg0 + R.ctl->legs));
+        if (!grid_sync(R.bar, R.err, &sflag)) return;
+        if (gt == 0) {
+            GCtl &c = *R.ctl;
+            const unsigned long long *lc = s.lc;
+            const int flag = lc[LC_BLOCKED] != 0ull;
+            if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
+            c.lifts += (int64_t)lc[LC_LIFTS];
+            c.p1_lifts += (int64_t)lc[LC_P1LIFTS];
+            if (flag) c.repair_lifts += (int64_t)lc[LC_LIFTS];
+            c.legs += 1;
+            c.conflict_legs += flag;
+            c.repaired += (int64_t)lc[LC_REPAIRED];
+            c.horizon += (int64_t)lc[LC_HORIZON];
+            c.order_err += (int64_t)lc[LC_ORDER];
+            if (lc[LC_ERR_REC]) c.err = 1;
+            if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
+        }
+        if (!grid_sync(R.bar, R.err, &sflag)) return;
+        mark(GPH_END);
+        if (*(volatile int32_t *)&R.ctl->done) break;
+    }
+}
+
+// Exports positions (per disk id), local times and active disks.
+__global__ void k_g_export(GDev s, double *x, double *t) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.n) return;
+    if (x) x[q] = s.g[q].x;
+    if (t) t[q] = s.g[q].t;
+}
+
+__global__ void k_g_export_active(GDev s, int32_t *active) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s.k) active[c] = (int32_t)s.ci[c];
+}
+
+// Direction change: the disks' x and y are exchanged (x from y_old, y from
+// x_old); the graph is then rebuilt for the new frame.
+__global__ void k_g_swap_xy(GDev s, double *xnew) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.n) return;
+    const double xo = s.g[q].x;
+    xnew[q] = s.y[q];
+    s.y[q] = xo;
+}
+
+__global__ void k_g_reset_chains(GDev s) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.k) return;
+    s.nrec[c] = 0;
+    s.ci0[c] = s.ci[c];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+
+struct GraphCtx {
+    GDev s;
+    int nc = 0;
+    double box = 0.0;
+    cudaStream_t st = nullptr;
+    std::vector<void *> allocs;
+    GCtl *d_ctl = nullptr;
+    unsigned int *d_bar = nullptr;
+    int32_t *d_err = nullptr;
+    unsigned long long *d_phase = nullptr;
+    uint8_t *d_flags = nullptr;
+    int32_t flags_cap = 0;
+    uint64_t windows_run = 0;
+    int64_t log_legs = 0;  // legs logged so far (leg index of the log)
+    int grid = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+template <typename T>
+int galloc(GraphCtx *g, T **ptr, size_t count, std::string &err) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        err = "cudaMalloc failed (graph state)";
+        return ECMC_ENOMEM;
+    }
+    g->allocs.push_back(p);
+    *ptr = (T *)p;
+    return 0;
+}
+
+// Builds the arrows (and x, t = 0) of every disk from positions x, y (device).
+int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err) {
+    GDev &s = g->s;
+    const int nc = g->nc;
+    const double a = g->box / nc;
+    // slots per cell: at most 4 centres at mutual distance >= d fit in a cell
+    // with a < sqrt(2) d, at most 6 for a < 1.664 d
+    const int C = a < std::sqrt(2.0) * s.d * (1.0 - 1e-9) ? 4 : 8;
+    GBuild b;
+    b.n = s.n;
+    b.nc = nc;
+    b.L = s.L;
+    b.d = s.d;
+    b.d2 = s.d * s.d;
+    b.a = a;
+    b.inv_a = (double)nc / s.L;
+    b.eps = std::ldexp(s.L, -30);
+    b.w = s.d / 128.0;
+    b.nb = (int)std::ceil(s.L / b.w);
+    b.x = x;
+    b.y = y;
+    b.g = s.g;
+    const size_t nslot = (size_t)nc * nc * C;
+    void *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    auto release = [&]() {
+        for (void *p : tmp) cudaFree(p);
+    };
+    if (cudaMalloc(&tmp[0], nslot * 4) != cudaSuccess ||
+        cudaMalloc(&tmp[1], nslot * 8) != cudaSuccess ||
+        cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
+        cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
+        cudaMalloc(&tmp[4], 8) != cudaSuccess) {
+        (void)cudaGetLastError();
+        release();
+        err = "cudaMalloc failed (graph build)";
+        return ECMC_ENOMEM;
+    }
+    b.cid = (uint32_t *)tmp[0];
+    b.cx = (double *)tmp[1];
+    b.cy = (double *)tmp[2];
+    b.bins = (int32_t *)tmp[3];
+    b.err = (unsigned long long *)tmp[4];
+    cudaStream_t st = g->st;
+    cudaMemsetAsync(b.cid, 0xFF, nslot * 4, st);
+    cudaMemsetAsync(b.bins, 0, ((size_t)b.nb + 1) * 4, st);
+    cudaMemsetAsync(b.err, 0, 8, st);
+    const unsigned nblk = (unsigned)((s.n + 255) / 256);
+    if (C == 4)
+        k_gb_cells<4><<<nblk, 256, 0, st>>>(b);
+    else
+        k_gb_cells<8><<<nblk, 256, 0, st>>>(b);
+    k_gb_scan<<<1, 1024, 0, st>>>(b);
+    int dev = 0, n_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned ablk = (unsigned)std::min<int64_t>((s.n + 7) / 8, (int64_t)n_sm * 16);
+    if (C == 4)
+        k_gb_arrows<4><<<ablk, 256, 0, st>>>(b);
+    else
+        k_gb_arrows<8><<<ablk, 256, 0, st>>>(b);
+    unsigned long long overflow = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&overflow, b.err, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) {
+        err = std::string("graph build: ") + cudaGetErrorString(e);
+        return ECMC_ECUDA;
+    }
+    if (overflow) {
+        err = "more disks in a cell than it has slots (overlapping input?)";
+        return ECMC_ECAPACITY;
+    }
+    return 0;
+}
+
+}  // namespace
+
+int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
+                 const int32_t *active, cudaStream_t st, GraphCtx **out, std::string &err) {
+    *out = nullptr;
+    if (p->n_chains > MAX_CHAINS) {
+        err = "graph mode supports at most 2^20 - 2 chains";
+        return ECMC_EINVAL;
+    }
+    GraphCtx *g = new (std::nothrow) GraphCtx();
+    if (!g) {
+        err = "host allocation";
+        return ECMC_ENOMEM;
+    }
+    g->nc = nc;
+    g->box = p->box;
+    g->st = st;
+    GDev &s = g->s;
+    memset(&s, 0, sizeof s);
+    s.n = p->n;
+    s.k = p->n_chains;
+    s.nc = nc;
+    s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
+    s.windows = p->windows > 0 ? p->windows : 1;
+    s.L = p->box;
+    s.d = p->d;
+    s.ell = p->ell;
+    s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
+    s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    int rc = 0;
+    auto chk = [&](int r) {
+        if (r && !rc) rc = r;
+    };
+    chk(galloc(g, &s.g, n, err));
+    chk(galloc(g, &s.y, n, err));
+    chk(galloc(g, &s.ci, k, err));
+    chk(galloc(g, &s.ci0, k, err));
+    chk(galloc(g, &s.D, k, err));
+    chk(galloc(g, &s.tc, k, err));
+    chk(galloc(g, &s.status, k, err));
+    chk(galloc(g, &s.partner, k, err));
+    chk(galloc(g, &s.nrec, k, err));
+    chk(galloc(g, &s.nlift, k, err));
+    chk(galloc(g, &s.rec, k * (size_t)s.cap, err));
+    chk(galloc(g, &s.ev_T, k, err));
+    chk(galloc(g, &s.ev_tau, k, err));
+    chk(galloc(g, &s.ev_xj, k, err));
+    chk(galloc(g, &s.ev_tj, k, err));
+    chk(galloc(g, &s.ev_j, k, err));
+    chk(galloc(g, &s.ev_a, 3 * k, err));
+    chk(galloc(g, &s.ev_lift, k, err));
+    chk(galloc(g, &s.vt, k, err));
+    chk(galloc(g, &s.uf, k, err));
+    chk(galloc(g, &s.fin, k, err));
+    chk(galloc(g, &s.comp_of, k, err));
+    chk(galloc(g, &s.abort_to, k, err));
+    chk(galloc(g, &s.comp_cnt, k, err));
+    chk(galloc(g, &s.comp_off, k + 1, err));
+    chk(galloc(g, &s.comp_root, k, err));
+    chk(galloc(g, &s.comp_mem, k, err));
+    chk(galloc(g, &s.ctl, CTL_N, err));
+    chk(galloc(g, &s.nabort, 2, err));
+    chk(galloc(g, &s.lc, LC_N, err));
+    chk(galloc(g, &s.tc_cnt, TC_N, err));
+    chk(galloc(g, &s.dbg, 16, err));
+    if (s.log_on) chk(galloc(g, &s.log, (size_t)s.log_cap, err));
+    chk(galloc(g, &g->d_ctl, 1, err));
+    chk(galloc(g, &g->d_bar, 2, err));
+    chk(galloc(g, &g->d_err, 1, err));
+    chk(galloc(g, &g->d_phase, GPH_N, err));
+    if (!rc && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess)) {
+        err = "event creation";
+        rc = ECMC_ECUDA;
+    }
+    if (rc) {
+        graph_destroy(g);
+        return rc;
+    }
+    cudaMemcpyAsync(s.y, y, n * 8, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(s.nrec, 0, k * 4, st);
+    cudaMemsetAsync(s.lc, 0, LC_N * 8, st);
+    cudaMemsetAsync(s.tc_cnt, 0, TC_N * 8, st);
+    cudaMemsetAsync(s.dbg, 0, 16 * 8, st);
+    rc = graph_build(g, x, s.y, err);
+    if (rc) {
+        graph_destroy(g);
+        return rc;
+    }
+    k_g_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s);
+    k_g_init_chains<<<(unsigned)((k + 127) / 128), 128, 0, st>>>(s, active);
+    int dev = 0, n_sm = 1, blocks = 0, coop = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_run_graph, GRUN_THREADS, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || !coop || blocks < 1) {
+        (void)cudaGetLastError();
+        err = e != cudaSuccess ? std::string("graph create: ") + cudaGetErrorString(e)
+                               : std::string("cooperative launch unavailable");
+        graph_destroy(g);
+        return ECMC_ECUDA;
+    }
+    g->grid = n_sm * std::min(blocks, GRUN_MIN_BLOCKS);
+    *out = g;
+    return 0;
+}
+
+int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
+              int32_t *legs_done, GraphTotals *tot, std::string &err) {
+    memset(tot, 0, sizeof *tot);
+    if (legs_done) *legs_done = 0;
+    if (n_legs <= 0) return 0;
+    cudaStream_t st = g->st;
+    if (g->flags_cap < n_legs) {
+        cudaFree(g->d_flags);
+        g->d_flags = nullptr;
+        g->flags_cap = 0;
+        if (cudaMalloc(&g->d_flags, (size_t)n_legs) != cudaSuccess) {
+            (void)cudaGetLastError();
+            err = "flags allocation";
+            return ECMC_ENOMEM;
+        }
+        g->flags_cap = n_legs;
+    }
+    GCtl ctl;
+    memset(&ctl, 0, sizeof ctl);
+    ctl.budget = (int64_t)budget;
+    ctl.flags = g->d_flags;
+    ctl.flags_cap = g->flags_cap;
+    int rc = 0;
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !rc) {
+            (void)cudaGetLastError();
+            err = std::string(what) + ": " + cudaGetErrorString(e);
+            rc = ECMC_ECUDA;
+        }
+    };
+    cu(cudaMemcpyAsync(g->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, st), "ctl");
+    cu(cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned int), st), "bar");
+    cu(cudaMemsetAsync(g->d_err, 0, sizeof(int32_t), st), "err");
+    cu(cudaMemsetAsync(g->d_phase, 0, GPH_N * sizeof(unsigned long long), st), "phase");
+    if (rc) return rc;
+    GRun R;
+    R.s = g->s;
+    R.ctl = g->d_ctl;
+    R.bar = g->d_bar;
+    R.err = g->d_err;
+    R.phase_ns = g->d_phase;
+    R.max_legs = n_legs;
+    R.win0 = (uint32_t)(g->windows_run % EPOCH_MAX);
+    R.leg0 = g->log_legs;
+    void *args[] = {&R};
+    cu(cudaEventRecord(g->ev0, st), "event");
+    cu(cudaLaunchCooperativeKernel((void *)k_run_graph, g->grid, GRUN_THREADS, args, 0, st),
+       "launch");
+    cu(cudaEventRecord(g->ev1, st), "event");
+    int32_t gerr = 0;
+    unsigned long long ph[GPH_N];
+    cu(cudaMemcpyAsync(&ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, st), "ctl");
+    cu(cudaMemcpyAsync(&gerr, g->d_err, sizeof gerr, cudaMemcpyDeviceToHost, st), "err");
+    cu(cudaMemcpyAsync(ph, g->d_phase, sizeof ph, cudaMemcpyDeviceToHost, st), "phase");
+    cu(cudaStreamSynchronize(st), "run");
+    if (rc) return rc;
+    float ms = 0.f;
+    cu(cudaEventElapsedTime(&ms, g->ev0, g->ev1), "elapsed");
+    g->windows_run += (uint64_t)ctl.legs * (uint64_t)g->s.windows;
+    g->log_legs += ctl.legs;
+    tot->legs = ctl.legs;
+    tot->lifts = ctl.lifts;
+    tot->conflict_legs = ctl.conflict_legs;
+    tot->repaired = ctl.repaired;
+    tot->horizon = ctl.horizon;
+    tot->order_err = ctl.order_err;
+    tot->p1_lifts = ctl.p1_lifts;
+    tot->repair_lifts = ctl.repair_lifts;
+    tot->ms = ms;
+    tot->pass1_ms = ph[GPH_PASS1] * 1e-6;
+    tot->repair_ms = ph[GPH_REPAIR] * 1e-6;
+    tot->other_ms = (ph[GPH_BEGIN] + ph[GPH_END]) * 1e-6;
+    if (legs_done) *legs_done = (int32_t)ctl.legs;
+    if (flags_host && ctl.legs > 0) {
+        cu(cudaMemcpy(flags_host, g->d_flags, (size_t)ctl.legs, cudaMemcpyDeviceToHost), "flags");
+        if (rc) return rc;
+    }
+    if (gerr == ECMC_ETIMEOUT) {
+        err = "a grid barrier wait passed its time limit";
+        return ECMC_ETIMEOUT;
+    }
+    if (ctl.err) {
+        err = "undo records or repair rounds overflowed";
+        return ECMC_ECAPACITY;
+    }
+    double dg[7];
+    if (cudaMemcpy(dg, g->s.dbg, sizeof dg, cudaMemcpyDeviceToHost) == cudaSuccess &&
+        dg[0] != 0.0) {
+        char buf[240];
+        snprintf(buf, sizeof buf, "internal check %g failed: %.17g %.17g %.17g %.17g %.17g %.17g",
+                 dg[0], dg[1], dg[2], dg[3], dg[4], dg[5], dg[6]);
+        err = buf;
+        return ECMC_ECUDA;
+    }
+    return 0;
+}
+
+int graph_export(GraphCtx *g, double *x, double *y, double *t, int32_t *active) {
+    const GDev &s = g->s;
+    cudaStream_t st = g->st;
+    if (x || t) k_g_export<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, x, t);
+    if (y) cudaMemcpyAsync(y, s.y, (size_t)s.n * 8, cudaMemcpyDeviceToDevice, st);
+    if (active) k_g_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, active);
+    return cudaGetLastError() == cudaSuccess ? 0 : ECMC_ECUDA;
+}
+
+int graph_transpose(GraphCtx *g, std::string &err) {
+    GDev &s = g->s;
+    double *xnew = nullptr;
+    if (cudaMalloc(&xnew, (size_t)s.n * 8) != cudaSuccess) {
+        (void)cudaGetLastError();
+        err = "transpose scratch";
+        return ECMC_ENOMEM;
+    }
+    k_g_swap_xy<<<(unsigned)((s.n + 255) / 256), 256, 0, g->st>>>(s, xnew);
+    k_g_reset_chains<<<(unsigned)((s.k + 127) / 128), 128, 0, g->st>>>(s);
+    int rc = graph_build(g, xnew, s.y, err);  // x, t = 0 and arrows for the new frame
+    cudaFree(xnew);
+    return rc;
+}
+
+int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
+                   std::string &err) {
+    const GDev &s = g->s;
+    if (!s.log_on) {
+        err = "lifting log not enabled";
+        return ECMC_EINVAL;
+    }
+    unsigned long long n = 0;
+    if (cudaMemcpy(&n, s.tc_cnt + TC_LOG_N, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        err = "log count";
+        return ECMC_ECUDA;
+    }
+    *n_out = (int64_t)n;
+    if ((int64_t)n > s.log_cap) {
+        err = "lifting log overflowed log_cap";
+        return ECMC_ECAPACITY;
+    }
+    std::vector<ecmc_lift_t> all((size_t)n);
+    if (n && cudaMemcpy(all.data(), s.log, n * sizeof(ecmc_lift_t), cudaMemcpyDeviceToHost) !=
+                 cudaSuccess) {
+        err = "log copy";
+        return ECMC_ECUDA;
+    }
+    std::stable_sort(all.begin(), all.end(), [](const ecmc_lift_t &a, const ecmc_lift_t &b) {
+        return a.leg != b.leg ? a.leg < b.leg : a.c < b.c;
+    });
+    if (buf && cap > 0)
+        memcpy(buf, all.data(), (size_t)std::min<int64_t>(cap, (int64_t)n) * sizeof(ecmc_lift_t));
+    return 0;
+}
+
+void graph_destroy(GraphCtx *g) {
+    if (!g) return;
+    for (void *p : g->allocs) cudaFree(p);
+    cudaFree(g->d_flags);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}

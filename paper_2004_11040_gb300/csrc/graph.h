@@ -1,0 +1,34 @@
+// graph.h -- internal interface between the C ABI (ecmc.cu) and the
+// constraint-graph path (graph.cu, ECMC_GRAPH). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ecmc.h"
+
+struct GraphCtx;
+
+// Totals of one graph_run call.
+struct GraphTotals {
+    int64_t legs, lifts, conflict_legs, repaired, horizon, order_err, p1_lifts, repair_lifts;
+    double ms, pass1_ms, repair_ms, other_ms;
+};
+
+// A context on device inputs x, y (n each) and active (k), all device
+// pointers valid until the call returns; nc cells per side are used only to
+// build the graph.
+int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
+                 const int32_t *active, cudaStream_t st, GraphCtx **out, std::string &err);
+int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
+              int32_t *legs_done, GraphTotals *tot, std::string &err);
+// Device outputs (each may be null), filled on the context's stream.
+int graph_export(GraphCtx *g, double *x, double *y, double *t, int32_t *active);
+// Exchanges x and y of every disk (the next legs move along the other axis),
+// clears the local times and rebuilds the graph.
+int graph_transpose(GraphCtx *g, std::string &err);
+int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
+                   std::string &err);
+void graph_destroy(GraphCtx *g);

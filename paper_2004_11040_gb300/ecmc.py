@@ -22,6 +22,7 @@ ECMC_ETIMEOUT = -4
 ECMC_ECAPACITY = -5
 ECMC_LOG_LIFTINGS = 0x1
 ECMC_INPUT_DEVICE = 0x2
+ECMC_GRAPH = 0x4
 
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
@@ -238,13 +239,15 @@ class System:
     """One ECMC system on the GPU: a thin owner of an ecmc_ctx handle."""
 
     def __init__(self, x, y, active, box, ell, *, d=1.0, cells_per_side=0, log=False,
-                 undo_cap=0, log_cap=0, stream=None, device_input=False, windows=1):
+                 undo_cap=0, log_cap=0, stream=None, device_input=False, windows=1,
+                 graph=False):
         x = x if device_input else np.ascontiguousarray(x, dtype=np.float64)
         y = y if device_input else np.ascontiguousarray(y, dtype=np.float64)
         active = active if device_input else np.ascontiguousarray(active, dtype=np.int32)
         self.n = int(x.shape[0])
         self.k = int(active.shape[0])
-        flags = (ECMC_LOG_LIFTINGS if log else 0) | (ECMC_INPUT_DEVICE if device_input else 0)
+        flags = (ECMC_LOG_LIFTINGS if log else 0) | (ECMC_INPUT_DEVICE if device_input else 0) \
+            | (ECMC_GRAPH if graph else 0)
         self.params = ecmc_params(self.n, float(box), float(d), float(ell), self.k,
                                   int(cells_per_side), flags, int(undo_cap), int(log_cap),
                                   int(windows), 0)

@@ -1,0 +1,145 @@
+"""Constraint-graph mode (ECMC_GRAPH, Sec. 3.1) of libecmc against the oracle.
+
+The oracle's graph-mode legs (search=2) take the liftings of Alg. 2 (pinned
+equal to the all-pairs definition in test_oracle_graph.py) and the flag from
+the disks isolated chains read. Tolerance: bit-exact, as for the cell scan.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2004_11040_gb300 import ecmc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def chain_order(log):
+    idx = np.lexsort((np.arange(len(log)), log["c"], log["leg"]))
+    return log[idx]
+
+
+def gpu_graph(start, ell, n_legs, windows=1, undo_cap=0, directions=None):
+    sysm = ecmc.System(start.x, start.y, start.active, start.box, ell, d=start.d, log=True,
+                       undo_cap=undo_cap, log_cap=max(1 << 16, 64 * start.k * n_legs * 64),
+                       windows=windows, graph=True)
+    flags = []
+    if directions is None:
+        f, done = sysm.run(n_legs)
+        assert done == n_legs
+        flags = list(f)
+    else:
+        for leg in range(n_legs):
+            sysm.set_direction(directions[leg])
+            f, done = sysm.run(1)
+            assert done == 1
+            flags += list(f)
+    x, y, t, a = sysm.positions()
+    log = sysm.liftings()
+    st = sysm.stats()
+    sysm.close()
+    return np.array(flags, dtype=np.uint8), x, y, t, a, log, st
+
+
+def oracle_graph(start, ell, n_legs, windows=1):
+    last, legs = O.run_legs(start.x, start.y, start.active, start.box, ell, n_legs,
+                            d=start.d, windows=windows, search=2)
+    flags = np.array([r.flag for r in legs], dtype=np.uint8)
+    log = np.concatenate([r.log for r in legs])
+    return flags, last, log
+
+
+def assert_graph_parity(start, ell, n_legs, windows=1):
+    gf, gx, gy, gt, ga, glog, st = gpu_graph(start, ell, n_legs, windows)
+    of, last, olog = oracle_graph(start, ell, n_legs, windows)
+    assert np.array_equal(gy, start.y)
+    assert np.array_equal(gf, of), (gf, of)
+    assert np.array_equal(ga, last.active)
+    assert np.array_equal(gx, last.x), np.max(np.abs(gx - last.x))
+    assert np.array_equal(gt, last.t), np.max(np.abs(gt - last.t))
+    a, b = chain_order(olog), chain_order(glog)
+    assert len(a) == len(b)
+    for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
+        assert np.array_equal(a[f], b[f]), f
+    assert st["liftings"] == len(olog)
+    assert st["horizon_asserts"] == 0
+    assert st["order_errors"] == 0
+    return gf, st
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_graph_config1_lattice_n256(seed):
+    s = synth.lattice_start(16, 0.70, 4, seed=seed)
+    assert_graph_parity(s, 0.5, 8)
+
+
+@pytest.mark.parametrize("seed,windows", [(21, 1), (22, 3), (23, 2)])
+def test_graph_random_2d(seed, windows):
+    """Random (RSA) starts: all three corridors in use, cross-row liftings."""
+    s = synth.rsa_start(400, 0.5, 16, seed=seed)
+    flags, st = assert_graph_parity(s, 1.5, 6, windows)
+    assert st["liftings"] > 500
+
+
+def test_graph_dense_chains_large_components():
+    """Many chains on a small lattice: conflict components of more than 32
+    chains replayed in global order."""
+    s = synth.lattice_start(16, 0.70, 120, seed=5)
+    flags, st = assert_graph_parity(s, 1.0, 4)
+    assert flags.all()
+    assert st["repaired_chains"] > 0
+
+
+def test_graph_config2_lattice_n16384():
+    s = synth.lattice_start(128, 0.708, 128, seed=7)
+    flags, st = assert_graph_parity(s, 1.0, 3)
+    assert st["liftings"] > 5000
+
+
+def test_graph_config3_lattice_n1m_one_leg():
+    """N=2^20 (1024x1024), eta=0.72, 1024 chains, ell=1, two claim windows."""
+    s = synth.lattice_start(1024, 0.72, 1024, seed=3)
+    assert_graph_parity(s, 1.0, 1, windows=2)
+
+
+def test_graph_equals_cell_scan_results():
+    """Both modes compute Alg. 2: positions and liftings agree; only the flags
+    (cells vs disks) may differ."""
+    s = synth.rsa_start(300, 0.45, 12, seed=31)
+    gf, gx, _, gt, ga, glog, _ = gpu_graph(s, 1.2, 5)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.2, log=True)
+    sysm.run(5)
+    x, _, t, a = sysm.positions()
+    clog = sysm.liftings()
+    sysm.close()
+    assert np.array_equal(gx, x) and np.array_equal(gt, t) and np.array_equal(ga, a)
+    a1, b1 = chain_order(glog), chain_order(clog)
+    for f in ("leg", "c", "i", "j", "t"):
+        assert np.array_equal(a1[f], b1[f]), f
+
+
+@pytest.mark.parametrize("kind", ["lattice", "rsa"])
+def test_graph_direction_alternation(kind):
+    """+x / +y legs: the graph is rebuilt for every direction; a +y leg equals
+    the oracle's +x leg on exchanged coordinates."""
+    if kind == "lattice":
+        s = synth.lattice_start(16, 0.70, 6, seed=2)
+    else:
+        s = synth.rsa_start(300, 0.45, 8, seed=3)
+    n_legs = 6
+    dirs = [leg % 2 for leg in range(n_legs)]
+    gf, gx, gy, gt, ga, glog, st = gpu_graph(s, 0.8, n_legs, directions=dirs)
+    x, y, act = s.x.copy(), s.y.copy(), s.active.copy()
+    oflags = []
+    for leg in range(n_legs):
+        if dirs[leg] == 0:
+            r = O.run_leg(x, y, act, s.box, 0.8, search=2)
+            x = r.x
+        else:
+            r = O.run_leg(y, x, act, s.box, 0.8, search=2)
+            y = r.x
+        act = r.active
+        oflags.append(r.flag)
+    assert np.array_equal(gx, x) and np.array_equal(gy, y)
+    assert np.array_equal(ga, act)
+    assert np.array_equal(gf, np.array(oflags, dtype=np.uint8))
+    assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
