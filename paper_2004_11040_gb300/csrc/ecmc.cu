@@ -2300,6 +2300,7 @@ extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t ev
         ctx->lifts_total += t.lifts;
         ctx->conflict_legs += t.conflict_legs;
         ctx->repaired += t.repaired;
+        ctx->continued += t.continued;
         ctx->horizon += t.horizon;
         ctx->order_err += t.order_err;
         ctx->device_ms += t.ms;

@@ -10,13 +10,15 @@
 // three target disks; b_ij = sqrt(d^2 - dy^2) is fixed with the arrow and
 // stored beside it, so the step does no square root.
 //
-// Layout: one 64-byte record per disk (x, local time, owner word, claim word,
-// three arrows and their b), y in its own array (it never changes along +x).
+// Layout: one 64-byte record per disk (x, local time, owner word, three arrows
+// and their b); y and the claim words in arrays of their own (y never
+// changes along +x; the claims are cleared window by window).
 //
 // Conflicts are claims on disks instead of cells: within a claim window a
-// chain claims (atomicCAS on the disk's claim word, tagged with the window's
-// epoch) every disk a step reads -- its active disk and the arrow targets --
-// before using what it read. A disk is therefore written only by its claimer
+// chain claims (atomicCAS of the disk's claim word from 0 to chain + 1; the
+// words are cleared between windows) every disk a step reads -- its active
+// disk and the arrow targets -- and uses what it read only once the claims
+// stand. A disk is therefore written only by its claimer
 // during a window, a chain that meets another chain's claim stops, and
 // without a meeting each chain follows the path it takes alone, which is the
 // global-time result (Lemma 2). The leg's flag is 1 iff the disks that two
@@ -43,18 +45,15 @@
 
 namespace {
 
-// claim word: epoch (1..EPOCH_MAX) << 20 | chain + 1; 0 or another epoch = free
-constexpr int CLAIM_SHIFT = 20;
-constexpr uint32_t CLAIM_CHAIN = (1u << CLAIM_SHIFT) - 1u;
-constexpr uint32_t EPOCH_MAX = 4095u;
-constexpr int MAX_CHAINS = (int)CLAIM_CHAIN - 1;
+// chains are numbered by the owner word's 30 bits
+constexpr int MAX_CHAINS = (int)OWN_CHAIN;
 
 struct __align__(64) GDisk {
     double x, t;    // position along the motion; local time (leg-relative)
     uint32_t own;   // owner word (static / active / stalled + chain)
-    uint32_t claim; // claim word of the current window
+    uint32_t pad0;
     uint32_t a[3];  // arrows: centre, upper, lower corridor (NONE: empty)
-    uint32_t pad;
+    uint32_t pad1;
     double b[3];    // b_ij = sqrt(d^2 - dy^2) of each arrow
 };
 static_assert(sizeof(GDisk) == 64, "one disk record is one 64-byte line");
@@ -72,8 +71,9 @@ struct GDev {
     int64_t n;
     int k, cap, windows, nc;
     double L, d, ell;
-    GDisk *g;   // [n]
-    double *y;  // [n]
+    GDisk *g;        // [n]
+    double *y;       // [n]
+    uint32_t *claim; // [n] 0, or chain + 1 holding the disk in this window
     // per chain
     uint32_t *ci, *ci0;  // active disk now / at the leg start
     double *D, *tc;
@@ -87,6 +87,7 @@ struct GDev {
     double *vt;
     int32_t *uf, *fin, *comp_of, *abort_to, *comp_cnt, *comp_off, *comp_root, *comp_mem, *ctl;
     int32_t *nabort;  // [2] components that met another chain, by round parity
+    uint64_t *memb;   // (window, round) << 32 | root of the component listing the chain
     unsigned long long *lc;      // [LC_N]
     unsigned long long *tc_cnt;  // [TC_N]
     ecmc_lift_t *log;
@@ -107,6 +108,12 @@ __device__ void gdiag(const GDev &s, int kind, double a, double b, double c, dou
     s.dbg[4] = d;
     s.dbg[5] = e;
     s.dbg[6] = f;
+}
+
+// Requests a disk record into this SM's L1 ahead of its load (no registers
+// held; the load that follows may still go to L2).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ double wrap_add(double x, double dx, double L) {
@@ -317,7 +324,7 @@ __global__ void k_gb_arrows(GBuild b) {
                 r.a[q] = bj[q];
                 r.b[q] = bj[q] == NONE ? 0.0 : bb[q];
             }
-            r.pad = 0;
+            r.pad0 = r.pad1 = 0;
         }
     }
 }
@@ -328,7 +335,7 @@ __global__ void k_g_init(GDev s) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < s.n) {
         s.g[q].own = OWN_STATIC;
-        s.g[q].claim = 0u;
+        s.claim[q] = 0u;
     }
 }
 
@@ -346,12 +353,18 @@ __global__ void k_g_init_chains(GDev s, const int32_t *active) {
 
 // --------------------------------------------------------------- one step
 
-__device__ __forceinline__ uint32_t claim_word(uint32_t epoch, int c) {
-    return (epoch << CLAIM_SHIFT) | (uint32_t)(c + 1);
-}
-
-__device__ __forceinline__ bool claim_live(uint32_t w, uint32_t epoch) {
-    return (w >> CLAIM_SHIFT) == epoch;
+// Another chain's active or stalled disk among the arrow targets of disk i
+// (record r, with b): in a run of Alg. 4 it stops chain i (Remark 10) only if
+// i could reach it within its remaining length D; beyond D it matters only
+// through Eq. 2 (t_i + tau > t_j), which must still hold.
+__device__ __forceinline__ bool active_in_reach(const GDisk &r, double b, double xi, double ti,
+                                                double D, double L) {
+    double dx = __dsub_rn(r.x, xi);
+    if (dneg(dx)) dx = __dadd_rn(dx, L);
+    double tau = __dsub_rn(dx, b);
+    if (dneg(tau)) tau = 0.0;
+    if (dbits(tau) < dbits(D)) return true;
+    return !(dbits(__dadd_rn(ti, tau)) > dbits(r.t));
 }
 
 // What one step found.
@@ -362,23 +375,58 @@ struct GStep {
     double xj, tj;     // the target's x and local time as read
     int conflict;      // a disk read is held by a chain of the other side
     uint32_t partner;  // that chain
-    int hz;            // PASS1: Eq. 2 failed on a disk touched in this window
+    int viol;          // a static target fails Eq. 2 (t_i + tau > t_j, strict)
+    int nonstatic;     // a target is another chain's active or stalled disk in reach ...
+    uint32_t ns_owner; // ... of this chain (the first such target)
     GDisk jr;          // the target's record as read: its arrows serve the next step
 };
 
+// Is chain h, which holds a claim a repair step met, on the repairing side?
+// Yes if this round's component lists it (memb == tag); with adopt, also if
+// it was, or now is, taken over: a chain in no component of this round whose
+// events are final since the round began joins the component (and any later
+// merge that reaches the component takes it along).
+__device__ __forceinline__ bool holder_ours(const GDev &s, int h, int root, uint64_t tag,
+                                            bool adopt) {
+    if (h < 0 || h >= s.k) return false;
+    if (__ldcg((const unsigned long long *)s.memb + h) == tag) return true;
+    if (!adopt) return false;
+    int hc = __ldcg(s.comp_of + h);
+    if (hc == h && h != root && __ldcg(s.fin + h) == 1) {
+        const int prev = atomicCAS(s.comp_of + h, h, root);
+        if (prev == h) {
+            uf_union(s.uf, h, root);
+            hc = root;
+        } else {
+            hc = prev;
+        }
+    }
+    return hc == root;
+}
+
 // Statements 1-9 of Alg. 5 for chain c along the arrows a[] (with b[]) of
 // its active disk i at x_i, t_i, with remaining length D. Every disk read is
-// claimed for the window: i itself when claim_i (wi: its claim word as read),
-// and each arrow target. A claim held by another chain is a conflict in
-// PASS1; in a repair only if that chain is not in the component `root`.
+// claimed for the window (atomicCAS of the disk's claim word from 0 to c + 1,
+// issued together with the loads; what was read is used only once the claims
+// stand): i itself when claim_i, and each arrow target. A claim held by
+// another chain is a conflict unless that chain is listed in this round's
+// component (memb == tag). adopt (continuation): a holder in no component of
+// this round, whose events are final since the round began, is taken over by
+// the component (it joins it for any later merge) instead of being a conflict;
+// the replay that a failed continuation falls back to does not count such
+// chains as members, so it meets them and merges them next round.
 // Candidates are the static targets (Alg. 2: j not active); a target with
 // t_i + tau < t_j became static after chain c's disk had passed it and is one
 // lap away (lazy per-chain frame); ties go to the lower disk index.
-template <bool PASS1>
-__device__ GStep graph_step(const GDev &s, int c, uint32_t epoch, int root, const uint32_t a[3],
+__device__ GStep graph_step(const GDev &s, int c, int root, uint64_t tag, const uint32_t a[3],
                             const double b[3], uint32_t i, double xi, double ti, double D,
-                            double tw, bool claim_i, uint32_t wi) {
-    const uint32_t mine = claim_word(epoch, c);
+                            bool claim_i, bool adopt = false) {
+    const uint32_t mine = (uint32_t)c + 1u;
+    uint32_t old[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (a[q] != NONE) old[q] = atomicCAS(s.claim + a[q], 0u, mine);
+    if (claim_i) old[3] = atomicCAS(s.claim + i, 0u, mine);
     GDisk r[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -386,72 +434,61 @@ __device__ GStep graph_step(const GDev &s, int c, uint32_t epoch, int root, cons
     GStep o;
     o.conflict = 0;
     o.partner = NONE;
-    o.hz = 0;
-    // a claim word held by chain h: is h on this side?
-    auto ours = [&](uint32_t w) {
-        const int h = (int)(w & CLAIM_CHAIN) - 1;
-        if (h == c) return true;
-        if (PASS1 || h < 0 || h >= s.k) return false;
-        return __ldcg(s.comp_of + h) == root;
-    };
-    auto meet = [&](uint32_t w) {
-        if (!o.conflict) {
-            o.conflict = 1;
-            o.partner = (w & CLAIM_CHAIN) - 1u;
-        }
-    };
-    // claims: a word of this window is read as it is; any other is taken
-    uint32_t seen[4], old[4];
-    bool cas[4] = {false, false, false, false};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const bool have = q < 3 ? a[q] != NONE : claim_i;
-        if (!have) continue;
-        const uint32_t w = q < 3 ? r[q].claim : wi;
-        seen[q] = w;
-        if (claim_live(w, epoch)) {
-            if (!ours(w)) meet(w);
-        } else {
-            GDisk *p = s.g + (q < 3 ? a[q] : i);
-            old[q] = atomicCAS(&p->claim, w, mine);
-            cas[q] = true;
-        }
-    }
+    o.viol = 0;
+    o.nonstatic = 0;
+    o.ns_owner = NONE;
     // time of flight to each static target (statement 4): forward image in x,
     // b_ij fixed with the arrow, clamped at 0
     unsigned long long bt = INF_BITS;
     int bq = -1;
+    uint32_t bjid = NONE;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        if (a[q] == NONE || r[q].own != OWN_STATIC) continue;
+        if (a[q] == NONE) continue;
+        if (r[q].own != OWN_STATIC) {
+            if (!o.nonstatic && active_in_reach(r[q], b[q], xi, ti, D, s.L)) {
+                o.ns_owner = r[q].own & OWN_CHAIN;
+                o.nonstatic = 1;
+            }
+            continue;
+        }
         double dx = __dsub_rn(r[q].x, xi);
         if (dneg(dx)) dx = __dadd_rn(dx, s.L);
         double tau = __dsub_rn(dx, b[q]);
         if (dneg(tau)) tau = 0.0;
         if (dbits(r[q].t) != 0ull) {
             const double sum = __dadd_rn(ti, tau);
-            if (dbits(sum) < dbits(r[q].t)) {
-                if (PASS1 && dbits(r[q].t) >= dbits(tw)) o.hz = 1;
-                tau = __dadd_rn(tau, s.L);
-            }
+            if (!(dbits(sum) > dbits(r[q].t))) o.viol = 1;
+            if (dbits(sum) < dbits(r[q].t)) tau = __dadd_rn(tau, s.L);
         }
         const unsigned long long tb = dbits(tau);
-        if (bq < 0 || tb < bt || (tb == bt && a[q] < a[bq])) {
+        if (bq < 0 || tb < bt || (tb == bt && a[q] < bjid)) {
             bt = tb;
             bq = q;
+            bjid = a[q];
         }
     }
-    // the claims taken above: a failed one names the chain that holds the disk
+    // the claims: a taken one names the chain that holds the disk
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (cas[q] && old[q] != seen[q] && !ours(old[q])) meet(old[q]);
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t w = old[q];
+        if (w == 0u || w == mine) continue;
+        const int h = (int)w - 1;
+        if (holder_ours(s, h, root, tag, adopt)) continue;
+        if (!o.conflict) {
+            o.conflict = 1;
+            o.partner = (uint32_t)h;
+        }
+    }
     if (bq >= 0 && bt < dbits(D)) {
         o.lift = 1;
         o.tau = __longlong_as_double((long long)bt);
-        o.j = a[bq];
-        o.xj = r[bq].x;
-        o.tj = r[bq].t;
-        o.jr = r[bq];
+        o.j = bjid;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q == bq) o.jr = r[q];  // a select, not an indexed (local-memory) load
+        o.xj = o.jr.x;
+        o.tj = o.jr.t;
     } else {
         o.lift = 0;
         o.tau = D;
@@ -462,15 +499,11 @@ __device__ GStep graph_step(const GDev &s, int c, uint32_t epoch, int root, cons
 }
 
 // Executes chain c's step from disk i (statements 10-19 for a lift, 21-24 for
-// a stall) and appends its record. Returns the new status, or ST_BLOCKED when
-// the record log is full (reported to the host).
-__device__ int graph_commit(const GDev &s, int c, uint32_t i, double xi, double ti, double D,
-                            const GStep &o, uint32_t seq) {
-    const int32_t nr = s.nrec[c];
-    if (nr >= s.cap) {
-        atomicAdd(s.lc + LC_ERR_REC, 1ull);
-        return ST_BLOCKED;
-    }
+// a stall) and writes its record at index nr (the caller checked the
+// capacity and counts records and liftings).
+__device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double ti, double D,
+                            int lift, uint32_t j, double tau, double xj, double tj,
+                            uint32_t seq, int32_t nr) {
     GEv u;
     u.i = i;
     u.seq = seq;
@@ -478,42 +511,37 @@ __device__ int graph_commit(const GDev &s, int c, uint32_t i, double xi, double 
     u.x_old = xi;
     u.ti_old = ti;
     GDisk &ri = s.g[i];
-    if (o.lift) {
-        const double tnew = __dadd_rn(ti, o.tau);     // statements 14, 15
-        const double xnew = wrap_add(xi, o.tau, s.L); // statement 16
-        GDisk &rj = s.g[o.j];
+    if (lift) {
+        const double tnew = __dadd_rn(ti, tau);       // statements 14, 15
+        const double xnew = wrap_add(xi, tau, s.L);   // statement 16
+        GDisk &rj = s.g[j];
         rj.own = OWN_ACTIVE | (uint32_t)c;             // statement 10 (the claim holds j)
         rj.t = tnew;
         ri.t = tnew;
         ri.x = xnew;
         ri.own = OWN_STATIC;                           // statement 17
-        u.j = o.j;
-        u.tj_old = o.tj;
+        u.j = j;
+        u.tj_old = tj;
         u.t = tnew;
-        u.tau = o.tau;
+        u.tau = tau;
         u.xi = xnew;
-        u.xj = o.xj;
-        u.d_after = __dsub_rn(D, o.tau);               // statement 18
-        s.rec[(size_t)c * s.cap + nr] = u;
-        s.nrec[c] = nr + 1;
-        s.nlift[c] += 1;
-        return ST_RUNNING;
+        u.xj = xj;
+        u.d_after = __dsub_rn(D, tau);                 // statement 18
+    } else {
+        const double tnew = __dadd_rn(ti, D);         // statement 21
+        const double xnew = wrap_add(xi, D, s.L);     // statement 22
+        ri.x = xnew;
+        ri.t = tnew;
+        ri.own = OWN_STALLED | (uint32_t)c;           // statement 24
+        u.j = NONE;
+        u.tj_old = 0.0;
+        u.t = tnew;
+        u.tau = D;
+        u.xi = xnew;
+        u.xj = 0.0;
+        u.d_after = 0.0;                              // statement 23
     }
-    const double tnew = __dadd_rn(ti, D);             // statement 21
-    const double xnew = wrap_add(xi, D, s.L);         // statement 22
-    ri.x = xnew;
-    ri.t = tnew;
-    ri.own = OWN_STALLED | (uint32_t)c;               // statement 24
-    u.j = NONE;
-    u.tj_old = 0.0;
-    u.t = tnew;
-    u.tau = D;
-    u.xi = xnew;
-    u.xj = 0.0;
-    u.d_after = 0.0;                                  // statement 23
     s.rec[(size_t)c * s.cap + nr] = u;
-    s.nrec[c] = nr + 1;
-    return ST_STALLED;
 }
 
 // ------------------------------------------------------------------ legs
@@ -540,56 +568,153 @@ __device__ void g_leg_begin_chain(const GDev &s, int c) {
 
 // Parallel pass of a claim window [tw, tend): one thread runs chain c from
 // its state through its events before tend, until it stalls, pauses at tend
-// or meets another chain's claim.
-__device__ void g_pass1_chain(const GDev &s, int c, uint32_t epoch, double tw, double tend) {
+// or meets another chain: a claim it holds, or its active or stalled disk
+// among the arrow targets within reach (the step is then not taken; cf.
+// Remark 10). Once a
+// step's winner j is known (and the step will be taken unless a claim of it
+// fails), the arrow targets of j are claimed and their records prefetched into
+// L1, so that the next step's trips overlap this step's wait and writes. Those
+// disks belong to the chain's run alone, so the claims change no flag.
+__device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, double tend) {
     if (s.status[c] != ST_RUNNING) return;
+    const uint32_t mine = (uint32_t)c + 1u;
     uint32_t i = s.ci[c];
-    GDisk ri = s.g[i];
+    const GDisk ri = s.g[i];
     if (ri.own != (OWN_ACTIVE | (uint32_t)c)) gdiag(s, 6, tw, c, i, ri.own, 0, 0);
     uint32_t a[3] = {ri.a[0], ri.a[1], ri.a[2]};
     double b[3] = {ri.b[0], ri.b[1], ri.b[2]};
     double xi = ri.x, ti = s.tc[c], D = s.D[c];
+    int32_t nr = s.nrec[c];
+    bool conflict = false;
+    uint32_t partner = NONE;
+    auto meet = [&](uint32_t h) {
+        if (!conflict) {
+            conflict = true;
+            partner = h;
+        }
+    };
+    // the first step of the window claims the active disk too
+    uint32_t old[3] = {0u, 0u, 0u};
+    {
+        const uint32_t oi = atomicCAS(s.claim + i, 0u, mine);
+        if (oi != 0u && oi != mine) meet(oi - 1u);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (a[q] != NONE) old[q] = atomicCAS(s.claim + a[q], 0u, mine);
+    }
     int st = ST_RUNNING;
-    bool blocked = false, first = true;
+    bool blocked = false;
     uint32_t lifts = 0;
     for (;;) {
-        const GStep o =
-            graph_step<true>(s, c, epoch, c, a, b, i, xi, ti, D, tw, first, ri.claim);
-        first = false;
-        if (o.conflict) {
-            s.partner[c] = o.partner < (uint32_t)s.k ? (int32_t)o.partner : -1;
+        GDisk r[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (a[q] != NONE) r[q] = s.g[a[q]];
+        // statements 4-9 over the static targets (see graph_step)
+        unsigned long long bt = INF_BITS;
+        int bq = -1;
+        uint32_t bjid = NONE, ns_owner = NONE;
+        bool hz = false;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (a[q] == NONE) continue;
+            if (r[q].own != OWN_STATIC) {
+                if (ns_owner == NONE && active_in_reach(r[q], b[q], xi, ti, D, s.L))
+                    ns_owner = r[q].own & OWN_CHAIN;
+                continue;
+            }
+            double dx = __dsub_rn(r[q].x, xi);
+            if (dneg(dx)) dx = __dadd_rn(dx, s.L);
+            double tau = __dsub_rn(dx, b[q]);
+            if (dneg(tau)) tau = 0.0;
+            if (dbits(r[q].t) != 0ull) {
+                const double sum = __dadd_rn(ti, tau);
+                if (dbits(sum) < dbits(r[q].t)) {
+                    if (dbits(r[q].t) >= dbits(tw)) hz = true;
+                    tau = __dadd_rn(tau, s.L);
+                }
+            }
+            const unsigned long long tb = dbits(tau);
+            if (bq < 0 || tb < bt || (tb == bt && a[q] < bjid)) {
+                bt = tb;
+                bq = q;
+                bjid = a[q];
+            }
+        }
+        const int lift = bq >= 0 && bt < dbits(D);
+        GDisk wr;  // the winner's record, by select (no indexed local-memory access)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q == bq) wr = r[q];
+        const double tau = lift ? __longlong_as_double((long long)bt) : D;
+        const double T = __dadd_rn(ti, tau);
+        const bool go = dbits(T) < dbits(tend) && ns_owner == NONE;
+        // the next step's claims and records, requested before this step's
+        // claims are resolved
+        uint32_t oldn[3] = {0u, 0u, 0u};
+        if (lift && go) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (wr.a[q] != NONE) {
+                    oldn[q] = atomicCAS(s.claim + wr.a[q], 0u, mine);
+                    prefetch_l1(s.g + wr.a[q]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (old[q] != 0u && old[q] != mine) meet(old[q] - 1u);
+        if (!conflict && ns_owner != NONE) meet(ns_owner);
+        if (conflict) {
             blocked = true;
             break;
         }
         // Eq. 2 (statement 5) on the disks of this window: cannot fail while
         // they are held by a lone chain; an assertion
-        if (o.hz) atomicAdd(s.lc + LC_HORIZON, 1ull);
-        const double T = __dadd_rn(ti, o.tau);
-        if (!(dbits(T) < dbits(tend))) break;  // pauses at the window end
+        if (hz) atomicAdd(s.lc + LC_HORIZON, 1ull);
+        if (!go) break;  // pauses at the window end
         if (dbits(T) < dbits(tw)) {
             atomicAdd(s.lc + LC_ORDER, 1ull);
-            gdiag(s, 9, tw, c, i, o.j, ti, o.tau);
+            gdiag(s, 9, tw, c, i, lift ? bjid : NONE, ti, tau);
         }
-        st = graph_commit(s, c, i, xi, ti, D, o, (uint32_t)s.nrec[c]);
-        if (st != ST_RUNNING) break;
+        if (nr >= s.cap) {
+            atomicAdd(s.lc + LC_ERR_REC, 1ull);
+            blocked = true;
+            partner = NONE;
+            break;
+        }
+        const uint32_t j = lift ? bjid : NONE;
+        graph_apply(s, c, i, xi, ti, D, lift, j, tau, lift ? wr.x : 0.0, lift ? wr.t : 0.0,
+                    (uint32_t)nr, nr);
+        ++nr;
+        if (!lift) {
+            st = ST_STALLED;
+            xi = wrap_add(xi, D, s.L);
+            ti = T;
+            D = 0.0;
+            break;
+        }
         ++lifts;
-        i = o.j;
-        xi = o.xj;
+        xi = wr.x;
+        i = j;
         ti = T;
-        D = __dsub_rn(D, o.tau);
+        D = __dsub_rn(D, tau);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            a[q] = o.jr.a[q];
-            b[q] = o.jr.b[q];
+            a[q] = wr.a[q];
+            b[q] = wr.b[q];
+            old[q] = oldn[q];
         }
     }
     if (blocked) st = ST_BLOCKED;
     // events before the blocking time, and all before the window, are exact
     s.vt[c] = blocked ? fmax(ti, tw) : INFINITY;
+    s.partner[c] = blocked && partner < (uint32_t)s.k ? (int32_t)partner : -1;
     s.status[c] = st;
     s.ci[c] = i;
     s.tc[c] = ti;
     s.D[c] = D;
+    s.nrec[c] = nr;
+    s.nlift[c] += (int32_t)lifts;
     if (blocked) {
         atomicAdd(s.lc + LC_BLOCKED, 1ull);
         atomicAdd(s.lc + LC_WBLOCKED, 1ull);
@@ -599,7 +724,7 @@ __device__ void g_pass1_chain(const GDev &s, int c, uint32_t epoch, double tw, d
 
 // --------------------------------------------------------------- repairs
 
-// Exact inverse of graph_commit for one record of chain c.
+// Exact inverse of graph_apply for one record of chain c.
 __device__ void g_undo(const GDev &s, int c, const GEv &u) {
     GDisk &ri = s.g[u.i];
     ri.x = u.x_old;
@@ -692,13 +817,12 @@ __device__ void g_resume(const GDev &s, int c) {
 }
 
 // Pending event of member c (one thread), kept with the arrows it read.
-__device__ void g_compute(const GDev &s, int c, int root, uint32_t epoch, bool &abort,
-                          int &met) {
+__device__ __noinline__ void g_compute(const GDev &s, int c, int root, uint64_t tag, bool &abort,
+                                       int &met) {
     const uint32_t i = s.ci[c];
     const GDisk ri = s.g[i];
     const double ti = s.tc[c], D = s.D[c];
-    const GStep o = graph_step<false>(s, c, epoch, root, ri.a, ri.b, i, ri.x, ti, D, 0.0,
-                                      true, ri.claim);
+    const GStep o = graph_step(s, c, root, tag, ri.a, ri.b, i, ri.x, ti, D, true);
     if (o.conflict && !abort) {
         abort = true;
         met = (int)o.partner;
@@ -714,8 +838,11 @@ __device__ void g_compute(const GDev &s, int c, int root, uint32_t epoch, bool &
 }
 
 // After a component's replay: record abort or success for the next round.
+// keep_vt (success by continuation): the members' vt becomes `now` instead of
+// infinity, so that a later merge rolls them back to `now` or earlier (their
+// events were applied chain by chain, not in time order).
 __device__ void g_finish(const GDev &s, const int32_t *mem, int m, int root, bool abort,
-                         int met, double now, int round) {
+                         int met, double now, int round, bool keep_vt = false) {
     const int lane = threadIdx.x & 31;
     if (abort) {
         // events before `now` are exact; the chain met joins next round
@@ -730,17 +857,191 @@ __device__ void g_finish(const GDev &s, const int32_t *mem, int m, int root, boo
     } else {
         for (int e = lane; e < m; e += 32) {
             s.fin[mem[e]] = 2;
-            s.vt[mem[e]] = INFINITY;
+            s.vt[mem[e]] = keep_vt ? now : INFINITY;
         }
     }
     __syncwarp();
+}
+
+// First repair round of a window: the blocked members continue from where
+// they stopped, one after another (lane 0), over the state the others left.
+// The parallel pass was a run of Alg. 4 in which every chain read only disks
+// it held, every step satisfied the horizon condition and no step was taken
+// towards another chain's active disk. If every continued step satisfies
+// Eq. 2 on each arrow target as well, the whole is a run of Alg. 4 without a
+// horizon violation, which by Lemma 2 ends where Alg. 2 ends: nothing has to
+// be redone. A chain that finds the active disk of another blocked member
+// among its arrow targets waits (Remark 10) while that member continues
+// first. Otherwise the caller rolls the component back to T* and replays it
+// in global order.
+enum { CONT_DONE = 0, CONT_FAIL = 1, CONT_FOREIGN = 2 };
+
+__device__ __noinline__ int g_continue(const GDev &s, const int32_t *mem, int m, int root,
+                                       uint64_t tag, int round, double tw, double tend,
+                                       int *met) {
+    const int lane = threadIdx.x & 31;
+    int how = CONT_DONE, who = -1;
+    if (lane == 0) {
+        uint32_t cnt = 0;
+        int switches = 0;
+        int e = 0;
+        int cur = -1;
+        int known = -1;  // a holder already found on this side
+        while (how == CONT_DONE) {
+            if (cur < 0) {  // the next member still blocked
+                while (e < m && s.status[mem[e]] != ST_BLOCKED) ++e;
+                if (e >= m) break;
+                cur = mem[e];
+            }
+            const int c = cur;
+            const uint32_t mine = (uint32_t)c + 1u;
+            uint32_t i = s.ci[c];
+            const GDisk ri = s.g[i];
+            uint32_t a[3] = {ri.a[0], ri.a[1], ri.a[2]};
+            double b[3] = {ri.b[0], ri.b[1], ri.b[2]};
+            double xi = ri.x, ti = s.tc[c], D = s.D[c];
+            int32_t nr = s.nrec[c], nl = 0;
+            int st = ST_RUNNING, next = -1;
+            // claims of the active disk (first step) and of the arrow targets
+            uint32_t oi = atomicCAS(s.claim + i, 0u, mine);
+            uint32_t old[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (a[q] != NONE) old[q] = atomicCAS(s.claim + a[q], 0u, mine);
+            auto ours = [&](uint32_t w) {
+                if (w == 0u || w == mine) return true;
+                const int h = (int)w - 1;
+                if (h == known) return true;
+                if (!holder_ours(s, h, root, tag, true)) {
+                    who = h;
+                    return false;
+                }
+                known = h;
+                return true;
+            };
+            for (;;) {
+                GDisk r[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (a[q] != NONE) r[q] = s.g[a[q]];
+                unsigned long long bt = INF_BITS;
+                int bq = -1;
+                uint32_t bjid = NONE, ns_owner = NONE;
+                bool viol = false;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (a[q] == NONE) continue;
+                    if (r[q].own != OWN_STATIC) {
+                        if (ns_owner == NONE && active_in_reach(r[q], b[q], xi, ti, D, s.L))
+                            ns_owner = r[q].own & OWN_CHAIN;
+                        continue;
+                    }
+                    double dx = __dsub_rn(r[q].x, xi);
+                    if (dneg(dx)) dx = __dadd_rn(dx, s.L);
+                    double tau = __dsub_rn(dx, b[q]);
+                    if (dneg(tau)) tau = 0.0;
+                    // Eq. 2, strict (a lap-away target fails it too)
+                    if (dbits(r[q].t) != 0ull && !(dbits(__dadd_rn(ti, tau)) > dbits(r[q].t)))
+                        viol = true;
+                    const unsigned long long tb = dbits(tau);
+                    if (bq < 0 || tb < bt || (tb == bt && a[q] < bjid)) {
+                        bt = tb;
+                        bq = q;
+                        bjid = a[q];
+                    }
+                }
+                const int lift = bq >= 0 && bt < dbits(D);
+                GDisk wr;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (q == bq) wr = r[q];
+                const double tau = lift ? __longlong_as_double((long long)bt) : D;
+                const double T = __dadd_rn(ti, tau);
+                const bool go = dbits(T) < dbits(tend) && !viol && ns_owner == NONE;
+                uint32_t oldn[3] = {0u, 0u, 0u};
+                if (lift && go) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (wr.a[q] != NONE) {
+                            oldn[q] = atomicCAS(s.claim + wr.a[q], 0u, mine);
+                            prefetch_l1(s.g + wr.a[q]);
+                        }
+                }
+                bool foreign = !ours(oi);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) foreign = foreign || !ours(old[q]);
+                oi = 0u;
+                if (foreign) {
+                    how = CONT_FOREIGN;
+                    break;
+                }
+                if (viol) {
+                    how = CONT_FAIL;
+                    break;
+                }
+                if (ns_owner != NONE) {
+                    const int h = (int)ns_owner;
+                    if (h != c && h >= 0 && h < s.k &&
+                        __ldcg((const unsigned long long *)s.memb + h) == tag &&
+                        s.status[h] == ST_BLOCKED && switches < 4 * m + 4) {
+                        next = h;  // wait for that member (Remark 10)
+                        st = ST_BLOCKED;
+                        ++switches;
+                    } else {
+                        how = CONT_FAIL;
+                    }
+                    break;
+                }
+                if (!(dbits(T) < dbits(tend))) break;  // pauses at the window end
+                if (dbits(T) < dbits(tw) || nr >= s.cap) {
+                    how = CONT_FAIL;
+                    break;
+                }
+                const uint32_t j = lift ? bjid : NONE;
+                graph_apply(s, c, i, xi, ti, D, lift, j, tau, lift ? wr.x : 0.0,
+                            lift ? wr.t : 0.0, ((uint32_t)round << 24) | cnt++, nr);
+                ++nr;
+                if (!lift) {
+                    st = ST_STALLED;
+                    ti = T;
+                    D = 0.0;
+                    break;
+                }
+                ++nl;
+                i = j;
+                xi = wr.x;
+                ti = T;
+                D = __dsub_rn(D, tau);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    a[q] = wr.a[q];
+                    b[q] = wr.b[q];
+                    old[q] = oldn[q];
+                }
+            }
+            // the events so far stand (a failure rolls them back with the rest)
+            s.nrec[c] = nr;
+            s.nlift[c] += nl;
+            if (how != CONT_DONE) break;
+            s.status[c] = st;
+            s.ci[c] = i;
+            s.tc[c] = ti;
+            s.D[c] = D;
+            cur = next;
+        }
+    }
+    how = __shfl_sync(FULL, how, 0);
+    *met = __shfl_sync(FULL, who, 0);
+    __syncwarp();
+    return how;
 }
 
 // Component q of this round (one warp): roll its members back to T*, then
 // replay them in global event-time order (Alg. 2) up to the window's end.
 // Members are spread over the lanes (member e on lane e mod 32); after each
 // event only the members whose arrows read a disk it changed recompute.
-__device__ void g_repair_component(const GDev &s, int q, int round, uint32_t epoch, double tw,
+__device__ __noinline__ void g_repair_component(const GDev &s, int q, int round, uint32_t wr_tag,
+                                                double tw,
                                    double tend) {
     const int lane = threadIdx.x & 31;
     const int root = s.comp_root[q];
@@ -752,13 +1053,32 @@ __device__ void g_repair_component(const GDev &s, int q, int round, uint32_t epo
     for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
     Ts = fmax(Ts, tw);  // earlier windows are final
     if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
+    // the members listed for this round of this window (wr_tag names both)
+    const uint64_t tag = ((uint64_t)wr_tag << 32) | (uint32_t)root;
+    for (int e = lane; e < m; e += 32) s.memb[mem[e]] = tag;
+    __syncwarp();
+    if (round == 1) {
+        int met = -1;
+        const int how = g_continue(s, mem, m, root, tag, round, tw, tend, &met);
+        if (how == CONT_DONE) {
+            if (lane == 0) atomicAdd(s.lc + LC_CONTINUED, (unsigned long long)m);
+            g_finish(s, mem, m, root, false, -1, Ts, round, true);
+            return;
+        }
+        if (how == CONT_FOREIGN) {
+            // the merged component's replay rolls back to T* (all of this
+            // round's events lie after it)
+            g_finish(s, mem, m, root, true, met, Ts, round);
+            return;
+        }
+    }
     g_rollback(s, mem, m, Ts);
     for (int e = lane; e < m; e += 32) g_resume(s, mem[e]);
     __syncwarp();
     bool abort = false;
     int met = -1;
     for (int e = lane; e < m; e += 32)
-        if (s.status[mem[e]] == ST_RUNNING) g_compute(s, mem[e], root, epoch, abort, met);
+        if (s.status[mem[e]] == ST_RUNNING) g_compute(s, mem[e], root, tag, abort, met);
     double now = Ts;
     uint32_t cnt = 0;
     for (;;) {
@@ -812,7 +1132,17 @@ __device__ void g_repair_component(const GDev &s, int q, int round, uint32_t epo
             o.xj = s.ev_xj[bc];
             o.tj = s.ev_tj[bc];
             const double xi = s.g[i].x;
-            st = graph_commit(s, bc, i, xi, ti, D, o, ((uint32_t)round << 24) | cnt);
+            const int32_t nr = s.nrec[bc];
+            if (nr >= s.cap) {
+                atomicAdd(s.lc + LC_ERR_REC, 1ull);
+                st = ST_BLOCKED;
+            } else {
+                graph_apply(s, bc, i, xi, ti, D, o.lift, o.j, o.tau, o.xj, o.tj,
+                            ((uint32_t)round << 24) | cnt, nr);
+                s.nrec[bc] = nr + 1;
+                if (o.lift) s.nlift[bc] += 1;
+                st = o.lift ? ST_RUNNING : ST_STALLED;
+            }
             ib = i;
             if (st == ST_RUNNING) {
                 jb = o.j;
@@ -844,7 +1174,7 @@ __device__ void g_repair_component(const GDev &s, int q, int round, uint32_t epo
                 const uint32_t v = s.ev_a[3 * (size_t)c + k2];
                 redo |= v != NONE && (v == ib || v == jb);
             }
-            if (redo) g_compute(s, c, root, epoch, abort, met);
+            if (redo) g_compute(s, c, root, tag, abort, met);
         }
         __syncwarp();
     }
@@ -882,7 +1212,8 @@ __device__ void g_leg_end_chain(const GDev &s, int c, int32_t leg) {
 
 struct GCtl {
     int64_t budget;  // liftings for this run (0: none)
-    int64_t lifts, legs, conflict_legs, repaired, horizon, order_err, p1_lifts, repair_lifts;
+    int64_t lifts, legs, conflict_legs, repaired, continued, horizon, order_err, p1_lifts,
+        repair_lifts;
     uint8_t *flags;  // per-leg conflict flags (device) or null
     int32_t flags_cap;
     int32_t done;    // budget reached or error
@@ -899,7 +1230,6 @@ struct GRun {
     int32_t *err;                    // ECMC_ETIMEOUT from a barrier
     unsigned long long *phase_ns;    // [GPH_N] device time per phase (block 0 clock)
     int32_t max_legs;
-    uint32_t win0;                   // claim windows run before this launch, mod EPOCH_MAX
     int64_t leg0;                    // legs run before this launch (lifting log)
 };
 
@@ -913,7 +1243,7 @@ __device__ __forceinline__ double g_window_end(const GDev &s, int w) {
 }
 
 constexpr int GRUN_THREADS = 256;
-constexpr int GRUN_MIN_BLOCKS = 2;
+constexpr int GRUN_MIN_BLOCKS = 1;
 
 // One cooperative launch runs up to max_legs legs. Per leg and claim window:
 // the parallel pass (one thread per chain), then repair rounds (conflict
@@ -928,6 +1258,8 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
     const int lane = threadIdx.x & 31;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
+    const int nwarps = nthreads >> 5;
+    const int gw = blockIdx.x + gridDim.x * (threadIdx.x >> 5);
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_prev = timer ? gtimer() : 0ull;
     auto mark = [&](int ph) {
@@ -939,20 +1271,22 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
     };
     for (int leg = 0; leg < R.max_legs; ++leg) {
         for (int c = gt; c < s.k; c += nthreads) g_leg_begin_chain(s, c);
+        for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
         if (gt < LC_N) s.lc[gt] = 0ull;
         if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
         if (!grid_sync(R.bar, R.err, &sflag)) return;
         mark(GPH_BEGIN);
         for (int w = 0; w < s.windows; ++w) {
-            const uint32_t epoch =
-                (uint32_t)(((uint64_t)R.win0 + (uint64_t)leg * s.windows + w) % EPOCH_MAX) + 1u;
-            if (epoch == 1u) {
-                // the epochs wrapped: no claim word may look like one of this window
-                for (int64_t q = gt; q < s.n; q += nthreads) s.g[q].claim = 0u;
+            if (w > 0) {
+                // a new claim window: the claims of the last one are void
+                for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
                 if (!grid_sync(R.bar, R.err, &sflag)) return;
             }
             const double tw = g_window_start(s, w), te = g_window_end(s, w);
-            for (int c = gt; c < s.k; c += nthreads) g_pass1_chain(s, c, epoch, tw, te);
+            // one chain per warp (lane 0) while they last, warps interleaved over
+            // the blocks so that the chains spread over all SMs
+            for (int c = gw + nwarps * lane; c < s.k; c += nwarps * 32)
+                g_pass1_chain(s, c, tw, te);
             if (!grid_sync(R.bar, R.err, &sflag)) return;
             mark(GPH_PASS1);
             if (gt == 0) s.nabort[1] = 0;  // the first round's abort count
@@ -983,7 +1317,9 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                     if (lane == 0) q = atomicAdd(s.ctl + CTL_WORK, 1);
                     q = __shfl_sync(FULL, q, 0);
                     if (q >= ncomp) break;
-                    g_repair_component(s, q, round, epoch, tw, te);
+                    g_repair_component(s, q, round,
+                                       ((uint32_t)(leg * s.windows + w) << 8) | (uint32_t)round,
+                                       tw, te);
                 }
                 if (!grid_sync(R.bar, R.err, &sflag)) return;
                 // no component met another chain: the window is repaired
@@ -1006,6 +1342,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
             c.legs += 1;
             c.conflict_legs += flag;
             c.repaired += (int64_t)lc[LC_REPAIRED];
+            c.continued += (int64_t)lc[LC_CONTINUED];
             c.horizon += (int64_t)lc[LC_HORIZON];
             c.order_err += (int64_t)lc[LC_ORDER];
             if (lc[LC_ERR_REC]) c.err = 1;
@@ -1063,7 +1400,6 @@ struct GraphCtx {
     unsigned long long *d_phase = nullptr;
     uint8_t *d_flags = nullptr;
     int32_t flags_cap = 0;
-    uint64_t windows_run = 0;
     int64_t log_legs = 0;  // legs logged so far (leg index of the log)
     int grid = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1166,7 +1502,7 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
                  const int32_t *active, cudaStream_t st, GraphCtx **out, std::string &err) {
     *out = nullptr;
     if (p->n_chains > MAX_CHAINS) {
-        err = "graph mode supports at most 2^20 - 2 chains";
+        err = "too many chains";
         return ECMC_EINVAL;
     }
     GraphCtx *g = new (std::nothrow) GraphCtx();
@@ -1204,6 +1540,8 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     chk(galloc(g, &s.partner, k, err));
     chk(galloc(g, &s.nrec, k, err));
     chk(galloc(g, &s.nlift, k, err));
+    chk(galloc(g, &s.claim, n, err));
+    chk(galloc(g, &s.memb, k, err));
     chk(galloc(g, &s.rec, k * (size_t)s.cap, err));
     chk(galloc(g, &s.ev_T, k, err));
     chk(galloc(g, &s.ev_tau, k, err));
@@ -1241,6 +1579,7 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     }
     cudaMemcpyAsync(s.y, y, n * 8, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(s.nrec, 0, k * 4, st);
+    cudaMemsetAsync(s.memb, 0xFF, k * 8, st);
     cudaMemsetAsync(s.lc, 0, LC_N * 8, st);
     cudaMemsetAsync(s.tc_cnt, 0, TC_N * 8, st);
     cudaMemsetAsync(s.dbg, 0, 16 * 8, st);
@@ -1276,6 +1615,10 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     memset(tot, 0, sizeof *tot);
     if (legs_done) *legs_done = 0;
     if (n_legs <= 0) return 0;
+    if ((int64_t)n_legs * g->s.windows >= ((int64_t)1 << 24)) {
+        err = "too many legs x windows for one call (< 2^24)";
+        return ECMC_EINVAL;
+    }
     cudaStream_t st = g->st;
     if (g->flags_cap < n_legs) {
         cudaFree(g->d_flags);
@@ -1305,6 +1648,8 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     cu(cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned int), st), "bar");
     cu(cudaMemsetAsync(g->d_err, 0, sizeof(int32_t), st), "err");
     cu(cudaMemsetAsync(g->d_phase, 0, GPH_N * sizeof(unsigned long long), st), "phase");
+    // member tags restart with the launch's window count
+    cu(cudaMemsetAsync(g->s.memb, 0xFF, (size_t)g->s.k * 8, st), "memb");
     if (rc) return rc;
     GRun R;
     R.s = g->s;
@@ -1313,7 +1658,6 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     R.err = g->d_err;
     R.phase_ns = g->d_phase;
     R.max_legs = n_legs;
-    R.win0 = (uint32_t)(g->windows_run % EPOCH_MAX);
     R.leg0 = g->log_legs;
     void *args[] = {&R};
     cu(cudaEventRecord(g->ev0, st), "event");
@@ -1329,12 +1673,12 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     if (rc) return rc;
     float ms = 0.f;
     cu(cudaEventElapsedTime(&ms, g->ev0, g->ev1), "elapsed");
-    g->windows_run += (uint64_t)ctl.legs * (uint64_t)g->s.windows;
     g->log_legs += ctl.legs;
     tot->legs = ctl.legs;
     tot->lifts = ctl.lifts;
     tot->conflict_legs = ctl.conflict_legs;
     tot->repaired = ctl.repaired;
+    tot->continued = ctl.continued;
     tot->horizon = ctl.horizon;
     tot->order_err = ctl.order_err;
     tot->p1_lifts = ctl.p1_lifts;
