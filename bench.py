@@ -9,6 +9,11 @@ buffers (create from host x/y, run, read positions back) inside the timed
 region. The working set (~100 MB) is below the 129 MB L2, so L2 is flushed
 with a 512 MB write between timed steps.
 
+The default run (--search cells: the cell scan, one warp per chain) also
+measures the same workload in constraint-graph mode (ECMC_GRAPH: liftings
+through the arrows of G(3), Sec. 3.1) and adds it as "graph_mode" with its own
+roofline and e2e numbers; --search graph makes graph mode the headline.
+
 --impl reference times the CPU oracle (plain C, one core) on a bounded
 sample of the same workload.
 
@@ -54,8 +59,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--k", type=int, default=1024, help="chains")
     p.add_argument("--legs", type=int, default=10, help="legs per step")
+    p.add_argument("--search", default="cells", choices=["cells", "graph"],
+                   help="lifting search of the headline: cell scan (default) or the "
+                        "constraint graph G(3); the default run measures graph mode too")
     p.add_argument("--windows", type=int, default=0,
-                   help="claim windows per leg (0: 2 up to 4096 chains, else 4)")
+                   help="claim windows per leg (0: cell scan 2 up to 4096 chains, else 4; "
+                        "graph 1)")
     p.add_argument("--workload", default="lattice",
                    choices=["lattice", "batched", "serve", "conflicts"])
     p.add_argument("--target", type=float, default=1e9,
@@ -71,16 +80,27 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     a = p.parse_args()
-    if a.windows <= 0:
-        a.windows = 2 if a.k <= 4096 else 4
+    a.windows_arg = a.windows
+    a.windows = windows_for(a, a.search)
     return a
 
 
-def workload(a):
+def windows_for(a, search):
+    """Claim windows per leg: as given, else the measured best of each search."""
+    if a.windows_arg > 0:
+        return a.windows_arg
+    if search == "graph":
+        return 1
+    return 2 if a.k <= 4096 else 4
+
+
+def workload(a, search=None):
+    search = search or a.search
     return {"workload": f"lattice {a.m}x{a.m} (N={a.m * a.m}) eta={a.eta} jitter=0.01, "
                         f"k={a.k} chains, ell={a.ell}, v=+x, {a.legs} legs/step",
             "n": a.m * a.m, "eta": a.eta, "k": a.k, "ell": a.ell, "legs_per_step": a.legs,
-            "claim_windows_per_leg": a.windows,
+            "search": "cell scan" if search == "cells" else "constraint graph G(3)",
+            "claim_windows_per_leg": windows_for(a, search),
             "seed": a.seed, "l2": "flushed between steps (512 MB write)"}
 
 
@@ -144,16 +164,17 @@ def peaks():
 
 
 def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source file is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2004_11040_gb300", "csrc", "ecmc.cu"), "rb").read()
-        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        k = d.get("kernels", {}).get(kernel, {})
+        src = open(os.path.join(ROOT, "paper_2004_11040_gb300", "csrc", k["source"]), "rb").read()
+        if k.get("source_sha256") != hashlib.sha256(src).hexdigest():
             return None
-        return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
+        return k.get("dram_bytes_per_launch")
     except Exception:
         return None
 
@@ -257,60 +278,40 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ ours
 
-def run_ours(a):
+def measure(a, search, start, stream, flush, barrier, ws):
+    """Times --steps steps of one search mode (after --warmup steps) and the
+    end-to-end C-ABI path; returns the numbers of one JSON line."""
     import numpy as np
     import torch
 
-    from paper_2004_11040_gb300 import build, ecmc, synth
-    build.build()
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    stream = torch.cuda.current_stream()
-    start = synth.lattice_start(a.m, a.eta, a.k, seed=a.seed + rank)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-            torch.cuda.synchronize()
-
+    from paper_2004_11040_gb300 import ecmc
+    graph = search == "graph"
+    W = windows_for(a, search)
     sysm = ecmc.System(start.x, start.y, start.active, start.box, a.ell, stream=stream,
-                       windows=a.windows)
+                       windows=W, graph=graph)
     for _ in range(a.warmup):
         sysm.run(a.legs)
     st0, pr0 = sysm.stats(), sysm.profile()
     dev_ms = 0.0
     lifts = 0
-    with ClockSampler(local) as clk:
-        barrier()
-        for _ in range(a.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            b = sysm.stats()
-            sysm.run(a.legs)
-            e = sysm.stats()
-            dev_ms += e["device_ms"] - b["device_ms"]
-            lifts += e["liftings"] - b["liftings"]
-        barrier()
+    barrier()
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        b = sysm.stats()
+        sysm.run(a.legs)
+        e = sysm.stats()
+        dev_ms += e["device_ms"] - b["device_ms"]
+        lifts += e["liftings"] - b["liftings"]
+    barrier()
     st1, pr1 = sysm.stats(), sysm.profile()
     t_max, tot_lifts = aggregate(dev_ms, lifts, ws, device="cuda")
-    value = tot_lifts / (t_max / 1000.0)
-
-    # the hot path is one persistent kernel launch (k_run) per step
-    d = {key: pr1[key] - pr0[key] for key in pr1}
-    kname = "k_run"
+    # the hot path is one persistent kernel launch per step
+    kname = "k_run_graph" if graph else "k_run"
     kms = dev_ms / a.steps  # CUDA events around each launch, on its stream
     kl = lifts / a.steps
     peak, peak_kind = peaks()
     achieved = (kl * BYTES_PER_LIFTING) / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
-    conflict_legs = st1["conflict_legs"] - st0["conflict_legs"]
-    legs = st1["legs"] - st0["legs"]
-    launches = a.steps
 
     # end to end through the C-ABI with host buffers
     nx = start.n
@@ -337,9 +338,54 @@ def run_ours(a):
         if s > 0:
             e2e_lifts += n_l
             e2e_s += el
-    e2e = {"value": e2e_lifts / e2e_s, "unit": "liftings/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
     sysm.close()
+    return {
+        "value": tot_lifts / (t_max / 1000.0), "t_max": t_max, "liftings": tot_lifts,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_for(kname), "kernel": kname,
+                     "peak_source": peak_kind, "bytes_per_lifting": BYTES_PER_LIFTING,
+                     "kernel_ms_per_launch": kms, "liftings_per_launch": kl},
+        "e2e": {"value": e2e_lifts / e2e_s, "unit": "liftings/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": a.steps,
+        "detail": {"legs": st1["legs"] - st0["legs"],
+                   "conflict_legs": st1["conflict_legs"] - st0["conflict_legs"],
+                   "repaired_chains": st1["repaired_chains"] - st0["repaired_chains"],
+                   "continued_chains": st1["continued_chains"] - st0["continued_chains"],
+                   "liftings": tot_lifts,
+                   "profile": {key: pr1[key] - pr0[key] for key in pr1},
+                   "horizon_asserts": st1["horizon_asserts"],
+                   "order_errors": st1["order_errors"]},
+    }
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2004_11040_gb300 import build, synth
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    start = synth.lattice_start(a.m, a.eta, a.k, seed=a.seed + rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        head = measure(a, a.search, start, stream, flush, barrier, ws)
+    other = None
+    if a.search == "cells":
+        # the constraint-graph mode on the same workload (same Alg. 2 results)
+        other = measure(a, "graph", start, stream, flush, barrier, ws)
 
     if rank != 0:
         return
@@ -347,26 +393,23 @@ def run_ours(a):
     if ws == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a, start, a.cpu_seconds)
         cbm = cpu_multicore(a, start, a.cpu_seconds / 2)
-    traffic = traffic_for(kname)
     line = {
-        "metric": METRIC, "value": value, "unit": "liftings/s", "n_gpus": ws,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+        "metric": METRIC, "value": head["value"], "unit": "liftings/s", "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": head["t_max"] / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload(a),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                     "peak_source": peak_kind,
-                     "bytes_per_lifting": BYTES_PER_LIFTING,
-                     "kernel_ms_per_launch": kms,
-                     "liftings_per_launch": kl},
+        "roofline": head["roofline"],
         "cpu_baseline": cb, "cpu_baseline_multicore": cbm, "host": host_info(),
-        "e2e": e2e, "gpu_launches": launches,
+        "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
         "clocks": clk.summary(),
-        "detail": {"legs": legs, "conflict_legs": conflict_legs,
-                   "liftings": tot_lifts, "profile": d,
-                   "horizon_asserts": st1["horizon_asserts"],
-                   "order_errors": st1["order_errors"]},
+        "detail": head["detail"],
     }
+    if other is not None:
+        line["graph_mode"] = {
+            "value": other["value"], "unit": "liftings/s",
+            "ms_per_step": other["t_max"] / a.steps, "config": workload(a, "graph"),
+            "roofline": other["roofline"], "e2e": other["e2e"],
+            "gpu_launches": other["gpu_launches"], "detail": other["detail"]}
     print(json.dumps(line), flush=True)
 
 

@@ -72,7 +72,6 @@ struct Dev {
     uint32_t *ci;  // active disk id
     double *D, *tc;
     int32_t *status, *partner, *nrec, *nlift;
-    int32_t *nocont;  // pass 1 saw another chain's active or stalled disk in its corridor
     Rec *rec;  // [k * cap]
     // pending events for the global-time repair of large components
     double *ev_T, *ev_tau, *ev_xj, *ev_yj, *ev_tj;
@@ -149,7 +148,12 @@ struct StepOut {
     int cx, cy, mlast;  // scanned footprint: rows cy-1..cy+1, columns cx..cx+mlast
     int conflict;
     uint32_t partner;
-    int nonstatic;  // an active or stalled disk of another chain lies in a scanned corridor
+    // a run of Alg. 4 stops here (Remark 10, taken conservatively): another
+    // chain's active or stalled disk in a scanned corridor lies within reach
+    // (its time of flight is below D) or fails Eq. 2; ns_owner is the chain of
+    // the nearest one
+    int nonstatic;
+    uint32_t ns_owner;
     int viol;       // CONT: a scanned corridor disk fails the horizon condition (Eq. 2)
     // empty slots of the middle row (the active disk's row) as scanned: C bits
     // per column offset m (bit m*C + slot), for the columns with (m+1)*C <= 64
@@ -172,6 +176,11 @@ struct StepOut {
 //   cannot occur while the cells are held and is counted as an assertion.
 // COMP: the owner is the conflict component `root` (any member's claim is its
 //   own).
+// CONT: as COMP, and the scan runs until (m*a - fx) - d > D + eps: the
+//   horizon condition must hold for the nearest disk of every corridor within
+//   reach (Lemma 2; the arrows of G(3)), not only for those before the winner.
+//   A disk another member moved can sit beyond the winner in one corridor
+//   while the continued chain's earlier sweep crossed its old place.
 __device__ void uf_union(int32_t *p, int a, int b);
 
 // nm > 0 (COMP, CONT): the component's members are the chains my_member of
@@ -215,7 +224,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool conflict = false;
     uint32_t partner = NONE;
     bool hz = false;
-    bool nonst = false;  // a scanned corridor holds another chain's active or stalled disk
+    unsigned long long ns_t = INF_BITS;  // least time of flight to another chain's disk
+    uint32_t ns_own = NONE;                // ... and its chain
+    bool ns_hv = false;                    // such a disk fails Eq. 2 (this lane)
     bool viol = false;   // CONT: a scanned corridor disk fails Eq. 2
     unsigned long long emask = 0ull;
 
@@ -290,7 +301,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         const bool corr = cst && dbits(ay) < dbits(s.d);
         const bool ncs = cand && own != OWN_STATIC && dbits(ay) < dbits(s.d);
         double b = 0.0;
-        if (__any_sync(FULL, corr)) b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(ay, ay)));
+        if (__any_sync(FULL, corr || ncs)) b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(ay, ay)));
         double dx = __dsub_rn(xj, r.xi);
         const bool neg = dneg(dx);
         const bool drop = neg && m == 0 && !near_d;
@@ -359,7 +370,9 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             bloc = g0l;
             improved = true;
         }
-        if (g0t < cur) {
+        // (a continued step checks Eq. 2 on every corridor disk within reach
+        // of D, so its scan does not stop at the best candidate)
+        if (MODE != MODE_CONT && g0t < cur) {
             cur = g0t;
             cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
         }
@@ -375,7 +388,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                     bloc = g1l;
                     improved = true;
                 }
-                if (g1t < cur) {
+                if (MODE != MODE_CONT && g1t < cur) {
                     cur = g1t;
                     cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
                 }
@@ -406,7 +419,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                 // not a listed member: taken over earlier, or takeable now
                 const int h = hq;
                 int hc = __ldcg(s.comp_of + h);
-                if (hc == h && hc != root && __ldcg(s.fin + h) == 1 && !__ldcg(s.nocont + h)) {
+                if (hc == h && hc != root && __ldcg(s.fin + h) == 1) {
                     const int old = atomicCAS(s.comp_of + h, h, root);
                     if (old == h) {
                         // its cells now hold this component's events: a later
@@ -430,7 +443,35 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // Eq. 2 (statement 5) on every scanned candidate touched in this window:
         // cannot fail while the cells are held by a lone chain; an assertion.
         if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
-        if (scanned && ncs) nonst = true;
+        // another chain's active or stalled disk in a scanned corridor: its
+        // time of flight (forward image, clamped) and Eq. 2
+        const bool nsl = scanned && ncs;
+        if (__any_sync(FULL, nsl)) {
+            unsigned long long nt = INF_BITS;
+            uint32_t no = NONE;
+            if (nsl) {
+                double dn = __dsub_rn(xj, r.xi);
+                if (dneg(dn)) dn = __dadd_rn(dn, s.L);
+                double tn = __dsub_rn(dn, b);
+                if (dneg(tn)) tn = 0.0;
+                nt = dbits(tn);
+                no = own & OWN_CHAIN;
+                if (dbits(tj) != 0ull && !(dbits(__dadd_rn(r.ti, tn)) > dbits(tj))) ns_hv = true;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t2 = shfl_xor_u64(nt, o);
+                const uint32_t o2 = __shfl_xor_sync(FULL, no, o);
+                if (t2 < nt || (t2 == nt && o2 < no)) {
+                    nt = t2;
+                    no = o2;
+                }
+            }
+            if (nt < ns_t) {
+                ns_t = nt;
+                ns_own = no;
+            }
+        }
         if (MODE == MODE_CONT && scanned && hzv) viol = true;
         if (!dneg(thr_next) && dbits(thr_next) > cur_eps) break;
         thr_first = thr_next;
@@ -441,7 +482,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     o.cy = cyi;
     o.mlast = mlast;
     o.emask = emask;
-    o.nonstatic = __ballot_sync(FULL, nonst) != 0u;
+    o.nonstatic = (__ballot_sync(FULL, ns_hv) != 0u) || ns_t < dbits(r.D);
+    o.ns_owner = ns_own;
     o.viol = MODE == MODE_CONT ? __ballot_sync(FULL, viol) != 0u : 0;
     o.conflict = 0;
     o.partner = NONE;
@@ -685,10 +727,7 @@ __global__ void k_leg_begin(Dev s) {
 template <int C>
 __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     const int lane = threadIdx.x & 31;
-    if (s.status[c] != ST_RUNNING) {
-        if (lane == 0) s.nocont[c] = 0;
-        return;
-    }
+    if (s.status[c] != ST_RUNNING) return;
     ChainReg r;
     r.iloc = s.aloc[c];
     r.i = s.ci[c];
@@ -703,11 +742,9 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
     int32_t cas_rec = -1;           // record of that lift, while unchecked
     bool blocked = false;
-    bool nonstatic = false;  // a scan met another chain's active or stalled disk
     uint32_t lifts = 0;
     while (st == ST_RUNNING) {
         const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r, tw);
-        nonstatic |= o.nonstatic != 0;
         if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
             const uint32_t old = __shfl_sync(FULL, cas_old, 0);
             if (old != OWN_STATIC) {
@@ -719,7 +756,6 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
                     s.partner[c] = (int32_t)(old & OWN_CHAIN);
                     atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
                 }
-                nonstatic = true;
                 blocked = true;
                 break;
             }
@@ -727,6 +763,13 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
         }
         if (o.conflict) {
             if (lane == 0) s.partner[c] = (int32_t)o.partner;
+            blocked = true;
+            break;
+        }
+        if (o.nonstatic) {
+            // Alg. 4 would lift onto another chain's disk (Remark 10): stop
+            // here, in one component with that chain (whose claims overlap)
+            if (lane == 0) s.partner[c] = o.ns_owner < (uint32_t)s.k ? (int32_t)o.ns_owner : -1;
             blocked = true;
             break;
         }
@@ -748,7 +791,6 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     if (lane == 0) {
         // events before the blocking time, and all before the window, are exact
         s.vt[c] = blocked ? fmax(r.ti, tw) : INFINITY;
-        s.nocont[c] = nonstatic;
         s.status[c] = st;
         s.aloc[c] = r.iloc;
         s.ci[c] = r.i;
@@ -1245,22 +1287,21 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
 // First repair round of a claim window: the blocked members continue from
 // where they stopped, one after another, over the state the other members
 // left. Pass 1 was a run of Alg. 4 (chains advanced one at a time: each
-// chain's cells were its own) in which every step satisfied the horizon
-// condition; if no member's pass 1 met another chain's active or stalled
-// disk, and every continued step satisfies the horizon condition (Eq. 2) for
-// every scanned corridor disk and meets no active or stalled disk either, the
-// whole run is one of Alg. 4 without a horizon violation, which by Lemma 2
-// ends where Alg. 2 ends: nothing has to be redone. Otherwise the caller
-// rolls the component back to T* and replays it in global order.
+// chain's cells were its own; a chain stopped where Alg. 4 would lift onto
+// another chain's disk) in which every step satisfied the horizon condition.
+// If every continued step satisfies the horizon condition (Eq. 2) for every
+// scanned corridor disk, the whole run is one of Alg. 4 without a horizon
+// violation, which by Lemma 2 ends where Alg. 2 ends: nothing has to be
+// redone. A member that would lift onto the active disk of another member
+// still blocked waits for it (Remark 10): that member continues first.
+// Otherwise the caller rolls the component back to T* and replays it in
+// global order.
 enum { CONT_DONE = 0, CONT_FAIL = 1, CONT_FOREIGN = 2 };
 
 template <int C>
 __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int root, int round,
                                   double tw, double tend, int *met) {
     const int lane = threadIdx.x & 31;
-    bool bad = false;
-    for (int e = lane; e < m; e += 32) bad |= s.nocont[mem[e]] != 0;
-    if (__any_sync(FULL, bad)) return CONT_FAIL;
     // up to 32 members: members by the lanes' registers, and the component may
     // take over chains that are in no component (the replay that a failure
     // falls back to tests membership against its own member list, so it
@@ -1270,9 +1311,15 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
     const int nm = m <= 32 ? -m : 0;
     const int my_member = lane < m ? mem[lane] : -1;
     uint32_t cnt = 0;
-    for (int e = 0; e < m; ++e) {
-        const int c = mem[e];
-        if (s.status[c] != ST_BLOCKED) continue;
+    int e = 0, cur = -1, switches = 0;
+    for (;;) {
+        if (cur < 0) {  // the next member still blocked
+            while (e < m && s.status[mem[e]] != ST_BLOCKED) ++e;
+            if (e >= m) break;
+            cur = mem[e];
+        }
+        const int c = cur;
+        int next = -1;
         ChainReg r;
         r.iloc = s.aloc[c];
         r.i = s.ci[c];
@@ -1288,7 +1335,22 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
                 *met = (int)o.partner;
                 return CONT_FOREIGN;
             }
-            if (o.viol || o.nonstatic) return CONT_FAIL;
+            if (o.viol) return CONT_FAIL;
+            if (o.nonstatic) {
+                const int h = (int)o.ns_owner;
+                bool member;
+                if (nm != 0)
+                    member = __any_sync(FULL, my_member == h && h >= 0);
+                else
+                    member = h >= 0 && h < s.k && __ldcg(s.comp_of + h) == root;
+                if (h != c && member && s.status[h] == ST_BLOCKED && switches < 4 * m + 4) {
+                    next = h;  // wait for that member
+                    st = ST_BLOCKED;
+                    ++switches;
+                    break;
+                }
+                return CONT_FAIL;
+            }
             const unsigned long long T = dbits(__dadd_rn(r.ti, o.tau));
             if (!(T < dbits(tend))) break;  // pauses at the window end
             if (T < dbits(tw)) return CONT_FAIL;
@@ -1306,6 +1368,7 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
             s.D[c] = r.D;
         }
         __syncwarp();
+        cur = next;
     }
     return CONT_DONE;
 }
@@ -1985,7 +2048,6 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.tc, k));
     chk(dalloc(ctx, &s.status, k));
     chk(dalloc(ctx, &s.partner, k));
-    chk(dalloc(ctx, &s.nocont, k));
     chk(dalloc(ctx, &s.nrec, k));
     chk(dalloc(ctx, &s.nlift, k));
     chk(dalloc(ctx, &s.rec, k * (size_t)s.cap));
@@ -2582,7 +2644,6 @@ static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t n
     s.tc = cv.take<double>(k);
     s.status = cv.take<int32_t>(k);
     s.partner = cv.take<int32_t>(k);
-    s.nocont = cv.take<int32_t>(k);
     s.nrec = cv.take<int32_t>(k);
     s.nlift = cv.take<int32_t>(k);
     s.ev_T = cv.take<double>(k);
