@@ -127,7 +127,7 @@ __device__ __forceinline__ double wrap_add(double x, double dx, double L) {
 struct GBuild {
     int64_t n;
     int nc, nb;
-    double L, d, d2, a, inv_a, eps, w;  // cells of side a; y bins of width w
+    double L, d, d2, a, inv_a, eps, w, inv_w;  // cells of side a; y bins of width w
     const double *x, *y;
     uint32_t *cid;       // [nc*nc*C] disk per slot, EMPTY
     double *cx, *cy;     // [nc*nc*C]
@@ -150,7 +150,8 @@ __global__ void k_gb_cells(GBuild b) {
     const double x = b.x[q], y = b.y[q];
     const uint32_t cell = (uint32_t)cell_coord(y, b.inv_a, b.nc) * (uint32_t)b.nc +
                           (uint32_t)cell_coord(x, b.inv_a, b.nc);
-    int bin = __double2int_rz(__ddiv_rn(y, b.w));
+    // bins only need a monotone map of y (the same one below): a product
+    int bin = __double2int_rz(__dmul_rn(y, b.inv_w));
     if (bin >= b.nb) bin = b.nb - 1;
     if (bin < 0) bin = 0;
     atomicAdd(b.bins + bin, 1);
@@ -194,7 +195,7 @@ __device__ int band_count(const GBuild &b, double lo, double hi) {
         hi = __dsub_rn(hi, b.L);
     }
     auto bin = [&](double v) {
-        int q = __double2int_rz(__ddiv_rn(v, b.w));
+        int q = __double2int_rz(__dmul_rn(v, b.inv_w));
         return min(max(q, 0), b.nb - 1);
     };
     const int b0 = bin(lo);
@@ -294,6 +295,7 @@ __global__ void k_gb_arrows(GBuild b) {
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
+                if (!play[q]) continue;  // warp-uniform: an empty corridor has no candidate
                 unsigned long long kt = kc == q ? dbits(tau) : INF_BITS;
                 uint32_t kj = kc == q ? id : NONE;
                 double kb = bv;
@@ -551,9 +553,19 @@ __device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double 
 __device__ void g_leg_begin_chain(const GDev &s, int c) {
     const int32_t nr = s.nrec[c];
     const GEv *q = s.rec + (size_t)c * s.cap;
-    for (int32_t e = 0; e < nr; ++e) {
-        s.g[q[e].i].t = 0.0;
-        if (q[e].j != NONE) s.g[q[e].j].t = 0.0;
+    // in batches: the record loads of a batch are issued before its stores
+    for (int32_t e0 = 0; e0 < nr; e0 += 8) {
+        uint32_t ii[8], jj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            ii[u] = e0 + u < nr ? q[e0 + u].i : NONE;
+            jj[u] = e0 + u < nr ? q[e0 + u].j : NONE;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (ii[u] != NONE) s.g[ii[u]].t = 0.0;
+            if (jj[u] != NONE) s.g[jj[u]].t = 0.0;
+        }
     }
     const uint32_t i = s.ci[c];
     s.g[i].own = OWN_ACTIVE | (uint32_t)c;
@@ -1231,6 +1243,7 @@ struct GRun {
     unsigned long long *phase_ns;    // [GPH_N] device time per phase (block 0 clock)
     int32_t max_legs;
     int64_t leg0;                    // legs run before this launch (lifting log)
+    int64_t budget;                  // liftings of this launch after which it stops (0: none)
 };
 
 __device__ __forceinline__ double g_window_start(const GDev &s, int w) {
@@ -1269,13 +1282,23 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
             t_prev = t;
         }
     };
-    for (int leg = 0; leg < R.max_legs; ++leg) {
+    // The per-leg counters accumulate over the launch: a leg's totals are
+    // differences, and every thread decides alike, after the leg's last
+    // barrier, whether the launch goes on. Without an event budget the next
+    // leg is begun in the same phase as this one ends.
+    unsigned long long prev[LC_N];
+#pragma unroll
+    for (int q = 0; q < LC_N; ++q) prev[q] = 0ull;
+    auto begin_leg = [&]() {
         for (int c = gt; c < s.k; c += nthreads) g_leg_begin_chain(s, c);
         for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
-        if (gt < LC_N) s.lc[gt] = 0ull;
-        if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
-        if (!grid_sync(R.bar, R.err, &sflag)) return;
-        mark(GPH_BEGIN);
+    };
+    begin_leg();
+    if (gt < LC_N) s.lc[gt] = 0ull;
+    if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
+    if (!grid_sync(R.bar, R.err, &sflag)) return;
+    mark(GPH_BEGIN);
+    for (int leg = 0; leg < R.max_legs; ++leg) {
         for (int w = 0; w < s.windows; ++w) {
             if (w > 0) {
                 // a new claim window: the claims of the last one are void
@@ -1303,7 +1326,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                         uf_block(s, round == 1, warp_tot, tot, false);
                     } else if (threadIdx.x == 0) {
                         s.ctl[CTL_NCOMP] = 0;
-                        if (need) R.ctl->err = 1;  // too many rounds
+                        if (need) atomicAdd(s.lc + LC_ERR_CAP, 1ull);  // too many rounds
                     }
                     __syncthreads();
                 }
@@ -1327,30 +1350,59 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
             }
             mark(GPH_REPAIR);
         }
-        // leg end: liftings and the log, then totals and the budget
-        for (int c = gt; c < s.k; c += nthreads)
-            g_leg_end_chain(s, c, (int32_t)(R.leg0 + R.ctl->legs));
+        // leg end: liftings and the log (and, without a budget, the next leg's
+        // start), then the totals. Every counter but the liftings is final
+        // since the last barrier (the next leg's pass may start as soon as the
+        // coming barrier is passed), so thread 0 takes them now.
+        const volatile unsigned long long *lcv = s.lc;
+        // errors of this leg are final too: all threads read them here, so
+        // that they all take the same decision below
+        const bool err = lcv[LC_ERR_REC] != 0ull || lcv[LC_ERR_CAP] != 0ull;
+        unsigned long long d[LC_N];
+        if (gt == 0) {
+#pragma unroll
+            for (int q = 0; q < LC_N; ++q) {
+                if (q == LC_LIFTS) continue;
+                const unsigned long long v = lcv[q];
+                d[q] = v - prev[q];
+                prev[q] = v;
+            }
+        }
+        const bool more = leg + 1 < R.max_legs && R.budget == 0;
+        for (int c = gt; c < s.k; c += nthreads) {
+            g_leg_end_chain(s, c, (int32_t)(R.leg0 + leg));
+            if (more) g_leg_begin_chain(s, c);
+        }
+        if (more)
+            for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
         if (!grid_sync(R.bar, R.err, &sflag)) return;
+        // (read by all threads; with a budget no next leg has begun)
+        const unsigned long long lifts_all = lcv[LC_LIFTS];
         if (gt == 0) {
             GCtl &c = *R.ctl;
-            const unsigned long long *lc = s.lc;
-            const int flag = lc[LC_BLOCKED] != 0ull;
+            d[LC_LIFTS] = lifts_all - prev[LC_LIFTS];
+            prev[LC_LIFTS] = lifts_all;
+            const int flag = d[LC_BLOCKED] != 0ull;
             if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
-            c.lifts += (int64_t)lc[LC_LIFTS];
-            c.p1_lifts += (int64_t)lc[LC_P1LIFTS];
-            if (flag) c.repair_lifts += (int64_t)lc[LC_LIFTS];
+            c.lifts += (int64_t)d[LC_LIFTS];
+            c.p1_lifts += (int64_t)d[LC_P1LIFTS];
+            if (flag) c.repair_lifts += (int64_t)d[LC_LIFTS];
             c.legs += 1;
             c.conflict_legs += flag;
-            c.repaired += (int64_t)lc[LC_REPAIRED];
-            c.continued += (int64_t)lc[LC_CONTINUED];
-            c.horizon += (int64_t)lc[LC_HORIZON];
-            c.order_err += (int64_t)lc[LC_ORDER];
-            if (lc[LC_ERR_REC]) c.err = 1;
-            if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
+            c.repaired += (int64_t)d[LC_REPAIRED];
+            c.continued += (int64_t)d[LC_CONTINUED];
+            c.horizon += (int64_t)d[LC_HORIZON];
+            c.order_err += (int64_t)d[LC_ORDER];
+            if (err) c.err = 1;
         }
-        if (!grid_sync(R.bar, R.err, &sflag)) return;
         mark(GPH_END);
-        if (*(volatile int32_t *)&R.ctl->done) break;
+        if (err || (R.budget > 0 && (int64_t)lifts_all >= R.budget)) break;
+        if (leg + 1 >= R.max_legs) break;
+        if (!more) {
+            begin_leg();
+            if (!grid_sync(R.bar, R.err, &sflag)) return;
+            mark(GPH_BEGIN);
+        }
     }
 }
 
@@ -1403,6 +1455,7 @@ struct GraphCtx {
     int64_t log_legs = 0;  // legs logged so far (leg index of the log)
     int grid = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void *build_tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -1438,24 +1491,28 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     b.inv_a = (double)nc / s.L;
     b.eps = std::ldexp(s.L, -30);
     b.w = s.d / 128.0;
+    b.inv_w = 1.0 / b.w;
     b.nb = (int)std::ceil(s.L / b.w);
     b.x = x;
     b.y = y;
     b.g = s.g;
     const size_t nslot = (size_t)nc * nc * C;
-    void *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    auto release = [&]() {
-        for (void *p : tmp) cudaFree(p);
-    };
-    if (cudaMalloc(&tmp[0], nslot * 4) != cudaSuccess ||
-        cudaMalloc(&tmp[1], nslot * 8) != cudaSuccess ||
-        cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
-        cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
-        cudaMalloc(&tmp[4], 8) != cudaSuccess) {
-        (void)cudaGetLastError();
-        release();
-        err = "cudaMalloc failed (graph build)";
-        return ECMC_ENOMEM;
+    // scratch of the build, kept by the context for the next direction change
+    void **tmp = g->build_tmp;
+    if (!tmp[0]) {
+        if (cudaMalloc(&tmp[0], nslot * 4) != cudaSuccess ||
+            cudaMalloc(&tmp[1], nslot * 8) != cudaSuccess ||
+            cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
+            cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
+            cudaMalloc(&tmp[4], 8) != cudaSuccess) {
+            (void)cudaGetLastError();
+            for (int q = 0; q < 5; ++q) {
+                cudaFree(tmp[q]);
+                tmp[q] = nullptr;
+            }
+            err = "cudaMalloc failed (graph build)";
+            return ECMC_ENOMEM;
+        }
     }
     b.cid = (uint32_t *)tmp[0];
     b.cx = (double *)tmp[1];
@@ -1484,7 +1541,6 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&overflow, b.err, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    release();
     if (e != cudaSuccess) {
         err = std::string("graph build: ") + cudaGetErrorString(e);
         return ECMC_ECUDA;
@@ -1659,6 +1715,7 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     R.phase_ns = g->d_phase;
     R.max_legs = n_legs;
     R.leg0 = g->log_legs;
+    R.budget = (int64_t)budget;
     void *args[] = {&R};
     cu(cudaEventRecord(g->ev0, st), "event");
     cu(cudaLaunchCooperativeKernel((void *)k_run_graph, g->grid, GRUN_THREADS, args, 0, st),
@@ -1770,6 +1827,7 @@ int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
 void graph_destroy(GraphCtx *g) {
     if (!g) return;
     for (void *p : g->allocs) cudaFree(p);
+    for (void *p : g->build_tmp) cudaFree(p);
     cudaFree(g->d_flags);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);

@@ -143,3 +143,45 @@ def test_graph_direction_alternation(kind):
     assert np.array_equal(ga, act)
     assert np.array_equal(gf, np.array(oflags, dtype=np.uint8))
     assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
+
+
+def test_graph_event_budget_stops_at_a_breakpoint():
+    """An event budget ends the run at the first breakpoint where the liftings
+    of the call reach it; the state is that of the oracle after as many legs."""
+    s = synth.lattice_start(16, 0.70, 6, seed=4)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 0.6, graph=True)
+    flags, done = sysm.run(20, event_budget=60)
+    x, y, t, a = sysm.positions()
+    st = sysm.stats()
+    sysm.close()
+    assert 1 <= done < 20
+    last, legs = O.run_legs(s.x, s.y, s.active, s.box, 0.6, done, search=2)
+    lifts = [r.lifts for r in legs]
+    assert sum(lifts) >= 60 and sum(lifts[:-1]) < 60
+    assert st["liftings"] == sum(lifts)
+    assert np.array_equal(flags, np.array([r.flag for r in legs], dtype=np.uint8))
+    assert np.array_equal(x, last.x) and np.array_equal(t, last.t)
+    assert np.array_equal(a, last.active)
+
+
+def test_graph_split_runs_equal_one_run():
+    """Legs are independent of how calls cut them: 2 + 4 legs equal 6 legs,
+    lifting log (leg indices included) and flags alike."""
+    s = synth.rsa_start(250, 0.45, 10, seed=17)
+    out = []
+    for cuts in ([6], [2, 4], [1, 1, 4]):
+        sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, log=True, graph=True)
+        flags = []
+        for n in cuts:
+            f, done = sysm.run(n)
+            assert done == n
+            flags += list(f)
+        x, y, t, a = sysm.positions()
+        log = chain_order(sysm.liftings())
+        sysm.close()
+        out.append((x, t, a, np.array(flags), log))
+    for o in out[1:]:
+        for u, v in zip(out[0][:4], o[:4]):
+            assert np.array_equal(u, v)
+        for f in ("leg", "c", "i", "j", "t"):
+            assert np.array_equal(out[0][4][f], o[4][f]), f
