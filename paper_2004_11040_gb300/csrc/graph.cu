@@ -127,7 +127,8 @@ __device__ __forceinline__ double wrap_add(double x, double dx, double L) {
 struct GBuild {
     int64_t n;
     int nc, nb;
-    double L, d, d2, a, inv_a, eps, w, inv_w;  // cells of side a; y bins of width w
+    double L, d, d2, a, inv_a, eps, w;  // cells of side a; y bins of width w
+    float Lf, wf, inv_wf, half_f, d_f;     // the same in FP32 (bins only)
     const double *x, *y;
     uint32_t *cid;       // [nc*nc*C] disk per slot, EMPTY
     double *cx, *cy;     // [nc*nc*C]
@@ -150,8 +151,8 @@ __global__ void k_gb_cells(GBuild b) {
     const double x = b.x[q], y = b.y[q];
     const uint32_t cell = (uint32_t)cell_coord(y, b.inv_a, b.nc) * (uint32_t)b.nc +
                           (uint32_t)cell_coord(x, b.inv_a, b.nc);
-    // bins only need a monotone map of y (the same one below): a product
-    int bin = __double2int_rz(__dmul_rn(y, b.inv_w));
+    // bins only need a monotone map of y, the same as in band_count: FP32
+    int bin = __float2int_rz(__fmul_rn(__double2float_rn(y), b.inv_wf));
     if (bin >= b.nb) bin = b.nb - 1;
     if (bin < 0) bin = 0;
     atomicAdd(b.bins + bin, 1);
@@ -185,22 +186,24 @@ __global__ void k_gb_scan(GBuild b) {
 }
 
 // Disks whose y falls in a bin that meets [lo, hi) (periodic, hi - lo < L):
-// an upper bound on the disks with y in that range.
-__device__ int band_count(const GBuild &b, double lo, double hi) {
-    if (lo < 0.0) {
-        lo = __dadd_rn(lo, b.L);
-        hi = __dadd_rn(hi, b.L);
-    } else if (lo >= b.L) {
-        lo = __dsub_rn(lo, b.L);
-        hi = __dsub_rn(hi, b.L);
+// an upper bound on the disks with y in that range. FP32 is enough: the map
+// to bins is monotone, and the callers' one-bin margin (d/128) is far above
+// the FP32 rounding of y, lo and hi.
+__device__ int band_count(const GBuild &b, float lo, float hi) {
+    if (lo < 0.f) {
+        lo = __fadd_rn(lo, b.Lf);
+        hi = __fadd_rn(hi, b.Lf);
+    } else if (lo >= b.Lf) {
+        lo = __fsub_rn(lo, b.Lf);
+        hi = __fsub_rn(hi, b.Lf);
     }
-    auto bin = [&](double v) {
-        int q = __double2int_rz(__dmul_rn(v, b.inv_w));
+    auto bin = [&](float v) {
+        int q = __float2int_rz(__fmul_rn(v, b.inv_wf));
         return min(max(q, 0), b.nb - 1);
     };
     const int b0 = bin(lo);
-    if (hi <= b.L) return b.bins[bin(hi) + 1] - b.bins[b0];
-    return (b.bins[b.nb] - b.bins[b0]) + (b.bins[bin(__dsub_rn(hi, b.L)) + 1] - b.bins[0]);
+    if (hi <= b.Lf) return b.bins[bin(hi) + 1] - b.bins[b0];
+    return (b.bins[b.nb] - b.bins[b0]) + (b.bins[bin(__fsub_rn(hi, b.Lf)) + 1] - b.bins[0]);
 }
 
 // Arrows of G(3): one warp per disk scans the columns ahead (rows cy-1..cy+1)
@@ -227,12 +230,10 @@ __global__ void k_gb_arrows(GBuild b) {
         const double fx = __dsub_rn(xi, __dmul_rn((double)cxi, b.a));
         // corridors that may hold a disk (one bin of margin on each side)
         bool play[3];
-        play[0] = band_count(b, __dsub_rn(__dsub_rn(yi, half), b.w),
-                             __dadd_rn(__dadd_rn(yi, half), b.w)) > 1;  // i itself is there
-        play[1] = band_count(b, __dsub_rn(__dadd_rn(yi, half), b.w),
-                             __dadd_rn(__dadd_rn(yi, b.d), b.w)) > 0;
-        play[2] = band_count(b, __dsub_rn(__dsub_rn(yi, b.d), b.w),
-                             __dadd_rn(__dsub_rn(yi, half), b.w)) > 0;
+        const float yf = __double2float_rn(yi);
+        play[0] = band_count(b, yf - b.half_f - b.wf, yf + b.half_f + b.wf) > 1;  // i is there
+        play[1] = band_count(b, yf + b.half_f - b.wf, yf + b.d_f + b.wf) > 0;
+        play[2] = band_count(b, yf - b.d_f - b.wf, yf - b.half_f + b.wf) > 0;
         unsigned long long bt[3] = {INF_BITS, INF_BITS, INF_BITS};
         uint32_t bj[3] = {NONE, NONE, NONE};
         double bb[3] = {0.0, 0.0, 0.0};
@@ -1491,8 +1492,12 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     b.inv_a = (double)nc / s.L;
     b.eps = std::ldexp(s.L, -30);
     b.w = s.d / 128.0;
-    b.inv_w = 1.0 / b.w;
-    b.nb = (int)std::ceil(s.L / b.w);
+    b.Lf = (float)s.L;
+    b.wf = (float)b.w;
+    b.inv_wf = 1.0f / b.wf;
+    b.half_f = (float)(0.5 * s.d);
+    b.d_f = (float)s.d;
+    b.nb = (int)std::ceil(s.L / b.w) + 1;
     b.x = x;
     b.y = y;
     b.g = s.g;
