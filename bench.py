@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--search", default="cells", choices=["cells", "graph"],
                    help="lifting search of the headline: cell scan (default) or the "
                         "constraint graph G(3); the default run measures graph mode too")
+    p.add_argument("--restart", action="store_true",
+                   help="graph mode: conflicts by restart strategy 2 (Sec. 3.4) instead of "
+                        "the local repair")
     p.add_argument("--windows", type=int, default=0,
                    help="claim windows per leg (0: cell scan 2 up to 4096 chains, else 4; "
                         "graph 1)")
@@ -99,7 +102,9 @@ def workload(a, search=None):
     return {"workload": f"lattice {a.m}x{a.m} (N={a.m * a.m}) eta={a.eta} jitter=0.01, "
                         f"k={a.k} chains, ell={a.ell}, v=+x, {a.legs} legs/step",
             "n": a.m * a.m, "eta": a.eta, "k": a.k, "ell": a.ell, "legs_per_step": a.legs,
-            "search": "cell scan" if search == "cells" else "constraint graph G(3)",
+            "search": "cell scan" if search == "cells" else (
+                "constraint graph G(3), restart strategy 2" if a.restart
+                else "constraint graph G(3)"),
             "claim_windows_per_leg": windows_for(a, search),
             "seed": a.seed, "l2": "flushed between steps (512 MB write)"}
 
@@ -288,7 +293,7 @@ def measure(a, search, start, stream, flush, barrier, ws):
     graph = search == "graph"
     W = windows_for(a, search)
     sysm = ecmc.System(start.x, start.y, start.active, start.box, a.ell, stream=stream,
-                       windows=W, graph=graph)
+                       windows=W, graph=graph, restart=graph and a.restart)
     for _ in range(a.warmup):
         sysm.run(a.legs)
     st0, pr0 = sysm.stats(), sysm.profile()
@@ -352,6 +357,7 @@ def measure(a, search, start, stream, flush, barrier, ws):
                    "conflict_legs": st1["conflict_legs"] - st0["conflict_legs"],
                    "repaired_chains": st1["repaired_chains"] - st0["repaired_chains"],
                    "continued_chains": st1["continued_chains"] - st0["continued_chains"],
+                   "restarts": st1["restarts"] - st0["restarts"],
                    "liftings": tot_lifts,
                    "profile": {key: pr1[key] - pr0[key] for key in pr1},
                    "horizon_asserts": st1["horizon_asserts"],

@@ -44,6 +44,8 @@ extern "C" {
 #define ECMC_INPUT_DEVICE 0x2u /* x, y, active passed to ecmc_create are device pointers */
 #define ECMC_GRAPH 0x4u        /* find liftings through the constraint graph G(3) (Sec. 3.1)
                                   instead of the cell scan; see "Constraint-graph mode" */
+#define ECMC_RESTART 0x8u      /* with ECMC_GRAPH and windows <= 1: conflicts handled by
+                                  restart strategy 2 (Sec. 3.4); see "Restart mode" */
 
 typedef struct ecmc_ctx ecmc_ctx;
 
@@ -75,6 +77,8 @@ typedef struct {
     double device_ms;        /* device time spent in ecmc_run_to_breakpoint */
     int64_t continued_chains; /* of repaired_chains: in components finished by continuing
                                  the blocked chains (Lemma 2), nothing redone */
+    int64_t restarts;         /* ECMC_RESTART: passes begun again at an earlier stop time
+                                 T* taken as a breakpoint (Sec. 3.4, strategy 2) */
 } ecmc_stats_t;
 
 /* One lifting i -> j (Eq. 1): chain c, leg index, time t (= new t_j),

@@ -1819,6 +1819,7 @@ struct ecmc_ctx {
     int64_t conflict_legs = 0;
     int64_t repaired = 0;
     int64_t continued = 0;
+    int64_t restarts = 0;
     int64_t horizon = 0;
     int64_t order_err = 0;
     int64_t inconsistent = 0;
@@ -1999,6 +2000,10 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     ctx->p = *p;
     ctx->stream = (cudaStream_t)stream;
     ctx->C = C;
+    if ((p->flags & ECMC_RESTART) && (!(p->flags & ECMC_GRAPH) || p->windows > 1)) {
+        delete ctx;
+        return fail(nullptr, ECMC_EINVAL, "ECMC_RESTART needs ECMC_GRAPH and one claim window");
+    }
     if (p->flags & ECMC_GRAPH) {
         memset(&ctx->s, 0, sizeof ctx->s);
         ctx->s.n = p->n;
@@ -2363,6 +2368,7 @@ extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t ev
         ctx->conflict_legs += t.conflict_legs;
         ctx->repaired += t.repaired;
         ctx->continued += t.continued;
+        ctx->restarts += t.restarts;
         ctx->horizon += t.horizon;
         ctx->order_err += t.order_err;
         ctx->device_ms += t.ms;
@@ -2514,6 +2520,7 @@ extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
     out->conflict_legs = ctx->conflict_legs;
     out->repaired_chains = ctx->repaired;
     out->continued_chains = ctx->continued;
+    out->restarts = ctx->restarts;
     out->horizon_asserts = ctx->horizon;
     out->order_errors = ctx->order_err;
     out->device_ms = ctx->device_ms;

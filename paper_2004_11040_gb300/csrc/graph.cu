@@ -88,6 +88,8 @@ struct GDev {
     int32_t *uf, *fin, *comp_of, *abort_to, *comp_cnt, *comp_off, *comp_root, *comp_mem, *ctl;
     int32_t *nabort;  // [2] components that met another chain, by round parity
     uint64_t *memb;   // (window, round) << 32 | root of the component listing the chain
+    int restart;      // conflicts by restart strategy 2 (Sec. 3.4) instead of local repair
+    double *tstar;    // [1] restart mode: the earliest stop time of a pass
     unsigned long long *lc;      // [LC_N]
     unsigned long long *tc_cnt;  // [TC_N]
     ecmc_lift_t *log;
@@ -850,6 +852,21 @@ __device__ __noinline__ void g_compute(const GDev &s, int c, int root, uint64_t 
     for (int q = 0; q < 3; ++q) s.ev_a[3 * (size_t)c + q] = ri.a[q];
 }
 
+// Restart mode: chain c back to time Ts. Its records at or after Ts are all
+// of the current pass, whose disks each chain held alone, so every chain
+// undoes its own (latest first) in parallel with the others.
+__device__ void g_rollback_chain(const GDev &s, int c, double Ts) {
+    int32_t nr = s.nrec[c];
+    while (nr > 0) {
+        const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+        if (!(u.t >= Ts)) break;
+        g_undo(s, c, u);
+        --nr;
+    }
+    s.nrec[c] = nr;
+    g_resume(s, c);
+}
+
 // After a component's replay: record abort or success for the next round.
 // keep_vt (success by continuation): the members' vt becomes `now` instead of
 // infinity, so that a later merge rolls them back to `now` or earlier (their
@@ -1226,7 +1243,7 @@ __device__ void g_leg_end_chain(const GDev &s, int c, int32_t leg) {
 struct GCtl {
     int64_t budget;  // liftings for this run (0: none)
     int64_t lifts, legs, conflict_legs, repaired, continued, horizon, order_err, p1_lifts,
-        repair_lifts;
+        repair_lifts, restarts;
     uint8_t *flags;  // per-leg conflict flags (device) or null
     int32_t flags_cap;
     int32_t done;    // budget reached or error
@@ -1258,6 +1275,7 @@ __device__ __forceinline__ double g_window_end(const GDev &s, int w) {
 
 constexpr int GRUN_THREADS = 256;
 constexpr int GRUN_MIN_BLOCKS = 1;
+constexpr int MAX_RESTARTS = 16;  // per leg, then the local repair takes over
 
 // One cooperative launch runs up to max_legs legs. Per leg and claim window:
 // the parallel pass (one thread per chain), then repair rounds (conflict
@@ -1299,20 +1317,65 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
     if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
     if (!grid_sync(R.bar, R.err, &sflag)) return;
     mark(GPH_BEGIN);
+    __shared__ double dmin[32];
     for (int leg = 0; leg < R.max_legs; ++leg) {
+        // restart mode (one claim window): a pass that meets a conflict is cut
+        // at T*, the earliest time a chain stopped -- every event before it is
+        // exact (Remark 6) -- all chains are rolled back to T*, and T* becomes
+        // the next breakpoint of the leg: a new pass from T* with new claims
+        // (Sec. 3.4, second restart strategy). A pass that cannot progress
+        // (T* at its own start), or the last one allowed, is repaired locally.
+        double tw_r = 0.0;
+        int sub = 0;
         for (int w = 0; w < s.windows; ++w) {
+          for (;;) {
             if (w > 0) {
                 // a new claim window: the claims of the last one are void
                 for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
                 if (!grid_sync(R.bar, R.err, &sflag)) return;
             }
-            const double tw = g_window_start(s, w), te = g_window_end(s, w);
+            const double tw = s.restart ? tw_r : g_window_start(s, w);
+            const double te = g_window_end(s, w);
             // one chain per warp (lane 0) while they last, warps interleaved over
             // the blocks so that the chains spread over all SMs
             for (int c = gw + nwarps * lane; c < s.k; c += nwarps * 32)
                 g_pass1_chain(s, c, tw, te);
             if (!grid_sync(R.bar, R.err, &sflag)) return;
             mark(GPH_PASS1);
+            if (s.restart) {
+                if (*(volatile unsigned long long *)(s.lc + LC_WBLOCKED) == 0ull) break;
+                if (blockIdx.x == 0) {  // T*: the earliest stop of this pass
+                    double m = INFINITY;
+                    for (int c = threadIdx.x; c < s.k; c += blockDim.x)
+                        if (s.status[c] == ST_BLOCKED) m = fmin(m, s.vt[c]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, o));
+                    if (lane == 0) dmin[threadIdx.x >> 5] = m;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = fmin(m, dmin[q]);
+                        s.tstar[0] = fmax(m, tw);
+                    }
+                    __syncthreads();
+                }
+                if (!grid_sync(R.bar, R.err, &sflag)) return;
+                const double Ts = *(volatile double *)s.tstar;
+                if (!(dbits(Ts) > dbits(tw)) || sub >= MAX_RESTARTS) {
+                    // no progress: the local repair below
+                } else {
+                    // every thread has read the blocked count: reset for the next pass
+                    if (gt == 0) {
+                        s.lc[LC_WBLOCKED] = 0ull;
+                        s.lc[LC_RESTARTS] += 1ull;
+                    }
+                    for (int c = gt; c < s.k; c += nthreads) g_rollback_chain(s, c, Ts);
+                    for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
+                    if (!grid_sync(R.bar, R.err, &sflag)) return;
+                    tw_r = Ts;
+                    ++sub;
+                    continue;
+                }
+            }
             if (gt == 0) s.nabort[1] = 0;  // the first round's abort count
             for (int round = 1;; ++round) {
                 if (blockIdx.x == 0) {
@@ -1350,6 +1413,8 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                 if (*(volatile int32_t *)(s.nabort + (round & 1)) == 0) break;
             }
             mark(GPH_REPAIR);
+            break;
+          }
         }
         // leg end: liftings and the log (and, without a budget, the next leg's
         // start), then the totals. Every counter but the liftings is final
@@ -1392,6 +1457,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
             c.conflict_legs += flag;
             c.repaired += (int64_t)d[LC_REPAIRED];
             c.continued += (int64_t)d[LC_CONTINUED];
+            c.restarts += (int64_t)d[LC_RESTARTS];
             c.horizon += (int64_t)d[LC_HORIZON];
             c.order_err += (int64_t)d[LC_ORDER];
             if (err) c.err = 1;
@@ -1603,6 +1669,8 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     chk(galloc(g, &s.nlift, k, err));
     chk(galloc(g, &s.claim, n, err));
     chk(galloc(g, &s.memb, k, err));
+    chk(galloc(g, &s.tstar, 1, err));
+    s.restart = (p->flags & ECMC_RESTART) ? 1 : 0;
     chk(galloc(g, &s.rec, k * (size_t)s.cap, err));
     chk(galloc(g, &s.ev_T, k, err));
     chk(galloc(g, &s.ev_tau, k, err));
@@ -1741,6 +1809,7 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     tot->conflict_legs = ctl.conflict_legs;
     tot->repaired = ctl.repaired;
     tot->continued = ctl.continued;
+    tot->restarts = ctl.restarts;
     tot->horizon = ctl.horizon;
     tot->order_err = ctl.order_err;
     tot->p1_lifts = ctl.p1_lifts;

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 def test_binding_structs_match_header_sizes():
     import ctypes as C
     assert C.sizeof(ecmc.ecmc_params) == 64
-    assert C.sizeof(ecmc.ecmc_stats_t) == 64
+    assert C.sizeof(ecmc.ecmc_stats_t) == 72
     assert ecmc.LIFT_DTYPE.itemsize == 48
 
 

@@ -185,3 +185,73 @@ def test_graph_split_runs_equal_one_run():
             assert np.array_equal(u, v)
         for f in ("leg", "c", "i", "j", "t"):
             assert np.array_equal(out[0][4][f], o[4][f]), f
+
+
+def _restart_run(s, ell, n_legs):
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, ell, log=True, graph=True, restart=True,
+                       log_cap=max(1 << 16, 64 * s.k * n_legs * 64))
+    flags, done = sysm.run(n_legs)
+    assert done == n_legs
+    x, y, t, a = sysm.positions()
+    log = chain_order(sysm.liftings())
+    st = sysm.stats()
+    sysm.close()
+    return flags, x, t, a, log, st
+
+
+@pytest.mark.parametrize("kind,seed", [("lattice", 1), ("lattice", 2), ("rsa", 3), ("rsa", 4)])
+def test_restart_mode_equals_oracle(kind, seed):
+    """Restart strategy 2 (Sec. 3.4): passes cut at the earliest stop time T*
+    and begun again from it give the oracle's legs exactly; the leg flag is
+    that of the first pass, the oracle's one-window flag."""
+    if kind == "lattice":
+        s = synth.lattice_start(24, 0.70, 12, seed=seed)
+        ell, n_legs = 1.0, 6
+    else:
+        s = synth.rsa_start(400, 0.5, 16, seed=seed)
+        ell, n_legs = 1.5, 5
+    flags, x, t, a, log, st = _restart_run(s, ell, n_legs)
+    of, last, olog = oracle_graph(s, ell, n_legs)
+    assert np.array_equal(flags, of)
+    assert np.array_equal(x, last.x) and np.array_equal(t, last.t)
+    assert np.array_equal(a, last.active)
+    o = chain_order(olog)
+    for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
+        assert np.array_equal(o[f], log[f]), f
+    assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
+
+
+def test_restart_mode_two_chains_in_a_row():
+    """The rear chain of one lattice row reaches the front chain's start disk
+    after a few liftings: the first pass stops there at T* > 0, both chains
+    go back to T*, and the leg goes on from T* as from a breakpoint."""
+    m, r = 16, 5
+    s = synth.lattice_start(m, 0.70, 2, seed=3)
+    s.active = np.array([0 * m + r, 5 * m + r], dtype=np.int32)  # columns 0 and 5 of row r
+    flags, x, t, a, log, st = _restart_run(s, 0.5, 3)
+    of, last, olog = oracle_graph(s, 0.5, 3)
+    assert np.array_equal(flags, of) and flags[0] == 1
+    assert np.array_equal(x, last.x) and np.array_equal(t, last.t)
+    assert np.array_equal(a, last.active)
+    o = chain_order(olog)
+    for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
+        assert np.array_equal(o[f], log[f]), f
+    assert st["restarts"] >= 1
+
+
+def test_restart_mode_n1m():
+    """N = 2^20, k = 1024: one leg against the oracle (passes that cannot
+    progress fall back to the local repair)."""
+    s = synth.lattice_start(1024, 0.72, 1024, seed=5)
+    flags, x, t, a, log, st = _restart_run(s, 1.0, 1)
+    of, last, olog = oracle_graph(s, 1.0, 1)
+    assert np.array_equal(flags, of)
+    assert np.array_equal(x, last.x) and np.array_equal(a, last.active)
+
+
+def test_restart_needs_graph_and_one_window():
+    s = synth.lattice_start(16, 0.70, 4, seed=0)
+    for kw in ({"graph": False}, {"graph": True, "windows": 2}):
+        with pytest.raises(ecmc.EcmcError) as e:
+            ecmc.System(s.x, s.y, s.active, s.box, 0.5, restart=True, **kw)
+        assert e.value.code == ecmc.ECMC_EINVAL
