@@ -587,8 +587,9 @@ __device__ void g_leg_begin_chain(const GDev &s, int c) {
 // among the arrow targets within reach (the step is then not taken; cf.
 // Remark 10). Once a
 // step's winner j is known (and the step will be taken unless a claim of it
-// fails), the arrow targets of j are claimed and their records prefetched into
-// L1, so that the next step's trips overlap this step's wait and writes. Those
+// fails), the arrow targets of j are claimed and their records loaded into
+// registers, so that the next step's trips overlap this step's wait and
+// writes (an L1 prefetch measured no better than a plain L2 load). Those
 // disks belong to the chain's run alone, so the claims change no flag.
 __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, double tend) {
     if (s.status[c] != ST_RUNNING) return;
@@ -620,11 +621,11 @@ __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, doub
     int st = ST_RUNNING;
     bool blocked = false;
     uint32_t lifts = 0;
-    for (;;) {
-        GDisk r[3];
+    GDisk r[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (a[q] != NONE) r[q] = s.g[a[q]];
+    for (int q = 0; q < 3; ++q)
+        if (a[q] != NONE) r[q] = s.g[a[q]];
+    for (;;) {
         // statements 4-9 over the static targets (see graph_step)
         unsigned long long bt = INF_BITS;
         int bq = -1;
@@ -667,12 +668,13 @@ __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, doub
         // the next step's claims and records, requested before this step's
         // claims are resolved
         uint32_t oldn[3] = {0u, 0u, 0u};
+        GDisk rn[3];
         if (lift && go) {
 #pragma unroll
             for (int q = 0; q < 3; ++q)
                 if (wr.a[q] != NONE) {
                     oldn[q] = atomicCAS(s.claim + wr.a[q], 0u, mine);
-                    prefetch_l1(s.g + wr.a[q]);
+                    rn[q] = s.g[wr.a[q]];
                 }
         }
 #pragma unroll
@@ -718,6 +720,7 @@ __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, doub
             a[q] = wr.a[q];
             b[q] = wr.b[q];
             old[q] = oldn[q];
+            r[q] = rn[q];
         }
     }
     if (blocked) st = ST_BLOCKED;
