@@ -66,8 +66,8 @@ def parse():
                    help="graph mode: conflicts by restart strategy 2 (Sec. 3.4) instead of "
                         "the local repair")
     p.add_argument("--windows", type=int, default=0,
-                   help="claim windows per leg (0: cell scan 2 up to 4096 chains, else 4; "
-                        "graph 1)")
+                   help="claim windows per leg (0: cell scan 1 up to 1024 chains, 2 up to 4096, "
+                        "else 4; graph 1)")
     p.add_argument("--workload", default="lattice",
                    choices=["lattice", "batched", "serve", "conflicts"])
     p.add_argument("--target", type=float, default=1e9,
@@ -94,7 +94,7 @@ def windows_for(a, search):
         return a.windows_arg
     if search == "graph":
         return 1
-    return 2 if a.k <= 4096 else 4
+    return 1 if a.k <= 1024 else (2 if a.k <= 4096 else 4)
 
 
 def workload(a, search=None):
