@@ -1808,6 +1808,11 @@ struct ecmc_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     std::vector<void *> allocs;
+    // device arrays requested by dalloc, placed in one allocation by pool_commit
+    std::vector<std::pair<void **, size_t>> pending;
+    // scratch of ecmc_positions, kept for the next call
+    double *exp_x = nullptr, *exp_y = nullptr, *exp_t = nullptr;
+    int32_t *exp_a = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     ecmc_profile_t prof = {};
@@ -1848,14 +1853,32 @@ static int fail(ecmc_ctx *ctx, int code, const std::string &msg) {
 
 template <typename T>
 static int dalloc(ecmc_ctx *ctx, T **ptr, size_t count) {
-    void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return fail(ctx, ECMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    *ptr = nullptr;
+    ctx->pending.emplace_back((void **)ptr, std::max<size_t>(count, 1) * sizeof(T));
+    return 0;
+}
+
+// One cudaMalloc for every array requested since the last commit, each
+// starting on a 256-byte boundary.
+static int pool_commit(ecmc_ctx *ctx) {
+    size_t total = 0;
+    for (auto &r : ctx->pending) total += (r.second + 255) & ~(size_t)255;
+    void *base = nullptr;
+    if (total) {
+        const cudaError_t e = cudaMalloc(&base, total);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            ctx->pending.clear();
+            return fail(ctx, ECMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        ctx->allocs.push_back(base);
     }
-    ctx->allocs.push_back(p);
-    *ptr = (T *)p;
+    size_t off = 0;
+    for (auto &r : ctx->pending) {
+        *r.first = (char *)base + off;
+        off += (r.second + 255) & ~(size_t)255;
+    }
+    ctx->pending.clear();
     return 0;
 }
 
@@ -2091,6 +2114,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         chk(dalloc(ctx, &dy, n));
         chk(dalloc(ctx, &dact, k));
     }
+    chk(pool_commit(ctx));
     if (rc) {
         g_create_err = ctx->err;
         ecmc_destroy(ctx);
@@ -2442,27 +2466,22 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
     cudaStream_t st = ctx->stream;
     const size_t n = (size_t)s.n;
     const size_t nslot = (size_t)s.nc * s.nc * ctx->C;
-    double *dx = nullptr, *dy = nullptr, *dt = nullptr;
-    int32_t *da = nullptr;
-    auto release = [&]() {
-        cudaFree(dx);
-        cudaFree(dy);
-        cudaFree(dt);
-        cudaFree(da);
-    };
-    if ((x && cudaMalloc(&dx, n * 8) != cudaSuccess) || (y && cudaMalloc(&dy, n * 8) != cudaSuccess) ||
-        (t && cudaMalloc(&dt, n * 8) != cudaSuccess) ||
-        (active && cudaMalloc(&da, (size_t)s.k * 4) != cudaSuccess)) {
-        (void)cudaGetLastError();
-        release();
-        return fail(ctx, ECMC_ENOMEM, "positions scratch");
+    // device scratch, allocated at the first call and kept by the context
+    if (!ctx->exp_x) {
+        dalloc(ctx, &ctx->exp_x, n);
+        dalloc(ctx, &ctx->exp_y, n);
+        dalloc(ctx, &ctx->exp_t, n);
+        dalloc(ctx, &ctx->exp_a, (size_t)s.k);
+        const int rc = pool_commit(ctx);
+        if (rc) return rc;
     }
+    double *dx = x ? ctx->exp_x : nullptr, *dy = y ? ctx->exp_y : nullptr;
+    double *dt = t ? ctx->exp_t : nullptr;
+    int32_t *da = active ? ctx->exp_a : nullptr;
     if (ctx->graph) {
         double *ex = ctx->direction ? dy : dx, *ey = ctx->direction ? dx : dy;
-        if (graph_export(ctx->graph, ex, ey, dt, da) != 0) {
-            release();
+        if (graph_export(ctx->graph, ex, ey, dt, da) != 0)
             return fail(ctx, ECMC_ECUDA, "positions (graph)");
-        }
     } else if (x || y || t) {
         // in a transposed context the stored x is the caller's y
         double *ex = ctx->direction ? dy : dx, *ey = ctx->direction ? dx : dy;
@@ -2480,7 +2499,6 @@ extern "C" int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, in
     if (e == cudaSuccess && active)
         e = cudaMemcpyAsync(active, da, (size_t)s.k * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    release();
     if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("positions: ") + cudaGetErrorString(e));
     return ECMC_OK;
 }

@@ -1526,20 +1526,39 @@ struct GraphCtx {
     int grid = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void *build_tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<std::pair<void **, size_t>> pending;
 };
 
 namespace {
 
+// Device arrays of a context: requested one by one, then placed in a single
+// allocation (each on a 256-byte boundary) by gcommit.
 template <typename T>
-int galloc(GraphCtx *g, T **ptr, size_t count, std::string &err) {
-    void *p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        err = "cudaMalloc failed (graph state)";
-        return ECMC_ENOMEM;
+int galloc(GraphCtx *g, T **ptr, size_t count, std::string &) {
+    *ptr = nullptr;
+    g->pending.emplace_back((void **)ptr, std::max<size_t>(count, 1) * sizeof(T));
+    return 0;
+}
+
+int gcommit(GraphCtx *g, std::string &err) {
+    size_t total = 0;
+    for (auto &r : g->pending) total += (r.second + 255) & ~(size_t)255;
+    void *base = nullptr;
+    if (total) {
+        if (cudaMalloc(&base, total) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g->pending.clear();
+            err = "cudaMalloc failed (graph state)";
+            return ECMC_ENOMEM;
+        }
+        g->allocs.push_back(base);
     }
-    g->allocs.push_back(p);
-    *ptr = (T *)p;
+    size_t off = 0;
+    for (auto &r : g->pending) {
+        *r.first = (char *)base + off;
+        off += (r.second + 255) & ~(size_t)255;
+    }
+    g->pending.clear();
     return 0;
 }
 
@@ -1701,6 +1720,7 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     chk(galloc(g, &g->d_bar, 2, err));
     chk(galloc(g, &g->d_err, 1, err));
     chk(galloc(g, &g->d_phase, GPH_N, err));
+    chk(gcommit(g, err));
     if (!rc && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess)) {
         err = "event creation";
         rc = ECMC_ECUDA;
