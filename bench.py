@@ -25,8 +25,9 @@ requests through the continuous-batching server (p50/p99 latency).
 --workload conflicts: the conflict (violation) rate per leg against the
 number of chains, n / sqrt(N): N = 128^2 at eta = 0.708 with 128 chains, and
 N = 2^20 at eta = 0.72 with 256 ... 16384 chains, each run to --target
-liftings; one claim window per leg (the leg-level flag) and the default
-windows (per-window flags, the throughput setting).
+liftings; cell claims with one window per leg (the leg-level flag) and with
+several windows (per-window flags), and graph mode with one window (the flag
+from the disks that isolated chains read).
 
 Multi-GPU: the path does not shard a single system; every rank runs an
 independent replica (its own seed), ``value`` sums all ranks' liftings over
@@ -525,8 +526,9 @@ def run_serve_bench(a):
 
 
 def run_conflicts(a):
-    """Conflict rate per leg (flag: claim sets of isolated chains overlap) and
-    the fraction of chains repaired, against n / sqrt(N)."""
+    """Conflict rate per leg and the fraction of chains repaired, against
+    n / sqrt(N). The flag: the cells (cell scan) or the disks (graph mode) that
+    isolated chains read overlap."""
     import torch
 
     from paper_2004_11040_gb300 import build, ecmc, synth
@@ -539,13 +541,20 @@ def run_conflicts(a):
     points = [(128, 0.708, 128), (1024, 0.72, 256), (1024, 0.72, 1024), (1024, 0.72, 4096),
               (1024, 0.72, 16384)]
     out = []
+    # (search, windows): cell claims with one and with several windows; graph
+    # mode (flag = overlap of the disks isolated chains read) with one window.
+    # --search graph: the graph-mode points alone
     for m, eta, k in points:
         start = synth.lattice_start(m, eta, k, seed=a.seed)
-        for windows in (1, 2 if k <= 4096 else 4):
+        modes = [("cells", 1), ("cells", 2 if k <= 4096 else 4), ("graph", 1)]
+        if a.search == "graph":
+            modes = modes[2:]
+        for search, windows in modes:
+            graph = search == "graph"
             sysm = ecmc.System(start.x, start.y, start.active, start.box, 1.0, stream=stream,
-                               windows=windows)
-            # the one-window runs of many chains repair for long: bounded sample
-            target = a.target if windows > 1 or k <= 1024 else min(a.target, 2e7)
+                               windows=windows, graph=graph)
+            # the one-window cell runs of many chains repair for long: bounded sample
+            target = a.target if graph or windows > 1 or k <= 1024 else min(a.target, 2e7)
             flags = []
             t0 = time.perf_counter()
             while sysm.stats()["liftings"] < target:
@@ -555,7 +564,7 @@ def run_conflicts(a):
             sysm.close()
             legs = st["legs"]
             out.append({"N": m * m, "eta": eta, "k": k, "n_over_sqrtN": k / m,
-                        "claim_windows": windows, "legs": legs, "liftings": st["liftings"],
+                        "search": search, "claim_windows": windows, "legs": legs, "liftings": st["liftings"],
                         "conflict_rate_per_leg": st["conflict_legs"] / legs,
                         "repaired_chains_per_leg_per_chain": st["repaired_chains"] / legs / k,
                         "liftings_per_s": st["liftings"] / (st["device_ms"] / 1e3),

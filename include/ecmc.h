@@ -180,6 +180,20 @@ int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
 int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out);
 
 /*
+ * ecmc_graph_arrows -- the constraint graph G(3) of a context created with
+ * ECMC_GRAPH (Sec. 3.1), in the context's current frame (motion along +x, or
+ * along +y after ecmc_set_direction(ctx, 1), with x and y exchanged):
+ *   a  host, 3n int32 or NULL: a[3i + q] = the arrow of disk i in corridor q
+ *      (0 centre |dy| < d/2, 1 upper d/2 <= dy < d, 2 lower -d < dy <= -d/2;
+ *      dy = y_j - y_i, minimum image), -1 if the corridor holds no disk;
+ *   b  host, 3n doubles or NULL: b[3i + q] = sqrt(d^2 - dy^2) of that arrow,
+ *      0 where there is none.
+ * Both caller-owned. Synchronises the context's stream.
+ * Errors: EINVAL (not a graph context), ECUDA.
+ */
+int ecmc_graph_arrows(ecmc_ctx *ctx, int32_t *a, double *b);
+
+/*
  * ecmc_profile -- device time per phase of the persistent kernel, read from
  * the device clock at the phase boundaries of every ecmc_run_to_breakpoint:
  *   pass1   the parallel pass (one warp per chain, Alg. 5/6 statements 1-26);

@@ -2551,6 +2551,14 @@ extern "C" int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out) {
     return ECMC_OK;
 }
 
+extern "C" int ecmc_graph_arrows(ecmc_ctx *ctx, int32_t *a, double *b) {
+    if (!ctx) return ECMC_EINVAL;
+    if (!ctx->graph) return fail(ctx, ECMC_EINVAL, "not a constraint-graph context");
+    std::string err;
+    const int rc = graph_arrows(ctx->graph, a, b, err);
+    return rc ? fail(ctx, rc, err) : ECMC_OK;
+}
+
 extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64_t *n_out) {
     if (!ctx || !n_out) return ECMC_EINVAL;
     if (ctx->graph) {

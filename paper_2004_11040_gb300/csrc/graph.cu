@@ -131,9 +131,11 @@ struct GBuild {
     int nc, nb;
     double L, d, d2, a, inv_a, eps, w;  // cells of side a; y bins of width w
     float Lf, wf, inv_wf, half_f, d_f;     // the same in FP32 (bins only)
+    float dcut_f;        // d + a margin above the FP32 error of |dy| (slot filter)
     const double *x, *y;
     uint32_t *cid;       // [nc*nc*C] disk per slot, EMPTY
     double *cx, *cy;     // [nc*nc*C]
+    float *cyf;          // [nc*nc*C] y in FP32
     int32_t *bins;       // [nb + 1]: counts, then their exclusive prefix
     GDisk *g;
     unsigned long long *err;  // cell overflow count
@@ -163,6 +165,7 @@ __global__ void k_gb_cells(GBuild b) {
         if (atomicCAS(b.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
             b.cx[loc] = x;
             b.cy[loc] = y;
+            b.cyf[loc] = __double2float_rn(y);
             return;
         }
     }
@@ -208,25 +211,26 @@ __device__ int band_count(const GBuild &b, float lo, float hi) {
     return (b.bins[b.nb] - b.bins[b0]) + (b.bins[bin(__fsub_rn(hi, b.Lf)) + 1] - b.bins[0]);
 }
 
-// Arrows of G(3): one warp per disk scans the columns ahead (rows cy-1..cy+1)
-// and keeps, per corridor, the least (tau, j). Before a pass whose first
-// column m >= 1 lies beyond (m a - fx) - d > max over the corridors still in
-// play of their best tau (+ eps), no later column can improve any of them and
-// the scan stops; a corridor that the y bins show empty is not in play, any
-// other one keeps the scan going (once round the box at most).
+// Arrows of G(3), one thread per disk: the thread scans the columns ahead
+// (rows cy-1..cy+1) and keeps, per corridor, the least (tau, j). Before
+// column m >= 1, if (m a - fx) - d exceeds the worst best tau of the
+// corridors still in play (+ eps), no later column can improve any of them
+// and the scan stops; a corridor that the y bins show empty is not in play,
+// any other one keeps the scan going (once round the box at most).
+// The FP64 pipe costs the same per warp instruction whatever the number of
+// active lanes, so every lane takes a disk of its own, and two tests keep
+// FP64 work off the slots that cannot matter, both exact:
+// - |dy| in FP32 above d plus a margin larger than its rounding error: the
+//   slot lies in no corridor;
+// - RN(dx - d) above the corridor's best: the computed tau = RN(dx - b) with
+//   b = RN(sqrt(d^2 - dy^2)) <= d is at least that (rounding is monotone),
+//   so the candidate can neither win nor tie, and its square root is skipped.
 template <int C>
-__global__ void k_gb_arrows(GBuild b) {
-    constexpr int LPC = (3 * C <= 16) ? 16 : 32;  // lanes per column
-    constexpr int CPP = 32 / LPC;                 // columns per pass
-    const int lane = threadIdx.x & 31;
-    const int grp = lane / LPC, sub = lane % LPC;
-    const int rr = sub / C, sl = sub % C;
-    const bool used = sub < 3 * C;
+__global__ void __launch_bounds__(256) k_gb_arrows(GBuild b) {
     const int nc = b.nc;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double half = __dmul_rn(0.5, b.d);
-    for (int64_t i = warp; i < b.n; i += nwarps) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += stride) {
         const double xi = b.x[i], yi = b.y[i];
         const int cxi = cell_coord(xi, b.inv_a, nc), cyi = cell_coord(yi, b.inv_a, nc);
         const double fx = __dsub_rn(xi, __dmul_rn((double)cxi, b.a));
@@ -239,13 +243,14 @@ __global__ void k_gb_arrows(GBuild b) {
         unsigned long long bt[3] = {INF_BITS, INF_BITS, INF_BITS};
         uint32_t bj[3] = {NONE, NONE, NONE};
         double bb[3] = {0.0, 0.0, 0.0};
-        int row = cyi + rr - 1;
-        if (row < 0) row += nc;
-        if (row >= nc) row -= nc;
-        for (int m0 = 0; m0 < nc; m0 += CPP) {
-            if (m0 >= 1) {
+        int rows[3] = {cyi - 1, cyi, cyi + 1};
+        if (rows[0] < 0) rows[0] += nc;
+        if (rows[2] >= nc) rows[2] -= nc;
+        for (int m = 0; m < nc; ++m) {
+            if (m >= 1) {
                 unsigned long long worst = 0ull;
                 bool any = false;
+#pragma unroll
                 for (int kc = 0; kc < 3; ++kc)
                     if (play[kc]) {
                         any = true;
@@ -254,83 +259,69 @@ __global__ void k_gb_arrows(GBuild b) {
                 if (!any) break;
                 if (worst != INF_BITS) {
                     const double thr =
-                        __dsub_rn(__dsub_rn(__dmul_rn((double)m0, b.a), fx), b.d);
+                        __dsub_rn(__dsub_rn(__dmul_rn((double)m, b.a), fx), b.d);
                     const double lim = __dadd_rn(__longlong_as_double((long long)worst), b.eps);
                     if (!dneg(thr) && dbits(thr) > dbits(lim)) break;
                 }
             }
-            const int m = m0 + grp;
             int col = cxi + m;
             if (col >= nc) col -= nc;
-            uint32_t id = EMPTY;
-            double xj = 0.0, yj = 0.0;
-            if (used && m < nc) {
-                const uint32_t loc = ((uint32_t)row * (uint32_t)nc + (uint32_t)col) * C + sl;
-                id = b.cid[loc];
-                xj = b.cx[loc];
-                yj = b.cy[loc];
-            }
-            int kc = -1;
-            double tau = 0.0, bv = 0.0;
-            if (id != EMPTY && id != (uint32_t)i) {
-                const double dy = __dsub_rn(yj, yi);
-                double ay = fabs(dy);
-                bool flip = false;
-                const double la = __dsub_rn(b.L, ay);
-                if (dbits(la) < dbits(ay)) {
-                    ay = la;
-                    flip = true;
-                }
-                if (dbits(ay) < dbits(b.d)) {
-                    if (dbits(ay) < dbits(half)) {
-                        kc = 0;
-                    } else {
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr) {
+                const uint32_t cell = (uint32_t)rows[rr] * (uint32_t)nc + (uint32_t)col;
+                for (int sl = 0; sl < C; ++sl) {
+                    const uint32_t loc = cell * C + sl;
+                    const uint32_t id = b.cid[loc];
+                    if (id == EMPTY) break;  // a cell's slots fill from the first
+                    if (id == (uint32_t)i) continue;
+                    const float ayf0 = fabsf(__fsub_rn(b.cyf[loc], yf));
+                    if (fminf(ayf0, __fsub_rn(b.Lf, ayf0)) > b.dcut_f) continue;
+                    const double dy = __dsub_rn(b.cy[loc], yi);
+                    double ay = fabs(dy);
+                    bool flip = false;
+                    const double la = __dsub_rn(b.L, ay);
+                    if (dbits(la) < dbits(ay)) {
+                        ay = la;
+                        flip = true;
+                    }
+                    if (dbits(ay) >= dbits(b.d)) continue;
+                    int kc = 0;
+                    if (dbits(ay) >= dbits(half)) {
                         bool up = !dneg(dy) && dbits(dy) != 0ull;
                         if (flip) up = !up;
                         kc = up ? 1 : 2;
                     }
-                    bv = __dsqrt_rn(__dsub_rn(b.d2, __dmul_rn(ay, ay)));
-                    double dx = __dsub_rn(xj, xi);
+                    // selects, not indexing, keep the corridor arrays in registers
+                    const bool pk = kc == 0 ? play[0] : kc == 1 ? play[1] : play[2];
+                    if (!pk) continue;
+                    const unsigned long long bk = kc == 0 ? bt[0] : kc == 1 ? bt[1] : bt[2];
+                    double dx = __dsub_rn(b.cx[loc], xi);
                     if (dneg(dx)) dx = __dadd_rn(dx, b.L);
-                    tau = __dsub_rn(dx, bv);
+                    const double lo = __dsub_rn(dx, b.d);
+                    if (!dneg(lo) && dbits(lo) > bk) continue;
+                    const double bv = __dsqrt_rn(__dsub_rn(b.d2, __dmul_rn(ay, ay)));
+                    double tau = __dsub_rn(dx, bv);
                     if (dneg(tau)) tau = 0.0;
-                }
-            }
+                    const unsigned long long kt = dbits(tau);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (!play[q]) continue;  // warp-uniform: an empty corridor has no candidate
-                unsigned long long kt = kc == q ? dbits(tau) : INF_BITS;
-                uint32_t kj = kc == q ? id : NONE;
-                double kb = bv;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long t2 = shfl_xor_u64(kt, o);
-                    const uint32_t j2 = __shfl_xor_sync(FULL, kj, o);
-                    const double b2 = __shfl_xor_sync(FULL, kb, o);
-                    if (t2 < kt || (t2 == kt && j2 < kj)) {
-                        kt = t2;
-                        kj = j2;
-                        kb = b2;
-                    }
-                }
-                if (kj != NONE && (kt < bt[q] || (kt == bt[q] && kj < bj[q]))) {
-                    bt[q] = kt;
-                    bj[q] = kj;
-                    bb[q] = kb;
+                    for (int q = 0; q < 3; ++q)
+                        if (q == kc && (kt < bt[q] || (kt == bt[q] && id < bj[q]))) {
+                            bt[q] = kt;
+                            bj[q] = id;
+                            bb[q] = bv;
+                        }
                 }
             }
         }
-        if (lane == 0) {
-            GDisk &r = b.g[i];
-            r.x = xi;
-            r.t = 0.0;
+        GDisk &r = b.g[i];
+        r.x = xi;
+        r.t = 0.0;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                r.a[q] = bj[q];
-                r.b[q] = bj[q] == NONE ? 0.0 : bb[q];
-            }
-            r.pad0 = r.pad1 = 0;
+        for (int q = 0; q < 3; ++q) {
+            r.a[q] = bj[q];
+            r.b[q] = bj[q] == NONE ? 0.0 : bb[q];
         }
+        r.pad0 = r.pad1 = 0;
     }
 }
 
@@ -1525,7 +1516,7 @@ struct GraphCtx {
     int64_t log_legs = 0;  // legs logged so far (leg index of the log)
     int grid = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    void *build_tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *build_tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<std::pair<void **, size_t>> pending;
 };
 
@@ -1585,6 +1576,10 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     b.inv_wf = 1.0f / b.wf;
     b.half_f = (float)(0.5 * s.d);
     b.d_f = (float)s.d;
+    // |dy| in FP32 is off by at most 2.5 ulp of L (three roundings of values
+    // below L, one of L itself): L * 1e-6 covers twice that, d * 1e-3 the
+    // rounding of the cut
+    b.dcut_f = (float)(s.d * (1.0 + 1e-3) + s.L * 1e-6);
     b.nb = (int)std::ceil(s.L / b.w) + 1;
     b.x = x;
     b.y = y;
@@ -1597,9 +1592,10 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
             cudaMalloc(&tmp[1], nslot * 8) != cudaSuccess ||
             cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
             cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
-            cudaMalloc(&tmp[4], 8) != cudaSuccess) {
+            cudaMalloc(&tmp[4], 8) != cudaSuccess ||
+            cudaMalloc(&tmp[5], nslot * 4) != cudaSuccess) {
             (void)cudaGetLastError();
-            for (int q = 0; q < 5; ++q) {
+            for (int q = 0; q < 6; ++q) {
                 cudaFree(tmp[q]);
                 tmp[q] = nullptr;
             }
@@ -1612,6 +1608,7 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     b.cy = (double *)tmp[2];
     b.bins = (int32_t *)tmp[3];
     b.err = (unsigned long long *)tmp[4];
+    b.cyf = (float *)tmp[5];
     cudaStream_t st = g->st;
     cudaMemsetAsync(b.cid, 0xFF, nslot * 4, st);
     cudaMemsetAsync(b.bins, 0, ((size_t)b.nb + 1) * 4, st);
@@ -1622,10 +1619,7 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     else
         k_gb_cells<8><<<nblk, 256, 0, st>>>(b);
     k_gb_scan<<<1, 1024, 0, st>>>(b);
-    int dev = 0, n_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned ablk = (unsigned)std::min<int64_t>((s.n + 7) / 8, (int64_t)n_sm * 16);
+    const unsigned ablk = (unsigned)((s.n + 255) / 256);  // one thread per disk
     if (C == 4)
         k_gb_arrows<4><<<ablk, 256, 0, st>>>(b);
     else
@@ -1873,6 +1867,25 @@ int graph_export(GraphCtx *g, double *x, double *y, double *t, int32_t *active) 
     if (y) cudaMemcpyAsync(y, s.y, (size_t)s.n * 8, cudaMemcpyDeviceToDevice, st);
     if (active) k_g_export_active<<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s, active);
     return cudaGetLastError() == cudaSuccess ? 0 : ECMC_ECUDA;
+}
+
+int graph_arrows(GraphCtx *g, int32_t *a, double *b, std::string &err) {
+    const GDev &s = g->s;
+    cudaStream_t st = g->st;
+    // strided copies straight out of the 64-byte records
+    cudaError_t e = cudaSuccess;
+    if (a)
+        e = cudaMemcpy2DAsync(a, 3 * sizeof(uint32_t), &s.g[0].a[0], sizeof(GDisk),
+                              3 * sizeof(uint32_t), (size_t)s.n, cudaMemcpyDeviceToHost, st);
+    if (b && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(b, 3 * sizeof(double), &s.g[0].b[0], sizeof(GDisk),
+                              3 * sizeof(double), (size_t)s.n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        err = std::string("graph arrows: ") + cudaGetErrorString(e);
+        return ECMC_ECUDA;
+    }
+    return 0;
 }
 
 int graph_transpose(GraphCtx *g, std::string &err) {

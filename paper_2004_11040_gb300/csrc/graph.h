@@ -30,6 +30,8 @@ int graph_export(GraphCtx *g, double *x, double *y, double *t, int32_t *active);
 // Exchanges x and y of every disk (the next legs move along the other axis),
 // clears the local times and rebuilds the graph.
 int graph_transpose(GraphCtx *g, std::string &err);
+// Host copies of the arrows (3 per disk, -1: none) and their b_ij.
+int graph_arrows(GraphCtx *g, int32_t *a, double *b, std::string &err);
 int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
                    std::string &err);
 void graph_destroy(GraphCtx *g);

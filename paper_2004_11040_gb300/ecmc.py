@@ -28,7 +28,8 @@ ECMC_RESTART = 0x8
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
            "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
-           "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction")
+           "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction",
+           "ecmc_graph_arrows")
 
 
 class ecmc_params(C.Structure):
@@ -88,6 +89,8 @@ def load(path: str | None = None):
     lib.ecmc_stats.restype = C.c_int
     lib.ecmc_profile.argtypes = [vp, C.POINTER(ecmc_profile_t)]
     lib.ecmc_profile.restype = C.c_int
+    lib.ecmc_graph_arrows.argtypes = [vp, vp, vp]
+    lib.ecmc_graph_arrows.restype = C.c_int
     lib.ecmc_liftings.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
     lib.ecmc_liftings.restype = C.c_int
     lib.ecmc_destroy.argtypes = [vp]
@@ -175,6 +178,15 @@ def ecmc_liftings(ctx) -> np.ndarray:
     buf = np.zeros(n.value, dtype=LIFT_DTYPE)
     _check(load().ecmc_liftings(ctx, _ptr(buf) if n.value else None, n.value, C.byref(n)), ctx)
     return buf
+
+
+def ecmc_graph_arrows(ctx, n: int):
+    """Arrows of G(3) and their b_ij, int32 and float64 arrays [n, 3] (-1 and
+    0 where a corridor is empty), in the context's current frame."""
+    a = np.empty((n, 3), dtype=np.int32)
+    b = np.empty((n, 3), dtype=np.float64)
+    _check(load().ecmc_graph_arrows(ctx, _ptr(a), _ptr(b)), ctx)
+    return a, b
 
 
 def ecmc_leg_noalloc(n, box, d, ell, n_chains, cells_per_side, x, y, active, t_out=None,
@@ -275,6 +287,9 @@ class System:
 
     def liftings(self):
         return ecmc_liftings(self.ctx)
+
+    def arrows(self):
+        return ecmc_graph_arrows(self.ctx, self.n)
 
     def profile(self):
         return ecmc_profile(self.ctx)

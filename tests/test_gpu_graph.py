@@ -255,3 +255,66 @@ def test_restart_needs_graph_and_one_window():
         with pytest.raises(ecmc.EcmcError) as e:
             ecmc.System(s.x, s.y, s.active, s.box, 0.5, restart=True, **kw)
         assert e.value.code == ecmc.ECMC_EINVAL
+
+
+def _b_of(x, y, a, L, d):
+    """b_ij = sqrt(d^2 - dy^2) of each arrow (dy minimum image), 0 for none."""
+    i = np.repeat(np.arange(len(x)), 3).reshape(-1, 3)
+    j = np.where(a >= 0, a, 0)
+    ay = np.abs(y[j] - y[i])
+    la = L - ay
+    ay = np.where(la < ay, la, ay)
+    return np.where(a >= 0, np.sqrt(d * d - ay * ay), 0.0)
+
+
+@pytest.mark.parametrize("kind,search", [("lattice16", 0), ("rsa", 0), ("rsa_dense", 0),
+                                         ("lattice128", 1), ("lattice1024", 1)])
+def test_graph_arrows_equal_oracle(kind, search):
+    """The arrows the device builds equal the oracle's G(3), all pairs (the
+    definition) on small starts and its cell scan on large ones, and every b_ij
+    is sqrt(d^2 - dy^2) of its arrow, bit for bit."""
+    if kind == "lattice16":
+        s = synth.lattice_start(16, 0.70, 4, seed=1)
+    elif kind == "rsa":
+        s = synth.rsa_start(500, 0.5, 8, seed=41)
+    elif kind == "rsa_dense":
+        s = synth.rsa_start(600, 0.52, 8, seed=42)
+    elif kind == "lattice128":
+        s = synth.lattice_start(128, 0.708, 128, seed=7)
+    else:
+        s = synth.lattice_start(1024, 0.72, 1024, seed=3)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, d=s.d, graph=True)
+    a, b = sysm.arrows()
+    sysm.close()
+    ids = np.arange(s.n)
+    if s.n > 100_000:  # the oracle's build takes seconds per 10^5 disks: a sample
+        rng = np.random.default_rng(5)
+        ids = np.unique(np.concatenate([np.arange(2048), s.n - 1 - np.arange(2048),
+                                        rng.choice(s.n, 16384, replace=False)]))
+    ref = O.graph3(s.x, s.y, s.box, d=s.d, search=search, ids=ids)
+    assert np.array_equal(a[ids], ref)
+    assert np.array_equal(b, _b_of(s.x, s.y, a, s.box, s.d))
+    if kind.startswith("rsa"):
+        assert (a[:, 1:] >= 0).any()  # the side corridors are in use
+
+
+def test_graph_arrows_after_direction_change():
+    """After set_direction(1) the graph is that of +x motion in the exchanged
+    frame: G(3) of (y, x)."""
+    s = synth.rsa_start(400, 0.5, 8, seed=43)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, d=s.d, graph=True)
+    sysm.set_direction(1)
+    a, b = sysm.arrows()
+    sysm.close()
+    ref = O.graph3(s.y, s.x, s.box, d=s.d, search=0)
+    assert np.array_equal(a, ref)
+    assert np.array_equal(b, _b_of(s.y, s.x, ref, s.box, s.d))
+
+
+def test_graph_arrows_need_a_graph_context():
+    s = synth.lattice_start(16, 0.70, 4, seed=0)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 0.5)
+    with pytest.raises(ecmc.EcmcError) as e:
+        sysm.arrows()
+    sysm.close()
+    assert e.value.code == ecmc.ECMC_EINVAL
