@@ -66,7 +66,15 @@ struct Dev {
     // owner word live in its slot and move with it
     double *cx, *cy, *ct;
     uint32_t *cid, *cown;
-    uint32_t *claim;  // per cell: 0 or chain+1
+    // rows a disk's scan need not read (moves along x never change a disk's
+    // cell row): bit 0 the row below, bit 1 the row above, when no disk of
+    // that row lies within d in y; per slot, moving with the disk (or null:
+    // every row is read)
+    uint8_t *cskp;
+    unsigned long long *rband;  // [2 nc]: least and largest y (bits) per cell row
+    // per cell: 0, chain+1 (the chain reads the cell) or chain+1 | CLAIM_WEAK
+    // (the chain's scan covers the cell but need not read it)
+    uint32_t *claim;
     // per chain
     uint32_t *aloc0, *aloc;
     uint32_t *ci;  // active disk id
@@ -138,7 +146,14 @@ enum { MODE_PASS1 = 0, MODE_COMP = 1, MODE_CONT = 2 };
 struct ChainReg {
     uint32_t i, iloc;
     double xi, yi, ti, D;
+    uint32_t skip;  // rows of the footprint the scan need not read (cskp)
 };
+
+constexpr uint32_t CLAIM_WEAK = 0x80000000u;
+
+__device__ __forceinline__ uint32_t skip_of(const Dev &s, uint32_t loc) {
+    return s.cskp ? (uint32_t)s.cskp[loc] : 0u;
+}
 
 struct StepOut {
     double tau;  // tau* (lift) or D (stall)
@@ -155,6 +170,10 @@ struct StepOut {
     int nonstatic;
     uint32_t ns_owner;
     int viol;       // CONT: a scanned corridor disk fails the horizon condition (Eq. 2)
+    // PASS1: the scan met another chain's claim on a cell it need not read, or
+    // took over another chain's weak claim: the claim sets overlap (the flag)
+    int weak;
+    uint32_t jskp;  // skip bits of the target's slot
     // empty slots of the middle row (the active disk's row) as scanned: C bits
     // per column offset m (bit m*C + slot), for the columns with (m+1)*C <= 64
     unsigned long long emask;
@@ -199,6 +218,11 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     const bool used = sub < 3 * C;
     const int nc = s.nc;
     const uint32_t mine = (uint32_t)c + 1u;
+    const uint32_t mine_w = mine | CLAIM_WEAK;
+    // a row none of whose disks lies within d in y of the active disk holds no
+    // candidate: its slots are not read, and in pass 1 its cells are claimed
+    // weakly (the claim set, hence the flag, is that of the full scan)
+    const bool need = rr == 1 || !((r.skip >> (rr >> 1)) & 1u);
 
     // the active disk's cell is that of its slot (cells always hold the
     // disks whose coordinates fall in them)
@@ -218,7 +242,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     unsigned long long cur_eps = dbits(__dadd_rn(r.D, s.eps));
     unsigned long long btau = INF_BITS;
     double bx = 0.0, by = 0.0, bt = 0.0;
-    uint32_t bj = NONE, bloc = 0;
+    uint32_t bj = NONE, bloc = 0, bskp = 0;
     int mlast = 0;
     bool stop = false;
     bool conflict = false;
@@ -228,6 +252,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     uint32_t ns_own = NONE;                // ... and its chain
     bool ns_hv = false;                    // such a disk fails Eq. 2 (this lane)
     bool viol = false;   // CONT: a scanned corridor disk fails Eq. 2
+    bool weakc = false;  // PASS1: claim sets overlap on a weak claim (this lane)
     unsigned long long emask = 0ull;
 
     double thr_first = 0.0;  // threshold of the pass's first column (column 0: scanned)
@@ -254,22 +279,25 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // read before its claim succeeds was not written in this window
         // (claims are taken before writes and never released in a window),
         // and a failed claim discards what was read.
-        uint32_t id = EMPTY, own = OWN_STATIC;
+        uint32_t id = EMPTY, own = OWN_STATIC, skp = 0;
         double xj = 0.0, yj = 0.0, tj = 0.0;
         // claim word: the raw result of the CAS (claimed_early) or the value
         // read; turned into the holder only where the conflict test needs it
         uint32_t claim_w = 0;
         bool claimed_early = false;
-        if (colok) {
+        const uint32_t word = need ? mine : mine_w;
+        if (colok && need) {
             id = s.cid[loc];
             xj = s.cx[loc];
             yj = s.cy[loc];
             tj = s.ct[loc];
             own = s.cown[loc];
+            if (s.cskp) skp = s.cskp[loc];
         }
-        if (colok && sl == 0) {
+        // repairs claim only the cells they read
+        if (colok && sl == 0 && (need || MODE == MODE_PASS1)) {
             if (certain) {
-                claim_w = atomicCAS(s.claim + cell, 0u, mine);
+                claim_w = atomicCAS(s.claim + cell, 0u, word);
                 claimed_early = true;
             } else {
                 // through L2: claims are reset between windows by other SMs, so
@@ -401,17 +429,34 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             bx = __shfl_sync(FULL, xj, src);
             by = __shfl_sync(FULL, yj, src);
             bt = __shfl_sync(FULL, tj, src);
+            bskp = __shfl_sync(FULL, skp, src);
         }
-        uint32_t holder = claimed_early ? (claim_w == 0u ? mine : claim_w) : claim_w;
-        if (scanned && sl == 0 && !claimed_early && holder == 0u) {
-            const uint32_t old = atomicCAS(s.claim + cell, 0u, mine);
-            holder = old == 0u ? mine : old;
+        uint32_t holder = claimed_early ? (claim_w == 0u ? word : claim_w) : claim_w;
+        // lanes that hold a cell's claim word
+        const bool cl = scanned && sl == 0 && (need || MODE == MODE_PASS1);
+        if (cl && !claimed_early && holder == 0u) {
+            const uint32_t old = atomicCAS(s.claim + cell, 0u, word);
+            holder = old == 0u ? word : old;
+        }
+        // A cell the step reads takes over a weak claim, its own or another
+        // chain's (whose holder neither read nor wrote the cell; another
+        // chain's means the claim sets overlap). A weak claim only ever turns
+        // into a strong one, so a failed exchange leaves a strong holder.
+        if (cl && need && (holder & CLAIM_WEAK)) {
+            if (MODE == MODE_PASS1 && holder != mine_w) weakc = true;
+            const uint32_t old = atomicCAS(s.claim + cell, holder, mine);
+            holder = old == holder ? mine : old;
         }
         bool foreign = false;
         if (MODE == MODE_PASS1) {
-            foreign = scanned && sl == 0 && holder != mine;
+            if (cl && !need) {
+                // a cell the step need not read never blocks it
+                if (holder != mine && holder != mine_w) weakc = true;
+            } else {
+                foreign = cl && holder != mine;
+            }
         } else if (nm != 0) {
-            const int hq = (scanned && sl == 0) ? (int)(holder - 1u) : -1;
+            const int hq = cl ? (int)(holder - 1u) : -1;
             bool member = hq < 0;
             const int nmem = nm > 0 ? nm : -nm;
             for (int q = 0; q < nmem; ++q) member |= __shfl_sync(FULL, my_member, q) == hq;
@@ -433,7 +478,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                 member = hc == root;
             }
             foreign = !member;
-        } else if (scanned && sl == 0) {
+        } else if (cl) {
             foreign = __ldcg(s.comp_of + (holder - 1u)) != root;
         }
         if (foreign) {
@@ -485,6 +530,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     o.nonstatic = (__ballot_sync(FULL, ns_hv) != 0u) || ns_t < dbits(r.D);
     o.ns_owner = ns_own;
     o.viol = MODE == MODE_CONT ? __ballot_sync(FULL, viol) != 0u : 0;
+    o.weak = MODE == MODE_PASS1 ? __ballot_sync(FULL, weakc) != 0u : 0;
     o.conflict = 0;
     o.partner = NONE;
     const unsigned cb = __ballot_sync(FULL, conflict);
@@ -506,6 +552,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         o.xj = bx;
         o.yj = by;
         o.tj = bt;
+        o.jskp = bskp;
     } else {
         o.lift = 0;
         o.tau = r.D;
@@ -514,6 +561,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         o.xj = 0.0;
         o.yj = 0.0;
         o.tj = 0.0;
+        o.jskp = 0;
     }
     return o;
 }
@@ -544,6 +592,7 @@ __device__ uint32_t move_active(const Dev &s, const ChainReg &r, const StepOut &
         if (lane == 0) {
             s.cx[newloc] = xnew;
             s.cy[newloc] = r.yi;
+            if (s.cskp) s.cskp[newloc] = (uint8_t)r.skip;
             s.ct[newloc] = tnew;
             s.cown[newloc] = own_new;
             s.cid[newloc] = r.i;
@@ -614,6 +663,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         r.xi = o.xj;
         r.yi = o.yj;
         r.ti = tnew;
+        // (pass 1 gathered them with the target's slot)
+        r.skip = pass1 ? o.jskp : skip_of(s, o.jloc);
         __syncwarp();
         return ST_RUNNING;
     }
@@ -673,6 +724,57 @@ __global__ void k_build_cells(Dev s, const double *x, const double *y) {
         }
     }
     atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+}
+
+// Least and largest y of each cell row, then the rows a disk's scan need not
+// read (Dev::cskp). Take a disk in row R with 1 <= R <= nc - 2 and nc >= 5, so
+// that rows R - 1 and R + 1 do not wrap and the scan takes |dy| without the
+// periodic image.
+// - It skips row R + 1 when RN(ylo(R + 1) - y) >= d. Every disk j there has
+//   y_j >= ylo, so the scan's |RN(y_j - y)| = RN(y_j - y) >= RN(ylo - y) >= d
+//   (rounding is monotone), and j lies in no corridor.
+// - It skips row R - 1 when RN(y - yhi(R - 1)) >= d, by the same argument.
+// An empty row is skipped. Moves along x never change a disk's row, so the
+// bits hold until the frame is transposed.
+__global__ void k_band_init(Dev s) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.nc) return;
+    s.rband[q] = INF_BITS;
+    s.rband[s.nc + q] = 0ull;
+}
+
+__global__ void k_bands(Dev s, int C) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)s.nc * s.nc * C || s.cid[q] == EMPTY) return;
+    const int R = (int)((q / C) / s.nc);
+    const unsigned long long b = dbits(s.cy[q]);  // y >= 0: bits order like values
+    atomicMin(s.rband + R, b);
+    atomicMax(s.rband + s.nc + R, b);
+}
+
+__global__ void k_skip(Dev s, int C) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = s.nc;
+    if (q >= (int64_t)nc * nc * C) return;
+    const int R = (int)((q / C) / nc);
+    uint8_t v = 0;
+    if (s.cid[q] != EMPTY && nc >= 5 && R >= 1 && R <= nc - 2) {
+        const double y = s.cy[q];
+        const unsigned long long lo_dn = s.rband[R - 1], lo_up = s.rband[R + 1];
+        const double hi_dn = __longlong_as_double((long long)s.rband[nc + R - 1]);
+        const double lo = __longlong_as_double((long long)lo_up);
+        if (lo_dn == INF_BITS || !(__dsub_rn(y, hi_dn) < s.d)) v |= 1;
+        if (lo_up == INF_BITS || !(__dsub_rn(lo, y) < s.d)) v |= 2;
+    }
+    s.cskp[q] = v;
+}
+
+// Skip bits for the current frame (after the cells are built or transposed).
+static void launch_skip(const Dev &s, int C, cudaStream_t st) {
+    const size_t nslot = (size_t)s.nc * s.nc * C;
+    k_band_init<<<(unsigned)((s.nc + 255) / 256), 256, 0, st>>>(s);
+    k_bands<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C);
+    k_skip<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C);
 }
 
 __global__ void k_locate(Dev s, int C, uint32_t *loc_of) {
@@ -737,14 +839,17 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
     r.yi = s.cy[r.iloc];
     r.ti = s.tc[c];
     r.D = s.D[c];
+    r.skip = skip_of(s, r.iloc);
     int st = ST_RUNNING;
     uint32_t seq = (uint32_t)s.nrec[c];
+    bool weak = false;  // the claim sets met on a weak claim
     uint32_t cas_old = OWN_STATIC;  // lane 0: owner word seen by the last lift's CAS
     int32_t cas_rec = -1;           // record of that lift, while unchecked
     bool blocked = false;
     uint32_t lifts = 0;
     while (st == ST_RUNNING) {
         const StepOut o = scan_step<C, MODE_PASS1>(s, c, c, r, tw);
+        weak |= o.weak != 0;
         if (cas_rec >= 0) {  // the CAS ran while this step's cells were loaded
             const uint32_t old = __shfl_sync(FULL, cas_old, 0);
             if (old != OWN_STATIC) {
@@ -800,6 +905,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
             atomicAdd(s.lc + LC_BLOCKED, 1ull);
             atomicAdd(s.lc + LC_WBLOCKED, 1ull);
         }
+        if (weak) atomicAdd(s.lc + LC_WEAK, 1ull);
         atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)lifts);
     }
     __syncwarp();
@@ -817,6 +923,7 @@ __device__ void undo_record(const Dev &s, int c, const Rec &u) {
     if (u.to != u.from) {
         s.cx[u.from] = u.x_old;
         s.cy[u.from] = s.cy[u.to];
+        if (s.cskp) s.cskp[u.from] = s.cskp[u.to];
         s.cid[u.from] = u.i;
         s.cid[u.to] = EMPTY;
     } else {
@@ -964,7 +1071,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
     const int lane = threadIdx.x & 31;
     const bool has = lane < m;
     const int my_c = has ? mem[lane] : 0x7FFFFFFF;
-    uint32_t my_loc = 0, my_id = 0;
+    uint32_t my_loc = 0, my_id = 0, my_skp = 0;
     double my_x = 0.0, my_y = 0.0, my_t = 0.0, my_D = 0.0;
     int my_st = ST_STALLED;
     int32_t my_nrec = 0;
@@ -973,6 +1080,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         my_nrec = s.nrec[my_c];
         my_x = s.cx[my_loc];
         my_y = s.cy[my_loc];
+        my_skp = skip_of(s, my_loc);
         if (s.cid[my_loc] != my_id) {
             const int32_t nr = s.nrec[my_c];
             diag(s, 1, round, my_c, my_loc, my_id, s.cid[my_loc],
@@ -1000,6 +1108,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         r.iloc = __shfl_sync(FULL, my_loc, q);
         r.xi = __shfl_sync(FULL, my_x, q);
         r.yi = __shfl_sync(FULL, my_y, q);
+        r.skip = __shfl_sync(FULL, my_skp, q);
         r.ti = __shfl_sync(FULL, my_t, q);
         r.D = __shfl_sync(FULL, my_D, q);
         const int cq = __shfl_sync(FULL, my_c, q);
@@ -1051,6 +1160,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         r.iloc = __shfl_sync(FULL, my_loc, bq);
         r.xi = __shfl_sync(FULL, my_x, bq);
         r.yi = __shfl_sync(FULL, my_y, bq);
+        r.skip = __shfl_sync(FULL, my_skp, bq);
         r.ti = __shfl_sync(FULL, my_t, bq);
         r.D = __shfl_sync(FULL, my_D, bq);
         StepOut o;
@@ -1082,6 +1192,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
             my_id = r.i;
             my_x = r.xi;
             my_y = r.yi;
+            my_skp = r.skip;
             my_t = r.ti;
             my_D = r.D;
         }
@@ -1137,6 +1248,7 @@ __device__ StepOut compute_event_global(const Dev &s, int c, int root) {
     r.i = s.ci[c];
     r.xi = s.cx[r.iloc];
     r.yi = s.cy[r.iloc];
+    r.skip = skip_of(s, r.iloc);
     r.ti = s.tc[c];
     r.D = s.D[c];
     const StepOut o = scan_step<C, MODE_COMP>(s, c, root, r, 0.0);
@@ -1223,6 +1335,7 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         r.i = s.ci[bc];
         r.xi = s.cx[r.iloc];
         r.yi = s.cy[r.iloc];
+        r.skip = skip_of(s, r.iloc);
         r.ti = s.tc[bc];
         r.D = s.D[bc];
         StepOut o;
@@ -1325,6 +1438,7 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
         r.i = s.ci[c];
         r.xi = s.cx[r.iloc];
         r.yi = s.cy[r.iloc];
+        r.skip = skip_of(s, r.iloc);
         r.ti = s.tc[c];
         r.D = s.D[c];
         int32_t nrec = s.nrec[c];
@@ -1747,7 +1861,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             if (!(c.live && !c.done)) continue;
             const Dev &s = b.reps[r];
             const unsigned long long *lc = s.lc;
-            const int flag = lc[LC_BLOCKED] != 0ull;
+            const int flag = lc[LC_BLOCKED] != 0ull || lc[LC_WEAK] != 0ull;
             if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
             c.lifts += (int64_t)lc[LC_LIFTS];
             c.p1_lifts += (int64_t)lc[LC_P1LIFTS];
@@ -2068,6 +2182,8 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.ct, nslot));
     chk(dalloc(ctx, &s.cid, nslot));
     chk(dalloc(ctx, &s.cown, nslot));
+    chk(dalloc(ctx, &s.cskp, nslot));
+    chk(dalloc(ctx, &s.rband, 2 * (size_t)nc));
     chk(dalloc(ctx, &s.claim, ncell));
     chk(dalloc(ctx, &s.aloc0, k));
     chk(dalloc(ctx, &s.aloc, k));
@@ -2148,6 +2264,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         launch_build<4>(ctx, sx, sy);
     else
         launch_build<8>(ctx, sx, sy);
+    launch_skip(s, C, st);
     k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
     k_init_chains<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(s, sa, loc_of);
     CU(cudaGetLastError());
@@ -2524,6 +2641,7 @@ extern "C" int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction) {
         k_transpose<8><<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(s);
         k_transpose_chains<8><<<(unsigned)((s.k + 127) / 128), 128, 0, st>>>(s);
     }
+    launch_skip(s, ctx->C, st);  // rows are the old columns
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("set_direction: ") + cudaGetErrorString(e));
@@ -2758,7 +2876,7 @@ static int noalloc_leg(Dev &s, cudaStream_t st, int n_sm, uint8_t *flag, int64_t
     CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
     CUN(cudaStreamSynchronize(st));
     if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) return ECMC_ECAPACITY;
-    if (flag) *flag = conflict ? 1 : 0;
+    if (flag) *flag = (conflict || lc[LC_WEAK] != 0) ? 1 : 0;
     if (lifts) *lifts = (int64_t)lc[LC_LIFTS];
     return ECMC_OK;
 }

@@ -114,6 +114,36 @@ def lattice_start(m: int, eta: float, k: int, seed: int, jitter: float = 0.01,
     return Start(x=x, y=y, active=active, box=L, d=d, m=m, seed=seed)
 
 
+def staggered_start(m: int, eta: float, k: int, seed: int, row_shift: float = 0.2,
+                    pair_shift: float = 0.0, jitter: float = 0.01,
+                    d: float = 1.0) -> Start:
+    """M x M lattice (M even) with every odd row moved by s/2 along x and row r
+    moved along y by (-1)^r pair_shift plus its own uniform draw in
+    [-row_shift, row_shift].
+
+    Some adjacent rows then lie within d in y and exchange liftings, others
+    lie farther apart (pair_shift > 0: rows 2p and 2p + 1 close, pairs far
+    apart). Draws: the jitter as in ``lattice_start``, then one per row, then
+    Floyd's start disks. At eta = 0.5 (s = 1.2533 d) total shifts up to
+    0.21 d keep every pair of disks at least d apart.
+    """
+    assert m % 2 == 0
+    n = m * m
+    L = box_side(n, eta, d)
+    s = L / m
+    u = to_unit(splitmix64(seed, 0, 2 * n))
+    ux = (2.0 * u[0::2] - 1.0) * jitter
+    uy = (2.0 * u[1::2] - 1.0) * jitter
+    shift = (2.0 * to_unit(splitmix64(seed, 2 * n, m)) - 1.0) * row_shift
+    shift = shift + np.where(np.arange(m) % 2 == 0, pair_shift, -pair_shift)
+    c = np.repeat(np.arange(m, dtype=np.float64), m)  # id = c*m + r
+    ri = np.tile(np.arange(m), m)
+    x = np.mod((c + 0.5 + 0.5 * (ri % 2)) * s + ux, L)
+    y = np.mod((ri + 0.5) * s + shift[ri] + uy, L)
+    active = floyd_sample(seed, 2 * n + m, n, k)
+    return Start(x=x, y=y, active=active, box=L, d=d, m=m, seed=seed)
+
+
 def rsa_start(n: int, eta: float, k: int, seed: int, d: float = 1.0,
               max_tries: int = 10_000_000) -> Start:
     """Random sequential addition of n disks (non-lattice test starts, eta <~ 0.5).

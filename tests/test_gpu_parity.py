@@ -229,3 +229,49 @@ def test_direction_alternation_equals_oracle_on_swapped_frame(kind):
     st = sysm.stats()
     assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
     sysm.close()
+
+
+@pytest.mark.parametrize("seed,windows", [(1, 1), (2, 1), (3, 2), (4, 3)])
+def test_staggered_rows_skip_and_cross(seed, windows):
+    """Rows in close pairs, the pairs far apart in y: a scan skips the row on
+    the far side of its pair (claimed weakly: the flag still sees it), and
+    chains lift between the two rows of a pair, taking over weak claims,
+    their own and other chains'."""
+    s = synth.staggered_start(16, 0.5, 12, seed, row_shift=0.05, pair_shift=0.15)
+    assert_parity(s, 1.5, 6, windows=windows)
+
+
+def test_staggered_rows_dense_chains():
+    s = synth.staggered_start(24, 0.5, 96, 7, row_shift=0.05, pair_shift=0.15)
+    flags, st = assert_parity(s, 1.0, 4)
+    assert st["repaired_chains"] > 0
+
+
+@pytest.mark.parametrize("seed", [8, 9])
+def test_staggered_rows_random_shifts(seed):
+    """Rows moved by independent shifts: some neighbours within d in y, some not."""
+    s = synth.staggered_start(32, 0.5, 24, seed, row_shift=0.2)
+    assert_parity(s, 1.5, 4)
+
+
+def test_staggered_rows_direction_alternation():
+    """The skipped rows are recomputed for the transposed frame; flags, positions
+    and active disks equal the oracle's on the exchanged coordinates."""
+    s = synth.staggered_start(16, 0.5, 10, 5, row_shift=0.05, pair_shift=0.15)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.2)
+    x, y, act = s.x.copy(), s.y.copy(), s.active.copy()
+    for leg in range(6):
+        d = leg % 2
+        sysm.set_direction(d)
+        f, _ = sysm.run(1)
+        if d == 0:
+            r = O.run_leg(x, y, act, s.box, 1.2, log=False)
+            x, act = r.x, r.active
+        else:
+            r = O.run_leg(y, x, act, s.box, 1.2, log=False)
+            y, act = r.x, r.active
+        gx, gy, _, ga = sysm.positions()
+        assert np.array_equal(gx, x) and np.array_equal(gy, y), leg
+        assert np.array_equal(ga, act), leg
+        assert int(f[0]) == r.flag, leg
+    sysm.close()
