@@ -30,7 +30,9 @@ constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
 // per-leg counters (reset at every leg start)
 enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
        LC_CONTINUED,
-       LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_RESTARTS, LC_WEAK, LC_N };
+       LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_RESTARTS, LC_WEAK,
+       LC_BADXY, LC_BADID,  // inputs out of range (creation only)
+       LC_N };
 enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };
 // cumulative counters
 enum { TC_LIFTS = 0, TC_LEGS, TC_CONFLICT_LEGS, TC_REPAIRED, TC_HORIZON, TC_ORDER,

@@ -777,6 +777,30 @@ static void launch_skip(const Dev &s, int C, cudaStream_t st) {
     k_skip<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C);
 }
 
+// Coordinates in [0, L) (counted in *bad_xy) and distinct active ids in
+// [0, n) (*bad_id), checked on the device where the inputs already are.
+// seen[] must be zero.
+__global__ void k_check_inputs(const double *x, const double *y, const int32_t *active,
+                               int64_t n, int k, double L, uint32_t *seen,
+                               unsigned long long *bad_xy, unsigned long long *bad_id) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t q = t0; q < n; q += stride)
+        if (!(x[q] >= 0.0 && x[q] < L && y[q] >= 0.0 && y[q] < L)) atomicAdd(bad_xy, 1ull);
+    for (int64_t c = t0; c < k; c += stride) {
+        const int32_t a = active[c];
+        if (a < 0 || (int64_t)a >= n || atomicExch(seen + a, 1u) != 0u) atomicAdd(bad_id, 1ull);
+    }
+}
+
+static void launch_check(const double *x, const double *y, const int32_t *active, int64_t n,
+                         int k, double L, uint32_t *seen, unsigned long long *bad_xy,
+                         unsigned long long *bad_id, cudaStream_t st) {
+    const int64_t work = std::max<int64_t>(n, k);
+    const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
+    k_check_inputs<<<blocks, 256, 0, st>>>(x, y, active, n, k, L, seen, bad_xy, bad_id);
+}
+
 __global__ void k_locate(Dev s, int C, uint32_t *loc_of) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (int64_t)s.nc * s.nc * C) return;
@@ -786,7 +810,7 @@ __global__ void k_locate(Dev s, int C, uint32_t *loc_of) {
 
 __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_of) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.k) return;
+    if (c >= s.k || s.lc[LC_BADID] != 0ull) return;  // ids checked before, in stream order
     const uint32_t a = (uint32_t)active[c];
     const uint32_t loc = loc_of[a];
     s.aloc[c] = loc;
@@ -1930,8 +1954,6 @@ struct ecmc_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     ecmc_profile_t prof = {};
-    unsigned long long *h_lc = nullptr;  // pinned
-    int32_t *h_ctl = nullptr;            // pinned
     int n_sm = 1;
     int64_t legs_total = 0;
     int64_t lifts_total = 0;
@@ -2020,72 +2042,30 @@ static int pick_cells(const ecmc_params *p, int *nc_out, int *C_out) {
     return 0;
 }
 
-// Inputs checked on a host copy: coordinates in [0, L), active ids distinct
-// and in [0, n). Returns 0 or an error code (message in g_create_err).
-static int check_inputs(const ecmc_params *p, const double *x, const double *y,
-                        const int32_t *active, bool dev_in) {
-    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
-    std::vector<double> hx, hy;
-    std::vector<int32_t> ha(k);
-    const double *vx = x, *vy = y;
-    const int32_t *va = active;
-    if (dev_in) {
-        hx.resize(n);
-        hy.resize(n);
-        if (cudaMemcpy(hx.data(), x, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(hy.data(), y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(ha.data(), active, k * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
-            (void)cudaGetLastError();
-            g_create_err = "cannot read device inputs";
-            return ECMC_ECUDA;
-        }
-        vx = hx.data();
-        vy = hy.data();
-        va = ha.data();
-    }
-    for (size_t q = 0; q < n; ++q) {
-        if (!(vx[q] >= 0.0 && vx[q] < p->box && vy[q] >= 0.0 && vy[q] < p->box)) {
-            g_create_err = "coordinate outside [0, L)";
-            return ECMC_EINVAL;
-        }
-    }
-    std::vector<char> seen(n, 0);
-    for (size_t c = 0; c < k; ++c) {
-        const int32_t a = va[c];
-        if (a < 0 || (size_t)a >= n || seen[a]) {
-            g_create_err = "active ids must be distinct and in [0, n)";
-            return ECMC_EINVAL;
-        }
-        seen[a] = 1;
-    }
-    return 0;
-}
-
 // ECMC_GRAPH: the state lives in the constraint-graph path (graph.cu).
 static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
                         const int32_t *active) {
     const ecmc_params *p = &ctx->p;
     const bool dev_in = (p->flags & ECMC_INPUT_DEVICE) != 0;
-    int rc = check_inputs(p, x, y, active, dev_in);
-    if (rc) return rc;
+    int rc = 0;
     const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
-    double *dx = nullptr, *dy = nullptr;
-    int32_t *da = nullptr;
+    // one scratch allocation: the uploaded inputs, the ids seen, two counters
+    const size_t off_y = n * 8, off_a = 2 * n * 8, off_seen = (off_a + k * 4 + 15) & ~(size_t)15;
+    const size_t off_bad = (off_seen + n * 4 + 15) & ~(size_t)15;
+    char *scratch = nullptr;
+    if (cudaMalloc(&scratch, off_bad + 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        g_create_err = "cudaMalloc failed (inputs)";
+        return ECMC_ENOMEM;
+    }
+    double *dx = (double *)scratch, *dy = (double *)(scratch + off_y);
+    int32_t *da = (int32_t *)(scratch + off_a);
+    uint32_t *seen = (uint32_t *)(scratch + off_seen);
+    unsigned long long *bad = (unsigned long long *)(scratch + off_bad);
     const double *sx = x, *sy = y;
     const int32_t *sa = active;
-    auto release = [&]() {
-        cudaFree(dx);
-        cudaFree(dy);
-        cudaFree(da);
-    };
+    auto release = [&]() { cudaFree(scratch); };
     if (!dev_in) {
-        if (cudaMalloc(&dx, n * 8) != cudaSuccess || cudaMalloc(&dy, n * 8) != cudaSuccess ||
-            cudaMalloc(&da, k * 4) != cudaSuccess) {
-            (void)cudaGetLastError();
-            release();
-            g_create_err = "cudaMalloc failed (inputs)";
-            return ECMC_ENOMEM;
-        }
         if (cudaMemcpyAsync(dx, x, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
             cudaMemcpyAsync(dy, y, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
             cudaMemcpyAsync(da, active, k * 4, cudaMemcpyHostToDevice, ctx->stream) !=
@@ -2098,6 +2078,27 @@ static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
         sx = dx;
         sy = dy;
         sa = da;
+    }
+    {
+        unsigned long long hb[2] = {0ull, 0ull};
+        cudaError_t e = cudaMemsetAsync(seen, 0, off_bad + 16 - off_seen, ctx->stream);
+        if (e == cudaSuccess) {
+            launch_check(sx, sy, sa, (int64_t)n, (int)k, p->box, seen, bad, bad + 1, ctx->stream);
+            e = cudaMemcpyAsync(hb, bad, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            release();
+            g_create_err = "input check";
+            return ECMC_ECUDA;
+        }
+        if (hb[0] || hb[1]) {
+            release();
+            g_create_err = hb[0] ? "coordinate outside [0, L)"
+                                 : "active ids must be distinct and in [0, n)";
+            return ECMC_EINVAL;
+        }
     }
     std::string err;
     rc = graph_create(p, nc, sx, sy, sa, ctx->stream, &ctx->graph, err);
@@ -2236,13 +2237,6 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         ecmc_destroy(ctx);
         return rc;
     }
-    {
-        const int vr = check_inputs(p, x, y, active, dev_in);
-        if (vr) {
-            ecmc_destroy(ctx);
-            return vr;
-        }
-    }
     cudaStream_t st = ctx->stream;
     const double *sx = x, *sy = y;
     const int32_t *sa = active;
@@ -2260,6 +2254,12 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
     CU(cudaMemsetAsync(s.dbg, 0, 16 * sizeof(double), st));
+    // the inputs are checked on the device (loc_of holds the ids seen until
+    // k_locate fills it); nothing below indexes by an active id before
+    // k_init_chains, which does nothing if an id failed
+    CU(cudaMemsetAsync(loc_of, 0, n * sizeof(uint32_t), st));
+    launch_check(sx, sy, sa, (int64_t)n, (int)k, s.L, loc_of, s.lc + LC_BADXY, s.lc + LC_BADID,
+                 st);
     if (C == 4)
         launch_build<4>(ctx, sx, sy);
     else
@@ -2268,16 +2268,21 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
     k_init_chains<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(s, sa, loc_of);
     CU(cudaGetLastError());
-    CU(cudaMallocHost(&ctx->h_lc, LC_N * sizeof(unsigned long long)));
-    CU(cudaMallocHost(&ctx->h_ctl, CTL_N * sizeof(int32_t)));
     {
         int dev = 0;
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev));
     }
-    CU(cudaMemcpyAsync(ctx->h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    unsigned long long h_lc[LC_N];
+    CU(cudaMemcpyAsync(h_lc, s.lc, LC_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (ctx->h_lc[LC_ERR_CAP]) {
+    if (h_lc[LC_BADXY] || h_lc[LC_BADID]) {
+        g_create_err = h_lc[LC_BADXY] ? "coordinate outside [0, L)"
+                                      : "active ids must be distinct and in [0, n)";
+        ecmc_destroy(ctx);
+        return ECMC_EINVAL;
+    }
+    if (h_lc[LC_ERR_CAP]) {
         g_create_err = "more disks in a cell than it has slots (overlapping input?)";
         ecmc_destroy(ctx);
         return ECMC_ECAPACITY;
@@ -2712,8 +2717,6 @@ extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
     runner_free(ctx->run);
     cudaFree(ctx->d_flags);
     for (void *p : ctx->allocs) cudaFree(p);
-    if (ctx->h_lc) cudaFreeHost(ctx->h_lc);
-    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (auto e : ctx->kev)
@@ -2824,20 +2827,6 @@ static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t n
     return cv.off;
 }
 
-// Coordinates in [0, L) and distinct active ids in range, checked on the
-// device (the caller's arrays are device memory). seen[] must be zero.
-__global__ void k_noalloc_check(const double *x, const double *y, const int32_t *active,
-                                int64_t n, int k, double L, uint32_t *seen,
-                                unsigned long long *bad) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride)
-        if (!(x[q] >= 0.0 && x[q] < L && y[q] >= 0.0 && y[q] < L)) atomicAdd(bad, 1ull);
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += stride) {
-        const int32_t a = active[c];
-        if (a < 0 || (int64_t)a >= n || atomicExch(seen + a, 1u) != 0u) atomicAdd(bad, 1ull);
-    }
-}
-
 #define CUN(call)                                   \
     do {                                            \
         if ((call) != cudaSuccess) {                \
@@ -2887,8 +2876,7 @@ static int noalloc_run(Dev &s, uint32_t *loc_of, double *x, const double *y, int
     const size_t nslot = (size_t)s.nc * s.nc * C;
     unsigned long long lc[LC_N];
     CUN(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
-    k_noalloc_check<<<(unsigned)std::min<int64_t>((s.n + 255) / 256, 4096), 256, 0, st>>>(
-        x, y, active, s.n, s.k, s.L, loc_of, s.lc + LC_ERR_CAP);
+    launch_check(x, y, active, s.n, s.k, s.L, loc_of, s.lc + LC_ERR_CAP, s.lc + LC_ERR_CAP, st);
     CUN(cudaGetLastError());
     CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
     CUN(cudaStreamSynchronize(st));

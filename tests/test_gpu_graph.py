@@ -318,3 +318,14 @@ def test_graph_arrows_need_a_graph_context():
         sysm.arrows()
     sysm.close()
     assert e.value.code == ecmc.ECMC_EINVAL
+
+
+def test_graph_inputs_checked():
+    """Out-of-box coordinates and repeated or out-of-range active ids are
+    reported as EINVAL by the device-side check, before the graph is built."""
+    s = synth.lattice_start(8, 0.6, 2, seed=1)
+    for x, act in ((s.x, [0, 0]), (s.x, [0, s.n]), (np.where(np.arange(s.n) == 3, s.box, s.x),
+                                                     [0, 1])):
+        with pytest.raises(ecmc.EcmcError) as e:
+            ecmc.System(x, s.y, act, s.box, 1.0, graph=True)
+        assert e.value.code == ecmc.ECMC_EINVAL
