@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "ecmc.h"
@@ -128,21 +129,41 @@ __device__ int block_exscan(int v, int *warp_tot, int *total) {
     return r;
 }
 
+// Shared-memory working set of uf_block: four int arrays of UF_SMEM_CAP
+// entries (union-find parents, counts, component roots, final flags).
+constexpr int UF_SMEM_CAP = 2048;
+constexpr size_t UF_SMEM_BYTES = 4 * UF_SMEM_CAP * sizeof(int32_t);
+
 // Conflict components (one block). first: edges from the parallel pass
 // (blocked chain -> holder of the claim it met); later rounds: edges from
 // components that met another chain. Components holding a chain whose events
 // are not final ("dirty") are listed for the repair with their members.
 // reset_abort: clear the abort count here (the persistent kernels clear it
 // elsewhere, after every block has read it).
+// sm (UF_SMEM_BYTES of shared memory, or null): with k <= UF_SMEM_CAP the
+// parents, counts, roots and flags live there during the phases (each phase
+// then waits on shared instead of global memory) and are written back to
+// s.uf, s.comp_of and s.fin at the end.
 template <class S>
-__device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool reset_abort) {
+__device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool reset_abort,
+                         int32_t *sm = nullptr) {
     const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
-    if (first)
-        for (int c = tid; c < k; c += nt) {
-            s.uf[c] = c;
-            s.fin[c] = s.status[c] != ST_BLOCKED;
+    const bool local = sm != nullptr && k <= UF_SMEM_CAP;
+    int32_t *uf = local ? sm : s.uf;
+    int32_t *cnt = local ? sm + UF_SMEM_CAP : s.comp_cnt;
+    int32_t *cof = local ? sm + 2 * UF_SMEM_CAP : s.comp_of;
+    int32_t *fin = local ? sm + 3 * UF_SMEM_CAP : s.fin;
+    for (int c = tid; c < k; c += nt) {
+        if (first) {
+            uf[c] = c;
+            fin[c] = s.status[c] != ST_BLOCKED;
             s.abort_to[c] = -1;
+        } else if (local) {
+            // (adoptions in the last round may have joined trees in s.uf)
+            uf[c] = s.uf[c];
+            fin[c] = s.fin[c];
         }
+    }
     __syncthreads();
     for (int c = tid; c < k; c += nt) {
         int other = -1;
@@ -152,50 +173,56 @@ __device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool re
             other = s.abort_to[c];
             s.abort_to[c] = -1;
         }
-        if (other >= 0 && other < k) uf_union(s.uf, c, other);
+        if (other >= 0 && other < k) uf_union(uf, c, other);
     }
     __syncthreads();
     for (int c = tid; c < k; c += nt) {
-        s.comp_of[c] = uf_find(s.uf, c);
-        s.comp_cnt[c] = 0;
+        cof[c] = uf_find(uf, c);
+        cnt[c] = 0;
     }
     __syncthreads();
     for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) s.comp_cnt[s.comp_of[c]] = -1;  // dirty root
+        if (!fin[c]) cnt[cof[c]] = -1;  // dirty root
     __syncthreads();
     for (int c = tid; c < k; c += nt)
-        if (s.comp_cnt[s.comp_of[c]] != 0) s.fin[c] = 0;
+        if (cnt[cof[c]] != 0) fin[c] = 0;
     __syncthreads();
     for (int c = tid; c < k; c += nt)
-        if (s.comp_cnt[c] == -1) s.comp_cnt[c] = 0;
+        if (cnt[c] == -1) cnt[c] = 0;
     __syncthreads();
     for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) atomicAdd(s.comp_cnt + s.comp_of[c], 1);
+        if (!fin[c]) atomicAdd(cnt + cof[c], 1);
     __syncthreads();
     // chunked exclusive scans over roots: member offsets and component index
     const int chunk = (k + nt - 1) / nt;
     const int lo = min(k, tid * chunk), hi = min(k, lo + chunk);
-    int sc = 0, sm = 0;
+    int sc = 0, sm_ = 0;
     for (int c = lo; c < hi; ++c) {
-        const int n = s.comp_cnt[c];
+        const int n = cnt[c];
         sc += n;
-        sm += n > 0;
+        sm_ += n > 0;
     }
     int oc = block_exscan(sc, warp_tot, tot);
-    int om = block_exscan(sm, warp_tot, tot + 1);
+    int om = block_exscan(sm_, warp_tot, tot + 1);
     for (int c = lo; c < hi; ++c) {
-        const int n = s.comp_cnt[c];
+        const int n = cnt[c];
         if (n > 0) {
             s.comp_root[om] = c;
             s.comp_off[om] = oc;
-            s.comp_cnt[c] = oc;  // becomes the write cursor
+            cnt[c] = oc;  // becomes the write cursor
             oc += n;
             ++om;
         }
     }
     __syncthreads();
     for (int c = tid; c < k; c += nt)
-        if (!s.fin[c]) s.comp_mem[atomicAdd(s.comp_cnt + s.comp_of[c], 1)] = c;
+        if (!fin[c]) s.comp_mem[atomicAdd(cnt + cof[c], 1)] = c;
+    if (local)
+        for (int c = tid; c < k; c += nt) {
+            s.uf[c] = uf[c];
+            s.comp_of[c] = cof[c];
+            s.fin[c] = fin[c];
+        }
     if (tid == 0) {
         s.comp_off[tot[1]] = tot[0];
         s.ctl[CTL_NCOMP] = tot[1];

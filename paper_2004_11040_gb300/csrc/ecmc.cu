@@ -62,6 +62,12 @@ struct Dev {
     double L, d, d2, ell, a, inv_a, eps;
     double far;  // L - 3a: a chain with less than this left never lifts onto a
                  // disk behind its active disk (that is more than L - 2a ahead)
+    // Exact tables of the cell map (null: computed in FP64):
+    const double *colx;                // [nc] RN(c a), the left edge of column c
+    const unsigned long long *xbound;  // [nc + 1] least x (bits) with
+                                       // cell_coord(x) >= c; [0] = 0, [nc] = +inf
+    // FP32 image of the scan's stop rule: |thr_f - lim_f - (thr - lim)| <= stop_e / 2
+    float af, df, epsf, stop_e;
     // cells: slot q of cell c at index c*C + q; a disk's x, y, local time and
     // owner word live in its slot and move with it
     double *cx, *cy, *ct;
@@ -130,6 +136,66 @@ __device__ __forceinline__ int cell_coord(double v, const Dev &s) {
 
 __device__ __forceinline__ uint32_t cell_of(double x, double y, const Dev &s) {
     return (uint32_t)cell_coord(y, s) * (uint32_t)s.nc + (uint32_t)cell_coord(x, s);
+}
+
+// v rounded toward zero to FP32 on the integer pipe (this chip's FP64 unit
+// costs ~64 cycles per warp instruction, conversions included): relative
+// error below 2^-23, and |v| < 2^-126 gives 0.
+__device__ __forceinline__ float d2f_trunc(double v) {
+    const unsigned long long b = dbits(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FFull) - 1023;
+    if (e < -126) return __int_as_float((int)sign);
+    if (e > 127) return __int_as_float((int)(sign | 0x7F800000u));
+    return __int_as_float(
+        (int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFull)));
+}
+
+// The scan's stop rule: is thr(m) = ((m a) - fx) - d above RN(cur + eps)?
+// Decided on the FP32 image thr_f - lim_f when that lies farther than stop_e
+// from 0 (its error bound is stop_e / 4, so the answer is the exact one),
+// else in FP64 as defined. lim_f = trunc(cur) + eps in FP32.
+__device__ __forceinline__ bool beyond(const Dev &s, int m, double fx, float fxf, float lim_f,
+                                       unsigned long long cur) {
+    if (s.stop_e > 0.f) {
+        const float thr_f =
+            __fsub_rn(__fsub_rn(__fmul_rn(__int2float_rn(m), s.af), fxf), s.df);
+        const float diff = __fsub_rn(thr_f, lim_f);
+        if (diff > s.stop_e) return true;
+        if (diff < -s.stop_e) return false;
+    }
+    const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, s.a), fx), s.d);
+    const double lim = __dadd_rn(__longlong_as_double((long long)cur), s.eps);
+    return !dneg(thr) && dbits(thr) > dbits(lim);
+}
+
+// thr(m) <= eps, where a column is scanned (and its cells claimed) whatever
+// the candidates: true only where certain (m = 0, or the FP32 image is below
+// eps by more than its error bound); false answers only delay claims.
+__device__ __forceinline__ bool surely_scanned(const Dev &s, int m, float fxf) {
+    if (m == 0) return true;
+    if (!(s.stop_e > 0.f)) return false;
+    const float thr_f = __fsub_rn(__fsub_rn(__fmul_rn(__int2float_rn(m), s.af), fxf), s.df);
+    return thr_f < __fsub_rn(s.epsf, s.stop_e);
+}
+
+// cell_of(x, y) of a disk that moved along x out of cell cell_old: the row
+// is unchanged, and the column is the last c with xbound[c] <= x (integer
+// compares of non-negative doubles), searched from the old column, or from 0
+// once x wrapped around the box. Long moves, or no table: cell_of.
+__device__ __forceinline__ uint32_t cell_after_move(const Dev &s, uint32_t cell_old, double x,
+                                                    double y) {
+    if (s.xbound) {
+        const uint32_t nc = (uint32_t)s.nc, row = cell_old / nc;
+        uint32_t col = cell_old % nc;
+        const unsigned long long xb = dbits(x);
+        if (xb < s.xbound[col]) col = 0;
+        for (int it = 0; it < 4; ++it) {
+            if (col + 1 >= nc || xb < s.xbound[col + 1]) return row * nc + col;
+            ++col;
+        }
+    }
+    return cell_of(x, y, s);
 }
 
 __device__ __forceinline__ double wrap_add(double x, double dx, const Dev &s) {
@@ -227,7 +293,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     // the active disk's cell is that of its slot (cells always hold the
     // disks whose coordinates fall in them)
     const int cxi = (int)((r.iloc / C) % (uint32_t)nc), cyi = (int)((r.iloc / C) / (uint32_t)nc);
-    const double fx = __dsub_rn(r.xi, __dmul_rn((double)cxi, s.a));
+    const double fx = __dsub_rn(r.xi, s.colx ? s.colx[cxi] : __dmul_rn((double)cxi, s.a));
+    const float fxf = d2f_trunc(fx);
     int row = cyi + rr - 1;
     if (row < 0) row += nc;
     if (row >= nc) row -= nc;
@@ -239,7 +306,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     const bool ywrap = cyi == 0 || cyi == nc - 1 || nc <= 4;
     const bool near_d = !(dbits(r.D) < dbits(s.far));
     unsigned long long cur = dbits(r.D);  // min(D, best tau so far): drives the stop rule
-    unsigned long long cur_eps = dbits(__dadd_rn(r.D, s.eps));
+    float lim_f = __fadd_rn(d2f_trunc(r.D), s.epsf);  // its FP32 image, + eps
     unsigned long long btau = INF_BITS;
     double bx = 0.0, by = 0.0, bt = 0.0;
     uint32_t bj = NONE, bloc = 0, bskp = 0;
@@ -255,24 +322,15 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     bool weakc = false;  // PASS1: claim sets overlap on a weak claim (this lane)
     unsigned long long emask = 0ull;
 
-    double thr_first = 0.0;  // threshold of the pass's first column (column 0: scanned)
     for (int m0 = 0; m0 < nc && !stop; m0 += CPP) {
-        // the stop rule for the next pass's first column, decided at the end
-        // of this pass before any of the next pass's loads (computed here so
-        // that its latency hides behind this pass)
-        const double thr_next =
-            __dsub_rn(__dsub_rn(__dmul_rn((double)(m0 + CPP), s.a), fx), s.d);
-        const double thr_second =
-            CPP == 2 ? __dsub_rn(__dsub_rn(__dmul_rn((double)(m0 + 1), s.a), fx), s.d) : 0.0;
         const int m = m0 + grp;
         const bool colok = used && m < nc;
         int col = cxi + m;
         if (col >= nc) col -= nc;
         const uint32_t cell = (uint32_t)row * (uint32_t)nc + (uint32_t)col;
         const uint32_t loc = cell * C + sl;
-        // threshold of this lane's column; <= eps means "scanned in any case"
-        const double thr = (CPP == 2 && grp == 1) ? thr_second : thr_first;
-        const bool certain = m == 0 || dneg(thr) || dbits(thr) <= dbits(s.eps);
+        // a column whose threshold is <= eps is scanned in any case
+        const bool certain = surely_scanned(s, m, fxf);
         // all loads of the slot at once (an empty slot's values are ignored;
         // they share the cell's sectors with the occupied ones). They are
         // issued before the claim so that both round trips overlap: a cell
@@ -402,10 +460,10 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
         // of D, so its scan does not stop at the best candidate)
         if (MODE != MODE_CONT && g0t < cur) {
             cur = g0t;
-            cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+            lim_f = __fadd_rn(d2f_trunc(__longlong_as_double((long long)cur)), s.epsf);
         }
         if (CPP == 2) {
-            if (m0 + 1 >= nc || (!dneg(thr_second) && dbits(thr_second) > cur_eps)) {
+            if (m0 + 1 >= nc || beyond(s, m0 + 1, fx, fxf, lim_f, cur)) {
                 stop = true;
             } else {
                 last_here = m0 + 1;
@@ -418,7 +476,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                 }
                 if (MODE != MODE_CONT && g1t < cur) {
                     cur = g1t;
-                    cur_eps = dbits(__dadd_rn(__longlong_as_double((long long)cur), s.eps));
+                    lim_f = __fadd_rn(d2f_trunc(__longlong_as_double((long long)cur)), s.epsf);
                 }
             }
         }
@@ -518,8 +576,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             }
         }
         if (MODE == MODE_CONT && scanned && hzv) viol = true;
-        if (!dneg(thr_next) && dbits(thr_next) > cur_eps) break;
-        thr_first = thr_next;
+        if (beyond(s, m0 + CPP, fx, fxf, lim_f, cur)) break;
     }
 
     StepOut o;
@@ -573,7 +630,7 @@ __device__ uint32_t move_active(const Dev &s, const ChainReg &r, const StepOut &
                                 double tnew, uint32_t own_new) {
     const int lane = threadIdx.x & 31;
     const uint32_t cell_old = r.iloc / C;
-    const uint32_t cell_new = cell_of(xnew, r.yi, s);
+    const uint32_t cell_new = cell_after_move(s, cell_old, xnew, r.yi);
     uint32_t newloc = r.iloc;
     if (cell_new != cell_old) {
         // the new cell lies in the active disk's row of the scanned footprint,
@@ -1755,6 +1812,7 @@ constexpr int RUN_MIN_BLOCKS = 2;
 
 template <int C>
 __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
+    extern __shared__ int32_t uf_sm[];  // UF_SMEM_BYTES: the union-find working set
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
     __shared__ int sflag;
@@ -1822,7 +1880,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                         need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
                     if (need && round == 1 && threadIdx.x == 0) s.lc[LC_CWINDOWS] += 1ull;
                     if (need && round <= 255) {
-                        uf_block(s, round == 1, warp_tot, tot, false);
+                        uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
                     } else if (threadIdx.x == 0) {
                         s.ctl[CTL_NCOMP] = 0;
                         if (need) b.ctl[r].err = 1;  // too many rounds
@@ -2018,6 +2076,43 @@ static int pool_commit(ecmc_ctx *ctx) {
     return 0;
 }
 
+// FP32 image of the stop rule thr(m) = ((m a) - fx) - d > RN(cur + eps):
+// thr_f = ((m af - fxf) - df) and lim_f = trunc(cur) + epsf, with af, df, epsf
+// the FP32 roundings, fxf = trunc(fx). Each of the four FP32 roundings and
+// the two truncations errs by at most 2^-23 of a term of magnitude at most
+// m a + a + d + cur + eps <= L + a + d + ell + eps (m < nc, |fx| <= a,
+// cur <= ell), so |(thr_f - lim_f) - (thr - lim)| < 2^-22 (L + a + d + ell +
+// eps) (the FP64 roundings are 2^29 times smaller). stop_e is 4 times that.
+static void set_stop_image(Dev &s) {
+    s.af = (float)s.a;
+    s.df = (float)s.d;
+    s.epsf = (float)s.eps;
+    s.stop_e = (float)std::ldexp(s.L + s.a + s.d + s.ell + s.eps + 1.0, -20);
+}
+
+// Exact tables of the cell map cell_coord(v) = min(nc - 1, trunc(RN(v inv_a))):
+// colx[c] = RN(c a) and xbound[c] = the least double v >= 0 with
+// cell_coord(v) >= c, found from c a by steps of one ulp (the map is
+// monotone). Host and device multiply alike (IEEE binary64, round to nearest).
+static void cell_tables(const Dev &s, std::vector<double> &colx,
+                        std::vector<unsigned long long> &xb) {
+    const int nc = s.nc;
+    colx.resize(nc);
+    xb.assign((size_t)nc + 1, 0ull);
+    auto at_least = [&](double v, int c) { return v * s.inv_a >= (double)c; };
+    for (int c = 0; c < nc; ++c) colx[c] = (double)c * s.a;
+    for (int c = 1; c < nc; ++c) {
+        double v = (double)c * s.a;
+        while (v > 0.0 && at_least(std::nextafter(v, 0.0), c)) v = std::nextafter(v, 0.0);
+        while (!at_least(v, c)) v = std::nextafter(v, INFINITY);
+        unsigned long long b;
+        memcpy(&b, &v, 8);
+        xb[c] = b;
+    }
+    const double inf = INFINITY;
+    memcpy(&xb[nc], &inf, 8);
+}
+
 static int pick_cells(const ecmc_params *p, int *nc_out, int *C_out) {
     const double d = p->d, L = p->box;
     int nc = p->cells_per_side;
@@ -2169,6 +2264,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     s.inv_a = (double)nc / p->box;
     s.far = s.L - 3.0 * s.a;
     s.eps = std::ldexp(p->box, -30);
+    set_stop_image(s);
     s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
     s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
     const size_t ncell = (size_t)nc * nc;
@@ -2185,6 +2281,10 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.cown, nslot));
     chk(dalloc(ctx, &s.cskp, nslot));
     chk(dalloc(ctx, &s.rband, 2 * (size_t)nc));
+    double *d_colx = nullptr;
+    unsigned long long *d_xbound = nullptr;
+    chk(dalloc(ctx, &d_colx, (size_t)nc));
+    chk(dalloc(ctx, &d_xbound, (size_t)nc + 1));
     chk(dalloc(ctx, &s.claim, ncell));
     chk(dalloc(ctx, &s.aloc0, k));
     chk(dalloc(ctx, &s.aloc, k));
@@ -2254,6 +2354,16 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
     CU(cudaMemsetAsync(s.dbg, 0, 16 * sizeof(double), st));
+    {
+        std::vector<double> colx;
+        std::vector<unsigned long long> xb;
+        cell_tables(s, colx, xb);
+        CU(cudaMemcpyAsync(d_colx, colx.data(), colx.size() * 8, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(d_xbound, xb.data(), xb.size() * 8, cudaMemcpyHostToDevice, st));
+        // (pageable sources: the copies are done when the calls return)
+        s.colx = d_colx;
+        s.xbound = d_xbound;
+    }
     // the inputs are checked on the device (loc_of holds the ids seen until
     // k_locate fills it); nothing below indexes by an active id before
     // k_init_chains, which does nothing if an id failed
@@ -2316,8 +2426,10 @@ static int runner_reserve(Runner &rn, int R, std::string &err) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, RUN_THREADS, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, RUN_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, RUN_THREADS, UF_SMEM_BYTES) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, RUN_THREADS, UF_SMEM_BYTES) !=
+            cudaSuccess ||
         !coop || b4 < 1 || b8 < 1) {
         (void)cudaGetLastError();
         runner_free(rn);
@@ -2417,9 +2529,11 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     void *args[] = {&b};
     cu(cudaEventRecord(rn.ev0, st), "event");
     if (C == 4)
-        cu(cudaLaunchCooperativeKernel((void *)k_run<4>, rn.grid4, RUN_THREADS, args, 0, st), "launch");
+        cu(cudaLaunchCooperativeKernel((void *)k_run<4>, rn.grid4, RUN_THREADS, args, UF_SMEM_BYTES,
+                                       st), "launch");
     else
-        cu(cudaLaunchCooperativeKernel((void *)k_run<8>, rn.grid8, RUN_THREADS, args, 0, st), "launch");
+        cu(cudaLaunchCooperativeKernel((void *)k_run<8>, rn.grid8, RUN_THREADS, args, UF_SMEM_BYTES,
+                                       st), "launch");
     cu(cudaEventRecord(rn.ev1, st), "event");
     int32_t g[G_N];
     unsigned long long ph[PH_N];
@@ -2932,6 +3046,7 @@ extern "C" int ecmc_leg_noalloc(int64_t n, double box, double d, double ell, int
     s.inv_a = (double)nc / box;
     s.far = s.L - 3.0 * s.a;
     s.eps = std::ldexp(box, -30);
+    set_stop_image(s);
     const size_t ncell = (size_t)nc * nc, nslot = ncell * C;
     uint32_t *loc_of = nullptr;
     // sizes beyond the fixed scratch array are rejected before any device work

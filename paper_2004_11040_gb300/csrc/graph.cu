@@ -1277,6 +1277,7 @@ constexpr int MAX_RESTARTS = 16;  // per leg, then the local repair takes over
 // met another chain. Phases are separated by grid barriers whose waits are
 // bounded (ECMC_ETIMEOUT).
 __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRun R) {
+    extern __shared__ int32_t uf_sm[];  // UF_SMEM_BYTES: the union-find working set
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
     __shared__ int sflag;
@@ -1381,7 +1382,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                         if (need) s.lc[LC_CWINDOWS] += 1ull;
                     }
                     if (need && round <= 255) {
-                        uf_block(s, round == 1, warp_tot, tot, false);
+                        uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
                     } else if (threadIdx.x == 0) {
                         s.ctl[CTL_NCOMP] = 0;
                         if (need) atomicAdd(s.lc + LC_ERR_CAP, 1ull);  // too many rounds
@@ -1742,7 +1743,8 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_run_graph, GRUN_THREADS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_run_graph, GRUN_THREADS,
+                                                          UF_SMEM_BYTES);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess || !coop || blocks < 1) {
         (void)cudaGetLastError();
@@ -1808,7 +1810,8 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     R.budget = (int64_t)budget;
     void *args[] = {&R};
     cu(cudaEventRecord(g->ev0, st), "event");
-    cu(cudaLaunchCooperativeKernel((void *)k_run_graph, g->grid, GRUN_THREADS, args, 0, st),
+    cu(cudaLaunchCooperativeKernel((void *)k_run_graph, g->grid, GRUN_THREADS, args, UF_SMEM_BYTES,
+                                   st),
        "launch");
     cu(cudaEventRecord(g->ev1, st), "event");
     int32_t gerr = 0;
