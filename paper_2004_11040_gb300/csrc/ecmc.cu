@@ -800,13 +800,32 @@ __global__ void k_band_init(Dev s) {
     s.rband[s.nc + q] = 0ull;
 }
 
+// A row is nc * C consecutive slots, so a warp's slots nearly always share
+// one: the warp reduces first and its lanes of each row issue one atomic pair.
 __global__ void k_bands(Dev s, int C) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)s.nc * s.nc * C || s.cid[q] == EMPTY) return;
-    const int R = (int)((q / C) / s.nc);
-    const unsigned long long b = dbits(s.cy[q]);  // y >= 0: bits order like values
-    atomicMin(s.rband + R, b);
-    atomicMax(s.rband + s.nc + R, b);
+    const int lane = threadIdx.x & 31;
+    const bool in = q < (int64_t)s.nc * s.nc * C;
+    const bool occ = in && s.cid[q] != EMPTY;
+    const int R = in ? (int)((q / C) / s.nc) : -1;
+    const unsigned long long y = occ ? dbits(s.cy[q]) : 0ull;  // y >= 0: bits order like values
+    unsigned long long lo = occ ? y : INF_BITS, hi = y;
+    const int R0 = __shfl_sync(FULL, R, 0);
+    if (__all_sync(FULL, R == R0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l2 = shfl_xor_u64(lo, o), h2 = shfl_xor_u64(hi, o);
+            lo = l2 < lo ? l2 : lo;
+            hi = h2 > hi ? h2 : hi;
+        }
+        if (lane == 0 && R0 >= 0 && lo != INF_BITS) {
+            atomicMin(s.rband + R0, lo);
+            atomicMax(s.rband + s.nc + R0, hi);
+        }
+    } else if (occ) {
+        atomicMin(s.rband + R, y);
+        atomicMax(s.rband + s.nc + R, y);
+    }
 }
 
 __global__ void k_skip(Dev s, int C) {
@@ -883,9 +902,24 @@ __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_
 __device__ void leg_begin_chain(const Dev &s, int c) {
     const int32_t nr = s.nrec[c];
     const Rec *q = s.rec + (size_t)c * s.cap;
-    for (int32_t e = 0; e < nr; ++e) {
-        s.ct[q[e].to] = 0.0;
-        if (q[e].j != NONE) s.ct[q[e].jloc] = 0.0;
+    // records read 8 at a time before their stores (a store between two loads
+    // could alias the next record and would serialise the round trips)
+    for (int32_t e0 = 0; e0 < nr; e0 += 8) {
+        uint32_t to[8], jl[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            to[u] = EMPTY;
+            jl[u] = EMPTY;
+            if (e0 + u < nr) {
+                to[u] = q[e0 + u].to;
+                if (q[e0 + u].j != NONE) jl[u] = q[e0 + u].jloc;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (to[u] != EMPTY) s.ct[to[u]] = 0.0;
+            if (jl[u] != EMPTY) s.ct[jl[u]] = 0.0;
+        }
     }
     const uint32_t loc = s.aloc[c];
     s.cown[loc] = OWN_ACTIVE | (uint32_t)c;
@@ -1617,9 +1651,11 @@ __global__ void k_repair(Dev s, int round) {
 }
 
 // Leg end: totals, and the lifting log (chain by chain).
-__device__ void leg_end_chain(const Dev &s, int c, int32_t leg) {
+// Returns the chain's liftings of the leg; count: add them to the leg total
+// here (else the caller adds a warp's sum at once).
+__device__ int32_t leg_end_chain(const Dev &s, int c, int32_t leg, bool count = true) {
     const int32_t nl = s.nlift[c];
-    atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
+    if (count) atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
     if (s.log_on && nl > 0) {
         const unsigned long long base = atomicAdd(s.tc_cnt + TC_LOG_N, (unsigned long long)nl);
         const Rec *q = s.rec + (size_t)c * s.cap;
@@ -1641,6 +1677,7 @@ __device__ void leg_end_chain(const Dev &s, int c, int32_t leg) {
             ++w;
         }
     }
+    return nl;
 }
 
 __global__ void k_leg_end(Dev s, int32_t leg) {
@@ -1930,12 +1967,27 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             }
             mark(PH_REPAIR);
         }
-        // leg end: liftings and the log, then per-replica totals and budgets
-        for (int w = gt; w < total_chains; w += nthreads) {
-            const int r = find_rep(b.chain_base, R, w);
-            if (rep_on(b, r))
-                leg_end_chain(b.reps[r], w - b.chain_base[r],
-                              (int32_t)(b.ctl[r].leg_index0 + b.ctl[r].legs));
+        // leg end: liftings and the log, then per-replica totals and budgets;
+        // a warp whose chains share a replica adds their liftings at once
+        for (int w0 = gt - lane; w0 < total_chains; w0 += nthreads) {
+            const int w = w0 + lane;
+            int r = -1;
+            int32_t nl = 0;
+            if (w < total_chains) {
+                r = find_rep(b.chain_base, R, w);
+                if (rep_on(b, r))
+                    nl = leg_end_chain(b.reps[r], w - b.chain_base[r],
+                                       (int32_t)(b.ctl[r].leg_index0 + b.ctl[r].legs), false);
+                else
+                    r = -1;
+            }
+            const int r0 = __shfl_sync(FULL, r, 0);
+            if (r0 >= 0 && __all_sync(FULL, r == r0 || r < 0)) {
+                const unsigned tot = __reduce_add_sync(FULL, (unsigned)nl);
+                if (lane == 0 && tot) atomicAdd(b.reps[r0].lc + LC_LIFTS, (unsigned long long)tot);
+            } else if (r >= 0 && nl) {
+                atomicAdd(b.reps[r].lc + LC_LIFTS, (unsigned long long)nl);
+            }
         }
         if (!grid_barrier(b, &sflag)) return;
         for (int r = gt; r < R; r += nthreads) {
