@@ -95,7 +95,9 @@ def windows_for(a, search):
         return a.windows_arg
     if search == "graph":
         return 1
-    return 1 if a.k <= 1024 else (2 if a.k <= 4096 else 4)
+    # measured (N = 2^20 lattices, W in 1, 2, 4): one window up to k = 4096,
+    # two at k = 16384
+    return 1 if a.k <= 4096 else 2
 
 
 def workload(a, search=None):
