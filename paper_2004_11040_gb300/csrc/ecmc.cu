@@ -12,8 +12,11 @@
 //   * Before a chain may use a cell it claims it for the leg with atomicCAS on
 //     a per-cell word (statement 10's CAS, lifted from disks to cells). Cells
 //     therefore change only under their claimer, and a chain that meets a cell
-//     claimed by another chain stops: the leg's conflict flag. The target disk
-//     is also claimed with atomicCAS on its per-disk owner word (statement 10).
+//     claimed by another chain stops: the leg's conflict flag. A cell whose
+//     row holds no disk within d in y of the active disk (y never changes
+//     along x) is claimed weakly and not read: it counts for the flag but
+//     blocks nobody. The target disk is also claimed with atomicCAS on its
+//     per-disk owner word (statement 10).
 //   * Without a conflict every chain followed exactly the path it would take
 //     alone, which equals the global-time result (Lemma 2). With a conflict
 //     the chains that met (connected components of the conflict graph) are
@@ -248,8 +251,9 @@ struct StepOut {
 // Statements 1-9 of Alg. 5 for one chain, with the cell scan: columns ahead
 // of the active disk are scanned until (m*a - fx) - d > min(D, best) + eps.
 // Every scanned cell is claimed for the leg (conflict if another owner holds
-// it). A column whose threshold is <= eps is scanned whatever the candidates,
-// so its cells are claimed together with their load.
+// it strongly; weakly, without a read, where the row is out of reach in y).
+// A column whose threshold is <= eps is scanned whatever the candidates, so
+// its cells are claimed together with their load.
 // In both modes the active and stalled disks of all chains are excluded
 // (Alg. 2), and a static disk with t_i + tau < t_j became static after the
 // chain's disk had passed it (lazy per-chain frame): it is one lap away.

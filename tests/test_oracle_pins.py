@@ -38,6 +38,29 @@ def test_lattice_start_geometry():
     assert len(set(s.active.tolist())) == 4
 
 
+@pytest.mark.parametrize("seed,row_shift,pair_shift", [(1, 0.05, 0.15), (5, 0.05, 0.15),
+                                                        (8, 0.2, 0.0), (9, 0.2, 0.0)])
+def test_staggered_start_geometry(seed, row_shift, pair_shift):
+    """The staggered starts of the GPU tests are hard-disk configurations (every
+    pair at least d apart, minimum image), with rows in close pairs (a gap
+    below d in y) and pairs far apart (a gap above d) where pair_shift > 0."""
+    s = synth.staggered_start(16, 0.5, 12, seed, row_shift=row_shift, pair_shift=pair_shift)
+    L = s.box
+    assert np.all((s.x >= 0) & (s.x < L) & (s.y >= 0) & (s.y < L))
+    dx = np.abs(s.x[:, None] - s.x[None, :])
+    dx = np.minimum(dx, L - dx)
+    dy = np.abs(s.y[:, None] - s.y[None, :])
+    dy = np.minimum(dy, L - dy)
+    d2 = dx * dx + dy * dy
+    np.fill_diagonal(d2, np.inf)
+    assert d2.min() >= 1.0
+    assert len(set(s.active.tolist())) == 12
+    if pair_shift > 0:
+        rows = np.sort(s.y.reshape(16, 16)[0])  # column 0 (id = c m + r): one disk per row
+        gaps = np.diff(np.concatenate([rows, rows[:1] + L]))
+        assert (gaps < 1.0).any() and (gaps > 1.1).any()
+
+
 # ------------------------------------------------------- closed forms
 
 
