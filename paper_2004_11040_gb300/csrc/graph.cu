@@ -172,22 +172,45 @@ __global__ void k_gb_cells(GBuild b) {
     atomicAdd(b.err, 1ull);
 }
 
-// Exclusive prefix of the y-bin counts (one block).
-__global__ void k_gb_scan(GBuild b) {
+// Exclusive prefix of the y-bin counts, in tiles of SCAN_TILE bins (one block
+// of 1024 threads, 4 consecutive bins per thread): k_gb_tile_sums adds each
+// tile, k_gb_scan_tiles scans each tile from the sum of the tiles before it;
+// the last tile also writes the total to bins[nb].
+constexpr int SCAN_TILE = 4096;
+
+__device__ __forceinline__ int tile_bin(const GBuild &b, int64_t q) {
+    return q < b.nb ? b.bins[q] : 0;
+}
+
+__global__ void k_gb_tile_sums(GBuild b, int32_t *part) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
-    const int nt = blockDim.x, tid = threadIdx.x;
-    const int chunk = (b.nb + nt - 1) / nt;
-    const int lo = min(b.nb, tid * chunk), hi = min(b.nb, lo + chunk);
-    int sum = 0;
-    for (int q = lo; q < hi; ++q) sum += b.bins[q];
-    int off = block_exscan(sum, warp_tot, tot);
-    for (int q = lo; q < hi; ++q) {
-        const int v = b.bins[q];
-        b.bins[q] = off;
-        off += v;
+    const int64_t q0 = (int64_t)blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    const int v = tile_bin(b, q0) + tile_bin(b, q0 + 1) + tile_bin(b, q0 + 2) + tile_bin(b, q0 + 3);
+    block_exscan(v, warp_tot, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+}
+
+__global__ void k_gb_scan_tiles(GBuild b, const int32_t *part) {
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    __shared__ int base;
+    if (threadIdx.x < 32) {  // sum of the tiles before this one
+        int acc = 0;
+        for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) acc += part[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (threadIdx.x == 0) base = acc;
     }
-    if (tid == 0) b.bins[b.nb] = tot[0];
+    const int64_t q0 = (int64_t)blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    const int v0 = tile_bin(b, q0), v1 = tile_bin(b, q0 + 1), v2 = tile_bin(b, q0 + 2),
+              v3 = tile_bin(b, q0 + 3);
+    const int off = block_exscan(v0 + v1 + v2 + v3, warp_tot, tot) + base;
+    const int o[4] = {off, off + v0, off + v0 + v1, off + v0 + v1 + v2};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (q0 + u < b.nb) b.bins[q0 + u] = o[u];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) b.bins[b.nb] = base + tot[0];
 }
 
 // Disks whose y falls in a bin that meets [lo, hi) (periodic, hi - lo < L):
@@ -1517,7 +1540,7 @@ struct GraphCtx {
     int64_t log_legs = 0;  // legs logged so far (leg index of the log)
     int grid = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    void *build_tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *build_tmp[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<std::pair<void **, size_t>> pending;
 };
 
@@ -1594,9 +1617,10 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
             cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
             cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
             cudaMalloc(&tmp[4], 8) != cudaSuccess ||
-            cudaMalloc(&tmp[5], nslot * 4) != cudaSuccess) {
+            cudaMalloc(&tmp[5], nslot * 4) != cudaSuccess ||
+            cudaMalloc(&tmp[6], (((size_t)b.nb + SCAN_TILE - 1) / SCAN_TILE) * 4) != cudaSuccess) {
             (void)cudaGetLastError();
-            for (int q = 0; q < 6; ++q) {
+            for (int q = 0; q < 7; ++q) {
                 cudaFree(tmp[q]);
                 tmp[q] = nullptr;
             }
@@ -1619,7 +1643,12 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
         k_gb_cells<4><<<nblk, 256, 0, st>>>(b);
     else
         k_gb_cells<8><<<nblk, 256, 0, st>>>(b);
-    k_gb_scan<<<1, 1024, 0, st>>>(b);
+    {
+        const unsigned tiles = (unsigned)((b.nb + SCAN_TILE - 1) / SCAN_TILE);
+        int32_t *part = (int32_t *)tmp[6];
+        k_gb_tile_sums<<<tiles, 1024, 0, st>>>(b, part);
+        k_gb_scan_tiles<<<tiles, 1024, 0, st>>>(b, part);
+    }
     const unsigned ablk = (unsigned)((s.n + 255) / 256);  // one thread per disk
     if (C == 4)
         k_gb_arrows<4><<<ablk, 256, 0, st>>>(b);
