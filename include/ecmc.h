@@ -123,8 +123,10 @@ int ecmc_create(const ecmc_params *p, const double *x, const double *y,
  * Conflicts. Within a claim window every chain claims, with atomicCAS, each
  * cell it scans; two chains that want one cell "meet". A leg's flag is 1 iff
  * in some window the cells that two chains would scan, each run alone from the
- * window's start, overlap; those chains are then rolled back and redone in
- * global time order, so results are always those of Alg. 2.
+ * window's start, overlap. A cell whose row holds no disk within d in y of the
+ * scanning chain's active disk is claimed weakly: it counts for the flag but
+ * stops no chain. Chains that met over a cell they read are rolled back and
+ * redone in global time order, so results are always those of Alg. 2.
  *
  * ecmc_run_to_breakpoint -- runs n_legs legs of length ell (Alg. 2 semantics:
  * each leg ends at the breakpoint h' with all chains stalled, Remark on
