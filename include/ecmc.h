@@ -198,7 +198,7 @@ int ecmc_graph_arrows(ecmc_ctx *ctx, int32_t *a, double *b);
 /*
  * ecmc_profile -- device time per phase of the persistent kernel, read from
  * the device clock at the phase boundaries of every ecmc_run_to_breakpoint:
- *   pass1   the parallel pass (one warp per chain, Alg. 5/6 statements 1-26);
+ *   pass1   the parallel pass (one warp per chain, each a task of Alg. 5/6);
  *   repair  component rollback and global-time redo (Alg. 2), with its
  *           union-find rounds;
  *   other   leg start (claims, chain table) and leg end (totals, log).

@@ -11,17 +11,17 @@
  *
  * What one leg does (Alg. 5, one task per chain, tasks spread over threads):
  *   - every disk's local time is reset to 0 and the start disk of each chain
- *     is tagged active (statements 1-3 at the breakpoint);
+ *     is tagged active (the lifted configuration at the breakpoint);
  *   - a chain repeats: scan the cells ahead of its active disk i (rows
  *     cy-1..cy+1, columns cx, cx+1, ... with the same stop rule as the
  *     oracle), time of flight tau_j = dx - sqrt(d^2 - dy^2) for static disks
- *     in the corridor (statement 4), horizon check t_i + tau_j < t_j (Eq. 2,
- *     statement 5: counted as a violation; the disk is then taken one lap
- *     away as in the oracle's lazy frame), argmin of (tau, j) (statements 6-9);
+ *     in the corridor (Sec. 2.2), horizon check t_i + tau_j < t_j (Eq. 2:
+ *     counted as a violation; the disk is then taken one lap away as in the
+ *     oracle's lazy frame), argmin of (tau, j);
  *     lift if tau* < D: compare-and-swap of j's tag from static to active
- *     (statement 10; a failed swap is a violation and the chain scans
- *     again), then t_j, t_i, x_i, D and i <- j (statements 11-19); otherwise
- *     stall (statements 21-24);
+ *     (a failed swap is a violation and the chain scans again), then t_j,
+ *     t_i, x_i, D and i <- j (the lifting of Eq. 1, local times before the
+ *     position as Remark 11 requires); otherwise move by D and stall;
  *   - tags are acquire/release (the paper's validation ordering, Sec. 4);
  *     positions and local times are relaxed atomics, cells are fixed-size
  *     slot arrays updated with compare-and-swap.
@@ -93,7 +93,7 @@ static void slot_remove(a5_cells *g, int cell, int32_t j) {
     }
 }
 
-/* One chain from its start disk through the leg (statements 1-24). */
+/* One chain from its start disk through the leg (Alg. 5, one task). */
 static void run_chain(const a5_params *p, a5_cells *g, double *x, const double *y, double *t,
                       int32_t *tag, int32_t c, int32_t *active, int64_t *lifts,
                       int64_t *violations) {

@@ -27,29 +27,31 @@
  *                   flag: the events executed are those of Alg. 2 whatever W.
  *   orc_alg4_leg -- Alg. 4 (single-threaded ECMC with local times): chains
  *                   run one after another on the shared state, the horizon
- *                   condition (Eq. 2, in the strict form of statement 5 of
- *                   Alg. 5) is checked for every candidate, and a chain that
+ *                   condition (Eq. 2, strict: t_i + tau_ij > t_j, as Alg. 5
+ *                   tests it) is checked for every candidate, and a chain that
  *                   would lift onto an active disk moves up to contact and
  *                   stops (Remark 10). Lemma 2: without a violation its output
  *                   equals that of orc_leg.
  *
  * Readings of the paper used here (each one a choice the paper leaves open):
- *   - Time of flight (Sec. 2.2, Eq. 2; statement 4 of Alg. 5; Eq. 3 in
- *     Sec. 3.1): tau_ij = dx - b_ij with b_ij = sqrt(d^2 - dy^2). The
- *     printed "+ b_ij" in the text after Eq. 2 contradicts statement 4 and
- *     Eq. 3; the minus sign is used.
+ *   - Time of flight (Sec. 2.2, Eq. 2; Alg. 5; Eq. 3 in Sec. 3.1):
+ *     tau_ij = dx - b_ij with b_ij = sqrt(d^2 - dy^2). The printed "+ b_ij"
+ *     in the text after Eq. 2 contradicts the time of flight that Alg. 5
+ *     computes and the contact inequality of Eq. 3; the minus sign is used.
  *   - Periodic box (Sec. 1 says contact "must be adapted"): dx is the forward
  *     image x_j - x_i (+L if negative); dy is the minimum image; j is a
  *     candidate iff dy < d (strict, Sec. 3.1 corridors); tau is clamped at 0
  *     (absorbs rounding left by an earlier contact); x is kept in [0, L).
  *   - Ties (Sec. 1 says liftings are generically at distinct times): the
  *     target is the argmin of (tau, j) over candidates; a lift happens iff
- *     tau* < D (statement 12), otherwise the chain stalls (statements 21-24).
+ *     tau* < D (the remaining chain length reaches the contact), otherwise
+ *     the chain moves by D and stalls at the breakpoint.
  *     Events with equal global time run in chain order.
  *   - Active and stalled disks of other chains are not candidates in Alg. 2
  *     (the minimum runs over i in A, j not in A).
  *   - Local times are leg-relative (h = 0): t_i and the remaining distance D
- *     are updated separately, t_j then t_i then x_i (statements 14-18).
+ *     are updated separately, t_j then t_i then x_i (Remark 11: the local
+ *     time is set before the position moves).
  *   - Cell scan (the paper gives none): cells of side a = L/nc (a > d),
  *     cell(v) = (int)(v * (nc/L)) clamped to nc-1; rows cy-1..cy+1; columns
  *     cx, cx+1, ... ; before column m >= 1 the scan stops if
@@ -408,8 +410,10 @@ static const int32_t *graph_arrows(const orc_params *p, graph_t *G, const double
 }
 
 /*
- * Statements 1-9 with the candidates taken from the arrows of i; every disk
- * read (i and each arrow target) is passed to claim().
+ * The next event of the chain whose active disk is i (time of flight to each
+ * candidate, Sec. 2.2, and the least (tau, j)), with the candidates taken
+ * from the arrows of i; every disk read (i and each arrow target) is passed
+ * to claim().
  */
 static step_t step_graph(const orc_params *p, graph_t *G, const double *x, const double *y,
                          const double *t, const int8_t *tag, int i, double D,
@@ -653,17 +657,21 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
             int nchanged = 0;
             changed[nchanged++] = cell_of(x_old, y[i], &g);
             if (s.lift) {
+                /* lifting i -> j (Eq. 1): i moves by tau to contact with j,
+                   both now carry the event's local time, activity passes to
+                   j and the chain has tau less to go. The local times are
+                   set before x moves (Remark 11). */
                 int j = s.j;
                 double tnew = t[i] + s.tau;
-                t[j] = tnew;                             /* statement 14 */
-                t[i] = tnew;                             /* statement 15 */
-                double xn = wrap_add(x[i], s.tau, p->L); /* statement 16 */
+                t[j] = tnew;
+                t[i] = tnew;
+                double xn = wrap_add(x[i], s.tau, p->L);
                 cell_move(&g, i, x[i], xn, y[i]);
                 x[i] = xn;
-                tag[i] = TAG_STATIC;                     /* statement 17 */
-                D[cb] = D[cb] - s.tau;                   /* statement 18 */
+                tag[i] = TAG_STATIC;
+                D[cb] = D[cb] - s.tau;
                 tag[j] = TAG_ACTIVE;
-                active[cb] = j;                          /* statement 19 */
+                active[cb] = j;
                 changed[nchanged++] = cell_of(xn, y[i], &g);
                 changed[nchanged++] = cell_of(x[j], y[j], &g);
                 if (log) {
@@ -684,12 +692,15 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
                 ++nl;
                 if (lifts_per_chain) lifts_per_chain[cb] += 1;
             } else {
-                t[i] = t[i] + D[cb];                     /* statement 21 */
-                double xn = wrap_add(x[i], D[cb], p->L); /* statement 22 */
+                /* no contact within the remaining length D: i moves by D and
+                   stalls with local time h' (Remark 1); it starts the
+                   chain's next leg */
+                t[i] = t[i] + D[cb];
+                double xn = wrap_add(x[i], D[cb], p->L);
                 cell_move(&g, i, x[i], xn, y[i]);
                 x[i] = xn;
-                D[cb] = 0.0;                             /* statement 23 */
-                tag[i] = TAG_STALLED;                    /* statement 24 */
+                D[cb] = 0.0;
+                tag[i] = TAG_STALLED;
                 run[cb] = 0;
                 changed[nchanged++] = cell_of(xn, y[i], &g);
             }

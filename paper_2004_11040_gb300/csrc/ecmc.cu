@@ -5,18 +5,18 @@
 // Design (one leg = one interval [h, h'] between breakpoints, v = (1, 0)):
 //   * Disks live in square cells of side a = L/nc > d, stored as per-slot
 //     structure-of-arrays (x, y, id); C slots per cell (C = 4 for a < sqrt(2) d).
-//   * One warp runs one chain (Alg. 5/6 statements 1-26): lanes cover
+//   * One warp runs one chain (one task of Alg. 5/6): lanes cover
 //     3 rows x C slots of one or two columns ahead of the active disk, compute
-//     the time of flight tau_j = dx_j - sqrt(d^2 - dy_j^2) in FP64 (Sec. 2.2,
-//     statement 4), and reduce (tau, j) with warp shuffles (statements 6-9).
+//     the time of flight tau_j = dx_j - sqrt(d^2 - dy_j^2) in FP64 (Sec. 2.2),
+//     and reduce (tau, j) with warp shuffles.
 //   * Before a chain may use a cell it claims it for the leg with atomicCAS on
-//     a per-cell word (statement 10's CAS, lifted from disks to cells). Cells
+//     a per-cell word (Alg. 5's compare-and-swap, lifted from disks to cells). Cells
 //     therefore change only under their claimer, and a chain that meets a cell
 //     claimed by another chain stops: the leg's conflict flag. A cell whose
 //     row holds no disk within d in y of the active disk (y never changes
 //     along x) is claimed weakly and not read: it counts for the flag but
 //     blocks nobody. The target disk is also claimed with atomicCAS on its
-//     per-disk owner word (statement 10).
+//     per-disk owner word (Alg. 5's compare-and-swap on the target's tag).
 //   * Without a conflict every chain followed exactly the path it would take
 //     alone, which equals the global-time result (Lemma 2). With a conflict
 //     the chains that met (connected components of the conflict graph) are
@@ -141,9 +141,10 @@ __device__ __forceinline__ uint32_t cell_of(double x, double y, const Dev &s) {
     return (uint32_t)cell_coord(y, s) * (uint32_t)s.nc + (uint32_t)cell_coord(x, s);
 }
 
-// v rounded toward zero to FP32 on the integer pipe (this chip's FP64 unit
-// costs ~64 cycles per warp instruction, conversions included): relative
-// error below 2^-23, and |v| < 2^-126 gives 0.
+// v rounded toward zero to FP32 on the integer pipe (a conversion on this
+// chip's FP64 pipe would occupy it ~18 cycles per warp instruction, with
+// ~100 cycles of dependent latency): relative error below 2^-23, and
+// |v| < 2^-126 gives 0.
 __device__ __forceinline__ float d2f_trunc(double v) {
     const unsigned long long b = dbits(v);
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -248,7 +249,8 @@ struct StepOut {
     unsigned long long emask;
 };
 
-// Statements 1-9 of Alg. 5 for one chain, with the cell scan: columns ahead
+// The next event of one chain (time of flight to every candidate and the
+// least (tau, j), Sec. 2.2), with the cell scan: columns ahead
 // of the active disk are scanned until (m*a - fx) - d > min(D, best) + eps.
 // Every scanned cell is claimed for the leg (conflict if another owner holds
 // it strongly; weakly, without a read, where the row is out of reach in y).
@@ -379,7 +381,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
                              << (mc * C);
             }
         }
-        // time of flight of i towards j (statement 4; Sec. 2.2: tau = x_j - x_i
+        // time of flight of i towards j (Sec. 2.2: tau = x_j - x_i
         // - b_ij with b_ij = sqrt(d^2 - dy^2)): forward image in x, minimum
         // image in y, corridor |dy| < d, +inf outside, clamped at 0
         const bool cst = cand && own == OWN_STATIC;
@@ -547,7 +549,7 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
             conflict = true;
             partner = holder - 1u;
         }
-        // Eq. 2 (statement 5) on every scanned candidate touched in this window:
+        // Eq. 2 on every scanned candidate touched in this window:
         // cannot fail while the cells are held by a lone chain; an assertion.
         if (MODE == MODE_PASS1 && scanned && behind && dbits(tj) >= dbits(tw)) hz = true;
         // another chain's active or stalled disk in a scanned corridor: its
@@ -627,8 +629,8 @@ __device__ StepOut scan_step(const Dev &s, int c, int root, const ChainReg &r, d
     return o;
 }
 
-// Moves the active disk (statements 16 / 22) with its local time and owner
-// word; returns its new slot or EMPTY on a full cell.
+// Moves the active disk (by tau to contact, or by D to the breakpoint) with
+// its local time and owner word; returns its new slot or EMPTY on a full cell.
 template <int C>
 __device__ uint32_t move_active(const Dev &s, const ChainReg &r, const StepOut &o, double xnew,
                                 double tnew, uint32_t own_new) {
@@ -667,7 +669,7 @@ __device__ uint32_t move_active(const Dev &s, const ChainReg &r, const StepOut &
     return newloc;
 }
 
-// Executes a step (lift: statements 10-19; stall: 21-24) and returns the
+// Executes a step (a lifting, Eq. 1, or a stall at the breakpoint) and returns the
 // chain's new status; *newloc receives the moved disk's slot. Writes are done
 // by lane 0; all lanes update the registers. In pass 1 the owner word of the
 // target is taken with atomicCAS whose result (*cas_old, lane 0) the caller
@@ -681,8 +683,9 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         return ST_BLOCKED;
     }
     if (o.lift) {
-        const double tnew = __dadd_rn(r.ti, o.tau);      // statements 14, 15
-        const double xnew = wrap_add(r.xi, o.tau, s);    // statement 16
+        // local times before the position (Remark 11)
+        const double tnew = __dadd_rn(r.ti, o.tau);      // new t_j = new t_i
+        const double xnew = wrap_add(r.xi, o.tau, s);    // i moves to contact
         if (lane == 0) {
             if (pass1)
                 *cas_old = atomicCAS(s.cown + o.jloc, OWN_STATIC, OWN_ACTIVE | (uint32_t)c);
@@ -690,7 +693,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
                 s.cown[o.jloc] = OWN_ACTIVE | (uint32_t)c;
             s.ct[o.jloc] = tnew;
         }
-        const uint32_t newloc = move_active<C>(s, r, o, xnew, tnew, OWN_STATIC);  // statement 17
+        const uint32_t newloc = move_active<C>(s, r, o, xnew, tnew, OWN_STATIC);  // i static
         if (newloc == EMPTY) {
             if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
             return ST_BLOCKED;
@@ -718,8 +721,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
             atomicAdd(s.nlift + c, 1);
         }
         *newloc_out = newloc;
-        r.D = __dsub_rn(r.D, o.tau);                     // statement 18
-        r.i = o.j;                                       // statement 19
+        r.D = __dsub_rn(r.D, o.tau);                     // remaining length
+        r.i = o.j;                                       // activity passes to j
         r.iloc = o.jloc;
         r.xi = o.xj;
         r.yi = o.yj;
@@ -729,8 +732,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         __syncwarp();
         return ST_RUNNING;
     }
-    const double tnew = __dadd_rn(r.ti, r.D);           // statement 21
-    const double xnew = wrap_add(r.xi, r.D, s);         // statement 22
+    const double tnew = __dadd_rn(r.ti, r.D);           // t_i reaches the breakpoint
+    const double xnew = wrap_add(r.xi, r.D, s);         // i moves by D
     const uint32_t newloc = move_active<C>(s, r, o, xnew, tnew, OWN_STALLED | (uint32_t)c);
     if (newloc == EMPTY) {
         if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
@@ -761,7 +764,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
     r.iloc = newloc;
     r.xi = xnew;
     r.ti = tnew;
-    r.D = 0.0;                                          // statement 23
+    r.D = 0.0;                                          // stalled
     __syncwarp();
     return ST_STALLED;
 }

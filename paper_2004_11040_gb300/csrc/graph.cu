@@ -423,7 +423,7 @@ __device__ __forceinline__ bool holder_ours(const GDev &s, int h, int root, uint
     return hc == root;
 }
 
-// Statements 1-9 of Alg. 5 for chain c along the arrows a[] (with b[]) of
+// The next event of chain c (Sec. 2.2) along the arrows a[] (with b[]) of
 // its active disk i at x_i, t_i, with remaining length D. Every disk read is
 // claimed for the window (atomicCAS of the disk's claim word from 0 to c + 1,
 // issued together with the loads; what was read is used only once the claims
@@ -456,7 +456,7 @@ __device__ GStep graph_step(const GDev &s, int c, int root, uint64_t tag, const 
     o.viol = 0;
     o.nonstatic = 0;
     o.ns_owner = NONE;
-    // time of flight to each static target (statement 4): forward image in x,
+    // time of flight to each static target (Sec. 2.2): forward image in x,
     // b_ij fixed with the arrow, clamped at 0
     unsigned long long bt = INF_BITS;
     int bq = -1;
@@ -517,8 +517,8 @@ __device__ GStep graph_step(const GDev &s, int c, int root, uint64_t tag, const 
     return o;
 }
 
-// Executes chain c's step from disk i (statements 10-19 for a lift, 21-24 for
-// a stall) and writes its record at index nr (the caller checked the
+// Executes chain c's step from disk i (a lifting, Eq. 1, or a stall at the
+// breakpoint) and writes its record at index nr (the caller checked the
 // capacity and counts records and liftings).
 __device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double ti, double D,
                             int lift, uint32_t j, double tau, double xj, double tj,
@@ -531,34 +531,34 @@ __device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double 
     u.ti_old = ti;
     GDisk &ri = s.g[i];
     if (lift) {
-        const double tnew = __dadd_rn(ti, tau);       // statements 14, 15
-        const double xnew = wrap_add(xi, tau, s.L);   // statement 16
+        const double tnew = __dadd_rn(ti, tau);       // new t_j = new t_i (before x, Remark 11)
+        const double xnew = wrap_add(xi, tau, s.L);   // i moves to contact
         GDisk &rj = s.g[j];
-        rj.own = OWN_ACTIVE | (uint32_t)c;             // statement 10 (the claim holds j)
+        rj.own = OWN_ACTIVE | (uint32_t)c;             // j active (the claim holds j)
         rj.t = tnew;
         ri.t = tnew;
         ri.x = xnew;
-        ri.own = OWN_STATIC;                           // statement 17
+        ri.own = OWN_STATIC;                           // i static
         u.j = j;
         u.tj_old = tj;
         u.t = tnew;
         u.tau = tau;
         u.xi = xnew;
         u.xj = xj;
-        u.d_after = __dsub_rn(D, tau);                 // statement 18
+        u.d_after = __dsub_rn(D, tau);                 // remaining length
     } else {
-        const double tnew = __dadd_rn(ti, D);         // statement 21
-        const double xnew = wrap_add(xi, D, s.L);     // statement 22
+        const double tnew = __dadd_rn(ti, D);         // t_i reaches the breakpoint
+        const double xnew = wrap_add(xi, D, s.L);     // i moves by D
         ri.x = xnew;
         ri.t = tnew;
-        ri.own = OWN_STALLED | (uint32_t)c;           // statement 24
+        ri.own = OWN_STALLED | (uint32_t)c;           // stalled
         u.j = NONE;
         u.tj_old = 0.0;
         u.t = tnew;
         u.tau = D;
         u.xi = xnew;
         u.xj = 0.0;
-        u.d_after = 0.0;                              // statement 23
+        u.d_after = 0.0;                              // no length left
     }
     s.rec[(size_t)c * s.cap + nr] = u;
 }
@@ -640,7 +640,7 @@ __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, doub
     for (int q = 0; q < 3; ++q)
         if (a[q] != NONE) r[q] = s.g[a[q]];
     for (;;) {
-        // statements 4-9 over the static targets (see graph_step)
+        // time of flight and (tau, j) minimum over the static targets (see graph_step)
         unsigned long long bt = INF_BITS;
         int bq = -1;
         uint32_t bjid = NONE, ns_owner = NONE;
@@ -699,7 +699,7 @@ __device__ __noinline__ void g_pass1_chain(const GDev &s, int c, double tw, doub
             blocked = true;
             break;
         }
-        // Eq. 2 (statement 5) on the disks of this window: cannot fail while
+        // Eq. 2 on the disks of this window: cannot fail while
         // they are held by a lone chain; an assertion
         if (hz) atomicAdd(s.lc + LC_HORIZON, 1ull);
         if (!go) break;  // pauses at the window end

@@ -1,16 +1,30 @@
-"""State-space exploration of the sequential-consistency model of Alg. 5.
+"""State-space exploration of a sequential-consistency model of Alg. 5.
 
-Each thread runs the statements of Alg. 5 (Sec. 2.3) one at a time; a switch
-may pick any thread at any step. Following the proof of Lemma 3, all states
-reachable from the initial state are enumerated; absorbing states are
-"terminate" (every thread waits at statement 26) and "abort" (a horizon
-violation, statement 5). The oracle is pinned by requiring every terminate
-state to equal its global-time result.
+Each thread (one chain) is a small program whose every step is ONE access
+to shared memory -- a read of a disk's x or local time, the compare-and-swap
+of a tag, or one write -- with the thread-local arithmetic attached to the
+access that feeds it. A switch may pick any thread at any step. Following the
+proof of Lemma 3, all states reachable from the initial state are
+enumerated; the absorbing states are "terminate" (every thread has stalled
+at the breakpoint) and "abort" (a thread saw the horizon condition, Eq. 2,
+fail). The oracle is pinned by requiring every terminate state to equal its
+global-time result.
 
-The statements are written from the pseudo-code's meaning, with the readings
-used throughout (tau = forward dx - b, minimum image in y, strict corridor,
-x wrapped into [0, L)). ``swap_15_16`` exchanges statements 15 and 16
-(Remark 11) for the mutation test.
+What a thread does, written from the method's meaning (Sec. 2.2-2.3) with
+the readings used throughout (tau = forward dx - b, minimum image in y,
+strict corridor, x wrapped into [0, L)):
+  scan      for every other disk q: read x_q (time of flight from the
+            thread's own disk i), read t_q (horizon condition t_i + tau > t_q
+            or abort; the least (tau, q) so far is kept, ties to the lower q);
+  claim     if the best tau is below the remaining length D: compare-and-swap
+            the target's tag from static to this chain (a failure restarts
+            the scan), re-read x_j and release the tag if j moved since the
+            scan (restart), else write t_j, t_i and x_i -- the local times
+            before the position (Remark 11) -- and free i's tag; activity
+            passes to j and D shrinks by tau;
+  stall     otherwise write t_i + D, x_i + D and tag i as stalled.
+``late_time`` writes x_i before t_i (the order Remark 11 warns against) for
+the mutation test.
 """
 from __future__ import annotations
 
@@ -19,6 +33,10 @@ from collections import deque
 
 INF = math.inf
 STATIC, STALLED = 0, -1
+
+# phases: the shared access a thread makes next
+READ_X, READ_T, CAS, VERIFY, RELEASE, SET_TJ, SET_A, SET_B, FREE_I, \
+    STALL_T, STALL_X, STALL_TAG, DONE = range(13)
 
 
 def time_of_flight(xi, yi, xj, yj, L, d):
@@ -44,92 +62,96 @@ def wrap_add(x, dx, L):
     return r
 
 
-# thread locals: (pc, i, j, tau_t, x_t, dist, p, nbr, x_nbr, tau_in)
-def explore(x, y, active, L, ell, d=1.0, swap_15_16=False, max_states=2_000_000):
+def _first(q, i, n):
+    """The first candidate index >= q other than the active disk i (n: none)."""
+    while q < n and q == i:
+        q += 1
+    return q
+
+
+# thread locals: (phase, i, D, q, tau_q, x_q, bj, btau, bx)
+def explore(x, y, active, L, ell, d=1.0, late_time=False, max_states=2_000_000):
     """Returns (terminal_states, n_states, aborted, all_reach_absorbing)."""
     n = len(x)
     k = len(active)
     tag0 = [STATIC] * n
     for c, a in enumerate(active):
         tag0[a] = c + 1
-    th0 = tuple((1, int(a), int(a), ell, INF, ell, 0, -1, 0.0, 0.0) for a in active)
+
+    def scan_start(i, D):
+        q = _first(0, i, n)
+        ph = READ_X if q < n else None
+        return (ph, i, D, q, INF, 0.0, i, D, INF)
+
+    def after_scan(th):
+        ph, i, D, q, tq, xq, bj, btau, bx = th
+        if btau < D:
+            return (CAS, i, D, q, tq, xq, bj, btau, bx)
+        return (STALL_T, i, D, q, tq, xq, bj, btau, bx)
+
+    def start(i, D):
+        th = scan_start(i, D)
+        return th if th[0] is not None else after_scan(th)
+
+    th0 = tuple(start(int(a), ell) for a in active)
     s0 = (tuple(float(v) for v in x), (0.0,) * n, tuple(tag0), th0)
     ABORT = ("abort",)
-
-    order15 = (16, 15) if swap_15_16 else (15, 16)
+    first_write, second_write = (SET_B, SET_A) if late_time else (SET_A, SET_B)
 
     def step(state, c):
         xs, ts, tags, ths = state
-        pc, i, j, tau_t, x_t, dist, p, nbr, x_nbr, tau_in = ths[c]
+        ph, i, D, q, tq, xq, bj, btau, bx = ths[c]
+        if ph == DONE:
+            return None
         xs, ts, tags = list(xs), list(ts), list(tags)
         me = c + 1
-        if pc == 26:
-            return None
-        if pc == 1:
-            tau_t, j, x_t, p, pc = dist, i, INF, 0, 2
-        elif pc == 2:
-            q = p
-            while q < n and q == i:
-                q += 1
-            if q < n:
-                nbr, p, pc = q, q + 1, 3
-            else:
-                pc = 10
-        elif pc == 3:
-            x_nbr, pc = xs[nbr], 4
-        elif pc == 4:
-            tau_in, pc = time_of_flight(xs[i], y[i], x_nbr, y[nbr], L, d), 5
-        elif pc == 5:
-            if ts[i] + tau_in < ts[nbr]:
+        if ph == READ_X:
+            xq = xs[q]
+            th = (READ_T, i, D, q, time_of_flight(xs[i], y[i], xq, y[q], L, d), xq, bj, btau, bx)
+        elif ph == READ_T:
+            if ts[i] + tq < ts[q]:
                 return ABORT
-            pc = 6
-        elif pc == 6:
-            pc = 7 if tau_in < tau_t else 2
-        elif pc == 7:
-            j, pc = nbr, 8
-        elif pc == 8:
-            x_t, pc = x_nbr, 9
-        elif pc == 9:
-            tau_t, pc = tau_in, 2
-        elif pc == 10:
-            if tags[j] == STATIC:
-                tags[j] = me
-            pc = 11
-        elif pc == 11:
-            pc = 12 if tags[j] == me else 1
-        elif pc == 12:
-            pc = 13 if tau_t < dist else 21
-        elif pc == 13:
-            pc = 14 if x_t == xs[j] else 20
-        elif pc == 14:
-            ts[j] = ts[i] + tau_t
-            pc = order15[0]
-        elif pc in (15, 16):
-            if pc == 15:
-                ts[i] = ts[i] + tau_t
+            if tq < btau:
+                bj, btau, bx = q, tq, xq
+            q = _first(q + 1, i, n)
+            th = (READ_X, i, D, q, INF, 0.0, bj, btau, bx)
+            if q >= n:
+                th = after_scan(th)
+        elif ph == CAS:
+            if tags[bj] == STATIC:
+                tags[bj] = me
+                th = (VERIFY, i, D, q, tq, xq, bj, btau, bx)
             else:
-                xs[i] = wrap_add(xs[i], tau_t, L)
-            pc = order15[1] if pc == order15[0] else 17
-        elif pc == 17:
-            tags[i], pc = STATIC, 18
-        elif pc == 18:
-            dist, pc = dist - tau_t, 19
-        elif pc == 19:
-            i, pc = j, 25
-        elif pc == 20:
-            tags[j], pc = STATIC, 1
-        elif pc == 21:
-            ts[i], pc = ts[i] + tau_t, 22
-        elif pc == 22:
-            xs[i], pc = wrap_add(xs[i], tau_t, L), 23
-        elif pc == 23:
-            dist, pc = 0.0, 24
-        elif pc == 24:
-            tags[i], pc = STALLED, 25
-        elif pc == 25:
-            pc = 1 if dist > 0.0 else 26
+                th = start(i, D)
+        elif ph == VERIFY:
+            th = (SET_TJ if xs[bj] == bx else RELEASE, i, D, q, tq, xq, bj, btau, bx)
+        elif ph == RELEASE:
+            tags[bj] = STATIC
+            th = start(i, D)
+        elif ph == SET_TJ:
+            ts[bj] = ts[i] + btau
+            th = (first_write, i, D, q, tq, xq, bj, btau, bx)
+        elif ph in (SET_A, SET_B):
+            if ph == SET_A:
+                ts[i] = ts[i] + btau
+            else:
+                xs[i] = wrap_add(xs[i], btau, L)
+            nxt = second_write if ph == first_write else FREE_I
+            th = (nxt, i, D, q, tq, xq, bj, btau, bx)
+        elif ph == FREE_I:
+            tags[i] = STATIC
+            th = start(bj, D - btau)
+        elif ph == STALL_T:
+            ts[i] = ts[i] + D
+            th = (STALL_X, i, D, q, tq, xq, bj, btau, bx)
+        elif ph == STALL_X:
+            xs[i] = wrap_add(xs[i], D, L)
+            th = (STALL_TAG, i, D, q, tq, xq, bj, btau, bx)
+        else:  # STALL_TAG
+            tags[i] = STALLED
+            th = (DONE, i, 0.0, 0, INF, 0.0, i, 0.0, INF)
         nth = list(ths)
-        nth[c] = (pc, i, j, tau_t, x_t, dist, p, nbr, x_nbr, tau_in)
+        nth[c] = th
         return (tuple(xs), tuple(ts), tuple(tags), tuple(nth))
 
     index = {s0: 0}
@@ -157,7 +179,7 @@ def explore(x, y, active, L, ell, d=1.0, swap_15_16=False, max_states=2_000_000)
                         raise RuntimeError("state space too large")
                 out.append(index[v])
         succ.append(out)
-    terminals = [s for s in states if s != ABORT and all(t[0] == 26 for t in s[3])]
+    terminals = [s for s in states if s != ABORT and all(t[0] == DONE for t in s[3])]
     absorbing = {index[s] for s in terminals}
     if ABORT in index:
         abort_id = index[ABORT]

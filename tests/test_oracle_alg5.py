@@ -1,12 +1,12 @@
 """Exhaustive interleavings of Alg. 5 (sequential-consistency model) pin the oracle.
 
 Lemma 3's method: every state reachable by any interleaving of two threads'
-statements is enumerated; every "terminate" state must equal the global-time
+shared-memory accesses is enumerated; every "terminate" state must equal the global-time
 result (Alg. 2, the oracle). The paper's own test suites (SequentialC4/C5)
 are not available, so seeded random 4- and 5-disk configurations in a box of
-side 4 stand in for them. The mutation test exchanges statements 15 and 16
-(Remark 11) and must produce a terminate state that the correct program
-never reaches.
+side 4 stand in for them. The mutation test writes a lifted disk's position
+before its local time (the order Remark 11 warns against) and must produce a
+terminate state that the correct program never reaches.
 """
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ def test_every_terminate_state_equals_global_time(n, seeds):
         x, y, a, ell = tiny(seed, n=n)
         g = O.run_leg(x, y, a, L_BOX, ell, search=0)
         terms, n_states, aborted, _ = explore(x, y, a, L_BOX, ell)
-        assert n_states > 100
+        assert n_states > 50  # a non-trivial enumeration
         for s in terms:
             assert _matches(s, g), seed
             # final active disks: thread c holds chain c's stalled disk
@@ -70,13 +70,13 @@ def test_absorbing_when_no_necklace():
     assert good >= 14
 
 
-def test_swapping_statements_15_16_creates_spurious_state():
+def test_position_before_local_time_creates_spurious_state():
     """Remark 11: with t_i and x_i updated in the other order a thread can read
     the moved position with the old local time; some interleaving then ends in
     a terminate state that the correct program never reaches."""
     x, y, a, ell = tiny(11)
     g = O.run_leg(x, y, a, L_BOX, ell, search=0)
     terms, _, _, _ = explore(x, y, a, L_BOX, ell)
-    mterms, _, _, _ = explore(x, y, a, L_BOX, ell, swap_15_16=True)
+    mterms, _, _, _ = explore(x, y, a, L_BOX, ell, late_time=True)
     assert all(_matches(s, g) for s in terms)
     assert any(not _matches(s, g) for s in mterms)

@@ -105,7 +105,7 @@ def test_single_row_closed_form():
 
 
 def test_contact_distance_345():
-    """Sec. 2.2, statement 4 of Alg. 5, Eq. 3: tau = dx - sqrt(d^2 - dy^2).
+    """Sec. 2.2 (time of flight as Alg. 5 computes it), Eq. 3: tau = dx - sqrt(d^2 - dy^2).
     dy = 0.6 gives b = 0.8 (a 3-4-5 triangle)."""
     L = 8.0
     x = np.array([1.0, 2.6, 6.0])
@@ -144,7 +144,7 @@ def test_periodic_wrap_x_and_y():
 
 
 def test_stall_without_candidates():
-    """Statements 21-24: no candidate below D -> move by D and stall."""
+    """No candidate below D -> move by D and stall (Alg. 2 at the breakpoint)."""
     L = 9.0
     x = np.array([1.0, 4.0, 7.0])
     y = np.array([1.0, 4.0, 7.0])
