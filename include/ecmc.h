@@ -46,6 +46,9 @@ extern "C" {
                                   instead of the cell scan; see "Constraint-graph mode" */
 #define ECMC_RESTART 0x8u      /* with ECMC_GRAPH and windows <= 1: conflicts handled by
                                   restart strategy 2 (Sec. 3.4); see "Restart mode" */
+#define ECMC_NO_ROWPASS 0x10u  /* cell scan: always use the general parallel pass, also in
+                                  windows where the row pass applies (see "Row pass");
+                                  results are the same either way */
 
 typedef struct ecmc_ctx ecmc_ctx;
 
@@ -57,7 +60,8 @@ typedef struct {
     int32_t n_chains;       /* k, 1 <= k <= n */
     int32_t cells_per_side; /* nc; 0 picks the largest nc with L/nc >= d*(1+2^-20).
                                Needs nc >= 3 and L/nc < 1.664*d. */
-    uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE | ECMC_GRAPH */
+    uint32_t flags;         /* ECMC_LOG_LIFTINGS | ECMC_INPUT_DEVICE | ECMC_GRAPH |
+                               ECMC_RESTART | ECMC_NO_ROWPASS */
     int32_t undo_cap;       /* per-chain event records per leg, < 2^24; 0 = 1024 */
     int64_t log_cap;        /* liftings kept with ECMC_LOG_LIFTINGS; 0 = 1<<22 */
     int32_t windows;        /* claim windows per leg, 1..4096; 0 = 1. A leg is run as W
@@ -79,6 +83,8 @@ typedef struct {
                                  the blocked chains (Lemma 2), nothing redone */
     int64_t restarts;         /* ECMC_RESTART: passes begun again at an earlier stop time
                                  T* taken as a breakpoint (Sec. 3.4, strategy 2) */
+    int64_t row_windows;      /* claim windows whose parallel pass was the row pass */
+    int64_t device_bytes;     /* device memory the context holds (its pooled state) */
 } ecmc_stats_t;
 
 /* One lifting i -> j (Eq. 1): chain c, leg index, time t (= new t_j),

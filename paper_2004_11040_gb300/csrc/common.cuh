@@ -32,6 +32,7 @@ constexpr int ST_RUNNING = 0, ST_STALLED = 1, ST_BLOCKED = 2;
 enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, LC_OWNER_FAIL,
        LC_CONTINUED,
        LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_RESTARTS, LC_WEAK,
+       LC_ROWWIN,  // claim windows run by the row pass (cell scan)
        LC_BADXY, LC_BADID,  // inputs out of range (creation only)
        LC_N };
 enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };

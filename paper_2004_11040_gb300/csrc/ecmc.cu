@@ -112,6 +112,16 @@ struct Dev {
     int64_t log_cap;
     int log_on;
     double *dbg;  // [16] first failed internal check (diagnostics)
+    // row pass (rowpass.cuh): claim keys, least and largest claiming chain per
+    // cell; per-system counters by window parity; the end of each chain's
+    // speculative run
+    int rp_ok;                   // the context may use the row pass
+    unsigned long long *ckey;    // [ncell], ~0 when unclaimed
+    uint32_t *camin, *camax;     // [ncell], chain + 1; ~0 and 0 when unclaimed
+    int32_t *rp;                 // [RP_N]: chains not eligible (by window parity), cancels
+    int32_t *rp_n, *rp_front, *rp_end, *rp_partner;
+    uint32_t *rp_aloc, *rp_ci;
+    double *rp_tc, *rp_D;
 };
 
 // ------------------------------------------------------------ FP64 geometry
@@ -155,22 +165,52 @@ __device__ __forceinline__ float d2f_trunc(double v) {
         (int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFull)));
 }
 
+// The stop rule in FP64 as defined (a call of its own, so that the compiler
+// never evaluates its five FP64 instructions -- ~64 cycles of the FP64 unit
+// each on this GPU -- on the path where the FP32 image decides).
+__device__ __noinline__ bool beyond_exact(double a, double d, double eps, int m, double fx,
+                                          unsigned long long cur) {
+    const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, a), fx), d);
+    const double lim = __dadd_rn(__longlong_as_double((long long)cur), eps);
+    return !dneg(thr) && dbits(thr) > dbits(lim);
+}
+
+// The constants of the stop rule, held in registers by the callers' loops.
+struct StopK {
+    float af, df, epsf, stop_e;
+    double a, d, eps;
+};
+
+__device__ __forceinline__ StopK stopk_of(const Dev &s) {
+    StopK k;
+    k.af = s.af;
+    k.df = s.df;
+    k.epsf = s.epsf;
+    k.stop_e = s.stop_e;
+    k.a = s.a;
+    k.d = s.d;
+    k.eps = s.eps;
+    return k;
+}
+
 // The scan's stop rule: is thr(m) = ((m a) - fx) - d above RN(cur + eps)?
 // Decided on the FP32 image thr_f - lim_f when that lies farther than stop_e
 // from 0 (its error bound is stop_e / 4, so the answer is the exact one),
 // else in FP64 as defined. lim_f = trunc(cur) + eps in FP32.
+__device__ __forceinline__ bool beyond_k(const StopK &k, int m, double fx, float fxf, float lim_f,
+                                         unsigned long long cur) {
+    if (k.stop_e > 0.f) {
+        const float thr_f = __fsub_rn(__fsub_rn(__fmul_rn(__int2float_rn(m), k.af), fxf), k.df);
+        const float diff = __fsub_rn(thr_f, lim_f);
+        if (diff > k.stop_e) return true;
+        if (diff < -k.stop_e) return false;
+    }
+    return beyond_exact(k.a, k.d, k.eps, m, fx, cur);
+}
+
 __device__ __forceinline__ bool beyond(const Dev &s, int m, double fx, float fxf, float lim_f,
                                        unsigned long long cur) {
-    if (s.stop_e > 0.f) {
-        const float thr_f =
-            __fsub_rn(__fsub_rn(__fmul_rn(__int2float_rn(m), s.af), fxf), s.df);
-        const float diff = __fsub_rn(thr_f, lim_f);
-        if (diff > s.stop_e) return true;
-        if (diff < -s.stop_e) return false;
-    }
-    const double thr = __dsub_rn(__dsub_rn(__dmul_rn((double)m, s.a), fx), s.d);
-    const double lim = __dadd_rn(__longlong_as_double((long long)cur), s.eps);
-    return !dneg(thr) && dbits(thr) > dbits(lim);
+    return beyond_k(stopk_of(s), m, fx, fxf, lim_f, cur);
 }
 
 // thr(m) <= eps, where a column is scanned (and its cells claimed) whatever
@@ -769,6 +809,8 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
     return ST_STALLED;
 }
 
+#include "rowpass.cuh"
+
 // ---------------------------------------------------------------- kernels
 
 // Cells from positions (slot order is irrelevant to every result).
@@ -792,8 +834,8 @@ __global__ void k_build_cells(Dev s, const double *x, const double *y) {
 
 // Least and largest y of each cell row, then the rows a disk's scan need not
 // read (Dev::cskp). Take a disk in row R with 1 <= R <= nc - 2 and nc >= 5, so
-// that rows R - 1 and R + 1 do not wrap and the scan takes |dy| without the
-// periodic image.
+// that rows R - 1 and R + 1 do not wrap and the scan's |dy| is the plain
+// difference (its periodic image is farther); the edge rows follow k_skip.
 // - It skips row R + 1 when RN(ylo(R + 1) - y) >= d. Every disk j there has
 //   y_j >= ylo, so the scan's |RN(y_j - y)| = RN(y_j - y) >= RN(ylo - y) >= d
 //   (rounding is monotone), and j lies in no corridor.
@@ -835,19 +877,38 @@ __global__ void k_bands(Dev s, int C) {
     }
 }
 
+// In the edge rows (R = 0 below, R = nc - 1 above) the neighbour row lies
+// across the box edge, and the scan takes the periodic image: for j in row
+// nc - 1 seen from row 0 its |dy| is RN(L - RN(y_j - y)), which only grows as
+// y_j falls, so RN(L - RN(yhi(nc - 1) - y)) >= d bounds the whole row; from row
+// nc - 1 towards row 0 it is RN(L - RN(y - y_j)), bounded by RN(L - RN(y -
+// ylo(0))). (The plain difference there is close to L, far above d.)
 __global__ void k_skip(Dev s, int C) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = s.nc;
     if (q >= (int64_t)nc * nc * C) return;
     const int R = (int)((q / C) / nc);
     uint8_t v = 0;
-    if (s.cid[q] != EMPTY && nc >= 5 && R >= 1 && R <= nc - 2) {
+    if (s.cid[q] != EMPTY && nc >= 5) {
         const double y = s.cy[q];
-        const unsigned long long lo_dn = s.rband[R - 1], lo_up = s.rband[R + 1];
-        const double hi_dn = __longlong_as_double((long long)s.rband[nc + R - 1]);
+        const int Rdn = R == 0 ? nc - 1 : R - 1, Rup = R == nc - 1 ? 0 : R + 1;
+        const unsigned long long lo_dn = s.rband[Rdn], lo_up = s.rband[Rup];
+        const double hi_dn = __longlong_as_double((long long)s.rband[nc + Rdn]);
         const double lo = __longlong_as_double((long long)lo_up);
-        if (lo_dn == INF_BITS || !(__dsub_rn(y, hi_dn) < s.d)) v |= 1;
-        if (lo_up == INF_BITS || !(__dsub_rn(lo, y) < s.d)) v |= 2;
+        if (lo_dn == INF_BITS) {
+            v |= 1;
+        } else if (R == 0) {
+            if (!(__dsub_rn(s.L, __dsub_rn(hi_dn, y)) < s.d)) v |= 1;
+        } else if (!(__dsub_rn(y, hi_dn) < s.d)) {
+            v |= 1;
+        }
+        if (lo_up == INF_BITS) {
+            v |= 2;
+        } else if (R == nc - 1) {
+            if (!(__dsub_rn(s.L, __dsub_rn(y, lo)) < s.d)) v |= 2;
+        } else if (!(__dsub_rn(lo, y) < s.d)) {
+            v |= 2;
+        }
     }
     s.cskp[q] = v;
 }
@@ -1772,6 +1833,7 @@ struct RepCtl {
     int64_t order_err;
     int64_t leg_index0;     // leg index of this run's first leg (lifting log)
     int64_t p1_lifts;       // liftings made by the parallel pass (redone ones included)
+    int64_t row_windows;    // claim windows run by the row pass
     int64_t repair_lifts;   // liftings of legs that needed a repair
     uint8_t *flags;         // per-leg conflict flags (device) or null
     int32_t flags_cap;
@@ -1847,6 +1909,24 @@ __device__ void check_chains(const Batch &b, int gt, int nthreads, int total_cha
     }
 }
 
+// The system description of the chain (or component) a warp works on, in the
+// warp's slot of shared memory: Dev stays constant during a launch, and a
+// field read from shared memory costs a few tens of cycles where a read of
+// the global copy, which the compiler repeats after every global store, goes
+// to L2. rep holds the system whose copy the slot has (-1: none).
+__device__ __forceinline__ const Dev &warp_dev(Dev *slot, int *rep, const Dev *reps, int r) {
+    if (*(volatile int *)rep != r) {
+        constexpr int WORDS = (int)(sizeof(Dev) / sizeof(uint32_t));
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(reps + r);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(slot);
+        for (int q = threadIdx.x & 31; q < WORDS; q += 32) dst[q] = src[q];
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) *(volatile int *)rep = r;
+        __syncwarp();
+    }
+    return *slot;
+}
+
 // Block shape of the persistent kernel: 8 warps per block, 2 blocks per SM
 // (16 warps per SM, 128 registers). Fewer, larger register files (3 blocks of
 // 4 warps, no spills) measured slower: the passes want warps more than
@@ -1860,6 +1940,12 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
     __shared__ int sflag;
+    __shared__ Dev wdev[RUN_THREADS / 32];  // per warp: its system's description
+    __shared__ int wrep[RUN_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wrep[threadIdx.x >> 5] = -1;
+    __syncthreads();
+    Dev *const my_dev = wdev + (threadIdx.x >> 5);
+    int *const my_rep = wrep + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
@@ -1876,43 +1962,110 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
         }
     };
     for (int leg = 0; leg < b.max_legs; ++leg) {
-        // leg start: chain table, local times, claims, per-leg counters
+        // leg start: chain table, local times, claims, per-leg counters; the
+        // chains whose rows are in reach (they rule out the row pass)
         for (int w = gt; w < total_chains; w += nthreads) {
             const int r = find_rep(b.chain_base, R, w);
-            if (rep_on(b, r)) leg_begin_chain(b.reps[r], w - b.chain_base[r]);
+            if (rep_on(b, r)) {
+                const Dev &s = b.reps[r];
+                const int c = w - b.chain_base[r];
+                leg_begin_chain(s, c);
+                if (s.rp_ok && skip_of(s, s.aloc[c]) != RP_SKIP_ALL) atomicAdd(s.rp + RP_BAD, 1);
+            }
         }
         for (int r = 0; r < R; ++r) {
             if (!rep_on(b, r)) continue;
             const Dev &s = b.reps[r];
             const int64_t ncell = (int64_t)s.nc * s.nc;
             for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
+            if (s.rp_ok)
+                for (int64_t q = gt; q < ncell; q += nthreads) {
+                    s.ckey[q] = ~0ull;
+                    s.camin[q] = ~0u;
+                    s.camax[q] = 0u;
+                }
             if (gt < LC_N) s.lc[gt] = 0ull;
+            if (gt == 0) {
+                s.rp[RP_BAD + 1] = 0;
+                s.rp[RP_ABORT + 1] = 0;
+            }
         }
         if (!grid_barrier(b, &sflag)) return;
         mark(PH_BEGIN);
         if (gt == 0) b.g[G_REMAIN0 + ((leg + 1) & 1)] = 0;
         for (int w = 0; w < b.windows; ++w) {
+            const int par = w & 1;
             if (w > 0) {
-                // new claim window: claims and the window's blocked count
+                // new claim window: claims, the window's blocked count, the
+                // chains whose rows are in reach; the other parity's row-pass
+                // counters (read in the last window) are cleared
                 for (int r = 0; r < R; ++r) {
                     if (!rep_on(b, r)) continue;
                     const Dev &s = b.reps[r];
                     const int64_t ncell = (int64_t)s.nc * s.nc;
                     for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
-                    if (gt == 0) s.lc[LC_WBLOCKED] = 0ull;
+                    if (s.rp_ok)
+                        for (int64_t q = gt; q < ncell; q += nthreads) {
+                            s.ckey[q] = ~0ull;
+                            s.camin[q] = ~0u;
+                            s.camax[q] = 0u;
+                        }
+                    if (gt == 0) {
+                        s.lc[LC_WBLOCKED] = 0ull;
+                        s.rp[RP_BAD + (par ^ 1)] = 0;
+                        s.rp[RP_ABORT + (par ^ 1)] = 0;
+                    }
+                }
+                for (int w2 = gt; w2 < total_chains; w2 += nthreads) {
+                    const int r = find_rep(b.chain_base, R, w2);
+                    if (!rep_on(b, r)) continue;
+                    const Dev &s = b.reps[r];
+                    const int c = w2 - b.chain_base[r];
+                    if (s.rp_ok && s.status[c] == ST_RUNNING &&
+                        skip_of(s, s.aloc[c]) != RP_SKIP_ALL)
+                        atomicAdd(s.rp + RP_BAD + par, 1);
                 }
                 if (!grid_barrier(b, &sflag)) return;
             }
-            // parallel pass: one warp per chain, chains spread over the blocks
+            // parallel pass: one warp per chain, chains spread over the
+            // blocks; the row pass where every running chain of the system
+            // moves along a row out of reach of its neighbours
             const int lw = threadIdx.x >> 5;
             for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
                 const int r = find_rep(b.chain_base, R, w2);
                 if (!rep_on(b, r)) continue;
-                const Dev &s = b.reps[r];
+                const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
                 const double tw = window_start(s, w), te = window_end(s, w);
-                pass1_chain<C>(s, w2 - b.chain_base[r], tw, te);
+                const int c = w2 - b.chain_base[r];
+                if (s.rp_ok && s.rp[RP_BAD + par] == 0) {
+                    if (!row_pass_chain<C>(s, c, tw, te) && lane == 0)
+                        atomicExch(s.rp + RP_ABORT + par, 1);
+                } else {
+                    pass1_chain<C>(s, c, tw, te);
+                }
             }
             if (!grid_barrier(b, &sflag)) return;
+            // row pass: the cells another chain holds, publication, claim
+            // words; a cancelled one runs pass1_chain now
+            int row_here = 0;
+            for (int r = threadIdx.x; r < R; r += blockDim.x)
+                if (rep_on(b, r) && b.reps[r].rp_ok && b.reps[r].rp[RP_BAD + par] == 0)
+                    row_here = 1;
+            if (__syncthreads_or(row_here)) {
+                for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
+                    const int r = find_rep(b.chain_base, R, w2);
+                    if (!rep_on(b, r)) continue;
+                    const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
+                    if (!(s.rp_ok && s.rp[RP_BAD + par] == 0)) continue;
+                    const double tw = window_start(s, w), te = window_end(s, w);
+                    const int c = w2 - b.chain_base[r];
+                    if (__ldcg(s.rp + RP_ABORT + par) != 0)
+                        pass1_chain<C>(s, c, tw, te);
+                    else
+                        row_resolve_chain<C>(s, c, tw);
+                }
+                if (!grid_barrier(b, &sflag)) return;
+            }
             mark(PH_PASS1);
             check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 1);
             // repair rounds
@@ -1960,7 +2113,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                     q = __shfl_sync(FULL, q, 0);
                     if (q >= ncomp) break;
                     const int r = find_rep(b.comp_base, R, q);
-                    const Dev &s = b.reps[r];
+                    const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
                     repair_component<C>(s, q - b.comp_base[r], round, window_start(s, w),
                                         window_end(s, w));
                 }
@@ -2011,10 +2164,15 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             c.conflict_legs += flag;
             c.repaired += (int64_t)lc[LC_REPAIRED];
             c.continued += (int64_t)lc[LC_CONTINUED];
+            c.row_windows += (int64_t)lc[LC_ROWWIN];
             c.horizon += (int64_t)lc[LC_HORIZON];
             c.order_err += (int64_t)lc[LC_ORDER];
             if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) c.err = 1;
             if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
+            s.rp[RP_BAD] = 0;
+            s.rp[RP_BAD + 1] = 0;
+            s.rp[RP_ABORT] = 0;
+            s.rp[RP_ABORT + 1] = 0;
             if (!c.done) atomicAdd(b.g + G_REMAIN0 + (leg & 1), 1);
         }
         if (!grid_barrier(b, &sflag)) return;
@@ -2078,6 +2236,8 @@ struct ecmc_ctx {
     int64_t repaired = 0;
     int64_t continued = 0;
     int64_t restarts = 0;
+    int64_t row_windows = 0;
+    int64_t device_bytes = 0;  // device memory held by the context
     int64_t horizon = 0;
     int64_t order_err = 0;
     int64_t inconsistent = 0;
@@ -2125,6 +2285,7 @@ static int pool_commit(ecmc_ctx *ctx) {
             return fail(ctx, ECMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
         ctx->allocs.push_back(base);
+        ctx->device_bytes += (int64_t)total;
     }
     size_t off = 0;
     for (auto &r : ctx->pending) {
@@ -2345,6 +2506,24 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &d_colx, (size_t)nc));
     chk(dalloc(ctx, &d_xbound, (size_t)nc + 1));
     chk(dalloc(ctx, &s.claim, ncell));
+    // the row pass needs a window of 32 / C columns well inside the ring and
+    // a leg shorter than L - 3a (no disk behind the active disk in reach)
+    s.rp_ok = (!(p->flags & ECMC_NO_ROWPASS) && nc >= 4 * (32 / C) && p->ell < s.far &&
+               p->n_chains < (1 << 29)) ? 1 : 0;
+    if (s.rp_ok) {
+        chk(dalloc(ctx, &s.ckey, ncell));
+        chk(dalloc(ctx, &s.camin, ncell));
+        chk(dalloc(ctx, &s.camax, ncell));
+    }
+    chk(dalloc(ctx, &s.rp, RP_N));
+    chk(dalloc(ctx, &s.rp_n, k));
+    chk(dalloc(ctx, &s.rp_front, k));
+    chk(dalloc(ctx, &s.rp_end, k));
+    chk(dalloc(ctx, &s.rp_partner, k));
+    chk(dalloc(ctx, &s.rp_aloc, k));
+    chk(dalloc(ctx, &s.rp_ci, k));
+    chk(dalloc(ctx, &s.rp_tc, k));
+    chk(dalloc(ctx, &s.rp_D, k));
     chk(dalloc(ctx, &s.aloc0, k));
     chk(dalloc(ctx, &s.aloc, k));
     chk(dalloc(ctx, &s.ci, k));
@@ -2409,6 +2588,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     }
     CU(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.claim, 0, ncell * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(s.rp, 0, RP_N * sizeof(int32_t), st));
     CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
@@ -2614,6 +2794,7 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         c->conflict_legs += q.conflict_legs;
         c->repaired += q.repaired;
         c->continued += q.continued;
+        c->row_windows += q.row_windows;
         c->horizon += q.horizon;
         c->order_err += q.order_err;
         c->prof.pass1_launches += q.legs;
@@ -2835,6 +3016,8 @@ extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
     out->repaired_chains = ctx->repaired;
     out->continued_chains = ctx->continued;
     out->restarts = ctx->restarts;
+    out->row_windows = ctx->row_windows;
+    out->device_bytes = ctx->graph ? graph_device_bytes(ctx->graph) : ctx->device_bytes;
     out->horizon_asserts = ctx->horizon;
     out->order_errors = ctx->order_err;
     out->device_ms = ctx->device_ms;

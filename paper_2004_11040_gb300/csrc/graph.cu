@@ -1542,6 +1542,7 @@ struct GraphCtx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void *build_tmp[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<std::pair<void **, size_t>> pending;
+    int64_t bytes = 0;  // device memory held
 };
 
 namespace {
@@ -1567,6 +1568,7 @@ int gcommit(GraphCtx *g, std::string &err) {
             return ECMC_ENOMEM;
         }
         g->allocs.push_back(base);
+        g->bytes += (int64_t)total;
     }
     size_t off = 0;
     for (auto &r : g->pending) {
@@ -1627,6 +1629,8 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
             err = "cudaMalloc failed (graph build)";
             return ECMC_ENOMEM;
         }
+        g->bytes += (int64_t)(nslot * 4 + nslot * 8 + nslot * 8 + ((size_t)b.nb + 1) * 4 + 8 +
+                              nslot * 4 + (((size_t)b.nb + SCAN_TILE - 1) / SCAN_TILE) * 4);
     }
     b.cid = (uint32_t *)tmp[0];
     b.cx = (double *)tmp[1];
@@ -1975,3 +1979,5 @@ void graph_destroy(GraphCtx *g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
 }
+
+int64_t graph_device_bytes(const GraphCtx *g) { return g ? g->bytes : 0; }

@@ -35,3 +35,5 @@ int graph_arrows(GraphCtx *g, int32_t *a, double *b, std::string &err);
 int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
                    std::string &err);
 void graph_destroy(GraphCtx *g);
+// Device memory held by the context (bytes).
+int64_t graph_device_bytes(const GraphCtx *g);

@@ -24,6 +24,7 @@ ECMC_LOG_LIFTINGS = 0x1
 ECMC_INPUT_DEVICE = 0x2
 ECMC_GRAPH = 0x4
 ECMC_RESTART = 0x8
+ECMC_NO_ROWPASS = 0x10
 
 EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stats",
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
@@ -43,7 +44,8 @@ class ecmc_stats_t(C.Structure):
     _fields_ = [("liftings", C.c_int64), ("legs", C.c_int64), ("conflict_legs", C.c_int64),
                 ("repaired_chains", C.c_int64), ("horizon_asserts", C.c_int64),
                 ("order_errors", C.c_int64), ("device_ms", C.c_double),
-                ("continued_chains", C.c_int64), ("restarts", C.c_int64)]
+                ("continued_chains", C.c_int64), ("restarts", C.c_int64),
+                ("row_windows", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 class ecmc_profile_t(C.Structure):
@@ -253,14 +255,15 @@ class System:
 
     def __init__(self, x, y, active, box, ell, *, d=1.0, cells_per_side=0, log=False,
                  undo_cap=0, log_cap=0, stream=None, device_input=False, windows=1,
-                 graph=False, restart=False):
+                 graph=False, restart=False, rowpass=True):
         x = x if device_input else np.ascontiguousarray(x, dtype=np.float64)
         y = y if device_input else np.ascontiguousarray(y, dtype=np.float64)
         active = active if device_input else np.ascontiguousarray(active, dtype=np.int32)
         self.n = int(x.shape[0])
         self.k = int(active.shape[0])
         flags = (ECMC_LOG_LIFTINGS if log else 0) | (ECMC_INPUT_DEVICE if device_input else 0) \
-            | (ECMC_GRAPH if graph else 0) | (ECMC_RESTART if restart else 0)
+            | (ECMC_GRAPH if graph else 0) | (ECMC_RESTART if restart else 0) \
+            | (0 if rowpass else ECMC_NO_ROWPASS)
         self.params = ecmc_params(self.n, float(box), float(d), float(ell), self.k,
                                   int(cells_per_side), flags, int(undo_cap), int(log_cap),
                                   int(windows), 0)

@@ -29,11 +29,25 @@ def test_library_exports_every_declared_symbol():
     assert set(ecmc.EXPORTS) <= names
 
 
-def test_binding_structs_match_header_sizes():
+def test_binding_structs_match_header_sizes(tmp_path):
+    """The ctypes structs have the sizes and field offsets a C compiler gives
+    the header's structs."""
     import ctypes as C
-    assert C.sizeof(ecmc.ecmc_params) == 64
-    assert C.sizeof(ecmc.ecmc_stats_t) == 72
-    assert ecmc.LIFT_DTYPE.itemsize == 48
+    import subprocess
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "ecmc.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(ecmc_params), '
+        'sizeof(ecmc_stats_t), sizeof(ecmc_lift_t), offsetof(ecmc_stats_t, row_windows), '
+        'offsetof(ecmc_stats_t, device_bytes)); return 0; }\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    p, st, lift, o_row, o_bytes = map(int, subprocess.check_output([str(exe)]).split())
+    assert C.sizeof(ecmc.ecmc_params) == p
+    assert C.sizeof(ecmc.ecmc_stats_t) == st
+    assert ecmc.LIFT_DTYPE.itemsize == lift
+    assert ecmc.ecmc_stats_t.row_windows.offset == o_row
+    assert ecmc.ecmc_stats_t.device_bytes.offset == o_bytes
 
 
 def test_create_rejects_bad_parameters_without_gpu():
