@@ -1626,7 +1626,29 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
         r.D = s.D[c];
         int32_t nrec = s.nrec[c];
         int st = ST_RUNNING;
+        // members along rows out of reach of their neighbours: the row
+        // window while it applies (rowpass.cuh), the general step after
+        bool row = s.rp_ok && nm != 0;
         while (st == ST_RUNNING) {
+            if (row && r.skip == RP_SKIP_ALL) {
+                uint32_t ns_own = NONE;
+                const int how = row_cont_member<C>(s, c, round, r, nrec, cnt, tw, tend,
+                                                   nm < 0 ? -nm : nm, my_member, st, &ns_own);
+                if (how == RC_FAIL) return CONT_FAIL;
+                if (how == RC_DONE) break;
+                if (how == RC_NONSTATIC) {
+                    const int h = (int)ns_own;
+                    const bool member = __any_sync(FULL, my_member == h && h >= 0);
+                    if (h != c && member && s.status[h] == ST_BLOCKED && switches < 4 * m + 4) {
+                        next = h;  // wait for that member
+                        st = ST_BLOCKED;
+                        ++switches;
+                        break;
+                    }
+                    return CONT_FAIL;
+                }
+                row = false;  // the general step from here on
+            }
             const StepOut o = scan_step<C, MODE_CONT>(s, c, root, r, tw, nm, my_member);
             if (o.conflict) {
                 *met = (int)o.partner;

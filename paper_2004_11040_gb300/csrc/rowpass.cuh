@@ -184,12 +184,14 @@ struct RowStep {
     int nonstatic;     // Remark 10 (as in scan_step)
     uint32_t ns_owner;
     int overflow;      // the scan does not end inside the window
+    int viol;          // CONT: a scanned corridor disk fails Eq. 2
 };
 
 // The step evaluated exactly over the window, lane by lane, with the
-// operations of scan_step (PASS1 mode) and its stop rule column by column.
-// vi: window position of the active disk's column.
-template <int C>
+// operations of scan_step (PASS1 mode, or CONT: the scan runs to D and Eq. 2
+// is checked on every scanned corridor disk) and its stop rule column by
+// column. vi: window position of the active disk's column.
+template <int C, bool CONT = false>
 __device__ RowStep rp_exact(const Dev &s, const StopK &sk, const RowChain &ch, const RowLane &w,
                             int vi, float fxf) {
     constexpr int G = 32 / C;
@@ -219,8 +221,12 @@ __device__ RowStep rp_exact(const Dev &s, const StopK &sk, const RowChain &ch, c
     // lazy frame: a disk that became static after the active disk passed it
     // is one lap away
     const bool tnz = tau != INFINITY && dbits(w.t) != 0ull;
+    bool hzv = false;
     if (__any_sync(FULL, tnz)) {
-        const bool behind = tnz && dbits(__dadd_rn(ch.ti, tau)) < dbits(w.t);
+        const double sum = __dadd_rn(ch.ti, tau);
+        const bool behind = tnz && dbits(sum) < dbits(w.t);
+        // the horizon condition t_i + tau > t_j (Eq. 2, strict)
+        if (CONT) hzv = tnz && !(dbits(sum) > dbits(w.t));
         if (__any_sync(FULL, behind) && behind) tau = __dadd_rn(tau, s.L);
     }
     // another chain's active or stalled disk: time of flight and Eq. 2
@@ -258,13 +264,14 @@ __device__ RowStep rp_exact(const Dev &s, const StopK &sk, const RowChain &ch, c
         }
     }
     const unsigned hvm = __ballot_sync(FULL, hv);
+    const unsigned vm = __ballot_sync(FULL, hzv);
     // columns in order, with the scan's stop rule
     unsigned long long cur = dbits(ch.D);
     float lim_f = __fadd_rn(d2f_trunc(ch.D), s.epsf);
     unsigned long long best = INF_BITS, ns_t = INF_BITS;
     uint32_t bj = NONE, ns_o = NONE;
     int bl = -1;
-    bool hvany = false;
+    bool hvany = false, vany = false;
     int m = 0;
     for (; vi + m < G; ++m) {
         if (m >= 1 && beyond_k(sk, m, ch.fx, fxf, lim_f, cur)) break;
@@ -277,7 +284,7 @@ __device__ RowStep rp_exact(const Dev &s, const StopK &sk, const RowChain &ch, c
             bj = j2;
             bl = l2;
         }
-        if (t2 < cur) {
+        if (!CONT && t2 < cur) {
             cur = t2;
             lim_f = __fadd_rn(d2f_trunc(__longlong_as_double((long long)cur)), s.epsf);
         }
@@ -288,8 +295,10 @@ __device__ RowStep rp_exact(const Dev &s, const StopK &sk, const RowChain &ch, c
             ns_o = o2;
         }
         hvany |= ((hvm >> src) & ((1u << C) - 1u)) != 0u;
+        vany |= ((vm >> src) & ((1u << C) - 1u)) != 0u;
     }
     RowStep r;
+    r.viol = vany;
     r.overflow = vi + m >= G;
     r.mstop = m;
     r.nonstatic = hvany || ns_t < dbits(ch.D);
@@ -492,6 +501,7 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
             rs.nonstatic = 0;
             rs.ns_owner = NONE;
             rs.overflow = 0;
+            rs.viol = 0;
         }
         rp_claim(s, ch, ch.wbase + vi, ch.wbase + vi + rs.mstop - 1, rowb);
         if (rs.nonstatic) {
@@ -801,3 +811,273 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
     (void)blocked;
     __syncwarp();
 }
+
+// ------------------------------------------------- continuation in a row
+
+// Outcome of row_cont_member.
+enum { RC_GENERAL = 0, RC_DONE = 1, RC_FAIL = 2, RC_NONSTATIC = 3 };
+
+// Continues member c of a repair component (the first repair round,
+// continue_component) along its row with the window of the row pass, for as
+// long as the general step would do nothing else: the member's disk and each
+// next one have both neighbour rows out of reach, and every cell the scan
+// covers is held by a member of the component (so no claim is needed and the
+// cells change only in this warp). The step follows scan_step in CONT mode:
+// the scan runs to D, and the horizon condition (Eq. 2) must hold for every
+// scanned corridor disk -- certified, for a disk with t_j != 0, by RN(t_i +
+// (dx - d)) > t_j, which bounds RN(t_i + tau) from below; the winner and
+// everything in doubt are evaluated exactly (rp_exact). Events are written at
+// once, as commit_step writes them. Returns RC_DONE (stalled or paused; st is
+// set), RC_FAIL, RC_NONSTATIC (*ns_owner: another chain's disk in reach) or
+// RC_GENERAL: the general step takes over from the state in r. members: the
+// component's members, one per lane (nmem <= 32).
+template <int C>
+__device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int32_t &nrec,
+                               uint32_t &cnt, double tw, double tend, int nmem, int my_member,
+                               int &st, uint32_t *ns_owner) {
+    constexpr int G = 32 / C;
+    const int lane = threadIdx.x & 31, gme = lane / C;
+    const StopK sk = stopk_of(s);
+    const double dd = s.d, LL = s.L;
+    const int cap = s.cap, nc = s.nc;
+    RowChain ch;
+    ch.c = c;
+    const uint32_t cell0 = r.iloc / C;
+    ch.row = (int)(cell0 / (uint32_t)nc);
+    ch.u0 = (int)(cell0 % (uint32_t)nc);
+    ch.wbase = 0;
+    ch.gbase = 0;
+    ch.i = r.i;
+    ch.xi = r.xi;
+    ch.yi = r.yi;
+    ch.ti = r.ti;
+    ch.D = r.D;
+    ch.front = -1;
+    ch.li = (int)(r.iloc % C);
+    ch.iskp = RP_SKIP_ALL;
+    RowLane w;
+    int hold = -1;     // the chain holding this lane's cell (strongly), -1 none
+    bool cok = false;  // ... and it is a member
+    auto load = [&](int pos) {  // (lanes may diverge: no shuffle)
+        rp_load<C>(s, ch, w, pos);
+        int col = ch.u0 + ch.wbase + pos;
+        if (col >= nc) col -= nc;
+        const uint32_t cw = __ldcg(s.claim + (uint32_t)ch.row * (uint32_t)nc + (uint32_t)col);
+        hold = (cw == 0u || (cw & CLAIM_WEAK)) ? -1 : (int)(cw - 1u);
+    };
+    auto members = [&]() {  // (uniform)
+        bool mem = false;
+        for (int q = 0; q < nmem; ++q) mem |= __shfl_sync(FULL, my_member, q) == hold;
+        cok = hold >= 0 && mem;
+    };
+    load(gme);
+    members();
+    int vi = 0;
+    ch.fx = __dsub_rn(ch.xi, __shfl_sync(FULL, w.colx, ch.li));
+    rp_links<C>(s, ch, w);
+    int nx = __shfl_sync(FULL, w.nx, ch.li);
+    double bnx = __shfl_sync(FULL, w.b, ch.li);
+    for (;;) {
+        if (vi >= G / 2) {
+            if (ch.wbase + vi + G > nc) return RC_GENERAL;
+            const int v0 = (gme - ch.gbase) & (G - 1);
+            const int h = vi;
+            ch.wbase += h;
+            ch.gbase = (ch.gbase + h) & (G - 1);
+            if (v0 < h) load(v0 + G - h);
+            members();
+            vi = 0;
+            rp_links<C>(s, ch, w);
+            nx = __shfl_sync(FULL, w.nx, ch.li);
+            bnx = __shfl_sync(FULL, w.b, ch.li);
+        }
+        const int v = (gme - ch.gbase) & (G - 1);
+        const float fxf = d2f_trunc(ch.fx);
+        const bool occ = w.id != EMPTY;
+        // the scan runs to D: its columns
+        const unsigned smask = rp_stop_mask(sk, ch.fx, fxf, dbits(ch.D), G - vi);
+        const unsigned above = smask & ~1u;
+        const int mstop = above ? __ffs(above) - 1 : G - vi;
+        if (mstop >= G - vi) return RC_GENERAL;
+        const bool scanned = v >= vi && v < vi + mstop;
+        if (__any_sync(FULL, scanned && !cok)) return RC_GENERAL;
+        const int pp = nx;
+        double dx = __dsub_rn(w.x, ch.xi);
+        const bool neg = dneg(dx);
+        const bool wl = occ && neg && v > vi;
+        if (__any_sync(FULL, wl) && wl) dx = rp_add(dx, LL);
+        const double sub = __dsub_rn(dx, lane == pp ? bnx : dd);
+        double taup = INFINITY;
+        if (pp >= 0) {
+            taup = __shfl_sync(FULL, sub, pp);
+            if (dneg(taup)) taup = 0.0;
+        }
+        const bool lift = pp >= 0 && dbits(taup) < dbits(ch.D);
+        const unsigned long long cur = lift ? dbits(taup) : dbits(ch.D);
+        const bool cnd = occ && scanned && w.id != ch.i && !(neg && v == vi);
+        bool bad = cnd && !(lift && lane == pp) &&
+                   (w.own != OWN_STATIC || dneg(sub) ||
+                    (lift ? !(dbits(sub) > cur) : !(dbits(sub) >= cur)));
+        if (lift && lane == pp && w.own != OWN_STATIC) bad = true;
+        // Eq. 2 on every scanned disk with t_j != 0, from the lower bound
+        // (for the target its exact tau): RN(t_i + sub) > t_j
+        const bool tz = cnd && dbits(w.t) != 0ull;
+        if (__any_sync(FULL, tz) && tz) {
+            if (dneg(sub) || !(dbits(__dadd_rn(ch.ti, sub)) > dbits(w.t))) bad = true;
+        }
+        RowStep rs;
+        if (__any_sync(FULL, bad) || (lift && (((pp / C) - ch.gbase) & (G - 1)) - vi >= mstop)) {
+            rs = rp_exact<C, true>(s, sk, ch, w, vi, fxf);
+            if (rs.overflow || rs.mstop != mstop) return RC_GENERAL;
+            if (rs.viol) return RC_FAIL;
+            if (rs.nonstatic) {
+                *ns_owner = rs.ns_owner;
+                return RC_NONSTATIC;
+            }
+        } else {
+            rs.lift = lift;
+            rs.p = lift ? pp : -1;
+            rs.tau = lift ? taup : ch.D;
+        }
+        // t_i + tau, x_i + tau, D - tau and the target's offset in its cell
+        const int p = rs.p;
+        const int pe = p >= 0 ? p : 0;
+        const int a0 = (pe + 1) & 31, a1 = (pe + 2) & 31, a2 = (pe + 3) & 31;
+        double opa = ch.D, opb = -rs.tau;
+        if (lane == a0) {
+            opa = ch.ti;
+            opb = rs.tau;
+        } else if (lane == a1) {
+            opa = ch.xi;
+            opb = rs.tau;
+        } else if (p >= 0 && lane == p) {
+            opa = w.x;
+            opb = -w.colx;
+        }
+        const double sum = __dadd_rn(opa, opb);
+        const double tnew = __shfl_sync(FULL, sum, a0);
+        double xnew = __shfl_sync(FULL, sum, a1);
+        if (!(dbits(tnew) < dbits(tend))) {  // pauses at the window end
+            st = ST_RUNNING;
+            return RC_DONE;
+        }
+        if (dbits(tnew) < dbits(tw)) return RC_FAIL;
+        if (nrec >= cap) {
+            if (lane == 0) atomicAdd(s.lc + LC_ERR_REC, 1ull);
+            return RC_FAIL;
+        }
+        if (dbits(xnew) >= dbits(LL)) xnew = rp_sub(xnew, LL);
+        const unsigned long long xb = dbits(xnew);
+        const unsigned hm =
+            __ballot_sync(FULL, lane % C == 0 && v >= vi && xb >= w.xlo && xb < w.xhi);
+        if (!hm) return RC_GENERAL;
+        const int gn = (__ffs(hm) - 1) / C;
+        int ln = ch.li;
+        if (gn != ch.li / C) {
+            const unsigned em =
+                __ballot_sync(FULL, w.id == EMPTY) & (((1u << C) - 1u) << (gn * C));
+            if (!em) {
+                if (lane == 0) atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+                return RC_FAIL;
+            }
+            ln = __ffs(em) - 1;
+        }
+        const uint32_t from = rp_loc_of<C>(s, ch, ch.li);
+        const uint32_t to = rp_loc_of<C>(s, ch, ln);
+        const uint32_t jloc = rs.lift ? rp_loc_of<C>(s, ch, p) : 0u;
+        const double dnew = rs.lift ? __shfl_sync(FULL, sum, a2) : 0.0;
+        const uint32_t own_i = rs.lift ? OWN_STATIC : (OWN_STALLED | (uint32_t)c);
+        const uint32_t seq = ((uint32_t)round << 24) | cnt;
+        // the event, written as commit_step writes it; the record by the
+        // target's lane (its fields) and lane 0
+        {
+            ulonglong2 *q = (ulonglong2 *)(s.rec + (size_t)c * cap + nrec);
+            const bool tl = rs.lift ? lane == p : lane == 0;
+            if (tl) {
+                const uint32_t jid = rs.lift ? w.id : NONE;
+                q[0] = make_ulonglong2((unsigned long long)ch.i | ((unsigned long long)from << 32),
+                                       (unsigned long long)to | ((unsigned long long)jid << 32));
+                q[3] = make_ulonglong2(rs.lift ? dbits(w.t) : 0ull, dbits(tnew));
+                q[5] = make_ulonglong2(rs.lift ? dbits(w.x) : 0ull, dbits(dnew));
+                if (rs.lift) {
+                    s.cown[jloc] = OWN_ACTIVE | (uint32_t)c;
+                    s.ct[jloc] = tnew;
+                }
+            }
+            if (lane == 0) {
+                q[1] = make_ulonglong2((unsigned long long)jloc | ((unsigned long long)seq << 32),
+                                       0ull);
+                q[2] = make_ulonglong2(dbits(ch.xi), dbits(ch.ti));
+                q[4] = make_ulonglong2(dbits(rs.tau), dbits(xnew));
+                if (to != from) {
+                    s.cx[to] = xnew;
+                    s.cy[to] = ch.yi;
+                    s.cskp[to] = (uint8_t)RP_SKIP_ALL;
+                    s.ct[to] = tnew;
+                    s.cown[to] = own_i;
+                    s.cid[to] = ch.i;
+                    s.cid[from] = EMPTY;
+                } else {
+                    s.cx[from] = xnew;
+                    s.ct[from] = tnew;
+                    s.cown[from] = own_i;
+                }
+                s.nrec[c] = nrec + 1;
+                if (rs.lift) atomicAdd(s.nlift + c, 1);
+            }
+        }
+        ++nrec;
+        ++cnt;
+        double xj = 0.0, yj = 0.0, fxn = 0.0;
+        uint32_t jid = NONE;
+        if (rs.lift) {
+            xj = __shfl_sync(FULL, w.x, p);
+            yj = __shfl_sync(FULL, w.y, p);
+            jid = __shfl_sync(FULL, w.id, p);
+            fxn = __shfl_sync(FULL, sum, p);
+            if (lane == p) {
+                w.t = tnew;
+                w.own = OWN_ACTIVE | (uint32_t)c;
+            }
+        }
+        if (ln != ch.li && lane == ch.li) w.id = EMPTY;
+        if (lane == ln) {
+            w.id = ch.i;
+            w.x = xnew;
+            w.y = ch.yi;
+            w.t = tnew;
+            w.own = own_i;
+            w.skp = RP_SKIP_ALL;
+            w.nx = -1;
+            w.bok = 0;
+        }
+        if (!rs.lift) {  // stalled
+            r.iloc = to;
+            r.xi = xnew;
+            r.ti = tnew;
+            r.D = 0.0;
+            st = ST_STALLED;
+            return RC_DONE;
+        }
+        const bool next_ok = !__ballot_sync(FULL, lane == p && w.skp != RP_SKIP_ALL);
+        r.iloc = jloc;
+        r.i = jid;
+        r.xi = xj;
+        r.yi = yj;
+        r.ti = tnew;
+        r.D = dnew;
+        r.skip = __shfl_sync(FULL, w.skp, p);
+        if (!next_ok) return RC_GENERAL;
+        nx = __shfl_sync(FULL, w.nx, p);
+        bnx = __shfl_sync(FULL, w.b, p);
+        ch.i = jid;
+        ch.li = p;
+        vi = (((p / C) - ch.gbase) & (G - 1));
+        ch.xi = xj;
+        ch.yi = yj;
+        ch.ti = tnew;
+        ch.D = dnew;
+        ch.fx = fxn;
+    }
+}
+
