@@ -175,7 +175,21 @@ int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *acti
  */
 int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction);
 
-/* ecmc_stats -- counters accumulated since ecmc_create (host struct). */
+/*
+ * ecmc_set_wait_limit -- bound on every wait of the persistent kernels of the
+ * cell-scan path (their grid barriers), in nanoseconds of the device clock;
+ * the default, and the largest value, is 60 s. A wait that runs out makes the
+ * launch return ECMC_ETIMEOUT (every block stops at its next barrier or
+ * gives up waiting for the blocks that stopped), and the context is then in
+ * an undefined state: destroy it. A short limit exercises that path; the
+ * paper has no counterpart (its threads wait without bound, Sec. 2.3).
+ * Errors: EINVAL (ns == 0 or above the default).
+ */
+int ecmc_set_wait_limit(ecmc_ctx *ctx, uint64_t ns);
+
+/* ecmc_stats -- counters accumulated since ecmc_create (Sec. 2.1's liftings
+ * and the flags of reading Eq. 2 as a claim conflict), host struct owned by
+ * the caller. Errors: EINVAL (null argument). */
 int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
 
 /*

@@ -234,30 +234,32 @@ __device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool re
     __syncthreads();
 }
 
-// Grid barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the
-// generation. A wait longer than BARRIER_TIMEOUT_NS records ECMC_ETIMEOUT in
-// *err and gives up; the return value is false once *err is set, and the
-// caller then returns.
-__device__ bool grid_sync(unsigned int *bar, int32_t *err, int *sflag) {
+// Grid barrier of a cooperative launch. bar[0] counts the arrivals of the
+// launch (zeroed before it): a block's arrival number old gives its barrier's
+// target, the next multiple of gridDim.x, and the block waits until the
+// count reaches it -- the last block to arrive has nothing further to do. A
+// wait longer than limit_ns records ECMC_ETIMEOUT in *err and gives up; the
+// return value is false once *err is set, and the caller then returns (every
+// block then stops at its next barrier, or gives up waiting for the blocks
+// that stopped).
+__device__ bool grid_sync(unsigned int *bar, int32_t *err, int *sflag,
+                          unsigned long long limit_ns = BARRIER_TIMEOUT_NS) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *gen = bar + 1;
-        const unsigned int g0 = *gen;
         __threadfence();
+        const unsigned int old = atomicAdd(bar, 1u);
+        const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+        volatile unsigned int *cnt = bar;
         int ok = 1;
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if ((int)(*cnt - target) < 0) {
             const unsigned long long t0 = gtimer();
-            while (*gen == g0) {
-                if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
+            while ((int)(*cnt - target) < 0) {
+                if (gtimer() - t0 > limit_ns) {
                     ok = 0;
                     atomicExch(err, ECMC_ETIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();

@@ -120,9 +120,16 @@ struct Dev {
     uint32_t *camin, *camax;     // [ncell], chain + 1; ~0 and 0 when unclaimed
     int32_t *rp;                 // [RP_N]: chains not eligible (by window parity), cancels
     int32_t *rp_n, *rp_front, *rp_end, *rp_partner;
-    uint32_t *rp_aloc, *rp_ci;
+    uint32_t *rp_aloc, *rp_ci, *rp_start;
     double *rp_tc, *rp_D;
 };
+
+// Record e of chain c. Records are stored by event index, then chain: the
+// first events of a leg of all chains lie in one dense block (one page per
+// chain, as with chain-major storage, costs a translation miss per chain).
+__device__ __forceinline__ Rec *rec_at(const Dev &s, int c, int e) {
+    return s.rec + (size_t)e * (size_t)s.k + (size_t)c;
+}
 
 // ------------------------------------------------------------ FP64 geometry
 
@@ -756,7 +763,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
             q.xi = xnew;
             q.xj = o.xj;
             q.d_after = __dsub_rn(r.D, o.tau);
-            s.rec[(size_t)c * s.cap + nrec] = q;
+            *rec_at(s, c, nrec) = q;
             s.nrec[c] = nrec + 1;
             atomicAdd(s.nlift + c, 1);
         }
@@ -797,7 +804,7 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
         q.xi = xnew;
         q.xj = 0.0;
         q.d_after = 0.0;
-        s.rec[(size_t)c * s.cap + nrec] = q;
+        *rec_at(s, c, nrec) = q;
         s.nrec[c] = nrec + 1;
     }
     *newloc_out = newloc;
@@ -968,8 +975,10 @@ __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_
 // names), then start every chain on its stalled disk with D = ell (Alg. 2
 // input at h).
 __device__ void leg_begin_chain(const Dev &s, int c) {
+    // (fields held in registers: the global Dev would be re-read after every
+    // store)
     const int32_t nr = s.nrec[c];
-    const Rec *q = s.rec + (size_t)c * s.cap;
+    double *const ct = s.ct;
     // records read 8 at a time before their stores (a store between two loads
     // could alias the next record and would serialise the round trips)
     for (int32_t e0 = 0; e0 < nr; e0 += 8) {
@@ -979,26 +988,34 @@ __device__ void leg_begin_chain(const Dev &s, int c) {
             to[u] = EMPTY;
             jl[u] = EMPTY;
             if (e0 + u < nr) {
-                to[u] = q[e0 + u].to;
-                if (q[e0 + u].j != NONE) jl[u] = q[e0 + u].jloc;
+                const Rec *q = rec_at(s, c, e0 + u);
+                to[u] = q->to;
+                if (q->j != NONE) jl[u] = q->jloc;
             }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            if (to[u] != EMPTY) s.ct[to[u]] = 0.0;
-            if (jl[u] != EMPTY) s.ct[jl[u]] = 0.0;
+            if (to[u] != EMPTY) ct[to[u]] = 0.0;
+            if (jl[u] != EMPTY) ct[jl[u]] = 0.0;
         }
     }
     const uint32_t loc = s.aloc[c];
-    s.cown[loc] = OWN_ACTIVE | (uint32_t)c;
-    s.ci[c] = s.cid[loc];
-    s.aloc0[c] = loc;
-    s.D[c] = s.ell;
-    s.tc[c] = 0.0;
-    s.status[c] = ST_RUNNING;
-    s.partner[c] = -1;
-    s.nrec[c] = 0;
-    s.nlift[c] = 0;
+    uint32_t *const cown = s.cown;
+    const uint32_t id = s.cid[loc];
+    const double ell = s.ell;
+    uint32_t *const ci = s.ci, *const aloc0 = s.aloc0;
+    double *const D = s.D, *const tc = s.tc;
+    int32_t *const status = s.status, *const partner = s.partner, *const nrec = s.nrec,
+                   *const nlift = s.nlift;
+    cown[loc] = OWN_ACTIVE | (uint32_t)c;
+    ci[c] = id;
+    aloc0[c] = loc;
+    D[c] = ell;
+    tc[c] = 0.0;
+    status[c] = ST_RUNNING;
+    partner[c] = -1;
+    nrec[c] = 0;
+    nlift[c] = 0;
 }
 
 __global__ void k_leg_begin(Dev s) {
@@ -1040,7 +1057,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
                 // so no other chain can have taken it: kept as a check that
                 // blocks the chain (and names the owner) should it ever fail
                 if (lane == 0) {
-                    s.rec[(size_t)c * s.cap + cas_rec].flags |= REC_NO_OWNER;
+                    rec_at(s, c, cas_rec)->flags |= REC_NO_OWNER;
                     s.partner[c] = (int32_t)(old & OWN_CHAIN);
                     atomicAdd(s.lc + LC_OWNER_FAIL, 1ull);
                 }
@@ -1152,7 +1169,7 @@ __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double
             const int c = mem[e];
             const int32_t nr = s.nrec[c];
             if (nr == 0) continue;
-            const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+            const Rec &u = *rec_at(s, c, nr - 1);
             if (!(u.t >= Ts) || u.seq < REPAIR_SEQ0) continue;
             if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
                 bseq = u.seq;
@@ -1172,7 +1189,7 @@ __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double
         if (lane == 0) {
             const int c = mem[bmem];
             const int32_t nr = s.nrec[c];
-            undo_record(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
+            undo_record(s, c, *rec_at(s, c, nr - 1));
             s.nrec[c] = nr - 1;
         }
         __syncwarp();
@@ -1181,7 +1198,7 @@ __device__ void rollback_members(const Dev &s, const int32_t *mem, int m, double
         const int c = mem[e];
         int32_t nr = s.nrec[c];
         while (nr > 0) {
-            const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+            const Rec &u = *rec_at(s, c, nr - 1);
             if (!(u.t >= Ts)) break;
             undo_record(s, c, u);
             --nr;
@@ -1203,7 +1220,7 @@ __device__ void resume_state(const Dev &s, int c, uint32_t &loc, uint32_t &id, d
         st = ST_RUNNING;
         return;
     }
-    const Rec &u = s.rec[(size_t)c * s.cap + nr - 1];
+    const Rec &u = *rec_at(s, c, nr - 1);
     if (u.j == NONE) {
         loc = u.to;
         id = u.i;
@@ -1267,7 +1284,7 @@ __device__ void repair_small(const Dev &s, const int32_t *mem, int m, int root, 
         if (s.cid[my_loc] != my_id) {
             const int32_t nr = s.nrec[my_c];
             diag(s, 1, round, my_c, my_loc, my_id, s.cid[my_loc],
-                 nr > 0 ? (double)s.rec[(size_t)my_c * s.cap + nr - 1].seq : -1.0);
+                 nr > 0 ? (double)rec_at(s, my_c, nr - 1)->seq : -1.0);
         }
     }
     // pending event
@@ -1466,7 +1483,7 @@ __device__ void repair_large(const Dev &s, const int32_t *mem, int m, int root, 
         if (s.cid[loc] != id) {
             const int32_t nr = s.nrec[c];
             diag(s, 11, round, c, loc, id, s.cid[loc],
-                 nr > 0 ? (double)s.rec[(size_t)c * s.cap + nr - 1].seq : -1.0);
+                 nr > 0 ? (double)rec_at(s, c, nr - 1)->seq : -1.0);
         }
         s.aloc[c] = loc;
         s.ci[c] = id;
@@ -1748,20 +1765,20 @@ __device__ int32_t leg_end_chain(const Dev &s, int c, int32_t leg, bool count = 
     if (count) atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
     if (s.log_on && nl > 0) {
         const unsigned long long base = atomicAdd(s.tc_cnt + TC_LOG_N, (unsigned long long)nl);
-        const Rec *q = s.rec + (size_t)c * s.cap;
         unsigned long long w = base;
         for (int32_t e = 0; e < s.nrec[c]; ++e) {
-            if (q[e].j == NONE) continue;
+            const Rec *q = rec_at(s, c, e);
+            if (q->j == NONE) continue;
             if ((int64_t)w < s.log_cap) {
                 ecmc_lift_t L;
                 L.leg = leg;
                 L.c = c;
-                L.i = (int32_t)q[e].i;
-                L.j = (int32_t)q[e].j;
-                L.t = q[e].t;
-                L.tau = q[e].tau;
-                L.xi = q[e].xi;
-                L.xj = q[e].xj;
+                L.i = (int32_t)q->i;
+                L.j = (int32_t)q->j;
+                L.t = q->t;
+                L.tau = q->tau;
+                L.xi = q->xi;
+                L.xj = q->xj;
                 s.log[w] = L;
             }
             ++w;
@@ -1882,6 +1899,8 @@ struct Batch {
     int32_t R;
     int32_t max_legs;
     int32_t windows;  // claim windows per leg (all replicas of a launch)
+    int32_t pad;
+    unsigned long long wait_ns;  // bound on every grid-barrier wait
 };
 
 __device__ __forceinline__ double window_start(const Dev &s, int w) {
@@ -1894,7 +1913,7 @@ __device__ __forceinline__ double window_end(const Dev &s, int w) {
 }
 
 __device__ bool grid_barrier(const Batch &b, int *sflag) {
-    return grid_sync(b.bar, b.g + G_ERR, sflag);
+    return grid_sync(b.bar, b.g + G_ERR, sflag, b.wait_ns);
 }
 
 // replica of flattened item w, with base[r] <= w < base[r+1]
@@ -1914,9 +1933,17 @@ __device__ __forceinline__ bool rep_on(const Batch &b, int r) {
     return b.ctl[r].live && !b.ctl[r].done;
 }
 
+// A thread's index for per-chain loops that spreads consecutive chains over
+// the blocks (and so over the SMs): with chains on consecutive threads a few
+// blocks would carry all the memory operations of a phase.
+__device__ __forceinline__ int spread_index() {
+    return (int)(threadIdx.x * gridDim.x + blockIdx.x);
+}
+
 // Invariant: a running or stalled chain's table slot holds its active disk.
 __device__ void check_chains(const Batch &b, int gt, int nthreads, int total_chains, int where) {
-    for (int w = gt; w < total_chains; w += nthreads) {
+    (void)gt;
+    for (int w = spread_index(); w < total_chains; w += nthreads) {
         const int r = find_rep(b.chain_base, b.R, w);
         if (!rep_on(b, r)) continue;
         const Dev &s = b.reps[r];
@@ -1928,6 +1955,26 @@ __device__ void check_chains(const Batch &b, int gt, int nthreads, int total_cha
                 b.ctl[r].bad_chain = c;
             }
         }
+    }
+}
+
+// Claim words cleared by the whole grid for the next window (pointers held
+// in registers: a field of the global Dev would be re-read after every store).
+__device__ __forceinline__ void clear_claims(const Dev &s, int gt, int nthreads) {
+    const int64_t ncell = (int64_t)s.nc * s.nc;
+    uint32_t *const cl = s.claim;
+    for (int64_t q = gt; q < ncell; q += nthreads) cl[q] = 0u;
+}
+
+// The row pass's claim arrays, all cells (after a cancelled row pass).
+__device__ __forceinline__ void clear_row_claims(const Dev &s, int gt, int nthreads) {
+    const int64_t ncell = (int64_t)s.nc * s.nc;
+    unsigned long long *const ck = s.ckey;
+    uint32_t *const mn = s.camin, *const mx = s.camax;
+    for (int64_t q = gt; q < ncell; q += nthreads) {
+        ck[q] = ~0ull;
+        mn[q] = ~0u;
+        mx[q] = 0u;
     }
 }
 
@@ -1948,6 +1995,7 @@ __device__ __forceinline__ const Dev &warp_dev(Dev *slot, int *rep, const Dev *r
     }
     return *slot;
 }
+
 
 // Block shape of the persistent kernel: 8 warps per block, 2 blocks per SM
 // (16 warps per SM, 128 registers). Fewer, larger register files (3 blocks of
@@ -1986,7 +2034,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     for (int leg = 0; leg < b.max_legs; ++leg) {
         // leg start: chain table, local times, claims, per-leg counters; the
         // chains whose rows are in reach (they rule out the row pass)
-        for (int w = gt; w < total_chains; w += nthreads) {
+        for (int w = spread_index(); w < total_chains; w += nthreads) {
             const int r = find_rep(b.chain_base, R, w);
             if (rep_on(b, r)) {
                 const Dev &s = b.reps[r];
@@ -1998,14 +2046,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
         for (int r = 0; r < R; ++r) {
             if (!rep_on(b, r)) continue;
             const Dev &s = b.reps[r];
-            const int64_t ncell = (int64_t)s.nc * s.nc;
-            for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
-            if (s.rp_ok)
-                for (int64_t q = gt; q < ncell; q += nthreads) {
-                    s.ckey[q] = ~0ull;
-                    s.camin[q] = ~0u;
-                    s.camax[q] = 0u;
-                }
+            // (claim words were cleared at the end of the last leg)
             if (gt < LC_N) s.lc[gt] = 0ull;
             if (gt == 0) {
                 s.rp[RP_BAD + 1] = 0;
@@ -2024,21 +2065,14 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                 for (int r = 0; r < R; ++r) {
                     if (!rep_on(b, r)) continue;
                     const Dev &s = b.reps[r];
-                    const int64_t ncell = (int64_t)s.nc * s.nc;
-                    for (int64_t q = gt; q < ncell; q += nthreads) s.claim[q] = 0u;
-                    if (s.rp_ok)
-                        for (int64_t q = gt; q < ncell; q += nthreads) {
-                            s.ckey[q] = ~0ull;
-                            s.camin[q] = ~0u;
-                            s.camax[q] = 0u;
-                        }
+                    clear_claims(s, gt, nthreads);
                     if (gt == 0) {
                         s.lc[LC_WBLOCKED] = 0ull;
                         s.rp[RP_BAD + (par ^ 1)] = 0;
                         s.rp[RP_ABORT + (par ^ 1)] = 0;
                     }
                 }
-                for (int w2 = gt; w2 < total_chains; w2 += nthreads) {
+                for (int w2 = spread_index(); w2 < total_chains; w2 += nthreads) {
                     const int r = find_rep(b.chain_base, R, w2);
                     if (!rep_on(b, r)) continue;
                     const Dev &s = b.reps[r];
@@ -2090,10 +2124,30 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             }
             mark(PH_PASS1);
             check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 1);
+            // the row pass's claim arrays back to empty where the chains
+            // claimed (every cell after a cancelled row pass); the union-find
+            // of this phase leaves most blocks idle
+            for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
+                const int r = find_rep(b.chain_base, R, w2);
+                if (!rep_on(b, r)) continue;
+                const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
+                if (!(s.rp_ok && s.rp[RP_BAD + par] == 0) || __ldcg(s.rp + RP_ABORT + par) != 0)
+                    continue;
+                row_reset_chain<C>(s, w2 - b.chain_base[r]);
+            }
+            for (int r = 0; r < R; ++r) {
+                if (!rep_on(b, r)) continue;
+                const Dev &s = b.reps[r];
+                if (s.rp_ok && s.rp[RP_BAD + par] == 0 && __ldcg(s.rp + RP_ABORT + par) != 0)
+                    clear_row_claims(s, gt, nthreads);
+            }
             // repair rounds
             for (int round = 1;; ++round) {
                 for (int r = blockIdx.x; r < R; r += gridDim.x) {
-                    const Dev &s = b.reps[r];
+                    // the block's copy of the system: warp 0's slot
+                    if (threadIdx.x < 32) (void)warp_dev(wdev, wrep, b.reps, r);
+                    __syncthreads();
+                    const Dev &s = wdev[0];
                     bool need = false;
                     if (rep_on(b, r))
                         need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
@@ -2150,8 +2204,14 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             mark(PH_REPAIR);
         }
         // leg end: liftings and the log, then per-replica totals and budgets;
-        // a warp whose chains share a replica adds their liftings at once
-        for (int w0 = gt - lane; w0 < total_chains; w0 += nthreads) {
+        // a warp whose chains share a replica adds their liftings at once.
+        // The claim words are cleared for the next leg here, off the next
+        // leg's begin (whose few dependent loads per chain would queue
+        // behind the stores)
+        for (int r = 0; r < R; ++r)
+            if (rep_on(b, r)) clear_claims(b.reps[r], gt, nthreads);
+        for (int w0 = (((int)threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32; w0 < total_chains;
+             w0 += nthreads) {
             const int w = w0 + lane;
             int r = -1;
             int32_t nl = 0;
@@ -2260,6 +2320,7 @@ struct ecmc_ctx {
     int64_t restarts = 0;
     int64_t row_windows = 0;
     int64_t device_bytes = 0;  // device memory held by the context
+    unsigned long long wait_ns = BARRIER_TIMEOUT_NS;  // bound on device waits
     int64_t horizon = 0;
     int64_t order_err = 0;
     int64_t inconsistent = 0;
@@ -2543,6 +2604,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.rp_end, k));
     chk(dalloc(ctx, &s.rp_partner, k));
     chk(dalloc(ctx, &s.rp_aloc, k));
+    chk(dalloc(ctx, &s.rp_start, k));
     chk(dalloc(ctx, &s.rp_ci, k));
     chk(dalloc(ctx, &s.rp_tc, k));
     chk(dalloc(ctx, &s.rp_D, k));
@@ -2611,6 +2673,11 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     CU(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.claim, 0, ncell * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.rp, 0, RP_N * sizeof(int32_t), st));
+    if (s.rp_ok) {
+        CU(cudaMemsetAsync(s.ckey, 0xFF, ncell * sizeof(unsigned long long), st));
+        CU(cudaMemsetAsync(s.camin, 0xFF, ncell * sizeof(uint32_t), st));
+        CU(cudaMemsetAsync(s.camax, 0, ncell * sizeof(uint32_t), st));
+    }
     CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.tc_cnt, 0, TC_N * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(s.nrec, 0, k * sizeof(int32_t), st));
@@ -2787,6 +2854,9 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     b.R = R;
     b.max_legs = max_legs;
     b.windows = W;
+    b.pad = 0;
+    b.wait_ns = BARRIER_TIMEOUT_NS;
+    for (int r = 0; r < R; ++r) b.wait_ns = std::min(b.wait_ns, ctxs[r]->wait_ns);
     void *args[] = {&b};
     cu(cudaEventRecord(rn.ev0, st), "event");
     if (C == 4)
@@ -3027,6 +3097,13 @@ extern "C" int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ctx, ECMC_ECUDA, std::string("set_direction: ") + cudaGetErrorString(e));
     ctx->direction = direction;
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_set_wait_limit(ecmc_ctx *ctx, uint64_t ns) {
+    if (!ctx) return ECMC_EINVAL;
+    if (ns == 0 || ns > BARRIER_TIMEOUT_NS) return fail(ctx, ECMC_EINVAL, "wait limit out of range");
+    ctx->wait_ns = ns;
     return ECMC_OK;
 }
 

@@ -97,6 +97,12 @@ struct GDev {
     int log_on;
     double *dbg;  // [16] first failed internal check
 };
+// Record e of chain c, stored by event index, then chain (the first events of
+// a leg of all chains lie in one dense block).
+__device__ __forceinline__ GEv *grec_at(const GDev &s, int c, int e) {
+    return s.rec + (size_t)e * (size_t)s.k + (size_t)c;
+}
+
 
 __device__ void gdiag(const GDev &s, int kind, double a, double b, double c, double d,
                       double e, double f) {
@@ -560,7 +566,7 @@ __device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double 
         u.xj = 0.0;
         u.d_after = 0.0;                              // no length left
     }
-    s.rec[(size_t)c * s.cap + nr] = u;
+    *grec_at(s, c, nr) = u;
 }
 
 // ------------------------------------------------------------------ legs
@@ -569,14 +575,13 @@ __device__ void graph_apply(const GDev &s, int c, uint32_t i, double xi, double 
 // records name), then start every chain on its stalled disk with D = ell.
 __device__ void g_leg_begin_chain(const GDev &s, int c) {
     const int32_t nr = s.nrec[c];
-    const GEv *q = s.rec + (size_t)c * s.cap;
     // in batches: the record loads of a batch are issued before its stores
     for (int32_t e0 = 0; e0 < nr; e0 += 8) {
         uint32_t ii[8], jj[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            ii[u] = e0 + u < nr ? q[e0 + u].i : NONE;
-            jj[u] = e0 + u < nr ? q[e0 + u].j : NONE;
+            ii[u] = e0 + u < nr ? grec_at(s, c, e0 + u)->i : NONE;
+            jj[u] = e0 + u < nr ? grec_at(s, c, e0 + u)->j : NONE;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -785,7 +790,7 @@ __device__ void g_rollback(const GDev &s, const int32_t *mem, int m, double Ts) 
             const int c = mem[e];
             const int32_t nr = s.nrec[c];
             if (nr == 0) continue;
-            const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+            const GEv &u = *grec_at(s, c, nr - 1);
             if (!(u.t >= Ts) || u.seq < REPAIR_SEQ0) continue;
             if (bmem < 0 || u.seq > bseq || (u.seq == bseq && e < bmem)) {
                 bseq = u.seq;
@@ -805,7 +810,7 @@ __device__ void g_rollback(const GDev &s, const int32_t *mem, int m, double Ts) 
         if (lane == 0) {
             const int c = mem[bmem];
             const int32_t nr = s.nrec[c];
-            g_undo(s, c, s.rec[(size_t)c * s.cap + nr - 1]);
+            g_undo(s, c, *grec_at(s, c, nr - 1));
             s.nrec[c] = nr - 1;
         }
         __syncwarp();
@@ -814,7 +819,7 @@ __device__ void g_rollback(const GDev &s, const int32_t *mem, int m, double Ts) 
         const int c = mem[e];
         int32_t nr = s.nrec[c];
         while (nr > 0) {
-            const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+            const GEv &u = *grec_at(s, c, nr - 1);
             if (!(u.t >= Ts)) break;
             g_undo(s, c, u);
             --nr;
@@ -834,7 +839,7 @@ __device__ void g_resume(const GDev &s, int c) {
         s.status[c] = ST_RUNNING;
         return;
     }
-    const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+    const GEv &u = *grec_at(s, c, nr - 1);
     if (u.j == NONE) {
         s.ci[c] = u.i;
         s.tc[c] = u.t;
@@ -875,7 +880,7 @@ __device__ __noinline__ void g_compute(const GDev &s, int c, int root, uint64_t 
 __device__ void g_rollback_chain(const GDev &s, int c, double Ts) {
     int32_t nr = s.nrec[c];
     while (nr > 0) {
-        const GEv &u = s.rec[(size_t)c * s.cap + nr - 1];
+        const GEv &u = *grec_at(s, c, nr - 1);
         if (!(u.t >= Ts)) break;
         g_undo(s, c, u);
         --nr;
@@ -1234,20 +1239,20 @@ __device__ void g_leg_end_chain(const GDev &s, int c, int32_t leg) {
     atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
     if (s.log_on && nl > 0) {
         const unsigned long long base = atomicAdd(s.tc_cnt + TC_LOG_N, (unsigned long long)nl);
-        const GEv *q = s.rec + (size_t)c * s.cap;
         unsigned long long w = base;
         for (int32_t e = 0; e < s.nrec[c]; ++e) {
-            if (q[e].j == NONE) continue;
+            const GEv *q = grec_at(s, c, e);
+            if (q->j == NONE) continue;
             if ((int64_t)w < s.log_cap) {
                 ecmc_lift_t L;
                 L.leg = leg;
                 L.c = c;
-                L.i = (int32_t)q[e].i;
-                L.j = (int32_t)q[e].j;
-                L.t = q[e].t;
-                L.tau = q[e].tau;
-                L.xi = q[e].xi;
-                L.xj = q[e].xj;
+                L.i = (int32_t)q->i;
+                L.j = (int32_t)q->j;
+                L.t = q->t;
+                L.tau = q->tau;
+                L.xi = q->xi;
+                L.xj = q->xj;
                 s.log[w] = L;
             }
             ++w;

@@ -384,7 +384,10 @@ template <int C>
 __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
     constexpr int G = 32 / C;
     const int lane = threadIdx.x & 31, gme = lane / C;
-    if (s.status[c] != ST_RUNNING) return true;
+    if (s.status[c] != ST_RUNNING) {
+        if (lane == 0) s.rp_front[c] = -1;  // claims nothing
+        return true;
+    }
     const StopK sk = stopk_of(s);
     const double dd = s.d, LL = s.L;
     const int cap = s.cap;
@@ -394,6 +397,7 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
     RowChain ch;
     ch.c = c;
     const uint32_t aloc = s.aloc[c];
+    if (lane == 0) s.rp_start[c] = aloc;
     const uint32_t cell0 = aloc / C;
     ch.row = (int)(cell0 / (uint32_t)s.nc);
     ch.u0 = (int)(cell0 % (uint32_t)s.nc);
@@ -565,7 +569,7 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
         const uint32_t jloc = rs.lift ? rp_loc_of<C>(s, ch, p) : 0u;
         {
             const double dnew = __shfl_sync(FULL, sum, a2);
-            ulonglong2 *q = (ulonglong2 *)(s.rec + (size_t)c * cap + ch.nrec0 + ch.n);
+            ulonglong2 *q = (ulonglong2 *)rec_at(s, c, ch.nrec0 + ch.n);
             const bool tl = rs.lift ? lane == p : lane == 0;
             if (tl) {
                 const uint32_t jid = rs.lift ? w.id : NONE;
@@ -647,6 +651,31 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
     return true;
 }
 
+// The claim arrays back to empty over the cells chain c claimed in the row
+// pass (rows row - 1 .. row + 1, columns 0 .. rp_front from its start).
+template <int C>
+__device__ void row_reset_chain(const Dev &s, int c) {
+    const int front = s.rp_front[c];
+    if (front < 0) return;
+    const int lane = threadIdx.x & 31, nc = s.nc;
+    const uint32_t cell0 = s.rp_start[c] / C;
+    const int row = (int)(cell0 / (uint32_t)nc), u0 = (int)(cell0 % (uint32_t)nc);
+    unsigned long long *const ck = s.ckey;
+    uint32_t *const mn = s.camin, *const mx = s.camax;
+    for (int e = lane; e < 3 * (front + 1); e += 32) {
+        const int o = e / 3;
+        int col = u0 + o;
+        if (col >= nc) col -= nc;
+        int r = row + e % 3 - 1;
+        if (r < 0) r += nc;
+        if (r >= nc) r -= nc;
+        const uint32_t cell = (uint32_t)r * (uint32_t)nc + (uint32_t)col;
+        ck[cell] = ~0ull;
+        mn[cell] = ~0u;
+        mx[cell] = 0u;
+    }
+}
+
 // After the pass: the first cell another chain holds, the events published
 // before it, the chain's state, the claim words and the flag.
 template <int C>
@@ -659,7 +688,6 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
     const int row = (int)(cell0 / (uint32_t)nc), u0 = (int)(cell0 % (uint32_t)nc);
     const int n = s.rp_n[c], front = s.rp_front[c], end = s.rp_end[c];
     const int32_t nrec0 = s.nrec[c];
-    const Rec *rec = s.rec + (size_t)c * s.cap + nrec0;
     // columns 0 .. front: holder of the active row's cell, two claimants anywhere
     int lost = -1;
     uint32_t holder = NONE;
@@ -703,7 +731,7 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
     if (lost >= 0) {
         for (int e0 = 0; e0 < n; e0 += 32) {
             const int e = e0 + lane;
-            const bool hit = e < n && (int)rec[e].pad >= lost;
+            const bool hit = e < n && (int)rec_at(s, c, nrec0 + e)->pad >= lost;
             const unsigned hm = __ballot_sync(FULL, hit);
             if (hm) {
                 sfail = e0 + __ffs(hm) - 1;
@@ -719,7 +747,7 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
         uint32_t ri = 0, rfrom = 0, rto = 0, rj = NONE, rjl = 0, rskp = 0;
         double rx = 0.0, rt = 0.0, ry = 0.0;
         if (e < sfail) {
-            const Rec &q = rec[e];
+            const Rec &q = *rec_at(s, c, nrec0 + e);
             ri = q.i;
             rfrom = q.from;
             rto = q.to;
@@ -768,11 +796,11 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
         double tc, D;
         int32_t partner = -1;
         if (sfail < n) {
-            const Rec &q = rec[sfail];
+            const Rec &q = *rec_at(s, c, nrec0 + sfail);
             al = q.from;
             id = q.i;
             tc = q.ti_old;
-            D = sfail > 0 ? rec[sfail - 1].d_after : s.D[c];
+            D = sfail > 0 ? rec_at(s, c, nrec0 + sfail - 1)->d_after : s.D[c];
             st = ST_BLOCKED;
             partner = (int32_t)holder;
         } else {
@@ -991,7 +1019,7 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
         // the event, written as commit_step writes it; the record by the
         // target's lane (its fields) and lane 0
         {
-            ulonglong2 *q = (ulonglong2 *)(s.rec + (size_t)c * cap + nrec);
+            ulonglong2 *q = (ulonglong2 *)rec_at(s, c, nrec);
             const bool tl = rs.lift ? lane == p : lane == 0;
             if (tl) {
                 const uint32_t jid = rs.lift ? w.id : NONE;

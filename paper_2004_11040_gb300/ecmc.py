@@ -30,7 +30,7 @@ EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stat
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
            "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
            "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction",
-           "ecmc_graph_arrows")
+           "ecmc_graph_arrows", "ecmc_set_wait_limit")
 
 
 class ecmc_params(C.Structure):
@@ -87,6 +87,8 @@ def load(path: str | None = None):
     lib.ecmc_positions.restype = C.c_int
     lib.ecmc_set_direction.argtypes = [vp, C.c_int32]
     lib.ecmc_set_direction.restype = C.c_int
+    lib.ecmc_set_wait_limit.argtypes = [vp, C.c_uint64]
+    lib.ecmc_set_wait_limit.restype = C.c_int
     lib.ecmc_stats.argtypes = [vp, C.POINTER(ecmc_stats_t)]
     lib.ecmc_stats.restype = C.c_int
     lib.ecmc_profile.argtypes = [vp, C.POINTER(ecmc_profile_t)]
@@ -155,6 +157,11 @@ def ecmc_run_to_breakpoint(ctx, n_legs: int, event_budget: int = 0, leg_flags_ou
 
 def ecmc_positions(ctx, x=None, y=None, t=None, active=None):
     _check(load().ecmc_positions(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(active)), ctx)
+
+
+def ecmc_set_wait_limit(ctx, ns: int):
+    """Bound (ns) on every device wait of the context's persistent kernels."""
+    _check(load().ecmc_set_wait_limit(ctx, int(ns)), ctx)
 
 
 def ecmc_set_direction(ctx, direction: int):
@@ -284,6 +291,9 @@ class System:
 
     def stats(self):
         return ecmc_stats(self.ctx)
+
+    def set_wait_limit(self, ns: int):
+        ecmc_set_wait_limit(self.ctx, ns)
 
     def set_direction(self, direction: int):
         ecmc_set_direction(self.ctx, direction)
