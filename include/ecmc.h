@@ -85,6 +85,11 @@ typedef struct {
                                  T* taken as a breakpoint (Sec. 3.4, strategy 2) */
     int64_t row_windows;      /* claim windows whose parallel pass was the row pass */
     int64_t device_bytes;     /* device memory the context holds (its pooled state) */
+    int64_t blocked_chains;   /* chains whose parallel pass stopped at a strong claim of
+                                 another chain, summed over windows and legs: the chains
+                                 that met another one (Sec. 3.4) */
+    int64_t conflict_windows; /* claim windows (legs x W in all) whose conflict flag is 1:
+                                 the claim sets of two chains met in the window */
 } ecmc_stats_t;
 
 /* One lifting i -> j (Eq. 1): chain c, leg index, time t (= new t_j),
@@ -109,6 +114,17 @@ typedef struct {
  */
 int ecmc_create(const ecmc_params *p, const double *x, const double *y,
                 const int32_t *active, void *stream, ecmc_ctx **out);
+
+/*
+ * ecmc_context_bytes -- the device memory a cell-scan context created with
+ * *p would hold, without allocating anything: its pooled arrays (cells, chain
+ * table, event records, claims) and the scratch of ecmc_positions, i.e. the
+ * device_bytes that ecmc_stats reports once positions have been read. (The
+ * persistent launch's scratch, a few kilobytes per system, is not included.)
+ * A scheduler admits systems by it. The paper has no counterpart.
+ * Errors: EINVAL (bad parameters, or ECMC_GRAPH).
+ */
+int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes);
 
 /*
  * Constraint-graph mode (ECMC_GRAPH). The context builds, at creation and at

@@ -238,7 +238,10 @@ static int better(double tau, int j, double btau, int bj) {
 }
 
 /* All-pairs definition: argmin over every candidate disk. */
-/* Time of flight in the lazily advanced frame of i (see the header). */
+/* Time of flight in the lazily advanced frame of i: each chain's disk keeps
+   (x_i, t_i) and moves only when its chain acts. A disk j with
+   t_i + tau < t_j became static after i had passed its position (the horizon
+   condition of Eq. 2 fails), so it is one lap away: tau + L. */
 static double lazy_tof(const orc_params *p, const double *x, const double *y,
                        const double *t, int i, int j) {
     double tau = time_of_flight(x[i], y[i], x[j], y[j], p->L, p->d);
@@ -550,6 +553,8 @@ static void compute_event(const orc_params *p, const cells_t *g, graph_t *G,
  *   flag   out: 1 iff the isolated claim sets of two chains share a cell
  *          (search 0 or 1) or a disk (search 2), computed window by window
  *   lifts  out: number of liftings in this leg
+ *   lifts_per_chain  optional [k] out: liftings of each chain
+ *   wflags optional [windows] out: the flag of each claim window
  * Returns 0, or -1 on allocation failure, -2 on log/undo overflow,
  * -3 on bad parameters, -6 if an event was found earlier than the last one
  * executed (a broken global-time order; never expected).
@@ -557,7 +562,7 @@ static void compute_event(const orc_params *p, const cells_t *g, graph_t *G,
 int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
             double *t, int32_t k, int32_t *active, orc_lift *log,
             int64_t log_cap, int64_t *log_n, uint8_t *flag, int64_t *lifts,
-            int64_t *lifts_per_chain) {
+            int64_t *lifts_per_chain, uint8_t *wflags) {
     if (p->n <= 0 || k <= 0 || k > p->n || p->nc < 3) return -3;
     if (!(p->L / (double)p->nc > p->d)) return -3;
     int64_t n = p->n;
@@ -635,6 +640,7 @@ int orc_leg(const orc_params *p, int32_t leg, double *x, const double *y,
                 goto done;
             }
             any_conflict |= cc.conflict;
+            if (wflags) wflags[w] = (uint8_t)cc.conflict;
         }
         /* Alg. 2: the events of the window in global-time order */
         for (;;) {

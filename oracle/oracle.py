@@ -66,7 +66,8 @@ def lib():
         ip = C.POINTER(C.c_int32)
         _lib.orc_leg.argtypes = [C.POINTER(Params), C.c_int32, dp, dp, dp, C.c_int32, ip,
                                  C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
-                                 C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.c_void_p]
+                                 C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.c_void_p,
+                                 C.c_void_p]
         _lib.orc_leg.restype = C.c_int
         _lib.orc_alg4_leg.argtypes = [C.POINTER(Params), C.c_int32, dp, dp, dp, C.c_int32, ip,
                                       C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
@@ -112,6 +113,7 @@ class LegResult:
     lifts: int
     lifts_per_chain: np.ndarray
     log: np.ndarray = field(default_factory=lambda: np.zeros(0, LIFT_DTYPE))
+    wflags: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))
 
 
 class OracleError(RuntimeError):
@@ -137,13 +139,16 @@ def run_leg(x, y, active, L, ell, *, d=1.0, nc=None, search=1, leg=0, log=True,
     flag = C.c_uint8(0)
     lifts = C.c_int64(0)
     per_chain = np.zeros(k, dtype=np.int64)
+    wflags = np.zeros(max(1, windows), dtype=np.uint8)
     rc = lib().orc_leg(C.byref(p), leg, _dptr(x), _dptr(y), _dptr(t), k, _iptr(act),
                        logbuf.ctypes.data if log else None, log_cap, C.byref(log_n),
-                       C.byref(flag), C.byref(lifts), per_chain.ctypes.data)
+                       C.byref(flag), C.byref(lifts), per_chain.ctypes.data,
+                       wflags.ctypes.data)
     if rc != 0:
         raise OracleError(f"orc_leg failed: {rc}")
     return LegResult(x=x, t=t, active=act, flag=int(flag.value), lifts=int(lifts.value),
-                     lifts_per_chain=per_chain, log=logbuf[: log_n.value].copy())
+                     lifts_per_chain=per_chain, log=logbuf[: log_n.value].copy(),
+                     wflags=wflags)
 
 
 def run_legs(x, y, active, L, ell, n_legs, **kw) -> tuple[LegResult, list[LegResult]]:

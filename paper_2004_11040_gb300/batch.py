@@ -1,6 +1,6 @@
 """Batched replicas: many independent ECMC systems of uneven size in one
 persistent launch, versus the same systems one at a time; and the autotuner
-that picks the cell size and the legs per launch.
+that picks the cell size, the parallel pass and the legs per launch.
 
 Replica recipe (the batched workload): N log-uniform in [1024, 65536] with
 M = round(sqrt(N)), N := M^2; eta uniform in [0.60, 0.74]; k = M chains
@@ -38,17 +38,23 @@ def make_replicas(count: int, seed: int, n_range=(1024, 65536), eta_range=(0.60,
     return out
 
 
-def cells_for(start: synth.Start, factor: float) -> int:
-    """Cells per side for a cell side of about factor * d (0 = default)."""
-    if factor <= 1.0:
+def cells_for(start: synth.Start, cells) -> int:
+    """Cells per side: "lattice" -- one cell per lattice site (cells aligned
+    with the start lattice, so that every row of disks lies inside one cell
+    row), "default" -- the library's choice (the smallest cells of side >= d),
+    or a number f > 1 for cells of side about f * d."""
+    if cells == "lattice":
+        return int(start.m) if start.m > 0 else 0
+    if cells == "default" or float(cells) <= 1.0:
         return 0
-    return max(3, int(start.box / (factor * start.d)))
+    return max(3, int(start.box / (float(cells) * start.d)))
 
 
-def create(reps: list[Replica], cell_factor: float = 1.0, undo_cap: int = 256, stream=None):
+def create(reps: list[Replica], cells="lattice", undo_cap: int = 256, stream=None,
+           rowpass: bool = True):
     return [ecmc.System(r.start.x, r.start.y, r.start.active, r.start.box, r.ell,
-                        cells_per_side=cells_for(r.start, cell_factor), undo_cap=undo_cap,
-                        stream=stream) for r in reps]
+                        cells_per_side=cells_for(r.start, cells), undo_cap=undo_cap,
+                        stream=stream, rowpass=rowpass) for r in reps]
 
 
 def run_batched(systems, budget: int, legs_per_launch: int, stream=None):
@@ -71,8 +77,10 @@ def run_batched(systems, budget: int, legs_per_launch: int, stream=None):
     return int(done.sum()), ms_total, launches
 
 
-def run_plain(systems, budget: int, legs_per_launch: int):
-    """One system at a time through ecmc_run_to_breakpoint."""
+def run_plain(systems, budget: int, legs_per_launch: int = 1 << 20):
+    """One system at a time through ecmc_run_to_breakpoint, each in as few
+    launches as the budget allows (the budget stops a launch at the first
+    breakpoint where it is met)."""
     total, ms_total, launches = 0, 0.0, 0
     for sysm in systems:
         got = 0
@@ -92,19 +100,40 @@ def run_plain(systems, budget: int, legs_per_launch: int):
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ecmc_gb300_autotune.json")
 
 
+def _hardware_key() -> str:
+    """The GPU and the build of the library: a cached choice holds for both."""
+    try:
+        import torch
+        gpu = torch.cuda.get_device_name(0).replace(" ", "_")
+    except Exception:  # pragma: no cover
+        gpu = "unknown"
+    try:
+        import hashlib
+        with open(ecmc.library_path(), "rb") as f:
+            lib = hashlib.sha256(f.read()).hexdigest()[:16]
+    except Exception:
+        lib = "unknown"
+    return f"{gpu}_{lib}"
+
+
 def _key(reps: list[Replica]) -> str:
     ns = sorted(r.start.n for r in reps)
-    return f"n{ns[0]}-{ns[-1]}_r{len(reps)}"
+    return f"{_hardware_key()}_n{ns[0]}-{ns[-1]}_r{len(reps)}"
 
 
 def autotune(reps: list[Replica], trial_budget: int = 20_000,
-             cell_factors=(1.0, 1.5), legs_options=(4, 16, 64), cache: str | None = CACHE,
-             stream=None) -> dict:
-    """Tries every (cell size, legs per launch) on a sample of the replicas and
-    keeps the fastest by liftings per device second; the choice is cached per
-    workload key. Warps per chain is 1: an FP64 warp instruction costs the same
-    whatever the number of active lanes on this GPU, so more warps per chain
-    buy no throughput."""
+             cells_options=("lattice", "default"), pass_options=(True, False),
+             legs_options=(4, 16, 64), cache: str | None = CACHE, stream=None) -> dict:
+    """Tries every (cell size, parallel pass, legs per launch) on a sample of
+    the replicas and keeps the fastest by liftings per device second; every
+    trial is recorded, and the choice is cached per GPU, library build and
+    workload. The parallel pass is the row pass (a warp holds 32 slots of
+    its chain's row and batches the square roots of several steps) or the
+    general pass (a warp scans 3 rows x 2 columns of cells per pass); both
+    run one chain per warp. Fewer warps per chain (two chains per warp) are
+    not offered: every FP64 warp instruction occupies the sub-partition's
+    FP64 unit ~64 cycles whatever its lane mask, so a warp's latency per step
+    is set by its FP64 instruction count, which two chains would not share."""
     key = _key(reps)
     if cache and os.path.exists(cache):
         try:
@@ -117,19 +146,23 @@ def autotune(reps: list[Replica], trial_budget: int = 20_000,
     sample = reps[: min(len(reps), 64)]
     best = None
     trials = []
-    for cf in cell_factors:
-        systems = create(sample, cf, stream=stream)
-        try:
-            for legs in legs_options:
-                lifts, ms, _ = run_batched(systems, trial_budget, legs, stream=stream)
-                rate = lifts / (ms / 1e3) if ms > 0 else 0.0
-                trials.append({"cell_factor": cf, "legs_per_launch": legs, "liftings_per_s": rate})
-                if best is None or rate > best["liftings_per_s"]:
-                    best = dict(trials[-1])
-        finally:
-            for s in systems:
-                s.close()
+    for cells in cells_options:
+        for rowpass in pass_options:
+            systems = create(sample, cells, stream=stream, rowpass=rowpass)
+            try:
+                for legs in legs_options:
+                    lifts, ms, _ = run_batched(systems, trial_budget, legs, stream=stream)
+                    rate = lifts / (ms / 1e3) if ms > 0 else 0.0
+                    rows = sum(q.stats()["row_windows"] for q in systems)
+                    trials.append({"cells": cells, "rowpass": rowpass, "legs_per_launch": legs,
+                                   "liftings_per_s": rate, "row_windows": rows})
+                    if best is None or rate > best["liftings_per_s"]:
+                        best = dict(trials[-1])
+            finally:
+                for q in systems:
+                    q.close()
     best["trials"] = trials
+    best["key"] = key
     if cache:
         try:
             os.makedirs(os.path.dirname(cache), exist_ok=True)
@@ -145,31 +178,43 @@ def autotune(reps: list[Replica], trial_budget: int = 20_000,
     return best
 
 
-def bench_batched(count: int = 512, budget: int = 1_000_000, plain_sample: int = 16,
-                  seed: int = 0, tune: bool = True, stream=None) -> dict:
-    """Batched throughput of `count` replicas to `budget` liftings each, and the
-    one-at-a-time throughput on the first `plain_sample` of them."""
+def bench_batched(count: int = 512, budget: int = 1_000_000, same_budget: int = 50_000,
+                  seed: int = 0, tune: bool = True, stream=None, cache: str | None = CACHE) -> dict:
+    """Batched throughput of `count` replicas to `budget` liftings each; and,
+    on the same replicas with `same_budget` liftings each, batched against one
+    at a time (both rates over the same systems and the same work)."""
     reps = make_replicas(count, seed)
-    choice = autotune(reps, stream=stream) if tune else {"cell_factor": 1.0,
-                                                          "legs_per_launch": 16}
+    choice = autotune(reps, stream=stream, cache=cache) if tune else {
+        "cells": "lattice", "rowpass": True, "legs_per_launch": 16}
+    cells, rowpass, legs = choice["cells"], choice["rowpass"], choice["legs_per_launch"]
     t0 = time.perf_counter()
-    systems = create(reps, choice["cell_factor"], stream=stream)
+    systems = create(reps, cells, stream=stream, rowpass=rowpass)
     t_create = time.perf_counter() - t0
     try:
-        lifts, ms, launches = run_batched(systems, budget, choice["legs_per_launch"], stream)
+        lifts, ms, launches = run_batched(systems, budget, legs, stream)
     finally:
-        for s in systems:
-            s.close()
-    plain_sys = create(reps[:plain_sample], choice["cell_factor"], stream=stream)
+        for q in systems:
+            q.close()
+    systems = create(reps, cells, stream=stream, rowpass=rowpass)
     try:
-        p_lifts, p_ms, p_launches = run_plain(plain_sys, budget, choice["legs_per_launch"])
+        s_lifts, s_ms, _ = run_batched(systems, same_budget, legs, stream)
     finally:
-        for s in plain_sys:
-            s.close()
-    batched = lifts / (ms / 1e3)
+        for q in systems:
+            q.close()
+    systems = create(reps, cells, stream=stream, rowpass=rowpass)
+    try:
+        p_lifts, p_ms, p_launches = run_plain(systems, same_budget)
+    finally:
+        for q in systems:
+            q.close()
+    same = s_lifts / (s_ms / 1e3)
     plain = p_lifts / (p_ms / 1e3)
     return {"replicas": count, "budget_per_replica": budget, "liftings": lifts,
-            "device_ms": ms, "launches": launches, "liftings_per_s": batched,
-            "plain_sample": plain_sample, "plain_liftings_per_s": plain,
-            "batched_over_plain": batched / plain if plain else None,
-            "create_s": t_create, "autotune": {k: v for k, v in choice.items() if k != "trials"}}
+            "device_ms": ms, "launches": launches, "liftings_per_s": lifts / (ms / 1e3),
+            "create_s": t_create,
+            "same_set": {"budget_per_replica": same_budget, "batched_liftings_per_s": same,
+                         "one_at_a_time_liftings_per_s": plain,
+                         "one_at_a_time_launches": p_launches,
+                         "batched_over_one_at_a_time": same / plain if plain else None},
+            "autotune": {k: v for k, v in choice.items() if k != "trials"},
+            "autotune_trials": choice.get("trials")}

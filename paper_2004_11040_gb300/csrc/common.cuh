@@ -33,6 +33,7 @@ enum { LC_BLOCKED = 0, LC_LIFTS, LC_HORIZON, LC_ERR_CAP, LC_ERR_REC, LC_ORDER, L
        LC_CONTINUED,
        LC_P1LIFTS, LC_REPAIRED, LC_WBLOCKED, LC_CWINDOWS, LC_RESTARTS, LC_WEAK,
        LC_ROWWIN,  // claim windows run by the row pass (cell scan)
+       LC_WWEAK,   // chains whose claim sets met on a weak claim, this window
        LC_BADXY, LC_BADID,  // inputs out of range (creation only)
        LC_N };
 enum { CTL_NCOMP = 0, CTL_WORK, CTL_NABORT, CTL_NMEMB, CTL_N };

@@ -1105,7 +1105,10 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
             atomicAdd(s.lc + LC_BLOCKED, 1ull);
             atomicAdd(s.lc + LC_WBLOCKED, 1ull);
         }
-        if (weak) atomicAdd(s.lc + LC_WEAK, 1ull);
+        if (weak) {
+            atomicAdd(s.lc + LC_WEAK, 1ull);
+            atomicAdd(s.lc + LC_WWEAK, 1ull);
+        }
         atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)lifts);
     }
     __syncwarp();
@@ -1874,6 +1877,8 @@ struct RepCtl {
     int64_t p1_lifts;       // liftings made by the parallel pass (redone ones included)
     int64_t row_windows;    // claim windows run by the row pass
     int64_t repair_lifts;   // liftings of legs that needed a repair
+    int64_t blocked;        // chains whose strong claim was blocked (all windows)
+    int64_t cwindows;       // claim windows that needed a repair
     uint8_t *flags;         // per-leg conflict flags (device) or null
     int32_t flags_cap;
     int32_t live;           // takes part in this run
@@ -2068,6 +2073,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                     clear_claims(s, gt, nthreads);
                     if (gt == 0) {
                         s.lc[LC_WBLOCKED] = 0ull;
+                        s.lc[LC_WWEAK] = 0ull;
                         s.rp[RP_BAD + (par ^ 1)] = 0;
                         s.rp[RP_ABORT + (par ^ 1)] = 0;
                     }
@@ -2151,7 +2157,10 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                     bool need = false;
                     if (rep_on(b, r))
                         need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
-                    if (need && round == 1 && threadIdx.x == 0) s.lc[LC_CWINDOWS] += 1ull;
+                    // the window's flag: the claim sets of two chains met
+                    if (round == 1 && threadIdx.x == 0 && rep_on(b, r) &&
+                        (s.lc[LC_WBLOCKED] != 0ull || s.lc[LC_WWEAK] != 0ull))
+                        s.lc[LC_CWINDOWS] += 1ull;
                     if (need && round <= 255) {
                         uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
                     } else if (threadIdx.x == 0) {
@@ -2247,6 +2256,8 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             c.repaired += (int64_t)lc[LC_REPAIRED];
             c.continued += (int64_t)lc[LC_CONTINUED];
             c.row_windows += (int64_t)lc[LC_ROWWIN];
+            c.blocked += (int64_t)lc[LC_BLOCKED];
+            c.cwindows += (int64_t)lc[LC_CWINDOWS];
             c.horizon += (int64_t)lc[LC_HORIZON];
             c.order_err += (int64_t)lc[LC_ORDER];
             if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) c.err = 1;
@@ -2319,6 +2330,8 @@ struct ecmc_ctx {
     int64_t continued = 0;
     int64_t restarts = 0;
     int64_t row_windows = 0;
+    int64_t blocked = 0;
+    int64_t cwindows = 0;
     int64_t device_bytes = 0;  // device memory held by the context
     unsigned long long wait_ns = BARRIER_TIMEOUT_NS;  // bound on device waits
     int64_t horizon = 0;
@@ -2512,46 +2525,19 @@ static void launch_build(ecmc_ctx *ctx, const double *x, const double *y) {
     k_build_cells<C><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->s, x, y);
 }
 
-extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *y,
-                           const int32_t *active, void *stream, ecmc_ctx **out) {
-    ecmc_ctx *ctx = nullptr;
-    if (!p || !x || !y || !active || !out) return fail(nullptr, ECMC_EINVAL, "null argument");
-    *out = nullptr;
-    if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF) return fail(nullptr, ECMC_EINVAL, "n out of range");
-    if (p->n_chains < 1 || p->n_chains > p->n) return fail(nullptr, ECMC_EINVAL, "n_chains out of range");
-    if (p->windows < 0 || p->windows > 4096) return fail(nullptr, ECMC_EINVAL, "windows out of range");
-    if (p->undo_cap < 0 || p->undo_cap >= (1 << 24))
-        return fail(nullptr, ECMC_EINVAL, "undo_cap out of range (0 .. 2^24 - 1)");
-    if (!(p->d > 0.0) || !(p->ell > 0.0) || !(p->box > 0.0) || !std::isfinite(p->box) ||
-        !std::isfinite(p->ell))
-        return fail(nullptr, ECMC_EINVAL, "d, ell and box must be positive and finite");
-    int nc = 0, C = 4;
-    if (pick_cells(p, &nc, &C))
-        return fail(nullptr, ECMC_EINVAL, "cell geometry: need nc >= 3 and d < L/nc < 1.664 d");
-    if ((int64_t)nc * nc * C > (int64_t)0xFFFFFFF0)
-        return fail(nullptr, ECMC_EINVAL, "too many cells");
+// Device arrays of a cell-scan context, set up but not allocated yet: the
+// scalar description in ctx->s and one request per array in ctx->pending
+// (ecmc_create commits them; ecmc_context_bytes only adds them up).
+struct CreateArrays {
+    double *colx = nullptr;
+    unsigned long long *xbound = nullptr;
+    uint32_t *loc_of = nullptr;
+    double *dx = nullptr, *dy = nullptr;
+    int32_t *dact = nullptr;
+};
 
-    ctx = new (std::nothrow) ecmc_ctx();
-    if (!ctx) return fail(nullptr, ECMC_ENOMEM, "host allocation");
-    ctx->p = *p;
-    ctx->stream = (cudaStream_t)stream;
-    ctx->C = C;
-    if ((p->flags & ECMC_RESTART) && (!(p->flags & ECMC_GRAPH) || p->windows > 1)) {
-        delete ctx;
-        return fail(nullptr, ECMC_EINVAL, "ECMC_RESTART needs ECMC_GRAPH and one claim window");
-    }
-    if (p->flags & ECMC_GRAPH) {
-        memset(&ctx->s, 0, sizeof ctx->s);
-        ctx->s.n = p->n;
-        ctx->s.k = p->n_chains;
-        const int rc = create_graph(ctx, nc, x, y, active);
-        if (rc) {
-            ecmc_destroy(ctx);
-            return rc;
-        }
-        *out = ctx;
-        return ECMC_OK;
-    }
+static int plan_cell_context(ecmc_ctx *ctx, const ecmc_params *p, int nc, int C,
+                             CreateArrays *out) {
     Dev &s = ctx->s;
     memset(&s, 0, sizeof s);
     s.n = p->n;
@@ -2584,10 +2570,8 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.cown, nslot));
     chk(dalloc(ctx, &s.cskp, nslot));
     chk(dalloc(ctx, &s.rband, 2 * (size_t)nc));
-    double *d_colx = nullptr;
-    unsigned long long *d_xbound = nullptr;
-    chk(dalloc(ctx, &d_colx, (size_t)nc));
-    chk(dalloc(ctx, &d_xbound, (size_t)nc + 1));
+    chk(dalloc(ctx, &out->colx, (size_t)nc));
+    chk(dalloc(ctx, &out->xbound, (size_t)nc + 1));
     chk(dalloc(ctx, &s.claim, ncell));
     // the row pass needs a window of 32 / C columns well inside the ring and
     // a leg shorter than L - 3a (no disk behind the active disk in reach)
@@ -2643,22 +2627,106 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     chk(dalloc(ctx, &s.lc, LC_N));
     chk(dalloc(ctx, &s.tc_cnt, TC_N));
     if (s.log_on) chk(dalloc(ctx, &s.log, (size_t)s.log_cap));
-    double *dx = nullptr, *dy = nullptr;
-    int32_t *dact = nullptr;
-    uint32_t *loc_of = nullptr;
-    chk(dalloc(ctx, &loc_of, n));
-    const bool dev_in = (p->flags & ECMC_INPUT_DEVICE) != 0;
-    if (!dev_in) {
-        chk(dalloc(ctx, &dx, n));
-        chk(dalloc(ctx, &dy, n));
-        chk(dalloc(ctx, &dact, k));
+    chk(dalloc(ctx, &out->loc_of, n));
+    if (!(p->flags & ECMC_INPUT_DEVICE)) {
+        chk(dalloc(ctx, &out->dx, n));
+        chk(dalloc(ctx, &out->dy, n));
+        chk(dalloc(ctx, &out->dact, k));
     }
+    return rc;
+}
+
+extern "C" int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes) {
+    if (!p || !bytes) return ECMC_EINVAL;
+    if (p->flags & ECMC_GRAPH) return ECMC_EINVAL;
+    if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF || p->n_chains < 1 || p->n_chains > p->n)
+        return ECMC_EINVAL;
+    if (p->undo_cap < 0 || p->undo_cap >= (1 << 24) || !(p->box > 0.0) || !(p->d > 0.0) ||
+        !(p->ell > 0.0))
+        return ECMC_EINVAL;
+    int nc = 0, C = 4;
+    if (pick_cells(p, &nc, &C)) return ECMC_EINVAL;
+    ecmc_ctx *ctx = new (std::nothrow) ecmc_ctx();
+    if (!ctx) return ECMC_ENOMEM;
+    CreateArrays arr;
+    plan_cell_context(ctx, p, nc, C, &arr);
+    // the export scratch of ecmc_positions (allocated by its first call)
+    dalloc(ctx, &ctx->exp_x, (size_t)p->n);
+    dalloc(ctx, &ctx->exp_y, (size_t)p->n);
+    dalloc(ctx, &ctx->exp_t, (size_t)p->n);
+    dalloc(ctx, &ctx->exp_a, (size_t)p->n_chains);
+    int64_t total = 0;
+    for (auto &r : ctx->pending) total += (int64_t)((r.second + 255) & ~(size_t)255);
+    ctx->pending.clear();
+    ctx->exp_x = nullptr;
+    ctx->exp_y = nullptr;
+    ctx->exp_t = nullptr;
+    ctx->exp_a = nullptr;
+    delete ctx;
+    *bytes = total;
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *y,
+                           const int32_t *active, void *stream, ecmc_ctx **out) {
+    ecmc_ctx *ctx = nullptr;
+    if (!p || !x || !y || !active || !out) return fail(nullptr, ECMC_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF) return fail(nullptr, ECMC_EINVAL, "n out of range");
+    if (p->n_chains < 1 || p->n_chains > p->n) return fail(nullptr, ECMC_EINVAL, "n_chains out of range");
+    if (p->windows < 0 || p->windows > 4096) return fail(nullptr, ECMC_EINVAL, "windows out of range");
+    if (p->undo_cap < 0 || p->undo_cap >= (1 << 24))
+        return fail(nullptr, ECMC_EINVAL, "undo_cap out of range (0 .. 2^24 - 1)");
+    if (!(p->d > 0.0) || !(p->ell > 0.0) || !(p->box > 0.0) || !std::isfinite(p->box) ||
+        !std::isfinite(p->ell))
+        return fail(nullptr, ECMC_EINVAL, "d, ell and box must be positive and finite");
+    int nc = 0, C = 4;
+    if (pick_cells(p, &nc, &C))
+        return fail(nullptr, ECMC_EINVAL, "cell geometry: need nc >= 3 and d < L/nc < 1.664 d");
+    if ((int64_t)nc * nc * C > (int64_t)0xFFFFFFF0)
+        return fail(nullptr, ECMC_EINVAL, "too many cells");
+
+    ctx = new (std::nothrow) ecmc_ctx();
+    if (!ctx) return fail(nullptr, ECMC_ENOMEM, "host allocation");
+    ctx->p = *p;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->C = C;
+    if ((p->flags & ECMC_RESTART) && (!(p->flags & ECMC_GRAPH) || p->windows > 1)) {
+        delete ctx;
+        return fail(nullptr, ECMC_EINVAL, "ECMC_RESTART needs ECMC_GRAPH and one claim window");
+    }
+    if (p->flags & ECMC_GRAPH) {
+        memset(&ctx->s, 0, sizeof ctx->s);
+        ctx->s.n = p->n;
+        ctx->s.k = p->n_chains;
+        const int rc = create_graph(ctx, nc, x, y, active);
+        if (rc) {
+            ecmc_destroy(ctx);
+            return rc;
+        }
+        *out = ctx;
+        return ECMC_OK;
+    }
+    Dev &s = ctx->s;
+    CreateArrays arr;
+    int rc = plan_cell_context(ctx, p, nc, C, &arr);
+    auto chk = [&](int r) {
+        if (r && !rc) rc = r;
+    };
+    const size_t ncell = (size_t)nc * nc;
+    const size_t nslot = ncell * C;
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    const bool dev_in = (p->flags & ECMC_INPUT_DEVICE) != 0;
     chk(pool_commit(ctx));
     if (rc) {
         g_create_err = ctx->err;
         ecmc_destroy(ctx);
         return rc;
     }
+    double *const dx = arr.dx, *const dy = arr.dy, *const d_colx = arr.colx;
+    int32_t *const dact = arr.dact;
+    uint32_t *const loc_of = arr.loc_of;
+    unsigned long long *const d_xbound = arr.xbound;
     cudaStream_t st = ctx->stream;
     const double *sx = x, *sy = y;
     const int32_t *sa = active;
@@ -2887,6 +2955,8 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         c->repaired += q.repaired;
         c->continued += q.continued;
         c->row_windows += q.row_windows;
+        c->blocked += q.blocked;
+        c->cwindows += q.cwindows;
         c->horizon += q.horizon;
         c->order_err += q.order_err;
         c->prof.pass1_launches += q.legs;
@@ -2961,6 +3031,8 @@ extern "C" int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t ev
         ctx->repaired += t.repaired;
         ctx->continued += t.continued;
         ctx->restarts += t.restarts;
+        ctx->blocked += t.blocked;
+        ctx->cwindows += t.cwindows;
         ctx->horizon += t.horizon;
         ctx->order_err += t.order_err;
         ctx->device_ms += t.ms;
@@ -3116,6 +3188,8 @@ extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
     out->continued_chains = ctx->continued;
     out->restarts = ctx->restarts;
     out->row_windows = ctx->row_windows;
+    out->blocked_chains = ctx->blocked;
+    out->conflict_windows = ctx->cwindows;
     out->device_bytes = ctx->graph ? graph_device_bytes(ctx->graph) : ctx->device_bytes;
     out->horizon_asserts = ctx->horizon;
     out->order_errors = ctx->order_err;

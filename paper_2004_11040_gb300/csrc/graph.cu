@@ -1265,7 +1265,7 @@ __device__ void g_leg_end_chain(const GDev &s, int c, int32_t leg) {
 struct GCtl {
     int64_t budget;  // liftings for this run (0: none)
     int64_t lifts, legs, conflict_legs, repaired, continued, horizon, order_err, p1_lifts,
-        repair_lifts, restarts;
+        repair_lifts, restarts, blocked, cwindows;
     uint8_t *flags;  // per-leg conflict flags (device) or null
     int32_t flags_cap;
     int32_t done;    // budget reached or error
@@ -1390,6 +1390,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                     if (gt == 0) {
                         s.lc[LC_WBLOCKED] = 0ull;
                         s.lc[LC_RESTARTS] += 1ull;
+                        if (sub == 0) s.lc[LC_CWINDOWS] += 1ull;  // the window's flag
                     }
                     for (int c = gt; c < s.k; c += nthreads) g_rollback_chain(s, c, Ts);
                     for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
@@ -1407,7 +1408,7 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
                     __syncthreads();
                     if (round == 1 && threadIdx.x == 0) {
                         s.lc[LC_WBLOCKED] = 0ull;
-                        if (need) s.lc[LC_CWINDOWS] += 1ull;
+                        if (need && sub == 0) s.lc[LC_CWINDOWS] += 1ull;
                     }
                     if (need && round <= 255) {
                         uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
@@ -1481,6 +1482,8 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
             c.repaired += (int64_t)d[LC_REPAIRED];
             c.continued += (int64_t)d[LC_CONTINUED];
             c.restarts += (int64_t)d[LC_RESTARTS];
+            c.blocked += (int64_t)d[LC_BLOCKED];
+            c.cwindows += (int64_t)d[LC_CWINDOWS];
             c.horizon += (int64_t)d[LC_HORIZON];
             c.order_err += (int64_t)d[LC_ORDER];
             if (err) c.err = 1;
@@ -1872,6 +1875,8 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     tot->order_err = ctl.order_err;
     tot->p1_lifts = ctl.p1_lifts;
     tot->repair_lifts = ctl.repair_lifts;
+    tot->blocked = ctl.blocked;
+    tot->cwindows = ctl.cwindows;
     tot->ms = ms;
     tot->pass1_ms = ph[GPH_PASS1] * 1e-6;
     tot->repair_ms = ph[GPH_REPAIR] * 1e-6;

@@ -14,7 +14,7 @@ struct GraphCtx;
 // Totals of one graph_run call.
 struct GraphTotals {
     int64_t legs, lifts, conflict_legs, repaired, continued, horizon, order_err, p1_lifts,
-        repair_lifts, restarts;
+        repair_lifts, restarts, blocked, cwindows;
     double ms, pass1_ms, repair_ms, other_ms;
 };
 

@@ -833,7 +833,10 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
         } else {
             s.vt[c] = INFINITY;
         }
-        if (over) atomicAdd(s.lc + LC_WEAK, 1ull);
+        if (over) {
+            atomicAdd(s.lc + LC_WEAK, 1ull);
+            atomicAdd(s.lc + LC_WWEAK, 1ull);
+        }
         atomicAdd(s.lc + LC_P1LIFTS, (unsigned long long)pub_lifts);
     }
     (void)blocked;

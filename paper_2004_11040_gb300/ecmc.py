@@ -30,7 +30,7 @@ EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stat
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
            "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
            "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction",
-           "ecmc_graph_arrows", "ecmc_set_wait_limit")
+           "ecmc_graph_arrows", "ecmc_set_wait_limit", "ecmc_context_bytes")
 
 
 class ecmc_params(C.Structure):
@@ -45,7 +45,8 @@ class ecmc_stats_t(C.Structure):
                 ("repaired_chains", C.c_int64), ("horizon_asserts", C.c_int64),
                 ("order_errors", C.c_int64), ("device_ms", C.c_double),
                 ("continued_chains", C.c_int64), ("restarts", C.c_int64),
-                ("row_windows", C.c_int64), ("device_bytes", C.c_int64)]
+                ("row_windows", C.c_int64), ("device_bytes", C.c_int64),
+                ("blocked_chains", C.c_int64), ("conflict_windows", C.c_int64)]
 
 
 class ecmc_profile_t(C.Structure):
@@ -69,6 +70,11 @@ class EcmcError(RuntimeError):
 _lib = None
 
 
+def library_path() -> str:
+    """Path of the in-tree libecmc.so."""
+    return _build.LIB
+
+
 def load(path: str | None = None):
     """Loads libecmc.so (built in-tree by build.build()); raises if absent."""
     global _lib
@@ -89,6 +95,8 @@ def load(path: str | None = None):
     lib.ecmc_set_direction.restype = C.c_int
     lib.ecmc_set_wait_limit.argtypes = [vp, C.c_uint64]
     lib.ecmc_set_wait_limit.restype = C.c_int
+    lib.ecmc_context_bytes.argtypes = [C.POINTER(ecmc_params), C.POINTER(C.c_int64)]
+    lib.ecmc_context_bytes.restype = C.c_int
     lib.ecmc_stats.argtypes = [vp, C.POINTER(ecmc_stats_t)]
     lib.ecmc_stats.restype = C.c_int
     lib.ecmc_profile.argtypes = [vp, C.POINTER(ecmc_profile_t)]
@@ -157,6 +165,15 @@ def ecmc_run_to_breakpoint(ctx, n_legs: int, event_budget: int = 0, leg_flags_ou
 
 def ecmc_positions(ctx, x=None, y=None, t=None, active=None):
     _check(load().ecmc_positions(ctx, _ptr(x), _ptr(y), _ptr(t), _ptr(active)), ctx)
+
+
+def ecmc_context_bytes(params) -> int:
+    """Device bytes a context created with `params` would hold (nothing allocated)."""
+    out = C.c_int64()
+    rc = load().ecmc_context_bytes(C.byref(params), C.byref(out))
+    if rc != ECMC_OK:
+        raise EcmcError(rc, "ecmc_context_bytes")
+    return int(out.value)
 
 
 def ecmc_set_wait_limit(ctx, ns: int):

@@ -21,20 +21,15 @@ import numpy as np
 
 from . import ecmc, synth
 
-RECORD_BYTES = 96  # one event record on the device
-
-
 def device_bytes(n: int, k: int, box: float, d: float = 1.0, undo_cap: int = 1024,
-                 log_cap: int = 0) -> int:
-    """Device memory an ECMC context takes (cells with 4 slots, chain table,
-    event records, persistent-launch scratch)."""
-    nc = int(box / (d * (1.0 + 2.0 ** -20)))
-    while nc > 3 and not (box / nc >= d * (1.0 + 2.0 ** -20)):
-        nc -= 1
-    nslot = 4 * nc * nc
-    cells = nslot * (8 + 8 + 8 + 4 + 4) + nc * nc * 4
-    chains = k * (16 * 8 + 24 * 4) + k * undo_cap * RECORD_BYTES
-    return cells + chains + n * 4 + log_cap * 48 + (1 << 16)
+                 log_cap: int = 0, cells_per_side: int = 0, ell: float = 1.0) -> int:
+    """Device memory an ECMC context of these parameters holds, as the
+    library computes it without allocating (ecmc_context_bytes): the same
+    number its ecmc_stats reports as device_bytes once created."""
+    p = ecmc.ecmc_params(int(n), float(box), float(d), float(ell), int(k), int(cells_per_side),
+                         ecmc.ECMC_LOG_LIFTINGS if log_cap else 0, int(undo_cap), int(log_cap),
+                         1, 0)
+    return ecmc.ecmc_context_bytes(p)
 
 
 @dataclass(order=True)
@@ -116,14 +111,18 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, ell: float = 1.0, slice_legs: int = 8,
                  max_resident: int = 4096, undo_cap: int = 1024, stream=None,
-                 keep_results: bool = False):
+                 keep_results: bool = False, cells: str = "lattice",
+                 release_starts: bool = False):
         self.hbm_budget = int(hbm_budget_bytes)
+        self.cells = cells
         self.ell = ell
         self.slice_legs = slice_legs
         self.max_resident = max_resident
         self.undo_cap = undo_cap
         self.stream = stream
         self.keep_results = keep_results
+        # drop a request's host copy of its start once it is on the device
+        self.release_starts = release_starts
         self.batch = ecmc.ecmc_batch_create(stream)
 
     def close(self):
@@ -131,10 +130,26 @@ class Server:
             ecmc.ecmc_batch_destroy(self.batch)
             self.batch = None
 
+    def _cells(self, r: Request) -> int:
+        # "lattice": one cell per site of the start lattice (every row of disks
+        # inside one cell row, where the row pass applies); else the default
+        return int(r.start.m) if self.cells == "lattice" else 0
+
+    def need(self, r: Request) -> int:
+        """Device bytes request r will hold (from the library, no allocation)."""
+        return device_bytes(r.n, r.k, r.start.box, undo_cap=self.undo_cap,
+                            cells_per_side=self._cells(r), ell=self.ell)
+
+    @staticmethod
+    def mean_budget(budget_range) -> float:
+        """Mean of a log-uniform budget on [a, b]: (b - a) / ln(b / a)."""
+        a, b = float(budget_range[0]), float(budget_range[1])
+        return a if b <= a else (b - a) / math.log(b / a)
+
     def _admit(self, r: Request):
         s = r.start
         return ecmc.System(s.x, s.y, s.active, s.box, self.ell, undo_cap=self.undo_cap,
-                           stream=self.stream)
+                           stream=self.stream, cells_per_side=self._cells(r))
 
     def serve(self, reqs: list[Request], clock=time.perf_counter) -> ServeStats:
         """Runs the stream to completion; arrival times are seconds after start."""
@@ -158,11 +173,13 @@ class Server:
             # admission: FIFO while the device budget and the slot count allow
             while pending and len(running) < self.max_resident:
                 r = pending[0]
-                need = device_bytes(r.n, r.k, r.start.box, undo_cap=self.undo_cap)
+                need = self.need(r)
                 if running and used + need > self.hbm_budget:
                     break
                 pending.pop(0)
                 sysm = self._admit(r)
+                if self.release_starts:
+                    r.start = None
                 r.admitted = clock() - t0
                 running[r.rid] = (r, sysm, need)
                 used += need
@@ -198,10 +215,12 @@ class Server:
                           peak_resident=peak_res, peak_bytes=peak_bytes)
 
 
-def run_alone(r: Request, ell: float = 1.0, undo_cap: int = 1024, stream=None):
+def run_alone(r: Request, ell: float = 1.0, undo_cap: int = 1024, stream=None,
+              cells: str = "lattice"):
     """The same request on its own: ecmc_run_to_breakpoint with the budget."""
     s = r.start
-    sysm = ecmc.System(s.x, s.y, s.active, s.box, ell, undo_cap=undo_cap, stream=stream)
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, ell, undo_cap=undo_cap, stream=stream,
+                       cells_per_side=int(s.m) if cells == "lattice" else 0)
     total = 0
     while total < r.budget:
         before = sysm.stats()["liftings"]
@@ -210,3 +229,19 @@ def run_alone(r: Request, ell: float = 1.0, undo_cap: int = 1024, stream=None):
     out = sysm.positions()
     sysm.close()
     return out, total
+
+
+def run_alone_timed(r: Request, ell: float = 1.0, undo_cap: int = 1024, stream=None,
+                    cells: str = "lattice") -> tuple[int, float]:
+    """The same request on its own, as few launches as the budget allows
+    (ecmc_run_to_breakpoint with the budget); returns (liftings, device ms)."""
+    s = r.start
+    sysm = ecmc.System(s.x, s.y, s.active, s.box, ell, undo_cap=undo_cap, stream=stream,
+                       cells_per_side=int(s.m) if cells == "lattice" else 0)
+    try:
+        while sysm.stats()["liftings"] < r.budget:
+            sysm.run(1 << 20, event_budget=r.budget - sysm.stats()["liftings"])
+        st = sysm.stats()
+    finally:
+        sysm.close()
+    return st["liftings"], st["device_ms"]

@@ -34,20 +34,26 @@ def test_binding_structs_match_header_sizes(tmp_path):
     the header's structs."""
     import ctypes as C
     import subprocess
+    structs = {"ecmc_params": ecmc.ecmc_params, "ecmc_stats_t": ecmc.ecmc_stats_t,
+               "ecmc_profile_t": ecmc.ecmc_profile_t}
+    lines = []
+    for name, cls in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {f[0]}));')
+    lines.append('printf("%zu\\n", sizeof(ecmc_lift_t));')
     src = tmp_path / "sz.c"
-    src.write_text(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "ecmc.h"\n'
-        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(ecmc_params), '
-        'sizeof(ecmc_stats_t), sizeof(ecmc_lift_t), offsetof(ecmc_stats_t, row_windows), '
-        'offsetof(ecmc_stats_t, device_bytes)); return 0; }\n')
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ecmc.h"\n'
+                   'int main(void) {\n' + "\n".join(lines) + '\nreturn 0; }\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
-    p, st, lift, o_row, o_bytes = map(int, subprocess.check_output([str(exe)]).split())
-    assert C.sizeof(ecmc.ecmc_params) == p
-    assert C.sizeof(ecmc.ecmc_stats_t) == st
-    assert ecmc.LIFT_DTYPE.itemsize == lift
-    assert ecmc.ecmc_stats_t.row_windows.offset == o_row
-    assert ecmc.ecmc_stats_t.device_bytes.offset == o_bytes
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for cls in structs.values():
+        want.append(C.sizeof(cls))
+        want.extend(getattr(cls, f[0]).offset for f in cls._fields_)
+    want.append(ecmc.LIFT_DTYPE.itemsize)
+    assert got == want
 
 
 def test_create_rejects_bad_parameters_without_gpu():

@@ -45,6 +45,7 @@ def oracle_graph(start, ell, n_legs, windows=1):
                             d=start.d, windows=windows, search=2)
     flags = np.array([r.flag for r in legs], dtype=np.uint8)
     log = np.concatenate([r.log for r in legs])
+    last.window_flags = int(sum(int(r.wflags.sum()) for r in legs))
     return flags, last, log
 
 
@@ -61,6 +62,7 @@ def assert_graph_parity(start, ell, n_legs, windows=1):
     for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
         assert np.array_equal(a[f], b[f]), f
     assert st["liftings"] == len(olog)
+    assert st["conflict_windows"] == last.window_flags
     assert st["horizon_asserts"] == 0
     assert st["order_errors"] == 0
     return gf, st
@@ -218,6 +220,7 @@ def test_restart_mode_equals_oracle(kind, seed):
     o = chain_order(olog)
     for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
         assert np.array_equal(o[f], log[f]), f
+    assert st["conflict_windows"] == last.window_flags == int(of.sum())
     assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
 
 

@@ -33,6 +33,7 @@ def run_oracle(start, ell, n_legs, nc=0, windows=1):
                             d=start.d, nc=ncell, windows=windows)
     flags = np.array([r.flag for r in legs], dtype=np.uint8)
     log = np.concatenate([r.log for r in legs]) if legs else np.zeros(0, O.LIFT_DTYPE)
+    last.window_flags = int(sum(int(r.wflags.sum()) for r in legs))
     return flags, last, log
 
 
@@ -55,6 +56,8 @@ def assert_parity(start, ell, n_legs, nc=0, windows=1):
     for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
         assert np.array_equal(a[f], b[f]), f
     assert st["liftings"] == len(olog)
+    # per-window flags (windows whose isolated claim sets met), counted
+    assert st["conflict_windows"] == last.window_flags
     assert st["horizon_asserts"] == 0
     assert st["order_errors"] == 0
     return gf, st

@@ -38,6 +38,7 @@ def oracle(start, ell, n_legs, windows=1, search=1, nc=0):
                             d=start.d, nc=ncell, windows=windows, search=search)
     flags = np.array([r.flag for r in legs], dtype=np.uint8)
     log = np.concatenate([r.log for r in legs])
+    last.window_flags = int(sum(int(r.wflags.sum()) for r in legs))
     return flags, last, log
 
 
@@ -57,6 +58,8 @@ def same(g, o):
     for f in ("leg", "c", "i", "j", "t", "tau", "xi", "xj"):
         assert np.array_equal(a[f], b[f]), f
     assert st["liftings"] == len(olog)
+    # the per-window flags: windows whose isolated claim sets met
+    assert st["conflict_windows"] == last.window_flags
     assert st["horizon_asserts"] == 0 and st["order_errors"] == 0
 
 

@@ -46,16 +46,25 @@ def test_batched_replicas_equal_alone_and_oracle():
         assert np.array_equal(finals[q][2], last.active)
 
 
-def test_autotune_picks_and_caches(tmp_path):
-    reps = batch.make_replicas(8, seed=9, n_range=(256, 2048))
+def test_autotune_picks_and_caches(tmp_path, monkeypatch):
+    reps = batch.make_replicas(8, seed=9, n_range=(1024, 4096))
     cache = str(tmp_path / "tune.json")
-    got = batch.autotune(reps, trial_budget=2000, cell_factors=(1.0, 1.5), legs_options=(2, 8),
-                         cache=cache)
-    assert got["cell_factor"] in (1.0, 1.5) and got["legs_per_launch"] in (2, 8)
-    assert len(got["trials"]) == 4 and all(t["liftings_per_s"] > 0 for t in got["trials"])
+    got = batch.autotune(reps, trial_budget=2000, cells_options=("lattice", "default"),
+                         pass_options=(True, False), legs_options=(2, 8), cache=cache)
+    assert got["cells"] in ("lattice", "default") and got["legs_per_launch"] in (2, 8)
+    assert got["rowpass"] in (True, False)
+    assert len(got["trials"]) == 8 and all(t["liftings_per_s"] > 0 for t in got["trials"])
+    # the row pass runs where the cells are aligned with the lattice
+    assert any(t["row_windows"] > 0 for t in got["trials"] if t["rowpass"] and t["cells"] == "lattice")
+    assert all(t["row_windows"] == 0 for t in got["trials"] if not t["rowpass"])
     again = batch.autotune(reps, cache=cache)  # served from the cache, no trials run
-    assert again["cell_factor"] == got["cell_factor"]
-    assert again["legs_per_launch"] == got["legs_per_launch"]
+    assert (again["cells"], again["rowpass"], again["legs_per_launch"]) == \
+        (got["cells"], got["rowpass"], got["legs_per_launch"])
+    # another GPU or library build: the cached choice does not apply
+    monkeypatch.setattr(batch, "_hardware_key", lambda: "other-gpu_other-build")
+    fresh = batch.autotune(reps, trial_budget=2000, cells_options=("lattice",),
+                           pass_options=(True,), legs_options=(2,), cache=cache)
+    assert len(fresh["trials"]) == 1 and fresh["key"].startswith("other-gpu_other-build")
 
 
 def test_server_mix_equals_alone():
@@ -63,7 +72,9 @@ def test_server_mix_equals_alone():
                                budget_range=(2e3, 5e4))
     serve.prepare(reqs)
     # a budget that holds about three of them at once forces queueing
-    need = sorted(serve.device_bytes(r.n, r.k, r.start.box) for r in reqs)
+    probe = serve.Server(hbm_budget_bytes=1, slice_legs=4)
+    need = sorted(probe.need(r) for r in reqs)
+    probe.close()
     srv = serve.Server(hbm_budget_bytes=sum(need[-3:]), slice_legs=4, keep_results=True)
     try:
         st = srv.serve(reqs)
@@ -94,3 +105,26 @@ def test_server_poisson_arrivals_complete():
     assert st.completed == 6
     assert all(lat >= 0 for lat in st.latencies)
     assert all(r.done >= r.admitted >= r.arrival for r in reqs)
+
+
+def test_context_bytes_are_what_a_context_holds():
+    """ecmc_context_bytes (nothing allocated) equals the device_bytes of the
+    created context, and the device's free memory drops by that much (to the
+    allocator's granularity)."""
+    import torch
+    from paper_2004_11040_gb300 import synth
+    for m, k, cells in ((64, 64, 64), (256, 512, 0), (512, 512, 512)):
+        s = synth.lattice_start(m, 0.70, k, seed=1)
+        need = serve.device_bytes(m * m, k, s.box, undo_cap=256, cells_per_side=cells)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, undo_cap=256, cells_per_side=cells)
+        sysm.positions()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        got = sysm.stats()["device_bytes"]
+        sysm.close()
+        assert got == need, (m, got, need)
+        drop = free0 - free1
+        assert need - (4 << 20) <= drop <= need + (8 << 20), (m, drop, need)
+
