@@ -167,11 +167,15 @@ int ecmc_run_to_breakpoint(ecmc_ctx *ctx, int32_t n_legs, uint64_t event_budget,
                            uint8_t *leg_flags_out, int32_t *legs_done);
 
 /*
- * ecmc_positions -- copies the current configuration to host arrays
- * (caller-owned; any pointer may be NULL to skip it):
- *   x, y, t  n doubles each, indexed by disk id; t is leg-relative.
+ * ecmc_positions -- copies the current configuration to host arrays: the
+ * lifted configuration {C_h, A_h} at the last breakpoint (Sec. 2.1; Alg. 2's
+ * output), with the local times of Remark 1 (every disk a chain moved in the
+ * last leg carries the time of its last event or stall, measured from the
+ * leg's start h, so t_i <= ell):
+ *   x, y, t  n doubles each, indexed by disk id (caller-owned; any pointer
+ *            may be NULL to skip it); t is leg-relative.
  *   active   k ints: chain c's active (stalled) disk.
- * Synchronises the context's stream.
+ * Synchronises the context's stream. Errors: EINVAL (null ctx), ECUDA.
  */
 int ecmc_positions(ecmc_ctx *ctx, double *x, double *y, double *t, int32_t *active);
 
@@ -203,9 +207,12 @@ int ecmc_set_direction(ecmc_ctx *ctx, int32_t direction);
  */
 int ecmc_set_wait_limit(ecmc_ctx *ctx, uint64_t ns);
 
-/* ecmc_stats -- counters accumulated since ecmc_create (Sec. 2.1's liftings
- * and the flags of reading Eq. 2 as a claim conflict), host struct owned by
- * the caller. Errors: EINVAL (null argument). */
+/* ecmc_stats -- counters accumulated since ecmc_create, into a host struct
+ * owned by the caller: liftings are the events of Eq. 1 (Sec. 2.1; stalls are
+ * not events), legs the breakpoints reached (Alg. 2), and the conflict
+ * counters read the horizon condition of Eq. 2 as a claim conflict between
+ * chains (Sec. 3.4: the violations whose probability grows with the number
+ * of chains). Errors: EINVAL (null argument). */
 int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out);
 
 /*
@@ -276,7 +283,10 @@ int ecmc_batch_run(ecmc_batch *b, ecmc_ctx *const *ctxs, int32_t n_ctx, int32_t 
 const char *ecmc_batch_last_error(const ecmc_batch *b);
 void ecmc_batch_destroy(ecmc_batch *b);
 
-/* ecmc_destroy -- frees every device allocation of ctx (NULL is a no-op). */
+/* ecmc_destroy -- frees every device allocation of ctx (NULL is a no-op) after
+ * the work queued on its stream has finished; the configuration is lost
+ * (read it first with ecmc_positions). The paper's programs keep their state
+ * for the whole run; this is the end of a run (Alg. 1 after its last leg). */
 void ecmc_destroy(ecmc_ctx *ctx);
 
 /* ecmc_last_error -- reason for the last failure on ctx ("" if none); the
@@ -290,6 +300,9 @@ const char *ecmc_last_error(const ecmc_ctx *ctx);
  * the device heap, real-time loops that may not pay allocation latency, and
  * plug-ins that are handed pointers only. The paper has no counterpart; this
  * is a deployment convenience.
+ *
+ * The call is synchronous: it returns after the leg has finished on the
+ * device (it reads the leg's counters back to decide on the repairs).
  *
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call, on
  * the device or the host). Its working memory is one file-scope device array

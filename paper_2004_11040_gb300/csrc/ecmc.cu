@@ -1023,6 +1023,39 @@ __global__ void k_leg_begin(Dev s) {
     if (c < s.k) leg_begin_chain(s, c);
 }
 
+// leg_begin_chain by a warp: the lanes clear the local times of the chain's
+// records in parallel (one round trip for up to 32 records), lane 0 sets the
+// chain table. Returns (on lane 0) whether the table named the disk that its
+// active slot holds (the chain-table invariant).
+__device__ bool leg_begin_chain_warp(const Dev &s, int c, int lane) {
+    const int32_t nr = s.nrec[c];
+    double *const ct = s.ct;
+    for (int32_t e = lane; e < nr; e += 32) {
+        const Rec *q = rec_at(s, c, e);
+        const uint32_t to = q->to, j = q->j, jl = q->jloc;
+        ct[to] = 0.0;
+        if (j != NONE) ct[jl] = 0.0;
+    }
+    bool ok = true;
+    if (lane == 0) {
+        const uint32_t loc = s.aloc[c];
+        const uint32_t id = s.cid[loc];
+        const uint32_t id_was = s.ci[c];
+        ok = id == id_was;
+        s.cown[loc] = OWN_ACTIVE | (uint32_t)c;
+        s.ci[c] = id;
+        s.aloc0[c] = loc;
+        s.D[c] = s.ell;
+        s.tc[c] = 0.0;
+        s.status[c] = ST_RUNNING;
+        s.partner[c] = -1;
+        s.nrec[c] = 0;
+        s.nlift[c] = 0;
+    }
+    __syncwarp();
+    return ok;
+}
+
 // Pass 1 of a claim window [tw, tend): one warp runs chain c from its current
 // state through its events before tend, until it stalls, pauses at tend or
 // meets a conflict.
@@ -1890,7 +1923,7 @@ struct RepCtl {
     int32_t pad2;
 };
 
-enum { G_WORK = 0, G_ANY, G_ERR, G_REMAIN0, G_REMAIN1, G_N };
+enum { G_WORK = 0, G_ANY, G_ERR, G_REMAIN0, G_REMAIN1, G_UFDONE, G_N };
 enum { PH_BEGIN = 0, PH_PASS1, PH_REPAIR, PH_END, PH_N };
 
 struct Batch {
@@ -1938,29 +1971,18 @@ __device__ __forceinline__ bool rep_on(const Batch &b, int r) {
     return b.ctl[r].live && !b.ctl[r].done;
 }
 
+// A replica with no liftings budget runs every leg of the launch: its next
+// leg is begun by its chains at this leg's end (one grid barrier and one pass
+// over the chains fewer). With a budget, the leg's totals decide first.
+__device__ __forceinline__ bool next_leg_at_end(const Batch &b, int r, int leg) {
+    return b.ctl[r].budget == 0 && leg + 1 < b.max_legs;
+}
+
 // A thread's index for per-chain loops that spreads consecutive chains over
 // the blocks (and so over the SMs): with chains on consecutive threads a few
 // blocks would carry all the memory operations of a phase.
 __device__ __forceinline__ int spread_index() {
     return (int)(threadIdx.x * gridDim.x + blockIdx.x);
-}
-
-// Invariant: a running or stalled chain's table slot holds its active disk.
-__device__ void check_chains(const Batch &b, int gt, int nthreads, int total_chains, int where) {
-    (void)gt;
-    for (int w = spread_index(); w < total_chains; w += nthreads) {
-        const int r = find_rep(b.chain_base, b.R, w);
-        if (!rep_on(b, r)) continue;
-        const Dev &s = b.reps[r];
-        const int c = w - b.chain_base[r];
-        if (s.status[c] == ST_BLOCKED) continue;
-        if (s.cid[s.aloc[c]] != s.ci[c]) {
-            if (atomicAdd(&b.ctl[r].incons, 1) == 0) {
-                b.ctl[r].bad_where = where;
-                b.ctl[r].bad_chain = c;
-            }
-        }
-    }
 }
 
 // Claim words cleared by the whole grid for the next window (pointers held
@@ -2015,6 +2037,7 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     __shared__ int warp_tot[32];
     __shared__ int tot[2];
     __shared__ int sflag;
+    __shared__ unsigned long long blk_lifts;
     __shared__ Dev wdev[RUN_THREADS / 32];  // per warp: its system's description
     __shared__ int wrep[RUN_THREADS / 32];
     if ((threadIdx.x & 31) == 0) wrep[threadIdx.x >> 5] = -1;
@@ -2036,33 +2059,97 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             t_prev = t;
         }
     };
+    // true in the last block to get here, of all blocks (each block comes
+    // once per use): that block finishes a phase's serial tail without a grid
+    // barrier before it; it sees every other block's writes of the phase
+    auto last_block = [&]() -> bool {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int old = atomicAdd(b.g + G_UFDONE, 1);
+            sflag = (old + 1) % (int)gridDim.x == 0;
+        }
+        __syncthreads();
+        const bool last = sflag != 0;
+        __syncthreads();
+        if (last) __threadfence();
+        return last;
+    };
+    // conflict components of replica r (one block): round 1 from the
+    // parallel pass's blocked chains, later rounds from the aborts
+    auto uf_replica = [&](int r, int round) {
+        // the block's copy of the system: warp 0's slot
+        if (threadIdx.x < 32) (void)warp_dev(wdev, wrep, b.reps, r);
+        __syncthreads();
+        const Dev &s = wdev[0];
+        bool need = false;
+        if (rep_on(b, r)) {
+            const unsigned long long wbl = s.lc[LC_WBLOCKED];
+            need = round == 1 ? wbl != 0ull : s.ctl[CTL_NABORT] != 0;
+            // the window's flag: the claim sets of two chains met
+            if (round == 1 && threadIdx.x == 0 && (wbl != 0ull || s.lc[LC_WWEAK] != 0ull))
+                atomicAdd(s.lc + LC_CWINDOWS, 1ull);
+        }
+        if (need && round <= 255) {
+            uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
+        } else if (threadIdx.x == 0) {
+            s.ctl[CTL_NCOMP] = 0;
+            if (need) b.ctl[r].err = 1;  // too many rounds
+        }
+        __syncthreads();
+    };
+    // prefix of component counts over replicas (one block)
+    auto comp_prefix = [&]() {
+        const int chunk = (R + blockDim.x - 1) / blockDim.x;
+        const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
+        int sum = 0;
+        for (int r = lo; r < hi; ++r) sum += b.reps[r].ctl[CTL_NCOMP];
+        int off = block_exscan(sum, warp_tot, tot);
+        for (int r = lo; r < hi; ++r) {
+            b.comp_base[r] = off;
+            off += b.reps[r].ctl[CTL_NCOMP];
+            // every block read the abort counts (the last round's check, this
+            // round's need) before it counted itself
+            b.reps[r].ctl[CTL_NABORT] = 0;
+        }
+        if (threadIdx.x == 0) {
+            b.comp_base[R] = tot[0];
+            b.g[G_WORK] = 0;
+            b.g[G_ANY] = tot[0];
+        }
+    };
     for (int leg = 0; leg < b.max_legs; ++leg) {
+        // parity of the row-pass counters of the leg's window w: that of the
+        // window's index counted over the launch's legs
+        const int p0 = (leg * b.windows) & 1;
         // leg start: chain table, local times, claims, per-leg counters; the
-        // chains whose rows are in reach (they rule out the row pass)
-        for (int w = spread_index(); w < total_chains; w += nthreads) {
-            const int r = find_rep(b.chain_base, R, w);
-            if (rep_on(b, r)) {
-                const Dev &s = b.reps[r];
-                const int c = w - b.chain_base[r];
-                leg_begin_chain(s, c);
-                if (s.rp_ok && skip_of(s, s.aloc[c]) != RP_SKIP_ALL) atomicAdd(s.rp + RP_BAD, 1);
+        // chains whose rows are in reach (they rule out the row pass). The
+        // replicas whose last leg began this one skip it.
+        bool begin_here = false;
+        for (int r = 0; r < R; ++r)
+            if (rep_on(b, r) && !(leg > 0 && next_leg_at_end(b, r, leg - 1))) begin_here = true;
+        if (begin_here) {
+            for (int w2 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; w2 < total_chains;
+                 w2 += nwarps) {
+                const int r = find_rep(b.chain_base, R, w2);
+                if (rep_on(b, r) && !(leg > 0 && next_leg_at_end(b, r, leg - 1))) {
+                    const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
+                    const int c = w2 - b.chain_base[r];
+                    (void)leg_begin_chain_warp(s, c, lane);
+                    if (lane == 0 && s.rp_ok && skip_of(s, s.aloc[c]) != RP_SKIP_ALL)
+                        atomicAdd(s.rp + RP_BAD + p0, 1);
+                }
             }
+            // (claim words were cleared at the end of the last leg, the
+            // row-pass counters by its totals)
+            for (int r = 0; r < R; ++r)
+                if (rep_on(b, r) && !(leg > 0 && next_leg_at_end(b, r, leg - 1)) && gt < LC_N)
+                    b.reps[r].lc[gt] = 0ull;
+            if (!grid_barrier(b, &sflag)) return;
         }
-        for (int r = 0; r < R; ++r) {
-            if (!rep_on(b, r)) continue;
-            const Dev &s = b.reps[r];
-            // (claim words were cleared at the end of the last leg)
-            if (gt < LC_N) s.lc[gt] = 0ull;
-            if (gt == 0) {
-                s.rp[RP_BAD + 1] = 0;
-                s.rp[RP_ABORT + 1] = 0;
-            }
-        }
-        if (!grid_barrier(b, &sflag)) return;
         mark(PH_BEGIN);
-        if (gt == 0) b.g[G_REMAIN0 + ((leg + 1) & 1)] = 0;
         for (int w = 0; w < b.windows; ++w) {
-            const int par = w & 1;
+            const int par = (p0 + w) & 1;
             if (w > 0) {
                 // new claim window: claims, the window's blocked count, the
                 // chains whose rows are in reach; the other parity's row-pass
@@ -2107,9 +2194,13 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                 }
             }
             if (!grid_barrier(b, &sflag)) return;
+            // the next leg's count of replicas to go (every block has read the
+            // last leg's count, the same word, before this barrier)
+            if (w == 0 && gt == 0) b.g[G_REMAIN0 + ((leg + 1) & 1)] = 0;
             // row pass: the cells another chain holds, publication, claim
             // words; a cancelled one runs pass1_chain now
             int row_here = 0;
+            bool uf_early = false;
             for (int r = threadIdx.x; r < R; r += blockDim.x)
                 if (rep_on(b, r) && b.reps[r].rp_ok && b.reps[r].rp[RP_BAD + par] == 0)
                     row_here = 1;
@@ -2126,70 +2217,49 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                     else
                         row_resolve_chain<C>(s, c, tw);
                 }
+                if (R == 1) {
+                    // one system: the last block to finish resolving takes
+                    // the first round's union-find and prefix (one grid
+                    // barrier for both)
+                    if (last_block()) {
+                        uf_replica(0, 1);
+                        comp_prefix();
+                    }
+                    uf_early = true;
+                }
                 if (!grid_barrier(b, &sflag)) return;
             }
             mark(PH_PASS1);
-            check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 1);
             // the row pass's claim arrays back to empty where the chains
-            // claimed (every cell after a cancelled row pass); the union-find
-            // of this phase leaves most blocks idle
-            for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
-                const int r = find_rep(b.chain_base, R, w2);
-                if (!rep_on(b, r)) continue;
-                const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
-                if (!(s.rp_ok && s.rp[RP_BAD + par] == 0) || __ldcg(s.rp + RP_ABORT + par) != 0)
-                    continue;
-                row_reset_chain<C>(s, w2 - b.chain_base[r]);
-            }
-            for (int r = 0; r < R; ++r) {
-                if (!rep_on(b, r)) continue;
-                const Dev &s = b.reps[r];
-                if (s.rp_ok && s.rp[RP_BAD + par] == 0 && __ldcg(s.rp + RP_ABORT + par) != 0)
-                    clear_row_claims(s, gt, nthreads);
+            // claimed (every cell after a cancelled row pass), before the
+            // next window's pass; after the leg's last window the leg end
+            // does it
+            if (w + 1 < b.windows) {
+                for (int w2 = lw * gridDim.x + blockIdx.x; w2 < total_chains; w2 += nwarps) {
+                    const int r = find_rep(b.chain_base, R, w2);
+                    if (!rep_on(b, r)) continue;
+                    const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
+                    if (!(s.rp_ok && s.rp[RP_BAD + par] == 0) ||
+                        __ldcg(s.rp + RP_ABORT + par) != 0)
+                        continue;
+                    row_reset_chain<C>(s, w2 - b.chain_base[r]);
+                }
+                for (int r = 0; r < R; ++r) {
+                    if (!rep_on(b, r)) continue;
+                    const Dev &s = b.reps[r];
+                    if (s.rp_ok && s.rp[RP_BAD + par] == 0 && __ldcg(s.rp + RP_ABORT + par) != 0)
+                        clear_row_claims(s, gt, nthreads);
+                }
             }
             // repair rounds
             for (int round = 1;; ++round) {
-                for (int r = blockIdx.x; r < R; r += gridDim.x) {
-                    // the block's copy of the system: warp 0's slot
-                    if (threadIdx.x < 32) (void)warp_dev(wdev, wrep, b.reps, r);
-                    __syncthreads();
-                    const Dev &s = wdev[0];
-                    bool need = false;
-                    if (rep_on(b, r))
-                        need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull : s.ctl[CTL_NABORT] != 0;
-                    // the window's flag: the claim sets of two chains met
-                    if (round == 1 && threadIdx.x == 0 && rep_on(b, r) &&
-                        (s.lc[LC_WBLOCKED] != 0ull || s.lc[LC_WWEAK] != 0ull))
-                        s.lc[LC_CWINDOWS] += 1ull;
-                    if (need && round <= 255) {
-                        uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
-                    } else if (threadIdx.x == 0) {
-                        s.ctl[CTL_NCOMP] = 0;
-                        if (need) b.ctl[r].err = 1;  // too many rounds
-                    }
-                    __syncthreads();
+                if (!(round == 1 && uf_early)) {
+                    for (int r = blockIdx.x; r < R; r += gridDim.x) uf_replica(r, round);
+                    // the last block to finish its union-finds takes the
+                    // prefix: no grid barrier between
+                    if (last_block()) comp_prefix();
+                    if (!grid_barrier(b, &sflag)) return;
                 }
-                if (!grid_barrier(b, &sflag)) return;
-                if (blockIdx.x == 0) {
-                    // prefix of component counts over replicas
-                    const int chunk = (R + blockDim.x - 1) / blockDim.x;
-                    const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
-                    int sum = 0;
-                    for (int r = lo; r < hi; ++r) sum += b.reps[r].ctl[CTL_NCOMP];
-                    int off = block_exscan(sum, warp_tot, tot);
-                    for (int r = lo; r < hi; ++r) {
-                        b.comp_base[r] = off;
-                        off += b.reps[r].ctl[CTL_NCOMP];
-                        // every block read the abort counts before the barrier above
-                        b.reps[r].ctl[CTL_NABORT] = 0;
-                    }
-                    if (threadIdx.x == 0) {
-                        b.comp_base[R] = tot[0];
-                        b.g[G_WORK] = 0;
-                        b.g[G_ANY] = tot[0];
-                    }
-                }
-                if (!grid_barrier(b, &sflag)) return;
                 const int ncomp = b.g[G_ANY];
                 if (ncomp == 0) break;
                 for (;;) {
@@ -2203,7 +2273,6 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
                                         window_end(s, w));
                 }
                 if (!grid_barrier(b, &sflag)) return;
-                check_chains(b, gt, nthreads, total_chains, leg * 65536 + w * 16 + 2 + round);
                 // no component met another chain: the window is repaired
                 int aborted = 0;
                 for (int r = threadIdx.x; r < R; r += blockDim.x)
@@ -2217,35 +2286,72 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
         // The claim words are cleared for the next leg here, off the next
         // leg's begin (whose few dependent loads per chain would queue
         // behind the stores)
-        for (int r = 0; r < R; ++r)
-            if (rep_on(b, r)) clear_claims(b.reps[r], gt, nthreads);
-        for (int w0 = (((int)threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32; w0 < total_chains;
-             w0 += nthreads) {
-            const int w = w0 + lane;
-            int r = -1;
+        // (and the row pass's claim arrays of the last window: where the
+        // chains claimed, or every cell after a cancelled row pass)
+        const int pl = (p0 + b.windows - 1) & 1;
+        for (int r = 0; r < R; ++r) {
+            if (!rep_on(b, r)) continue;
+            const Dev &s = b.reps[r];
+            clear_claims(s, gt, nthreads);
+            if (s.rp_ok && s.rp[RP_BAD + pl] == 0 && __ldcg(s.rp + RP_ABORT + pl) != 0)
+                clear_row_claims(s, gt, nthreads);
+        }
+        // one chain per warp (the next leg's start clears the chain's records
+        // lane-parallel); with one system the block adds its liftings at once
+        if (threadIdx.x == 0) blk_lifts = 0ull;
+        __syncthreads();
+        for (int w2 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; w2 < total_chains;
+             w2 += nwarps) {
+            const int r = find_rep(b.chain_base, R, w2);
+            if (!rep_on(b, r)) continue;
+            const Dev &s = warp_dev(my_dev, my_rep, b.reps, r);
+            const int c = w2 - b.chain_base[r];
+            if (s.rp_ok && s.rp[RP_BAD + pl] == 0 && __ldcg(s.rp + RP_ABORT + pl) == 0)
+                row_reset_chain<C>(s, c);
             int32_t nl = 0;
-            if (w < total_chains) {
-                r = find_rep(b.chain_base, R, w);
-                if (rep_on(b, r))
-                    nl = leg_end_chain(b.reps[r], w - b.chain_base[r],
-                                       (int32_t)(b.ctl[r].leg_index0 + b.ctl[r].legs), false);
-                else
-                    r = -1;
+            if (lane == 0)
+                nl = leg_end_chain(s, c, (int32_t)(b.ctl[r].leg_index0 + b.ctl[r].legs), false);
+            __syncwarp();
+            bool ok = true;
+            if (next_leg_at_end(b, r, leg)) {
+                ok = leg_begin_chain_warp(s, c, lane);
+                if (lane == 0 && s.rp_ok && skip_of(s, s.aloc[c]) != RP_SKIP_ALL)
+                    atomicAdd(s.rp + RP_BAD + (((leg + 1) * b.windows) & 1), 1);
+            } else if (lane == 0) {
+                ok = s.cid[s.aloc[c]] == s.ci[c];
             }
-            const int r0 = __shfl_sync(FULL, r, 0);
-            if (r0 >= 0 && __all_sync(FULL, r == r0 || r < 0)) {
-                const unsigned tot = __reduce_add_sync(FULL, (unsigned)nl);
-                if (lane == 0 && tot) atomicAdd(b.reps[r0].lc + LC_LIFTS, (unsigned long long)tot);
-            } else if (r >= 0 && nl) {
-                atomicAdd(b.reps[r].lc + LC_LIFTS, (unsigned long long)nl);
+            if (lane == 0) {
+                // chain table against the cells (must hold: every chain has
+                // stalled on the disk its slot names)
+                if (!ok && atomicAdd(&b.ctl[r].incons, 1) == 0) {
+                    b.ctl[r].bad_where = leg * 65536 + (b.windows - 1) * 16 + 15;
+                    b.ctl[r].bad_chain = c;
+                }
+                if (nl) {
+                    if (R == 1)
+                        atomicAdd(&blk_lifts, (unsigned long long)nl);
+                    else
+                        atomicAdd(s.lc + LC_LIFTS, (unsigned long long)nl);
+                }
             }
         }
-        if (!grid_barrier(b, &sflag)) return;
-        for (int r = gt; r < R; r += nthreads) {
-            RepCtl &c = b.ctl[r];
+        __syncthreads();
+        if (R == 1 && threadIdx.x == 0 && blk_lifts)
+            atomicAdd(b.reps[0].lc + LC_LIFTS, blk_lifts);
+        // the last block to finish takes the totals (one grid barrier for
+        // both)
+        const bool totals_here = last_block();
+        for (int r = threadIdx.x; totals_here && r < R; r += blockDim.x) {
+            // (the control block, the counters and the pointers read into
+            // registers first: one round trip, not one per field)
+            RepCtl *const cp = b.ctl + r;
+            RepCtl c = *cp;
             if (!(c.live && !c.done)) continue;
-            const Dev &s = b.reps[r];
-            const unsigned long long *lc = s.lc;
+            unsigned long long *const lcp = b.reps[r].lc;
+            int32_t *const rpp = b.reps[r].rp;
+            unsigned long long lc[LC_N];
+#pragma unroll
+            for (int q = 0; q < LC_N; ++q) lc[q] = __ldcg(lcp + q);
             const int flag = lc[LC_BLOCKED] != 0ull || lc[LC_WEAK] != 0ull;
             if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
             c.lifts += (int64_t)lc[LC_LIFTS];
@@ -2262,10 +2368,22 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
             c.order_err += (int64_t)lc[LC_ORDER];
             if (lc[LC_ERR_CAP] || lc[LC_ERR_REC]) c.err = 1;
             if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
-            s.rp[RP_BAD] = 0;
-            s.rp[RP_BAD + 1] = 0;
-            s.rp[RP_ABORT] = 0;
-            s.rp[RP_ABORT + 1] = 0;
+            const bool next_begun = c.budget == 0 && leg + 1 < b.max_legs;
+            *cp = c;
+            // per-leg counters back to zero for the next leg; the row-pass
+            // counters of the leg's last window (a next leg begun above has
+            // counted into the other parity)
+#pragma unroll
+            for (int q = 0; q < LC_N; ++q) lcp[q] = 0ull;
+            if (next_begun) {
+                rpp[RP_BAD + pl] = 0;
+                rpp[RP_ABORT + pl] = 0;
+            } else {
+                rpp[RP_BAD] = 0;
+                rpp[RP_BAD + 1] = 0;
+                rpp[RP_ABORT] = 0;
+                rpp[RP_ABORT + 1] = 0;
+            }
             if (!c.done) atomicAdd(b.g + G_REMAIN0 + (leg & 1), 1);
         }
         if (!grid_barrier(b, &sflag)) return;

@@ -125,10 +125,43 @@ __device__ void rp_load(const Dev &s, const RowChain &ch, RowLane &w, int pos) {
     w.colx = s.colx[col];
 }
 
+// L2 prefetch of the G columns that follow the window (offsets off .. off +
+// G - 1 from the chain's start column): the slot arrays of the active row,
+// the row-skip bits and the column bounds that the next slide loads. After
+// the L2 flush between launches every window's first touch would otherwise
+// wait on DRAM (a chain moves forward, never back, within a leg).
+template <int C>
+__device__ __forceinline__ void rp_prefetch(const Dev &s, const RowChain &ch, int off) {
+    constexpr int G = 32 / C;
+    const int lane = threadIdx.x & 31;
+    const int e = lane >> 2, f = lane & 3;  // column off + e (e < 8), field pair f
+    if (e >= G) return;
+    int col = ch.u0 + off + e;
+    while (col >= s.nc) col -= s.nc;
+    const uint32_t loc = ((uint32_t)ch.row * (uint32_t)s.nc + (uint32_t)col) * C;
+    const void *p0, *p1;
+    if (f == 0) {
+        p0 = s.cx + loc;
+        p1 = s.cy + loc;
+    } else if (f == 1) {
+        p0 = s.ct + loc;
+        p1 = s.cid + loc;
+    } else if (f == 2) {
+        p0 = s.cown + loc;
+        p1 = s.cskp + loc;
+    } else {
+        p0 = s.xbound + col;
+        p1 = s.colx + col;
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p0));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p1));
+}
+
 // Next disk in x order within the window (by window position, then x) and b
 // towards it, for every lane: one FP64 instruction sequence for all lanes.
 template <int C>
-__device__ void rp_links(const Dev &s, const RowChain &ch, RowLane &w) {
+__device__ void rp_links(const Dev &s, const RowChain &ch, RowLane &w, int *nx_raw = nullptr,
+                         int *rank_out = nullptr) {
     constexpr int G = 32 / C;
     const int lane = threadIdx.x & 31, g = lane / C, q = lane % C;
     const int v = (g - ch.gbase) & (G - 1);
@@ -167,6 +200,8 @@ __device__ void rp_links(const Dev &s, const RowChain &ch, RowLane &w) {
         }
     }
     w.nx = nx;
+    if (nx_raw) *nx_raw = nx;
+    if (rank_out) *rank_out = rank;
     // the same operations as scan_step: |y_target - y_active| (one row: no
     // periodic image), then sqrt(d^2 - ay^2)
     const double yn = __shfl_sync(FULL, w.y, nx >= 0 ? nx : lane);
@@ -174,6 +209,168 @@ __device__ void rp_links(const Dev &s, const RowChain &ch, RowLane &w) {
     w.bok = nx >= 0 && dbits(ay) < dbits(s.d);
     w.b = __dsqrt_rn(__dsub_rn(s.d2, __dmul_rn(ay, ay)));
     if (!w.bok) w.nx = -1;
+}
+
+// Rare FP64 fix-ups, out of line: the compiler then never evaluates them on
+// the common path (each FP64 instruction occupies the FP64 unit ~64 cycles).
+__device__ __noinline__ double rp_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __noinline__ double rp_sub(double a, double b) { return __dsub_rn(a, b); }
+
+// Each lane's step decided ahead, as the step would decide it, for the
+// moment its disk becomes the active one (rp_prep): RP_PREP_OK when the
+// predicted target is certain (the step's own test would find no candidate
+// in doubt, the scan ends inside the window), with the target's lane and
+// the scanned columns; the step then takes the lift whenever tau < D.
+// Between slides the window changes only behind the active disk (a moved
+// disk lands at contact with the next one), so what a lane's step reads --
+// its disk, the disks after it, their owners and columns -- is as at the
+// slide.
+constexpr uint32_t RP_PREP_OK = 1u << 31;
+constexpr uint32_t RP_PREP_CELL = 1u << 30;  // bits 16-20: the slot the moved disk takes
+
+template <int C>
+__device__ void rp_prep(const Dev &s, const StopK &sk, const RowChain &ch, const RowLane &w,
+                        int nxr, int rnk, double &ptau, double &pxn, uint32_t &pinfo) {
+    constexpr int G = 32 / C;
+    const int lane = threadIdx.x & 31, g = lane / C;
+    const int v = (g - ch.gbase) & (G - 1);
+    const bool occ = w.id != EMPTY;
+    const int nx = w.nx;
+    // the predicted target (the next disk in x order) and the disk after it
+    const int src = nx >= 0 ? nx : lane;
+    const double xn = __shfl_sync(FULL, w.x, src);
+    const uint32_t ownn = __shfl_sync(FULL, w.own, src);
+    const int tzn = __shfl_sync(FULL, (int)(dbits(w.t) != 0ull), src);
+    const uint32_t skn = __shfl_sync(FULL, w.skp, src);
+    const int nx2 = __shfl_sync(FULL, nxr, src);
+    const int src2 = (nx >= 0 && nx2 >= 0) ? nx2 : lane;
+    const double xn2 = __shfl_sync(FULL, w.x, src2);
+    const int vn = ((src / C) - ch.gbase) & (G - 1);
+    const int vn2 = ((src2 / C) - ch.gbase) & (G - 1);
+    // window ranks (position, then x) of the disks of other chains
+    const int R = v * C + rnk;
+    const unsigned nsR = __reduce_or_sync(FULL, (occ && w.own != OWN_STATIC) ? (1u << R) : 0u);
+    // lazy frame (a target with t != 0), and a target whose rows are in
+    // reach (the row pass cancels there), are left to the step
+    bool ok = occ && nx >= 0 && ownn == OWN_STATIC && !tzn && skn == RP_SKIP_ALL;
+    // tau of the target, with the step's operations
+    double dx = __dsub_rn(xn, w.x);
+    const bool wl = ok && dneg(dx) && vn > v;
+    if (__any_sync(FULL, wl) && wl) dx = rp_add(dx, s.L);
+    double tau = __dsub_rn(dx, w.b);
+    if (dneg(tau)) tau = 0.0;
+    const unsigned long long cur = dbits(tau);
+    // the stop rule with best = tau: the scan reaches the target's column and
+    // stops inside the window
+    const double fx = __dsub_rn(w.x, w.colx);
+    const float fxf = d2f_trunc(fx);
+    const float lim_f = __fadd_rn(d2f_trunc(tau), sk.epsf);
+    const int mp = vn - v;
+    int mstop = G;
+    if (ok) {
+        if (mp >= 1 && beyond_k(sk, mp, fx, fxf, lim_f, cur)) ok = false;
+        for (int m = mp + 1; ok && m < G - v; ++m)
+            if (beyond_k(sk, m, fx, fxf, lim_f, cur)) {
+                mstop = m;
+                break;
+            }
+        if (mstop >= G - v) ok = false;
+    }
+    // no other chain's disk after this one in the scanned columns (the
+    // target included), and the next candidate's lower bound dx - d above tau
+    // (every later one's is larger: RN is monotone)
+    if (ok) {
+        const int lim = (v + mstop) * C;
+        const unsigned inrange = lim >= 32 ? ~0u : ((1u << lim) - 1u);
+        const unsigned after = R >= 31 ? 0u : ~((2u << R) - 1u);
+        if (nsR & inrange & after) ok = false;
+    }
+    const bool chk2 = ok && nx2 >= 0 && vn2 < v + mstop;
+    if (__any_sync(FULL, chk2) && chk2) {
+        double dx2 = __dsub_rn(xn2, w.x);
+        if (dneg(dx2) && vn2 > v) dx2 = rp_add(dx2, s.L);
+        const double sub2 = __dsub_rn(dx2, sk.d);
+        if (dneg(sub2) || !(dbits(sub2) > cur)) ok = false;
+    }
+    // the moved disk's new cell: its own column (same slot) or the next one
+    // (its lowest empty slot; that column is as at the slide)
+    double xnew = __dadd_rn(w.x, tau);
+    const bool wrap = ok && !(dbits(xnew) < dbits(s.L));
+    if (__any_sync(FULL, wrap) && wrap) xnew = rp_sub(xnew, s.L);
+    const unsigned long long xb = dbits(xnew);
+    const int g1 = ((g + 1) & (G - 1)) * C;
+    const unsigned long long xlo1 = shfl_u64(w.xlo, g1), xhi1 = shfl_u64(w.xhi, g1);
+    const unsigned em = __ballot_sync(FULL, w.id == EMPTY);
+    uint32_t cell = 0u;
+    if (ok) {
+        if (xb >= w.xlo && xb < w.xhi) {
+            cell = RP_PREP_CELL | ((uint32_t)lane << 16);
+        } else if (v + 1 < G && xb >= xlo1 && xb < xhi1) {
+            const unsigned m1 = em & (((1u << C) - 1u) << g1);
+            if (m1) cell = RP_PREP_CELL | ((uint32_t)(__ffs(m1) - 1) << 16);
+        }
+    }
+    ptau = tau;
+    pxn = xnew;
+    pinfo = ok ? (RP_PREP_OK | cell | (uint32_t)nx | ((uint32_t)mstop << 8)) : 0u;
+}
+
+// The continuation's steps decided ahead where D does not enter: the
+// target (static, rows out of reach, t_i + tau moves the disk within its
+// slot) and tau, the disk's fx, its window rank, and whether the candidate
+// after the target has its lower bound above tau. The scan to D, the owners
+// and the cells' holders over it, and Eq. 2 are the batch's, per step.
+constexpr uint32_t RC_PREP_OK = 1u << 31;
+constexpr uint32_t RC_PREP_NX2OK = 1u << 30;
+
+template <int C>
+__device__ void rc_prep(const Dev &s, const RowChain &ch, const RowLane &w, int nxr, int rnk,
+                        double &ptau, double &pxn, double &pfx, int &pR, unsigned &nsR,
+                        uint32_t &pinfo) {
+    constexpr int G = 32 / C;
+    const int lane = threadIdx.x & 31, g = lane / C;
+    const int v = (g - ch.gbase) & (G - 1);
+    const bool occ = w.id != EMPTY;
+    const int nx = w.nx;
+    const int src = nx >= 0 ? nx : lane;
+    const double xn = __shfl_sync(FULL, w.x, src);
+    const uint32_t ownn = __shfl_sync(FULL, w.own, src);
+    const uint32_t skn = __shfl_sync(FULL, w.skp, src);
+    const int nx2 = __shfl_sync(FULL, nxr, src);
+    const int src2 = (nx >= 0 && nx2 >= 0) ? nx2 : lane;
+    const double xn2 = __shfl_sync(FULL, w.x, src2);
+    const int vn = ((src / C) - ch.gbase) & (G - 1);
+    const int vn2 = ((src2 / C) - ch.gbase) & (G - 1);
+    pR = v * C + rnk;
+    nsR = __reduce_or_sync(FULL, (occ && w.own != OWN_STATIC) ? (1u << pR) : 0u);
+    bool ok = occ && nx >= 0 && ownn == OWN_STATIC && skn == RP_SKIP_ALL;
+    double dx = __dsub_rn(xn, w.x);
+    const bool wl = ok && dneg(dx) && vn > v;
+    if (__any_sync(FULL, wl) && wl) dx = rp_add(dx, s.L);
+    double tau = __dsub_rn(dx, w.b);
+    // (a negative dx - b is the step's: Eq. 2 there reads the unclamped value)
+    if (dneg(tau)) {
+        tau = 0.0;
+        ok = false;
+    }
+    pfx = __dsub_rn(w.x, w.colx);
+    bool nx2ok = true;
+    const bool chk2 = ok && nx2 >= 0;
+    if (__any_sync(FULL, chk2) && chk2) {
+        double dx2 = __dsub_rn(xn2, w.x);
+        if (dneg(dx2) && vn2 > v) dx2 = rp_add(dx2, s.L);
+        const double sub2 = __dsub_rn(dx2, s.d);
+        nx2ok = !dneg(sub2) && dbits(sub2) > dbits(tau);
+    }
+    // the moved disk stays in its slot (else the step below)
+    double xnew = __dadd_rn(w.x, tau);
+    const bool wrap = ok && !(dbits(xnew) < dbits(s.L));
+    if (__any_sync(FULL, wrap) && wrap) xnew = rp_sub(xnew, s.L);
+    if (ok && !(dbits(xnew) >= w.xlo && dbits(xnew) < w.xhi)) ok = false;
+    ptau = tau;
+    pxn = xnew;
+    const uint32_t p2 = (nx2 >= 0 && ok) ? (uint32_t)vn2 : 31u;
+    pinfo = ok ? (RC_PREP_OK | (nx2ok ? RC_PREP_NX2OK : 0u) | (uint32_t)nx | (p2 << 8)) : 0u;
 }
 
 struct RowStep {
@@ -348,10 +545,6 @@ __device__ __forceinline__ void rp_claim(const Dev &s, RowChain &ch, int first, 
     ch.front = last;
 }
 
-// Rare FP64 fix-ups, out of line: the compiler then never evaluates them on
-// the common path (each FP64 instruction occupies the FP64 unit ~64 cycles).
-__device__ __noinline__ double rp_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __noinline__ double rp_sub(double a, double b) { return __dsub_rn(a, b); }
 
 // The stop rule for the column offsets 1 .. mmax - 1 from the active disk's
 // column, one per lane: bit m is beyond(m, cur) (FP32 image; exact FP64 for
@@ -419,25 +612,61 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
     }
     RowLane w;
     rp_load<C>(s, ch, w, gme);
+    rp_prefetch<C>(s, ch, G);
     ch.li = (int)(aloc % C);  // position 0 is group 0
     int vi = 0;
+    // claims of prepared steps, held until their column leaves the window:
+    // lane q < 3 of a column's group claims row q - 1 of it (the key of the
+    // first step that scanned it, as rp_claim computes it)
+    const int qrow = lane % C;
+    uint32_t prowb;
+    {
+        int r = ch.row + qrow - 1;
+        if (r < 0) r += s.nc;
+        if (r >= s.nc) r -= s.nc;
+        prowb = (uint32_t)r * (uint32_t)s.nc;
+    }
+    unsigned long long pk = ~0ull;
+    auto flush = [&](int vmax) {  // the held claims of window positions < vmax
+        const int vq = (gme - ch.gbase) & (G - 1);
+        if (pk != ~0ull && vq < vmax) {
+            int col = ch.u0 + ch.wbase + vq;
+            while (col >= s.nc) col -= s.nc;
+            const uint32_t cell = prowb + (uint32_t)col;
+            const uint32_t cm = (uint32_t)c + 1u;
+            red_min_u64(s.ckey + cell, pk);
+            red_min_u32(s.camin + cell, cm);
+            red_max_u32(s.camax + cell, cm);
+            pk = ~0ull;
+        }
+    };
     ch.xi = __shfl_sync(FULL, w.x, ch.li);
     ch.yi = __shfl_sync(FULL, w.y, ch.li);
     ch.iskp = __shfl_sync(FULL, w.skp, ch.li);
     ch.fx = __dsub_rn(ch.xi, __shfl_sync(FULL, w.colx, ch.li));
-    rp_links<C>(s, ch, w);
+    double ptau, pxn;  // this lane's step, decided ahead (rp_prep)
+    uint32_t pinfo;
+    {
+        int nxr, rnk;
+        rp_links<C>(s, ch, w, &nxr, &rnk);
+        rp_prep<C>(s, sk, ch, w, nxr, rnk, ptau, pxn, pinfo);
+    }
     int nx = __shfl_sync(FULL, w.nx, ch.li);
     double bnx = __shfl_sync(FULL, w.b, ch.li);
     // slides the window by h columns (the active disk's column moves to
     // position vi - h); false if the window would reach the start column
     auto slide = [&](int h) -> bool {
         if (ch.wbase + h + G > far_cols) return false;
+        flush(h);
         const int v0 = (gme - ch.gbase) & (G - 1);
         ch.wbase += h;
         ch.gbase = (ch.gbase + h) & (G - 1);
         if (v0 < h) rp_load<C>(s, ch, w, v0 + G - h);
+        rp_prefetch<C>(s, ch, ch.wbase + G);
         vi -= h;
-        rp_links<C>(s, ch, w);
+        int nxr, rnk;
+        rp_links<C>(s, ch, w, &nxr, &rnk);
+        rp_prep<C>(s, sk, ch, w, nxr, rnk, ptau, pxn, pinfo);
         nx = __shfl_sync(FULL, w.nx, ch.li);
         bnx = __shfl_sync(FULL, w.b, ch.li);
         return true;
@@ -445,12 +674,133 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
     int end = RP_END_PAUSE;
     uint32_t ns_owner = NONE;
     bool ok = ch.iskp == RP_SKIP_ALL;
+    // slide once the active column reaches SLIDE_AT: a step's scan reads its
+    // own column and the next one or two (a scan that would leave the window
+    // slides first, below)
+    constexpr int SLIDE_AT = G > 4 ? G - 2 : G / 2;
+    auto v_of_lane = [&](int l) { return ((l / C) - ch.gbase) & (G - 1); };
     while (ok) {
-        if (vi >= G / 2 && !slide(vi)) {
+        if (vi >= SLIDE_AT && !slide(vi)) {
             ok = false;
             break;
         }
         const int v = (gme - ch.gbase) & (G - 1);
+        // a batch of prepared steps that keep the moved disk in its slot: the
+        // chain through them in uniform registers (the target, tau, the
+        // claims, t_i + tau and D - tau), then each step's record and window
+        // update by the lane of the disk that moved, all at once
+        {
+            int lk = ch.li, K = 0, front = ch.front;
+            double t = ch.ti, D = ch.D;
+            bool pause = false;
+            int my_k = -1, my_front = 0;
+            double my_t = 0.0, my_tn = 0.0, my_dn = 0.0;
+            for (;;) {
+                const uint32_t info = __shfl_sync(FULL, pinfo, lk);
+                if ((info & (RP_PREP_OK | RP_PREP_CELL)) != (RP_PREP_OK | RP_PREP_CELL) ||
+                    (int)((info >> 16) & 31u) != lk)
+                    break;
+                const int vk = ((lk / C) - ch.gbase) & (G - 1);
+                if (K > 0 && vk >= SLIDE_AT) break;
+                if (ch.nrec0 + ch.n + K >= cap) break;
+                const double tau = __shfl_sync(FULL, ptau, lk);
+                if (!(dbits(tau) < dbits(D))) break;  // a stall: the step below
+                const double tn = __dadd_rn(t, tau);
+                if (dbits(tn) < dbits(tw)) break;     // (never: the step below reports it)
+                const int last = ch.wbase + vk + (int)((info >> 8) & 31u) - 1;
+                if (last > front) {
+                    const int oabs = ch.wbase + v;
+                    if (qrow < 3 && oabs > front && oabs <= last)
+                        pk = rp_key(c, t, v - vk, qrow != 1);
+                    front = last;
+                }
+                if (!(dbits(tn) < dbits(tend))) {  // pauses at the window end
+                    pause = true;
+                    break;
+                }
+                const double dn = __dsub_rn(D, tau);
+                if (lane == lk) {
+                    my_k = K;
+                    my_t = t;
+                    my_tn = tn;
+                    my_dn = dn;
+                    my_front = front;
+                }
+                t = tn;
+                D = dn;
+                ++K;
+                lk = (int)(info & 31u);
+            }
+            if (K > 0) {
+                // the records, with the targets' fields as they were
+                const int nxl = w.nx;
+                const int srcp = my_k >= 0 ? nxl : lane;
+                const double xp = __shfl_sync(FULL, w.x, srcp);
+                const double tp = __shfl_sync(FULL, w.t, srcp);
+                const uint32_t idp = __shfl_sync(FULL, w.id, srcp);
+                if (my_k >= 0) {
+                    const uint32_t from = rp_loc_of<C>(s, ch, lane);
+                    const uint32_t jloc = rp_loc_of<C>(s, ch, nxl);
+                    const uint32_t e = (uint32_t)(ch.nrec0 + ch.n + my_k);
+                    ulonglong2 *q = (ulonglong2 *)rec_at(s, c, (int32_t)e);
+                    q[0] = make_ulonglong2((unsigned long long)w.id | ((unsigned long long)from << 32),
+                                           (unsigned long long)from | ((unsigned long long)idp << 32));
+                    q[1] = make_ulonglong2((unsigned long long)jloc | ((unsigned long long)e << 32),
+                                           (unsigned long long)(uint32_t)my_front << 32);
+                    q[2] = make_ulonglong2(dbits(w.x), dbits(my_t));
+                    q[3] = make_ulonglong2(dbits(tp), dbits(my_tn));
+                    q[4] = make_ulonglong2(dbits(ptau), dbits(pxn));
+                    q[5] = make_ulonglong2(dbits(xp), dbits(my_dn));
+                    // the disk moved within its slot and is static now
+                    w.x = pxn;
+                    w.t = my_tn;
+                    w.own = OWN_STATIC;
+                    w.nx = -1;
+                    w.bok = 0;
+                } else if (lane == lk) {
+                    w.t = t;
+                    w.own = OWN_ACTIVE | (uint32_t)c;
+                }
+                ch.n += K;
+                ch.lifts += K;
+                ch.front = front;
+                ch.li = lk;
+                ch.i = __shfl_sync(FULL, w.id, lk);
+                ch.xi = __shfl_sync(FULL, w.x, lk);
+                ch.yi = __shfl_sync(FULL, w.y, lk);
+                ch.ti = t;
+                ch.D = D;
+                ch.fx = __dsub_rn(ch.xi, __shfl_sync(FULL, w.colx, lk));
+                vi = v_of_lane(lk);
+                nx = __shfl_sync(FULL, w.nx, lk);
+                bnx = __shfl_sync(FULL, w.b, lk);
+            } else if (pause) {
+                ch.front = front;
+            }
+            if (pause) break;
+            if (K > 0) continue;
+        }
+        RowStep rs;
+        // the step decided at the slide (the common case), else below
+        bool fast = false;
+        const uint32_t pinf = __shfl_sync(FULL, pinfo, ch.li);
+        {
+            if (pinf & RP_PREP_OK) {
+                const double tp = __shfl_sync(FULL, ptau, ch.li);
+                if (dbits(tp) < dbits(ch.D)) {
+                    fast = true;
+                    rs.lift = 1;
+                    rs.p = (int)(pinf & 31u);
+                    rs.tau = tp;
+                    rs.mstop = (int)((pinf >> 8) & 31u);
+                    rs.nonstatic = 0;
+                    rs.ns_owner = NONE;
+                    rs.overflow = 0;
+                    rs.viol = 0;
+                }
+            }
+        }
+        if (!fast) {
         const float fxf = d2f_trunc(ch.fx);
         const bool occ = w.id != EMPTY;
         // prediction: the next disk in x order (nx), b towards it cached
@@ -489,7 +839,6 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
             }
             if (__any_sync(FULL, bad)) exact = true;
         }
-        RowStep rs;
         if (exact) {
             rs = rp_exact<C>(s, sk, ch, w, vi, fxf);
             if (rs.overflow) {
@@ -507,7 +856,18 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
             rs.overflow = 0;
             rs.viol = 0;
         }
-        rp_claim(s, ch, ch.wbase + vi, ch.wbase + vi + rs.mstop - 1, rowb);
+        }
+        if (fast) {
+            const int last = ch.wbase + vi + rs.mstop - 1;
+            if (last > ch.front) {
+                const int oabs = ch.wbase + v;
+                if (qrow < 3 && oabs > ch.front && oabs <= last)
+                    pk = rp_key(c, ch.ti, v - vi, qrow != 1);
+                ch.front = last;
+            }
+        } else {
+            rp_claim(s, ch, ch.wbase + vi, ch.wbase + vi + rs.mstop - 1, rowb);
+        }
         if (rs.nonstatic) {
             end = RP_END_NONSTATIC;
             ns_owner = rs.ns_owner;
@@ -543,23 +903,28 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
         }
         if (dbits(xnew) >= dbits(LL)) xnew = rp_sub(xnew, LL);
         // the moved disk's new cell: a column of the window at or after its own
-        const unsigned long long xb = dbits(xnew);
-        const unsigned hm =
-            __ballot_sync(FULL, lane % C == 0 && v >= vi && xb >= w.xlo && xb < w.xhi);
-        if (!hm) {
-            ok = false;
-            break;
-        }
-        const int gn = (__ffs(hm) - 1) / C;
+        // (decided at the slide for a prepared step)
         int ln = ch.li;
-        if (gn != ch.li / C) {
-            const unsigned em =
-                __ballot_sync(FULL, w.id == EMPTY) & (((1u << C) - 1u) << (gn * C));
-            if (!em) {
+        if (fast && (pinf & RP_PREP_CELL)) {
+            ln = (int)((pinf >> 16) & 31u);
+        } else {
+            const unsigned long long xb = dbits(xnew);
+            const unsigned hm =
+                __ballot_sync(FULL, lane % C == 0 && v >= vi && xb >= w.xlo && xb < w.xhi);
+            if (!hm) {
                 ok = false;
                 break;
             }
-            ln = __ffs(em) - 1;
+            const int gn = (__ffs(hm) - 1) / C;
+            if (gn != ch.li / C) {
+                const unsigned em =
+                    __ballot_sync(FULL, w.id == EMPTY) & (((1u << C) - 1u) << (gn * C));
+                if (!em) {
+                    ok = false;
+                    break;
+                }
+                ln = __ffs(em) - 1;
+            }
         }
         // the event record (as commit_step writes it; pad: the scan's last
         // column): the target's lane stores the words that carry its fields,
@@ -637,6 +1002,7 @@ __device__ bool row_pass_chain(const Dev &s, int c, double tw, double tend) {
         ch.fx = fxn;
     }
     if (!ok) return false;
+    flush(G);
     // the end of the speculative run, for row_resolve_chain
     if (lane == 0) {
         s.rp_n[c] = ch.n;
@@ -902,12 +1268,25 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
         cok = hold >= 0 && mem;
     };
     load(gme);
+    rp_prefetch<C>(s, ch, G);
     members();
     int vi = 0;
     ch.fx = __dsub_rn(ch.xi, __shfl_sync(FULL, w.colx, ch.li));
-    rp_links<C>(s, ch, w);
+    // this lane's step decided ahead where D does not enter (rc_prep)
+    double ptau, pxn, pfx;
+    int pR;
+    unsigned nsR, cokm;
+    uint32_t pinfo;
+    auto links = [&]() {
+        int nxr, rnk;
+        rp_links<C>(s, ch, w, &nxr, &rnk);
+        rc_prep<C>(s, ch, w, nxr, rnk, ptau, pxn, pfx, pR, nsR, pinfo);
+        cokm = __ballot_sync(FULL, cok);
+    };
+    links();
     int nx = __shfl_sync(FULL, w.nx, ch.li);
     double bnx = __shfl_sync(FULL, w.b, ch.li);
+    auto v_of_lane = [&](int l) { return ((l / C) - ch.gbase) & (G - 1); };
     for (;;) {
         if (vi >= G / 2) {
             if (ch.wbase + vi + G > nc) return RC_GENERAL;
@@ -916,13 +1295,156 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
             ch.wbase += h;
             ch.gbase = (ch.gbase + h) & (G - 1);
             if (v0 < h) load(v0 + G - h);
+            rp_prefetch<C>(s, ch, ch.wbase + G);
             members();
             vi = 0;
-            rp_links<C>(s, ch, w);
+            links();
             nx = __shfl_sync(FULL, w.nx, ch.li);
             bnx = __shfl_sync(FULL, w.b, ch.li);
         }
         const int v = (gme - ch.gbase) & (G - 1);
+        // a batch of steps that lift within their slots: per step in uniform
+        // registers the scan to D (its columns all held by members, no other
+        // chain's disk after the active one in them, the candidate after the
+        // target above tau), Eq. 2 on every scanned disk with t_j != 0 (lane
+        // by lane), t_i + tau and D - tau; then each step's record and cell
+        // writes by the lane of the disk that moved, all at once. What the
+        // batch cannot decide is left to the step below.
+        {
+            int lk = ch.li, K = 0;
+            double t = ch.ti, D = ch.D;
+            bool pause = false;
+            int my_k = -1;
+            double my_t = 0.0, my_tn = 0.0, my_dn = 0.0;
+            for (;;) {
+                const uint32_t ci = __shfl_sync(FULL, pinfo, lk);
+                if (!(ci & RC_PREP_OK)) break;
+                const int vk = v_of_lane(lk);
+                if (K > 0 && vk >= G / 2) break;
+                if (nrec + K >= cap) break;
+                const double tau = __shfl_sync(FULL, ptau, lk);
+                if (!(dbits(tau) < dbits(D))) break;  // a stall: the step below
+                // the scan to D: its columns
+                const double fxk = __shfl_sync(FULL, pfx, lk);
+                const float fxfk = d2f_trunc(fxk);
+                const float limk = __fadd_rn(d2f_trunc(D), sk.epsf);
+                int mst = 1;
+                while (mst < G - vk && !beyond_k(sk, mst, fxk, fxfk, limk, dbits(D))) ++mst;
+                if (mst >= G - vk) break;
+                const int pp = (int)(ci & 31u);
+                if (v_of_lane(pp) - vk >= mst) break;
+                unsigned sm = 0u;
+                for (int m = 0; m < mst; ++m)
+                    sm |= ((1u << C) - 1u) << (((ch.gbase + vk + m) & (G - 1)) * C);
+                if (sm & ~cokm) break;
+                const int Rk = __shfl_sync(FULL, pR, lk);
+                {
+                    const int lim = (vk + mst) * C;
+                    const unsigned inrange = lim >= 32 ? ~0u : ((1u << lim) - 1u);
+                    const unsigned after = Rk >= 31 ? 0u : ~((2u << Rk) - 1u);
+                    if (nsR & inrange & after) break;
+                }
+                if ((int)((ci >> 8) & 31u) < vk + mst && !(ci & RC_PREP_NX2OK)) break;
+                // Eq. 2 on the scanned disks with t_j != 0 (the target by its tau)
+                const bool cz = w.id != EMPTY && pR > Rk && v < vk + mst && dbits(w.t) != 0ull;
+                if (__any_sync(FULL, cz)) {
+                    const double xk = __shfl_sync(FULL, w.x, lk);
+                    bool bad = false;
+                    if (cz) {
+                        double sb = tau;
+                        if (lane != pp) {
+                            double dx = __dsub_rn(w.x, xk);
+                            if (dneg(dx) && v > vk) dx = rp_add(dx, LL);
+                            sb = __dsub_rn(dx, dd);
+                        }
+                        bad = dneg(sb) || !(dbits(__dadd_rn(t, sb)) > dbits(w.t));
+                    }
+                    if (__any_sync(FULL, bad)) break;
+                }
+                const double tn = __dadd_rn(t, tau);
+                if (!(dbits(tn) < dbits(tend))) {  // pauses at the window end
+                    pause = true;
+                    break;
+                }
+                if (dbits(tn) < dbits(tw)) break;
+                const double dn = __dsub_rn(D, tau);
+                if (lane == lk) {
+                    my_k = K;
+                    my_t = t;
+                    my_tn = tn;
+                    my_dn = dn;
+                }
+                t = tn;
+                D = dn;
+                ++K;
+                lk = pp;
+            }
+            if (K > 0) {
+                const int nxl = w.nx;
+                const int srcp = my_k >= 0 ? nxl : lane;
+                const double xp = __shfl_sync(FULL, w.x, srcp);
+                const double tp = __shfl_sync(FULL, w.t, srcp);
+                const uint32_t idp = __shfl_sync(FULL, w.id, srcp);
+                if (my_k >= 0) {
+                    const uint32_t from = rp_loc_of<C>(s, ch, lane);
+                    const uint32_t jloc = rp_loc_of<C>(s, ch, nxl);
+                    const uint32_t seq = ((uint32_t)round << 24) | (cnt + (uint32_t)my_k);
+                    ulonglong2 *q = (ulonglong2 *)rec_at(s, c, nrec + my_k);
+                    q[0] = make_ulonglong2((unsigned long long)w.id | ((unsigned long long)from << 32),
+                                           (unsigned long long)from | ((unsigned long long)idp << 32));
+                    q[1] = make_ulonglong2((unsigned long long)jloc | ((unsigned long long)seq << 32),
+                                           0ull);
+                    q[2] = make_ulonglong2(dbits(w.x), dbits(my_t));
+                    q[3] = make_ulonglong2(dbits(tp), dbits(my_tn));
+                    q[4] = make_ulonglong2(dbits(ptau), dbits(pxn));
+                    q[5] = make_ulonglong2(dbits(xp), dbits(my_dn));
+                    // the disk moved within its slot and is static now
+                    s.cx[from] = pxn;
+                    s.ct[from] = my_tn;
+                    s.cown[from] = OWN_STATIC;
+                    w.x = pxn;
+                    w.t = my_tn;
+                    w.own = OWN_STATIC;
+                    w.nx = -1;
+                    w.bok = 0;
+                } else if (lane == lk) {
+                    const uint32_t al = rp_loc_of<C>(s, ch, lane);
+                    s.cown[al] = OWN_ACTIVE | (uint32_t)c;
+                    s.ct[al] = t;
+                    w.t = t;
+                    w.own = OWN_ACTIVE | (uint32_t)c;
+                }
+                if (lane == 0) {
+                    s.nrec[c] = nrec + K;
+                    atomicAdd(s.nlift + c, K);
+                }
+                __syncwarp();
+                nrec += K;
+                cnt += (uint32_t)K;
+                ch.li = lk;
+                ch.i = __shfl_sync(FULL, w.id, lk);
+                ch.xi = __shfl_sync(FULL, w.x, lk);
+                ch.yi = __shfl_sync(FULL, w.y, lk);
+                ch.ti = t;
+                ch.D = D;
+                ch.fx = __shfl_sync(FULL, pfx, lk);
+                vi = v_of_lane(lk);
+                nx = __shfl_sync(FULL, w.nx, lk);
+                bnx = __shfl_sync(FULL, w.b, lk);
+                r.iloc = rp_loc_of<C>(s, ch, lk);
+                r.i = ch.i;
+                r.xi = ch.xi;
+                r.yi = ch.yi;
+                r.ti = t;
+                r.D = D;
+                r.skip = __shfl_sync(FULL, w.skp, lk);
+            }
+            if (pause) {
+                st = ST_RUNNING;
+                return RC_DONE;
+            }
+            if (K > 0) continue;
+        }
         const float fxf = d2f_trunc(ch.fx);
         const bool occ = w.id != EMPTY;
         // the scan runs to D: its columns
