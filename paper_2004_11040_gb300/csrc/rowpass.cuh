@@ -1105,55 +1105,53 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
             }
         }
     }
-    // publish records 0 .. sfail - 1 in order (their fields gathered by the
-    // lanes first; lane 0 stores)
+    // publish records 0 .. sfail - 1: their final effect, one record per
+    // lane. Each record's disk moved once (the chain only moves forward), its
+    // destination was an empty slot, and a target's own record (the next one)
+    // rewrites it: so the slots vacated by a cell change are emptied first,
+    // then every record writes its disk's new slot, and the target of the
+    // last one becomes the chain's active disk. (A vacated slot keeps its
+    // other fields: an empty slot's fields are never read.)
     int pub_lifts = 0;
     for (int e0 = 0; e0 < sfail; e0 += 32) {
         const int e = e0 + lane;
-        uint32_t ri = 0, rfrom = 0, rto = 0, rj = NONE, rjl = 0, rskp = 0;
-        double rx = 0.0, rt = 0.0, ry = 0.0;
         if (e < sfail) {
             const Rec &q = *rec_at(s, c, nrec0 + e);
-            ri = q.i;
-            rfrom = q.from;
-            rto = q.to;
-            rj = q.j;
-            rjl = q.jloc;
-            rx = q.xi;
-            rt = q.t;
-            ry = s.cy[rfrom];
-            rskp = s.cskp[rfrom];
-        }
-        pub_lifts += __popc(__ballot_sync(FULL, e < sfail && rj != NONE));
-        const int cnt = min(32, sfail - e0);
-        for (int u = 0; u < cnt; ++u) {
-            const uint32_t i = __shfl_sync(FULL, ri, u), from = __shfl_sync(FULL, rfrom, u);
-            const uint32_t to = __shfl_sync(FULL, rto, u), j = __shfl_sync(FULL, rj, u);
-            const uint32_t jl = __shfl_sync(FULL, rjl, u), skp = __shfl_sync(FULL, rskp, u);
-            const double x = __shfl_sync(FULL, rx, u), t = __shfl_sync(FULL, rt, u);
-            const double y = __shfl_sync(FULL, ry, u);
-            if (lane == 0) {
-                const uint32_t own = j != NONE ? OWN_STATIC : (OWN_STALLED | (uint32_t)c);
-                if (j != NONE) {
-                    s.cown[jl] = OWN_ACTIVE | (uint32_t)c;
-                    s.ct[jl] = t;
-                }
-                if (to != from) {
-                    s.cx[to] = x;
-                    s.cy[to] = y;
-                    s.cskp[to] = (uint8_t)skp;
-                    s.ct[to] = t;
-                    s.cown[to] = own;
-                    s.cid[to] = i;
-                    s.cid[from] = EMPTY;
-                } else {
-                    s.cx[from] = x;
-                    s.ct[from] = t;
-                    s.cown[from] = own;
-                }
-            }
+            if (q.to != q.from) s.cid[q.from] = EMPTY;
         }
     }
+    __syncwarp();
+    for (int e0 = 0; e0 < sfail; e0 += 32) {
+        const int e = e0 + lane;
+        uint32_t rj = NONE;
+        if (e < sfail) {
+            const Rec &q = *rec_at(s, c, nrec0 + e);
+            const uint32_t i = q.i, from = q.from, to = q.to, jl = q.jloc;
+            const double x = q.xi, t = q.t;
+            rj = q.j;
+            const uint32_t own = rj != NONE ? OWN_STATIC : (OWN_STALLED | (uint32_t)c);
+            if (to != from) {
+                const double y = s.cy[from];
+                const uint8_t skp = s.cskp[from];
+                s.cx[to] = x;
+                s.cy[to] = y;
+                s.cskp[to] = skp;
+                s.ct[to] = t;
+                s.cown[to] = own;
+                s.cid[to] = i;
+            } else {
+                s.cx[from] = x;
+                s.ct[from] = t;
+                s.cown[from] = own;
+            }
+            if (e == sfail - 1 && rj != NONE) {
+                s.cown[jl] = OWN_ACTIVE | (uint32_t)c;
+                s.ct[jl] = t;
+            }
+        }
+        pub_lifts += __popc(__ballot_sync(FULL, e < sfail && rj != NONE));
+    }
+    __syncwarp();
     // the chain's state
     const bool blocked = lost >= 0 || end == RP_END_NONSTATIC;
     if (lane == 0) {
