@@ -159,8 +159,9 @@ __device__ __forceinline__ uint32_t cell_of(double x, double y, const Dev &s) {
 }
 
 // v rounded toward zero to FP32 on the integer pipe (a conversion on this
-// chip's FP64 pipe would occupy it ~18 cycles per warp instruction, with
-// ~100 cycles of dependent latency): relative error below 2^-23, and
+// chip's FP64 pipe would occupy it ~64 cycles per warp instruction, whatever
+// the lane mask, with ~60 cycles of dependent latency): relative error below
+// 2^-23, and
 // |v| < 2^-126 gives 0.
 __device__ __forceinline__ float d2f_trunc(double v) {
     const unsigned long long b = dbits(v);
