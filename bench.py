@@ -16,7 +16,7 @@ The default run also measures, each with the same timing rules:
   graph_mode      the headline workload in constraint-graph mode (ECMC_GRAPH,
                   Sec. 3.1), with its own roofline and e2e;
   config3_sweep   k in {256, 1024, 4096, 16384} chains (n / sqrt(N) = 1/4 ..
-                  16): liftings/s, roofline, claim windows, conflict rates;
+                  16), W = 1: liftings/s, roofline, conflict rates;
   batched         512 replicas (N log-uniform in [1024, 65536], eta uniform
                   in [0.60, 0.74], k = sqrt(N)) to 10^6 liftings each in
                   persistent launches over all of them; and, on the same 512
@@ -76,7 +76,7 @@ def parse():
                    help="graph mode: conflicts by restart strategy 2 (Sec. 3.4) instead of "
                         "the local repair")
     p.add_argument("--windows", type=int, default=0,
-                   help="claim windows per leg (0: 1 up to 4096 chains, else 2; graph 1)")
+                   help="claim windows per leg (0: one window, the measured best)")
     p.add_argument("--workload", default="lattice",
                    choices=["lattice", "batched", "serve", "conflicts"])
     p.add_argument("--quick", action="store_true",
@@ -110,11 +110,9 @@ def windows_for(a, search, k=None):
     k = a.k if k is None else k
     if a.windows > 0:
         return a.windows
-    if search == "graph":
-        return 1
-    # measured (N = 2^20 lattices, W in 1, 2, 4): one window up to k = 4096,
-    # two at k = 16384
-    return 1 if k <= 4096 else 2
+    # measured on N = 2^20 lattices (W in 1, 2, 16, 64): one window per leg is the
+    # fastest at every k in both searches
+    return 1
 
 
 def cells_of(a):
