@@ -116,13 +116,14 @@ int ecmc_create(const ecmc_params *p, const double *x, const double *y,
                 const int32_t *active, void *stream, ecmc_ctx **out);
 
 /*
- * ecmc_context_bytes -- the device memory a cell-scan context created with
- * *p would hold, without allocating anything: its pooled arrays (cells, chain
- * table, event records, claims) and the scratch of ecmc_positions, i.e. the
- * device_bytes that ecmc_stats reports once positions have been read. (The
- * persistent launch's scratch, a few kilobytes per system, is not included.)
- * A scheduler admits systems by it. The paper has no counterpart.
- * Errors: EINVAL (bad parameters, or ECMC_GRAPH).
+ * ecmc_context_bytes -- the device memory a context created with *p would
+ * hold, without allocating anything: its arrays (cells, chain table, event
+ * records, claims; with ECMC_GRAPH the disk records, arrows and the graph
+ * build's scratch instead of the cells) and the scratch of ecmc_positions,
+ * i.e. the device_bytes that ecmc_stats reports once positions have been
+ * read. (The persistent launch's scratch, a few kilobytes per system, is not
+ * included.) A scheduler admits systems by it. The paper has no counterpart.
+ * Errors: EINVAL (bad parameters).
  */
 int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes);
 
@@ -138,9 +139,10 @@ int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes);
  * the cell scan, i.e. of Alg. 2. Claims are taken on the disks a step reads
  * (the active disk and its arrow targets) instead of cells, so a leg's flag
  * is 1 iff in some window the disks that two chains read, each run alone,
- * overlap. Limits: n_chains <= 2^20 - 2; such contexts cannot be batched
- * (ecmc_batch_run returns EINVAL). cells_per_side only sets the cell scan
- * that builds the graph.
+ * overlap. Limits: n_chains <= 2^20 - 2. Such contexts are batched with
+ * each other only (their own persistent kernel; same claim windows, no
+ * ECMC_RESTART). cells_per_side only sets the cell scan that builds the
+ * graph.
  *
  * Conflicts. Within a claim window every chain claims, with atomicCAS, each
  * cell it scans; two chains that want one cell "meet". A leg's flag is 1 iff
@@ -264,7 +266,9 @@ int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out);
  *
  * ecmc_batch_create -- launch scratch for batches, queued on `stream`.
  * ecmc_batch_run    -- runs up to max_legs legs of each of the n_ctx contexts
- *   (distinct, same cell slots C; their streams are synchronised first).
+ *   (distinct; all cell-scan contexts with the same cell slots C and claim
+ *   windows, or all constraint-graph contexts with the same claim windows and
+ *   without ECMC_RESTART; their streams are synchronised first).
  *   budgets       host, n_ctx liftings or NULL: a context stops at the first
  *                 breakpoint at which its liftings in this call reach its
  *                 budget (0 = no budget); the launch ends when all stopped.

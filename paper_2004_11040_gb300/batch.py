@@ -51,10 +51,18 @@ def cells_for(start: synth.Start, cells) -> int:
 
 
 def create(reps: list[Replica], cells="lattice", undo_cap: int = 256, stream=None,
-           rowpass: bool = True):
+           rowpass: bool = True, graph: bool = False):
+    """The replicas' contexts: cell scan (with or without the row pass), or the
+    constraint graph (graph=True; cells then only set the graph's build)."""
     return [ecmc.System(r.start.x, r.start.y, r.start.active, r.start.box, r.ell,
                         cells_per_side=cells_for(r.start, cells), undo_cap=undo_cap,
-                        stream=stream, rowpass=rowpass) for r in reps]
+                        stream=stream, rowpass=rowpass, graph=graph) for r in reps]
+
+
+# parallel pass of a trial: the row pass (cell scan), the general pass (cell
+# scan), or the constraint graph
+SEARCHES = {"row": dict(rowpass=True, graph=False), "general": dict(rowpass=False, graph=False),
+            "graph": dict(rowpass=False, graph=True)}
 
 
 def run_batched(systems, budget: int, legs_per_launch: int, stream=None):
@@ -122,18 +130,20 @@ def _key(reps: list[Replica]) -> str:
 
 
 def autotune(reps: list[Replica], trial_budget: int = 20_000,
-             cells_options=("lattice", "default"), pass_options=(True, False),
+             cells_options=("lattice", "default"), search_options=("row", "general", "graph"),
              legs_options=(4, 16, 64), cache: str | None = CACHE, stream=None) -> dict:
     """Tries every (cell size, parallel pass, legs per launch) on a sample of
     the replicas and keeps the fastest by liftings per device second; every
     trial is recorded, and the choice is cached per GPU, library build and
     workload. The parallel pass is the row pass (a warp holds 32 slots of
-    its chain's row and batches the square roots of several steps) or the
-    general pass (a warp scans 3 rows x 2 columns of cells per pass); both
-    run one chain per warp. Fewer warps per chain (two chains per warp) are
-    not offered: every FP64 warp instruction occupies the sub-partition's
-    FP64 unit ~64 cycles whatever its lane mask, so a warp's latency per step
-    is set by its FP64 instruction count, which two chains would not share."""
+    its chain's row and runs prepared steps in batches), the general pass (a
+    warp scans 3 rows x 2 columns of cells per pass), both one chain per
+    warp, or the constraint graph (one chain per thread; its cell size only
+    sets the graph's build, so it is tried once). Fewer warps per chain (two
+    chains per warp) are not offered: every FP64 warp instruction occupies
+    the sub-partition's FP64 unit ~64 cycles whatever its lane mask, so a
+    warp's latency per step is set by its FP64 instruction count, which two
+    chains would not share."""
     key = _key(reps)
     if cache and os.path.exists(cache):
         try:
@@ -146,21 +156,22 @@ def autotune(reps: list[Replica], trial_budget: int = 20_000,
     sample = reps[: min(len(reps), 64)]
     best = None
     trials = []
-    for cells in cells_options:
-        for rowpass in pass_options:
-            systems = create(sample, cells, stream=stream, rowpass=rowpass)
-            try:
-                for legs in legs_options:
-                    lifts, ms, _ = run_batched(systems, trial_budget, legs, stream=stream)
-                    rate = lifts / (ms / 1e3) if ms > 0 else 0.0
-                    rows = sum(q.stats()["row_windows"] for q in systems)
-                    trials.append({"cells": cells, "rowpass": rowpass, "legs_per_launch": legs,
-                                   "liftings_per_s": rate, "row_windows": rows})
-                    if best is None or rate > best["liftings_per_s"]:
-                        best = dict(trials[-1])
-            finally:
-                for q in systems:
-                    q.close()
+    combos = [(cells, search) for search in search_options for cells in cells_options
+              if search != "graph" or cells == cells_options[0]]
+    for cells, search in combos:
+        systems = create(sample, cells, stream=stream, **SEARCHES[search])
+        try:
+            for legs in legs_options:
+                lifts, ms, _ = run_batched(systems, trial_budget, legs, stream=stream)
+                rate = lifts / (ms / 1e3) if ms > 0 else 0.0
+                rows = sum(q.stats()["row_windows"] for q in systems)
+                trials.append({"cells": cells, "search": search, "legs_per_launch": legs,
+                               "liftings_per_s": rate, "row_windows": rows})
+                if best is None or rate > best["liftings_per_s"]:
+                    best = dict(trials[-1])
+        finally:
+            for q in systems:
+                q.close()
     best["trials"] = trials
     best["key"] = key
     if cache:
@@ -185,23 +196,24 @@ def bench_batched(count: int = 512, budget: int = 1_000_000, same_budget: int = 
     at a time (both rates over the same systems and the same work)."""
     reps = make_replicas(count, seed)
     choice = autotune(reps, stream=stream, cache=cache) if tune else {
-        "cells": "lattice", "rowpass": True, "legs_per_launch": 16}
-    cells, rowpass, legs = choice["cells"], choice["rowpass"], choice["legs_per_launch"]
+        "cells": "lattice", "search": "row", "legs_per_launch": 16}
+    cells, legs = choice["cells"], choice["legs_per_launch"]
+    mode = SEARCHES[choice["search"]]
     t0 = time.perf_counter()
-    systems = create(reps, cells, stream=stream, rowpass=rowpass)
+    systems = create(reps, cells, stream=stream, **mode)
     t_create = time.perf_counter() - t0
     try:
         lifts, ms, launches = run_batched(systems, budget, legs, stream)
     finally:
         for q in systems:
             q.close()
-    systems = create(reps, cells, stream=stream, rowpass=rowpass)
+    systems = create(reps, cells, stream=stream, **mode)
     try:
         s_lifts, s_ms, _ = run_batched(systems, same_budget, legs, stream)
     finally:
         for q in systems:
             q.close()
-    systems = create(reps, cells, stream=stream, rowpass=rowpass)
+    systems = create(reps, cells, stream=stream, **mode)
     try:
         p_lifts, p_ms, p_launches = run_plain(systems, same_budget)
     finally:

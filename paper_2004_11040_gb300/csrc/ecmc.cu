@@ -2408,9 +2408,12 @@ struct Runner {
     unsigned long long *d_phase = nullptr;
     int grid4 = 0, grid8 = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    GBatchScratch *gscratch = nullptr;  // batches of constraint-graph contexts
 };
 
 static void runner_free(Runner &rn) {
+    graph_batch_free(rn.gscratch);
+    rn.gscratch = nullptr;
     cudaFree(rn.d_reps);
     cudaFree(rn.d_ctl);
     cudaFree(rn.d_chain_base);
@@ -2757,7 +2760,6 @@ static int plan_cell_context(ecmc_ctx *ctx, const ecmc_params *p, int nc, int C,
 
 extern "C" int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes) {
     if (!p || !bytes) return ECMC_EINVAL;
-    if (p->flags & ECMC_GRAPH) return ECMC_EINVAL;
     if (p->n < 3 || p->n > (int64_t)0x3FFFFFFF || p->n_chains < 1 || p->n_chains > p->n)
         return ECMC_EINVAL;
     if (p->undo_cap < 0 || p->undo_cap >= (1 << 24) || !(p->box > 0.0) || !(p->d > 0.0) ||
@@ -2768,13 +2770,23 @@ extern "C" int ecmc_context_bytes(const ecmc_params *p, int64_t *bytes) {
     ecmc_ctx *ctx = new (std::nothrow) ecmc_ctx();
     if (!ctx) return ECMC_ENOMEM;
     CreateArrays arr;
-    plan_cell_context(ctx, p, nc, C, &arr);
+    int64_t graph_bytes = 0;
+    if (p->flags & ECMC_GRAPH) {
+        // the graph context's own arrays; the cell-scan arrays are not made
+        graph_bytes = graph_plan_bytes(p, nc);
+        if (graph_bytes < 0) {
+            delete ctx;
+            return ECMC_EINVAL;
+        }
+    } else {
+        plan_cell_context(ctx, p, nc, C, &arr);
+    }
     // the export scratch of ecmc_positions (allocated by its first call)
     dalloc(ctx, &ctx->exp_x, (size_t)p->n);
     dalloc(ctx, &ctx->exp_y, (size_t)p->n);
     dalloc(ctx, &ctx->exp_t, (size_t)p->n);
     dalloc(ctx, &ctx->exp_a, (size_t)p->n_chains);
-    int64_t total = 0;
+    int64_t total = graph_bytes;
     for (auto &r : ctx->pending) total += (int64_t)((r.second + 255) & ~(size_t)255);
     ctx->pending.clear();
     ctx->exp_x = nullptr;
@@ -2966,13 +2978,56 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
         err = "bad batch size or leg count";
         return ECMC_EINVAL;
     }
+    for (int r = 0; r < R; ++r)
+        if (!ctxs[r] || (ctxs[r]->graph != nullptr) != (ctxs[0]->graph != nullptr)) {
+            err = "a batch holds either constraint-graph contexts or cell-scan contexts";
+            return ECMC_EINVAL;
+        }
+    if (ctxs[0]->graph) {
+        // constraint-graph contexts: their own persistent kernel over all of them
+        for (int r = 0; r < R; ++r)
+            for (int q = 0; q < r; ++q)
+                if (ctxs[q] == ctxs[r]) {
+                    err = "a context appears twice in a batch";
+                    return ECMC_EINVAL;
+                }
+        std::vector<GraphCtx *> gs(R);
+        std::vector<GraphTotals> tots(R);
+        for (int r = 0; r < R; ++r) gs[r] = ctxs[r]->graph;
+        double ms = 0.0;
+        const int grc = graph_batch_run(&rn.gscratch, gs.data(), R, max_legs, budgets, st,
+                                        tots.data(), legs_out, &ms, err);
+        if (ms_out) *ms_out = ms;
+        for (int r = 0; r < R; ++r) {
+            ecmc_ctx *c = ctxs[r];
+            const GraphTotals &t = tots[r];
+            c->legs_total += t.legs;
+            c->lifts_total += t.lifts;
+            c->conflict_legs += t.conflict_legs;
+            c->repaired += t.repaired;
+            c->continued += t.continued;
+            c->blocked += t.blocked;
+            c->cwindows += t.cwindows;
+            c->horizon += t.horizon;
+            c->order_err += t.order_err;
+            c->prof.pass1_launches += t.legs;
+            c->prof.other_launches += t.legs;
+            c->prof.repair_launches += t.conflict_legs;
+            c->prof.pass1_liftings += t.p1_lifts;
+            c->prof.repair_liftings += t.repair_lifts;
+            if (R == 1) {
+                c->device_ms += t.ms;
+                c->prof.pass1_ms += t.pass1_ms;
+                c->prof.repair_ms += t.repair_ms;
+                c->prof.other_ms += t.other_ms;
+            }
+            if (lifts_out) lifts_out[r] = t.lifts;
+        }
+        return grc;
+    }
     const int C = ctxs[0]->C;
     const int W = ctxs[0]->s.windows;
     for (int r = 0; r < R; ++r) {
-        if (ctxs[r] && ctxs[r]->graph) {
-            err = "constraint-graph contexts run alone (ecmc_run_to_breakpoint)";
-            return ECMC_EINVAL;
-        }
         if (!ctxs[r] || ctxs[r]->C != C || ctxs[r]->s.windows != W) {
             err = "all contexts of a batch need the same cell slots (cell size) and windows";
             return ECMC_EINVAL;
@@ -3309,7 +3364,7 @@ extern "C" int ecmc_stats(ecmc_ctx *ctx, ecmc_stats_t *out) {
     out->row_windows = ctx->row_windows;
     out->blocked_chains = ctx->blocked;
     out->conflict_windows = ctx->cwindows;
-    out->device_bytes = ctx->graph ? graph_device_bytes(ctx->graph) : ctx->device_bytes;
+    out->device_bytes = (ctx->graph ? graph_device_bytes(ctx->graph) : 0) + ctx->device_bytes;
     out->horizon_asserts = ctx->horizon;
     out->order_errors = ctx->order_err;
     out->device_ms = ctx->device_ms;

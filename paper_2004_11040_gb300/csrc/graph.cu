@@ -1271,6 +1271,7 @@ struct GCtl {
     int32_t done;    // budget reached or error
     int32_t err;     // LC_ERR_* seen, or too many repair rounds
     int32_t pad;
+    int64_t leg0;    // batches: legs run before this launch (lifting log)
 };
 
 enum { GPH_BEGIN = 0, GPH_PASS1, GPH_REPAIR, GPH_END, GPH_N };
@@ -1499,6 +1500,224 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph(GRu
     }
 }
 
+// ------------------------------------- batches of constraint-graph systems
+
+// Launch state of a batch: R systems (descriptors in device memory), their
+// chains and conflict components flattened by prefix offsets.
+struct GBatchDev {
+    const GDev *S;          // [R]
+    GCtl *ctl;              // [R]
+    const int32_t *chain_base;  // [R + 1]
+    int32_t *comp_base;     // [R + 1]
+    int32_t *g;             // [GB_N]
+    unsigned int *bar;      // [1] grid barrier
+    int32_t *err;           // ECMC_ETIMEOUT from a barrier
+    unsigned long long *phase_ns;  // [GPH_N]
+    int32_t R, max_legs, windows;
+    int32_t pad;
+};
+
+enum { GB_WORK = 0, GB_ANY, GB_DONE, GB_REMAIN0, GB_REMAIN1, GB_N };
+
+// replica of flattened item f, with base[r] <= f < base[r + 1]
+__device__ __forceinline__ int g_find_rep(const int32_t *base, int R, int f) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool g_rep_on(const GBatchDev &B, int r) {
+    return !B.ctl[r].done;
+}
+
+// k_run_graph over R systems (the local repair; no restart mode): every
+// system's legs exactly as k_run_graph computes them. Per leg and claim
+// window: the parallel pass over all systems' chains (one thread per chain),
+// the union-find of each system's conflict components (one block per
+// system), their repairs from one work queue (one warp per component), the
+// leg end and each system's totals; the launch ends when every system has
+// reached max_legs or its liftings budget.
+__global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph_batch(GBatchDev B) {
+    extern __shared__ int32_t uf_sm[];
+    __shared__ int warp_tot[32];
+    __shared__ int tot[2];
+    __shared__ int sflag;
+    const int lane = threadIdx.x & 31;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const int nwarps = nthreads >> 5;
+    const int gw = blockIdx.x + gridDim.x * (threadIdx.x >> 5);
+    const int R = B.R;
+    const int total_chains = B.chain_base[R];
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = timer ? gtimer() : 0ull;
+    auto mark = [&](int ph) {
+        if (timer) {
+            const unsigned long long t = gtimer();
+            B.phase_ns[ph] += t - t_prev;
+            t_prev = t;
+        }
+    };
+    // true in the last block to get here, of all blocks (each comes once per use)
+    auto last_block = [&]() -> bool {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int old = atomicAdd(B.g + GB_DONE, 1);
+            sflag = (old + 1) % (int)gridDim.x == 0;
+        }
+        __syncthreads();
+        const bool last = sflag != 0;
+        __syncthreads();
+        if (last) __threadfence();
+        return last;
+    };
+    for (int leg = 0; leg < B.max_legs; ++leg) {
+        // leg start of every running system: chains, claims, per-leg counters
+        for (int f = gt; f < total_chains; f += nthreads) {
+            const int r = g_find_rep(B.chain_base, R, f);
+            if (g_rep_on(B, r)) g_leg_begin_chain(B.S[r], f - B.chain_base[r]);
+        }
+        for (int r = 0; r < R; ++r) {
+            if (!g_rep_on(B, r)) continue;
+            const GDev &s = B.S[r];
+            for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
+            if (gt < LC_N) s.lc[gt] = 0ull;
+            if (gt == 0) s.nabort[0] = s.nabort[1] = 0;
+        }
+        if (!grid_sync(B.bar, B.err, &sflag)) return;
+        if (gt == 0) B.g[GB_REMAIN0 + ((leg + 1) & 1)] = 0;
+        mark(GPH_BEGIN);
+        for (int w = 0; w < B.windows; ++w) {
+            if (w > 0) {
+                for (int r = 0; r < R; ++r) {
+                    if (!g_rep_on(B, r)) continue;
+                    const GDev &s = B.S[r];
+                    for (int64_t q = gt; q < s.n; q += nthreads) s.claim[q] = 0u;
+                }
+                if (!grid_sync(B.bar, B.err, &sflag)) return;
+            }
+            // one chain per thread, warps interleaved over the blocks
+            for (int f = gw + nwarps * lane; f < total_chains; f += nwarps * 32) {
+                const int r = g_find_rep(B.chain_base, R, f);
+                if (!g_rep_on(B, r)) continue;
+                const GDev &s = B.S[r];
+                g_pass1_chain(s, f - B.chain_base[r], g_window_start(s, w), g_window_end(s, w));
+            }
+            if (!grid_sync(B.bar, B.err, &sflag)) return;
+            mark(GPH_PASS1);
+            for (int r = gt; r < R; r += nthreads)
+                if (g_rep_on(B, r)) B.S[r].nabort[1] = 0;  // the first round's abort count
+            for (int round = 1;; ++round) {
+                for (int r = blockIdx.x; r < R; r += gridDim.x) {
+                    const GDev &s = B.S[r];
+                    bool need = false;
+                    if (g_rep_on(B, r))
+                        need = round == 1 ? s.lc[LC_WBLOCKED] != 0ull
+                                          : s.nabort[(round - 1) & 1] != 0;
+                    __syncthreads();
+                    if (round == 1 && threadIdx.x == 0 && g_rep_on(B, r)) {
+                        s.lc[LC_WBLOCKED] = 0ull;
+                        if (need) s.lc[LC_CWINDOWS] += 1ull;
+                    }
+                    if (need && round <= 255) {
+                        uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
+                    } else if (threadIdx.x == 0) {
+                        s.ctl[CTL_NCOMP] = 0;
+                        if (need) atomicAdd(s.lc + LC_ERR_CAP, 1ull);  // too many rounds
+                    }
+                    __syncthreads();
+                }
+                if (last_block()) {
+                    // prefix of component counts over systems
+                    const int chunk = (R + blockDim.x - 1) / blockDim.x;
+                    const int lo = min(R, (int)threadIdx.x * chunk), hi = min(R, lo + chunk);
+                    int sum = 0;
+                    for (int r = lo; r < hi; ++r) sum += B.S[r].ctl[CTL_NCOMP];
+                    int off = block_exscan(sum, warp_tot, tot);
+                    for (int r = lo; r < hi; ++r) {
+                        B.comp_base[r] = off;
+                        off += B.S[r].ctl[CTL_NCOMP];
+                    }
+                    if (threadIdx.x == 0) {
+                        B.comp_base[R] = tot[0];
+                        B.g[GB_WORK] = 0;
+                        B.g[GB_ANY] = tot[0];
+                    }
+                }
+                if (!grid_sync(B.bar, B.err, &sflag)) return;
+                // every block has read the previous round's abort counts
+                for (int r = gt; r < R; r += nthreads)
+                    if (g_rep_on(B, r)) B.S[r].nabort[(round + 1) & 1] = 0;
+                const int ncomp = B.g[GB_ANY];
+                if (ncomp == 0) break;
+                for (;;) {
+                    int q = 0;
+                    if (lane == 0) q = atomicAdd(B.g + GB_WORK, 1);
+                    q = __shfl_sync(FULL, q, 0);
+                    if (q >= ncomp) break;
+                    const int r = g_find_rep(B.comp_base, R, q);
+                    const GDev &s = B.S[r];
+                    g_repair_component(s, q - B.comp_base[r], round,
+                                       ((uint32_t)(leg * B.windows + w) << 8) | (uint32_t)round,
+                                       g_window_start(s, w), g_window_end(s, w));
+                }
+                if (!grid_sync(B.bar, B.err, &sflag)) return;
+                // no component met another chain: the window is repaired
+                int aborted = 0;
+                for (int r = threadIdx.x; r < R; r += blockDim.x)
+                    if (g_rep_on(B, r) &&
+                        *(volatile int32_t *)(B.S[r].nabort + (round & 1)) != 0)
+                        aborted = 1;
+                if (!__syncthreads_or(aborted)) break;
+            }
+            mark(GPH_REPAIR);
+        }
+        // leg end: liftings and the log; the last block takes each system's
+        // totals and budget
+        for (int f = gt; f < total_chains; f += nthreads) {
+            const int r = g_find_rep(B.chain_base, R, f);
+            if (g_rep_on(B, r))
+                g_leg_end_chain(B.S[r], f - B.chain_base[r],
+                                (int32_t)(B.ctl[r].leg0 + B.ctl[r].legs));
+        }
+        if (last_block()) {
+            for (int r = threadIdx.x; r < R; r += blockDim.x) {
+                GCtl *const cp = B.ctl + r;
+                GCtl c = *cp;
+                if (c.done) continue;
+                const unsigned long long *lcp = B.S[r].lc;
+                unsigned long long lc[LC_N];
+#pragma unroll
+                for (int q = 0; q < LC_N; ++q) lc[q] = __ldcg(lcp + q);
+                const int flag = lc[LC_BLOCKED] != 0ull;
+                if (c.flags && c.legs < c.flags_cap) c.flags[c.legs] = (uint8_t)flag;
+                c.lifts += (int64_t)lc[LC_LIFTS];
+                c.p1_lifts += (int64_t)lc[LC_P1LIFTS];
+                if (flag) c.repair_lifts += (int64_t)lc[LC_LIFTS];
+                c.legs += 1;
+                c.conflict_legs += flag;
+                c.repaired += (int64_t)lc[LC_REPAIRED];
+                c.continued += (int64_t)lc[LC_CONTINUED];
+                c.blocked += (int64_t)lc[LC_BLOCKED];
+                c.cwindows += (int64_t)lc[LC_CWINDOWS];
+                c.horizon += (int64_t)lc[LC_HORIZON];
+                c.order_err += (int64_t)lc[LC_ORDER];
+                if (lc[LC_ERR_REC] != 0ull || lc[LC_ERR_CAP] != 0ull) c.err = 1;
+                if (c.err || (c.budget > 0 && c.lifts >= c.budget)) c.done = 1;
+                *cp = c;
+                if (!c.done) atomicAdd(B.g + GB_REMAIN0 + (leg & 1), 1);
+            }
+        }
+        if (!grid_sync(B.bar, B.err, &sflag)) return;
+        mark(GPH_END);
+        if (B.g[GB_REMAIN0 + (leg & 1)] == 0) break;
+    }
+}
+
 // Exports positions (per disk id), local times and active disks.
 __global__ void k_g_export(GDev s, double *x, double *t) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1588,6 +1807,14 @@ int gcommit(GraphCtx *g, std::string &err) {
 }
 
 // Builds the arrows (and x, t = 0) of every disk from positions x, y (device).
+// Bytes of the build's scratch (kept by the context for direction changes).
+static int64_t graph_build_bytes(double L, double d, int nc, int C) {
+    const size_t nslot = (size_t)nc * nc * C;
+    const size_t nb = (size_t)((int)std::ceil(L / (d / 128.0)) + 1);
+    return (int64_t)(nslot * 4 + nslot * 8 + nslot * 8 + (nb + 1) * 4 + 8 + nslot * 4 +
+                     ((nb + SCAN_TILE - 1) / SCAN_TILE) * 4);
+}
+
 int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err) {
     GDev &s = g->s;
     const int nc = g->nc;
@@ -1637,8 +1864,7 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
             err = "cudaMalloc failed (graph build)";
             return ECMC_ENOMEM;
         }
-        g->bytes += (int64_t)(nslot * 4 + nslot * 8 + nslot * 8 + ((size_t)b.nb + 1) * 4 + 8 +
-                              nslot * 4 + (((size_t)b.nb + SCAN_TILE - 1) / SCAN_TILE) * 4);
+        g->bytes += graph_build_bytes(s.L, s.d, nc, C);
     }
     b.cid = (uint32_t *)tmp[0];
     b.cx = (double *)tmp[1];
@@ -1683,33 +1909,10 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
 
 }  // namespace
 
-int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
-                 const int32_t *active, cudaStream_t st, GraphCtx **out, std::string &err) {
-    *out = nullptr;
-    if (p->n_chains > MAX_CHAINS) {
-        err = "too many chains";
-        return ECMC_EINVAL;
-    }
-    GraphCtx *g = new (std::nothrow) GraphCtx();
-    if (!g) {
-        err = "host allocation";
-        return ECMC_ENOMEM;
-    }
-    g->nc = nc;
-    g->box = p->box;
-    g->st = st;
+// The device arrays of a graph context, requested from the pool (galloc):
+// graph_create commits them, graph_plan_bytes only adds them up.
+static int graph_plan(GraphCtx *g, const ecmc_params *p, std::string &err) {
     GDev &s = g->s;
-    memset(&s, 0, sizeof s);
-    s.n = p->n;
-    s.k = p->n_chains;
-    s.nc = nc;
-    s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
-    s.windows = p->windows > 0 ? p->windows : 1;
-    s.L = p->box;
-    s.d = p->d;
-    s.ell = p->ell;
-    s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
-    s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
     const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
     int rc = 0;
     auto chk = [&](int r) {
@@ -1756,6 +1959,43 @@ int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
     chk(galloc(g, &g->d_bar, 2, err));
     chk(galloc(g, &g->d_err, 1, err));
     chk(galloc(g, &g->d_phase, GPH_N, err));
+    return rc;
+}
+
+
+int graph_create(const ecmc_params *p, int nc, const double *x, const double *y,
+                 const int32_t *active, cudaStream_t st, GraphCtx **out, std::string &err) {
+    *out = nullptr;
+    if (p->n_chains > MAX_CHAINS) {
+        err = "too many chains";
+        return ECMC_EINVAL;
+    }
+    GraphCtx *g = new (std::nothrow) GraphCtx();
+    if (!g) {
+        err = "host allocation";
+        return ECMC_ENOMEM;
+    }
+    g->nc = nc;
+    g->box = p->box;
+    g->st = st;
+    GDev &s = g->s;
+    memset(&s, 0, sizeof s);
+    s.n = p->n;
+    s.k = p->n_chains;
+    s.nc = nc;
+    s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
+    s.windows = p->windows > 0 ? p->windows : 1;
+    s.L = p->box;
+    s.d = p->d;
+    s.ell = p->ell;
+    s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
+    s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
+    const size_t n = (size_t)p->n, k = (size_t)p->n_chains;
+    int rc = 0;
+    auto chk = [&](int r) {
+        if (r && !rc) rc = r;
+    };
+    chk(graph_plan(g, p, err));
     chk(gcommit(g, err));
     if (!rc && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess)) {
         err = "event creation";
@@ -1906,6 +2146,219 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     return 0;
 }
 
+struct GBatchScratch {
+    int cap = 0;
+    GDev *d_S = nullptr;
+    GCtl *d_ctl = nullptr;
+    int32_t *d_chain_base = nullptr, *d_comp_base = nullptr, *d_g = nullptr, *d_err = nullptr;
+    unsigned int *d_bar = nullptr;
+    unsigned long long *d_phase = nullptr;
+    int grid = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+void graph_batch_free(GBatchScratch *b) {
+    if (!b) return;
+    cudaFree(b->d_S);
+    cudaFree(b->d_ctl);
+    cudaFree(b->d_chain_base);
+    cudaFree(b->d_comp_base);
+    cudaFree(b->d_g);
+    cudaFree(b->d_err);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_phase);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+int graph_batch_run(GBatchScratch **scratch, GraphCtx *const *gs, int32_t n, int32_t max_legs,
+                    const uint64_t *budgets, cudaStream_t st, GraphTotals *tots,
+                    int32_t *legs_out, double *ms_out, std::string &err) {
+    if (ms_out) *ms_out = 0.0;
+    if (n < 1 || max_legs < 0) {
+        err = "bad batch size or leg count";
+        return ECMC_EINVAL;
+    }
+    const int W = gs[0]->s.windows;
+    for (int r = 0; r < n; ++r) {
+        if (!gs[r] || gs[r]->s.windows != W) {
+            err = "all contexts of a batch need the same claim windows";
+            return ECMC_EINVAL;
+        }
+        if (gs[r]->s.restart) {
+            err = "restart-mode contexts run alone (ecmc_run_to_breakpoint)";
+            return ECMC_EINVAL;
+        }
+        if ((int64_t)max_legs * W >= ((int64_t)1 << 24)) {
+            err = "too many legs x windows for one call (< 2^24)";
+            return ECMC_EINVAL;
+        }
+    }
+    for (int r = 0; r < n; ++r) {
+        memset(&tots[r], 0, sizeof tots[r]);
+        if (legs_out) legs_out[r] = 0;
+    }
+    if (max_legs == 0) return 0;
+    GBatchScratch *b = *scratch;
+    if (!b) {
+        b = new (std::nothrow) GBatchScratch();
+        if (!b) return ECMC_ENOMEM;
+        *scratch = b;
+    }
+    if (b->cap < n) {
+        cudaFree(b->d_S);
+        cudaFree(b->d_ctl);
+        cudaFree(b->d_chain_base);
+        cudaFree(b->d_comp_base);
+        b->d_S = nullptr;
+        b->d_ctl = nullptr;
+        b->d_chain_base = b->d_comp_base = nullptr;
+        b->cap = 0;
+        const int cap = std::max(n, 2 * b->cap);
+        if (cudaMalloc(&b->d_S, (size_t)cap * sizeof(GDev)) != cudaSuccess ||
+            cudaMalloc(&b->d_ctl, (size_t)cap * sizeof(GCtl)) != cudaSuccess ||
+            cudaMalloc(&b->d_chain_base, (size_t)(cap + 1) * 4) != cudaSuccess ||
+            cudaMalloc(&b->d_comp_base, (size_t)(cap + 1) * 4) != cudaSuccess) {
+            (void)cudaGetLastError();
+            err = "batch scratch";
+            return ECMC_ENOMEM;
+        }
+        b->cap = cap;
+    }
+    if (!b->d_g) {
+        int dev = 0, n_sm = 1, blocks = 0;
+        if (cudaMalloc(&b->d_g, GB_N * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&b->d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
+            cudaMalloc(&b->d_phase, GPH_N * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_run_graph_batch,
+                                                          GRUN_THREADS, UF_SMEM_BYTES) !=
+                cudaSuccess ||
+            blocks < 1) {
+            (void)cudaGetLastError();
+            err = "batch scratch";
+            return ECMC_ENOMEM;
+        }
+        b->grid = n_sm * std::min(blocks, GRUN_MIN_BLOCKS);
+    }
+    std::vector<GDev> S(n);
+    std::vector<GCtl> ctl(n);
+    std::vector<int32_t> base(n + 1, 0);
+    int rc = 0;
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !rc) {
+            (void)cudaGetLastError();
+            err = std::string(what) + ": " + cudaGetErrorString(e);
+            rc = ECMC_ECUDA;
+        }
+    };
+    for (int r = 0; r < n; ++r) {
+        GraphCtx *g = gs[r];
+        if (g->st != st) cu(cudaStreamSynchronize(g->st), "context stream");
+        if (g->flags_cap < max_legs) {
+            cudaFree(g->d_flags);
+            g->d_flags = nullptr;
+            g->flags_cap = 0;
+            if (cudaMalloc(&g->d_flags, (size_t)max_legs) != cudaSuccess) {
+                (void)cudaGetLastError();
+                err = "flags allocation";
+                return ECMC_ENOMEM;
+            }
+            g->flags_cap = max_legs;
+        }
+        S[r] = g->s;
+        memset(&ctl[r], 0, sizeof(GCtl));
+        ctl[r].budget = budgets ? (int64_t)budgets[r] : 0;
+        ctl[r].flags = g->d_flags;
+        ctl[r].flags_cap = g->flags_cap;
+        ctl[r].leg0 = g->log_legs;
+        base[r + 1] = base[r] + g->s.k;
+        // member tags restart with the launch's window count
+        cu(cudaMemsetAsync(g->s.memb, 0xFF, (size_t)g->s.k * 8, st), "memb");
+    }
+    if (rc) return rc;
+    cu(cudaMemcpyAsync(b->d_S, S.data(), (size_t)n * sizeof(GDev), cudaMemcpyHostToDevice, st),
+       "descriptors");
+    cu(cudaMemcpyAsync(b->d_ctl, ctl.data(), (size_t)n * sizeof(GCtl), cudaMemcpyHostToDevice, st),
+       "ctl");
+    cu(cudaMemcpyAsync(b->d_chain_base, base.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice,
+                       st),
+       "chain base");
+    cu(cudaMemsetAsync(b->d_g, 0, GB_N * sizeof(int32_t), st), "counters");
+    cu(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), st), "bar");
+    cu(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), st), "err");
+    cu(cudaMemsetAsync(b->d_phase, 0, GPH_N * sizeof(unsigned long long), st), "phase");
+    if (rc) return rc;
+    GBatchDev B;
+    B.S = b->d_S;
+    B.ctl = b->d_ctl;
+    B.chain_base = b->d_chain_base;
+    B.comp_base = b->d_comp_base;
+    B.g = b->d_g;
+    B.bar = b->d_bar;
+    B.err = b->d_err;
+    B.phase_ns = b->d_phase;
+    B.R = n;
+    B.max_legs = max_legs;
+    B.windows = W;
+    B.pad = 0;
+    void *args[] = {&B};
+    cu(cudaEventRecord(b->ev0, st), "event");
+    cu(cudaLaunchCooperativeKernel((void *)k_run_graph_batch, b->grid, GRUN_THREADS, args,
+                                   UF_SMEM_BYTES, st),
+       "launch");
+    cu(cudaEventRecord(b->ev1, st), "event");
+    int32_t gerr = 0;
+    unsigned long long ph[GPH_N];
+    cu(cudaMemcpyAsync(ctl.data(), b->d_ctl, (size_t)n * sizeof(GCtl), cudaMemcpyDeviceToHost, st),
+       "ctl");
+    cu(cudaMemcpyAsync(&gerr, b->d_err, sizeof gerr, cudaMemcpyDeviceToHost, st), "err");
+    cu(cudaMemcpyAsync(ph, b->d_phase, sizeof ph, cudaMemcpyDeviceToHost, st), "phase");
+    cu(cudaStreamSynchronize(st), "run");
+    if (rc) return rc;
+    float ms = 0.f;
+    cu(cudaEventElapsedTime(&ms, b->ev0, b->ev1), "elapsed");
+    if (ms_out) *ms_out = ms;
+    bool cap_err = false;
+    for (int r = 0; r < n; ++r) {
+        const GCtl &c = ctl[r];
+        gs[r]->log_legs += c.legs;
+        GraphTotals &t = tots[r];
+        t.legs = c.legs;
+        t.lifts = c.lifts;
+        t.conflict_legs = c.conflict_legs;
+        t.repaired = c.repaired;
+        t.continued = c.continued;
+        t.horizon = c.horizon;
+        t.order_err = c.order_err;
+        t.p1_lifts = c.p1_lifts;
+        t.repair_lifts = c.repair_lifts;
+        t.blocked = c.blocked;
+        t.cwindows = c.cwindows;
+        if (n == 1) {
+            t.ms = ms;
+            t.pass1_ms = ph[GPH_PASS1] * 1e-6;
+            t.repair_ms = ph[GPH_REPAIR] * 1e-6;
+            t.other_ms = (ph[GPH_BEGIN] + ph[GPH_END]) * 1e-6;
+        }
+        if (legs_out) legs_out[r] = (int32_t)c.legs;
+        if (c.err) cap_err = true;
+    }
+    if (gerr == ECMC_ETIMEOUT) {
+        err = "a grid barrier wait passed its time limit";
+        return ECMC_ETIMEOUT;
+    }
+    if (cap_err) {
+        err = "undo records or repair rounds overflowed";
+        return ECMC_ECAPACITY;
+    }
+    return 0;
+}
+
 int graph_export(GraphCtx *g, double *x, double *y, double *t, int32_t *active) {
     const GDev &s = g->s;
     cudaStream_t st = g->st;
@@ -1991,3 +2444,25 @@ void graph_destroy(GraphCtx *g) {
 }
 
 int64_t graph_device_bytes(const GraphCtx *g) { return g ? g->bytes : 0; }
+
+int64_t graph_plan_bytes(const ecmc_params *p, int nc) {
+    GraphCtx *g = new (std::nothrow) GraphCtx();
+    if (!g) return -1;
+    GDev &s = g->s;
+    memset(&s, 0, sizeof s);
+    s.cap = p->undo_cap > 0 ? p->undo_cap : 1024;
+    s.log_on = (p->flags & ECMC_LOG_LIFTINGS) ? 1 : 0;
+    s.log_cap = s.log_on ? (p->log_cap > 0 ? p->log_cap : ((int64_t)1 << 22)) : 0;
+    std::string err;
+    int64_t total = -1;
+    if (graph_plan(g, p, err) == 0) {
+        total = 0;
+        for (auto &r : g->pending) total += (int64_t)((r.second + 255) & ~(size_t)255);
+        const double a = p->box / nc;
+        const int C = a < std::sqrt(2.0) * p->d * (1.0 - 1e-9) ? 4 : 8;
+        total += graph_build_bytes(p->box, p->d, nc, C);
+    }
+    g->pending.clear();
+    delete g;
+    return total;
+}

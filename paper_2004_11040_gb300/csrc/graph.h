@@ -35,5 +35,18 @@ int graph_arrows(GraphCtx *g, int32_t *a, double *b, std::string &err);
 int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
                    std::string &err);
 void graph_destroy(GraphCtx *g);
+// Batches of graph contexts: one persistent launch advances n contexts (same
+// claim windows, no restart mode), each to max_legs legs or its liftings
+// budget (budgets may be null; 0: none), exactly as graph_run would. The
+// scratch (launch tables) is kept by the caller between calls and freed with
+// graph_batch_free. tots[r] and legs_out[r] (may be null) receive each
+// context's totals; *ms_out the launch's device time.
+struct GBatchScratch;
+int graph_batch_run(GBatchScratch **scratch, GraphCtx *const *gs, int32_t n, int32_t max_legs,
+                    const uint64_t *budgets, cudaStream_t st, GraphTotals *tots,
+                    int32_t *legs_out, double *ms_out, std::string &err);
+void graph_batch_free(GBatchScratch *scratch);
 // Device memory held by the context (bytes).
 int64_t graph_device_bytes(const GraphCtx *g);
+// What graph_create(p, nc, ...) would hold, without allocating (-1: error).
+int64_t graph_plan_bytes(const ecmc_params *p, int nc);

@@ -22,13 +22,14 @@ import numpy as np
 from . import ecmc, synth
 
 def device_bytes(n: int, k: int, box: float, d: float = 1.0, undo_cap: int = 1024,
-                 log_cap: int = 0, cells_per_side: int = 0, ell: float = 1.0) -> int:
+                 log_cap: int = 0, cells_per_side: int = 0, ell: float = 1.0,
+                 graph: bool = False) -> int:
     """Device memory an ECMC context of these parameters holds, as the
     library computes it without allocating (ecmc_context_bytes): the same
     number its ecmc_stats reports as device_bytes once created."""
+    flags = (ecmc.ECMC_LOG_LIFTINGS if log_cap else 0) | (ecmc.ECMC_GRAPH if graph else 0)
     p = ecmc.ecmc_params(int(n), float(box), float(d), float(ell), int(k), int(cells_per_side),
-                         ecmc.ECMC_LOG_LIFTINGS if log_cap else 0, int(undo_cap), int(log_cap),
-                         1, 0)
+                         flags, int(undo_cap), int(log_cap), 1, 0)
     return ecmc.ecmc_context_bytes(p)
 
 
@@ -112,7 +113,7 @@ class Server:
     def __init__(self, hbm_budget_bytes: int, ell: float = 1.0, slice_legs: int = 8,
                  max_resident: int = 4096, undo_cap: int = 1024, stream=None,
                  keep_results: bool = False, cells: str = "lattice",
-                 release_starts: bool = False):
+                 release_starts: bool = False, graph: bool = False):
         self.hbm_budget = int(hbm_budget_bytes)
         self.cells = cells
         self.ell = ell
@@ -123,6 +124,8 @@ class Server:
         self.keep_results = keep_results
         # drop a request's host copy of its start once it is on the device
         self.release_starts = release_starts
+        # constraint-graph contexts (a batch holds one kind only)
+        self.graph = graph
         self.batch = ecmc.ecmc_batch_create(stream)
 
     def close(self):
@@ -138,7 +141,7 @@ class Server:
     def need(self, r: Request) -> int:
         """Device bytes request r will hold (from the library, no allocation)."""
         return device_bytes(r.n, r.k, r.start.box, undo_cap=self.undo_cap,
-                            cells_per_side=self._cells(r), ell=self.ell)
+                            cells_per_side=self._cells(r), ell=self.ell, graph=self.graph)
 
     @staticmethod
     def mean_budget(budget_range) -> float:
@@ -149,7 +152,7 @@ class Server:
     def _admit(self, r: Request):
         s = r.start
         return ecmc.System(s.x, s.y, s.active, s.box, self.ell, undo_cap=self.undo_cap,
-                           stream=self.stream, cells_per_side=self._cells(r))
+                           stream=self.stream, cells_per_side=self._cells(r), graph=self.graph)
 
     def serve(self, reqs: list[Request], clock=time.perf_counter) -> ServeStats:
         """Runs the stream to completion; arrival times are seconds after start."""
@@ -216,11 +219,11 @@ class Server:
 
 
 def run_alone(r: Request, ell: float = 1.0, undo_cap: int = 1024, stream=None,
-              cells: str = "lattice"):
+              cells: str = "lattice", graph: bool = False):
     """The same request on its own: ecmc_run_to_breakpoint with the budget."""
     s = r.start
     sysm = ecmc.System(s.x, s.y, s.active, s.box, ell, undo_cap=undo_cap, stream=stream,
-                       cells_per_side=int(s.m) if cells == "lattice" else 0)
+                       cells_per_side=int(s.m) if cells == "lattice" else 0, graph=graph)
     total = 0
     while total < r.budget:
         before = sysm.stats()["liftings"]

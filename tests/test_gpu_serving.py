@@ -50,20 +50,24 @@ def test_autotune_picks_and_caches(tmp_path, monkeypatch):
     reps = batch.make_replicas(8, seed=9, n_range=(1024, 4096))
     cache = str(tmp_path / "tune.json")
     got = batch.autotune(reps, trial_budget=2000, cells_options=("lattice", "default"),
-                         pass_options=(True, False), legs_options=(2, 8), cache=cache)
+                         search_options=("row", "general", "graph"), legs_options=(2, 8),
+                         cache=cache)
     assert got["cells"] in ("lattice", "default") and got["legs_per_launch"] in (2, 8)
-    assert got["rowpass"] in (True, False)
-    assert len(got["trials"]) == 8 and all(t["liftings_per_s"] > 0 for t in got["trials"])
+    assert got["search"] in ("row", "general", "graph")
+    # cells x {row, general} and the graph once, each with both leg counts
+    assert len(got["trials"]) == 10 and all(t["liftings_per_s"] > 0 for t in got["trials"])
+    assert sum(t["search"] == "graph" for t in got["trials"]) == 2
     # the row pass runs where the cells are aligned with the lattice
-    assert any(t["row_windows"] > 0 for t in got["trials"] if t["rowpass"] and t["cells"] == "lattice")
-    assert all(t["row_windows"] == 0 for t in got["trials"] if not t["rowpass"])
+    assert any(t["row_windows"] > 0 for t in got["trials"]
+               if t["search"] == "row" and t["cells"] == "lattice")
+    assert all(t["row_windows"] == 0 for t in got["trials"] if t["search"] != "row")
     again = batch.autotune(reps, cache=cache)  # served from the cache, no trials run
-    assert (again["cells"], again["rowpass"], again["legs_per_launch"]) == \
-        (got["cells"], got["rowpass"], got["legs_per_launch"])
+    assert (again["cells"], again["search"], again["legs_per_launch"]) == \
+        (got["cells"], got["search"], got["legs_per_launch"])
     # another GPU or library build: the cached choice does not apply
     monkeypatch.setattr(batch, "_hardware_key", lambda: "other-gpu_other-build")
     fresh = batch.autotune(reps, trial_budget=2000, cells_options=("lattice",),
-                           pass_options=(True,), legs_options=(2,), cache=cache)
+                           search_options=("row",), legs_options=(2,), cache=cache)
     assert len(fresh["trials"]) == 1 and fresh["key"].startswith("other-gpu_other-build")
 
 
@@ -93,6 +97,30 @@ def test_server_mix_equals_alone():
         assert np.array_equal(x, rx) and np.array_equal(t, rt) and np.array_equal(a, ra), r.rid
 
 
+def test_server_graph_mode_mix_equals_alone():
+    """The server with constraint-graph contexts (batched by their own
+    kernel): each request ends where the same request alone ends."""
+    reqs = serve.make_requests(8, seed=6, rate=0.0, n_range=(1024, 16384),
+                               budget_range=(2e3, 5e4))
+    serve.prepare(reqs)
+    probe = serve.Server(hbm_budget_bytes=1, slice_legs=4, graph=True)
+    need = sorted(probe.need(r) for r in reqs)
+    probe.close()
+    srv = serve.Server(hbm_budget_bytes=sum(need[-3:]), slice_legs=4, keep_results=True,
+                       graph=True)
+    try:
+        st = srv.serve(reqs)
+    finally:
+        srv.close()
+    assert st.completed == len(reqs)
+    assert st.peak_bytes <= sum(need[-3:])
+    for r in reqs:
+        (x, y, t, a), total = serve.run_alone(r, graph=True)
+        rx, ry, rt, ra = r.result
+        assert total == r.liftings, r.rid
+        assert np.array_equal(x, rx) and np.array_equal(t, rt) and np.array_equal(a, ra), r.rid
+
+
 def test_server_poisson_arrivals_complete():
     reqs = serve.make_requests(6, seed=4, rate=200.0, n_range=(1024, 8192),
                                budget_range=(1e3, 2e4))
@@ -113,12 +141,15 @@ def test_context_bytes_are_what_a_context_holds():
     allocator's granularity)."""
     import torch
     from paper_2004_11040_gb300 import synth
-    for m, k, cells in ((64, 64, 64), (256, 512, 0), (512, 512, 512)):
+    for m, k, cells, graph in ((64, 64, 64, False), (256, 512, 0, False), (512, 512, 512, False),
+                               (64, 64, 0, True), (512, 512, 512, True)):
         s = synth.lattice_start(m, 0.70, k, seed=1)
-        need = serve.device_bytes(m * m, k, s.box, undo_cap=256, cells_per_side=cells)
+        need = serve.device_bytes(m * m, k, s.box, undo_cap=256, cells_per_side=cells,
+                                  graph=graph)
         torch.cuda.synchronize()
         free0, _ = torch.cuda.mem_get_info()
-        sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, undo_cap=256, cells_per_side=cells)
+        sysm = ecmc.System(s.x, s.y, s.active, s.box, 1.0, undo_cap=256, cells_per_side=cells,
+                           graph=graph)
         sysm.positions()
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
