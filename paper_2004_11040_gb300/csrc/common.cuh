@@ -146,10 +146,95 @@ constexpr size_t UF_SMEM_BYTES = 4 * UF_SMEM_CAP * sizeof(int32_t);
 // parents, counts, roots and flags live there during the phases (each phase
 // then waits on shared instead of global memory) and are written back to
 // s.uf, s.comp_of and s.fin at the end.
+// Round 1 when every blocked chain makes a pair with its partner alone (the
+// common case): blist[0 .. nblk) are the window's blocked chains, pcnt[c]
+// the blocked chains naming c as partner. A pair {a, p} is a component when
+// nobody names a (pcnt[a] = 0), only a names p (pcnt[p] = 1) and p is not
+// blocked; a chain without a partner is a component alone. Then the result
+// is the dense union-find's, written directly: identity for every chain in
+// no component, the root (the smaller index) for the members, components in
+// increasing root order, the blocked member first. Returns false (nothing
+// written) otherwise. Either way pcnt is back to 0 for the chains listed.
+template <class S>
+__device__ bool uf_pairs(const S &s, const int32_t *blist, int32_t *pcnt, int nblk,
+                         bool reset_abort, int32_t *sm) {
+    const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
+    int a = -1, p = -1;
+    bool simple = true;
+    if (tid < nblk) {
+        a = blist[tid];
+        p = s.partner[a];
+        if (p < 0 || p >= k) p = -1;
+        const int pa = pcnt[a];
+        const int pp = p >= 0 ? pcnt[p] : 1;
+        const int sp = p >= 0 ? s.status[p] : ST_STALLED;
+        simple = pa == 0 && (p < 0 || (pp == 1 && sp != ST_BLOCKED));
+    }
+    const bool ok = __syncthreads_and(simple) != 0;
+    if (tid < nblk && p >= 0) pcnt[p] = 0;
+    if (!ok) return false;
+    for (int c = tid; c < k; c += nt) {
+        s.uf[c] = c;
+        s.comp_of[c] = c;
+        s.fin[c] = 1;
+        s.abort_to[c] = -1;
+    }
+    // the pairs by root: rank and offset among them
+    int32_t *root_sm = sm, *size_sm = sm + 64;
+    const int root = p >= 0 ? min(a, p) : a;
+    if (tid < nblk) {
+        root_sm[tid] = root;
+        size_sm[tid] = p >= 0 ? 2 : 1;
+    }
+    __syncthreads();
+    if (tid < nblk) {
+        int rank = 0, off = 0, total = 0;
+        for (int j = 0; j < nblk; ++j) {
+            total += size_sm[j];
+            if (root_sm[j] < root) {
+                ++rank;
+                off += size_sm[j];
+            }
+        }
+        s.uf[a] = root;
+        s.comp_of[a] = root;
+        s.fin[a] = 0;
+        s.comp_root[rank] = root;
+        s.comp_off[rank] = off;
+        s.comp_mem[off] = a;
+        if (p >= 0) {
+            s.uf[p] = root;
+            s.comp_of[p] = root;
+            s.fin[p] = 0;
+            s.comp_mem[off + 1] = p;
+        }
+        if (rank == 0) {
+            s.comp_off[nblk] = total;
+            s.ctl[CTL_NCOMP] = nblk;
+            s.ctl[CTL_NMEMB] = total;
+            s.ctl[CTL_WORK] = 0;
+            if (reset_abort) s.ctl[CTL_NABORT] = 0;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 template <class S>
 __device__ void uf_block(const S &s, int first, int *warp_tot, int *tot, bool reset_abort,
-                         int32_t *sm = nullptr) {
+                         int32_t *sm = nullptr, const int32_t *blist = nullptr,
+                         int32_t *pcnt = nullptr, int nblk = -1) {
     const int k = s.k, tid = threadIdx.x, nt = blockDim.x;
+    if (first && blist && sm && nblk >= 1 && nblk <= 64 && nblk <= nt) {
+        if (uf_pairs(s, blist, pcnt, nblk, reset_abort, sm)) return;
+        __syncthreads();
+    } else if (first && blist && pcnt) {
+        // (the dense pass does not read the partner counts: back to 0)
+        for (int q = tid; q < nblk && q < k; q += nt) {
+            const int p = s.partner[blist[q]];
+            if (p >= 0 && p < k) pcnt[p] = 0;
+        }
+    }
     const bool local = sm != nullptr && k <= UF_SMEM_CAP;
     int32_t *uf = local ? sm : s.uf;
     int32_t *cnt = local ? sm + UF_SMEM_CAP : s.comp_cnt;

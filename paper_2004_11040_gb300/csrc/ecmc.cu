@@ -105,6 +105,8 @@ struct Dev {
     int32_t *comp_off;   // [k+1] offsets of dirty components
     int32_t *comp_root;  // root of the q-th dirty component
     int32_t *comp_mem;   // members, grouped by component
+    int32_t *blist;      // [k] the window's blocked chains (their count: LC_WBLOCKED)
+    int32_t *pcnt;       // [k] blocked chains naming the chain as partner (0 between uses)
     int32_t *ctl;        // [CTL_N]
     unsigned long long *lc;      // [LC_N]
     unsigned long long *tc_cnt;  // [TC_N]
@@ -817,6 +819,15 @@ __device__ int commit_step(const Dev &s, int c, ChainReg &r, const StepOut &o, b
     return ST_STALLED;
 }
 
+// A chain blocked by the window's parallel pass (lane 0): counted, listed for
+// the union-find, and counted against its partner.
+__device__ __forceinline__ void note_blocked(const Dev &s, int c, int32_t partner) {
+    atomicAdd(s.lc + LC_BLOCKED, 1ull);
+    const unsigned long long ix = atomicAdd(s.lc + LC_WBLOCKED, 1ull);
+    if (ix < (unsigned long long)s.k) s.blist[ix] = c;
+    if (partner >= 0 && partner < s.k) atomicAdd(s.pcnt + partner, 1);
+}
+
 #include "rowpass.cuh"
 
 // ---------------------------------------------------------------- kernels
@@ -1135,10 +1146,7 @@ __device__ void pass1_chain(const Dev &s, int c, double tw, double tend) {
         s.ci[c] = r.i;
         s.tc[c] = r.ti;
         s.D[c] = r.D;
-        if (blocked) {
-            atomicAdd(s.lc + LC_BLOCKED, 1ull);
-            atomicAdd(s.lc + LC_WBLOCKED, 1ull);
-        }
+        if (blocked) note_blocked(s, c, s.partner[c]);
         if (weak) {
             atomicAdd(s.lc + LC_WEAK, 1ull);
             atomicAdd(s.lc + LC_WWEAK, 1ull);
@@ -2084,15 +2092,17 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
         __syncthreads();
         const Dev &s = wdev[0];
         bool need = false;
+        unsigned long long wbl = 0ull;
         if (rep_on(b, r)) {
-            const unsigned long long wbl = s.lc[LC_WBLOCKED];
+            wbl = s.lc[LC_WBLOCKED];
             need = round == 1 ? wbl != 0ull : s.ctl[CTL_NABORT] != 0;
             // the window's flag: the claim sets of two chains met
             if (round == 1 && threadIdx.x == 0 && (wbl != 0ull || s.lc[LC_WWEAK] != 0ull))
                 atomicAdd(s.lc + LC_CWINDOWS, 1ull);
         }
         if (need && round <= 255) {
-            uf_block(s, round == 1, warp_tot, tot, false, uf_sm);
+            uf_block(s, round == 1, warp_tot, tot, false, uf_sm, s.blist, s.pcnt,
+                     round == 1 ? (int)min(wbl, (unsigned long long)s.k) : -1);
         } else if (threadIdx.x == 0) {
             s.ctl[CTL_NCOMP] = 0;
             if (need) b.ctl[r].err = 1;  // too many rounds
@@ -2738,6 +2748,8 @@ static int plan_cell_context(ecmc_ctx *ctx, const ecmc_params *p, int nc, int C,
     chk(dalloc(ctx, &s.comp_off, k + 1));
     chk(dalloc(ctx, &s.comp_root, k));
     chk(dalloc(ctx, &s.comp_mem, k));
+    chk(dalloc(ctx, &s.blist, k));
+    chk(dalloc(ctx, &s.pcnt, k));
     chk(dalloc(ctx, &s.ctl, CTL_N));
     chk(dalloc(ctx, &s.dbg, 16));
     chk(dalloc(ctx, &s.ev_j, k));
@@ -2871,6 +2883,7 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
     }
     CU(cudaMemsetAsync(s.cid, 0xFF, nslot * sizeof(uint32_t), st));
     CU(cudaMemsetAsync(s.claim, 0, ncell * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(s.pcnt, 0, (size_t)s.k * sizeof(int32_t), st));
     CU(cudaMemsetAsync(s.rp, 0, RP_N * sizeof(int32_t), st));
     if (s.rp_ok) {
         CU(cudaMemsetAsync(s.ckey, 0xFF, ncell * sizeof(unsigned long long), st));
@@ -3523,6 +3536,8 @@ static size_t noalloc_layout(Dev &s, unsigned char *base, size_t nslot, size_t n
     s.comp_off = cv.take<int32_t>(k + 1);
     s.comp_root = cv.take<int32_t>(k);
     s.comp_mem = cv.take<int32_t>(k);
+    s.blist = cv.take<int32_t>(k);
+    s.pcnt = cv.take<int32_t>(k);
     s.ctl = cv.take<int32_t>(CTL_N);
     s.lc = cv.take<unsigned long long>(LC_N);
     s.tc_cnt = cv.take<unsigned long long>(TC_N);
@@ -3544,6 +3559,7 @@ static int noalloc_leg(Dev &s, cudaStream_t st, int n_sm, uint8_t *flag, int64_t
     int32_t ctl[CTL_N];
     const unsigned kb = (unsigned)((s.k + 127) / 128);
     CUN(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
+    CUN(cudaMemsetAsync(s.pcnt, 0, (size_t)s.k * sizeof(int32_t), st));
     k_leg_begin<<<kb, 128, 0, st>>>(s);
     CUN(cudaMemsetAsync(s.claim, 0, (size_t)s.nc * s.nc * sizeof(uint32_t), st));
     k_pass1<C><<<(unsigned)((s.k + 3) / 4), 128, 0, st>>>(s);

@@ -1192,8 +1192,7 @@ __device__ void row_resolve_chain(const Dev &s, int c, double tw) {
         if (st == ST_BLOCKED) {
             s.partner[c] = partner;
             s.vt[c] = fmax(tc, tw);
-            atomicAdd(s.lc + LC_BLOCKED, 1ull);
-            atomicAdd(s.lc + LC_WBLOCKED, 1ull);
+            note_blocked(s, c, partner);
         } else {
             s.vt[c] = INFINITY;
         }
@@ -1285,8 +1284,12 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
     int nx = __shfl_sync(FULL, w.nx, ch.li);
     double bnx = __shfl_sync(FULL, w.b, ch.li);
     auto v_of_lane = [&](int l) { return ((l / C) - ch.gbase) & (G - 1); };
+    // the window slides when a step's scan to D would leave it (or the
+    // active column reaches G - 2)
+    bool need_slide = false;
     for (;;) {
-        if (vi >= G / 2) {
+        if (vi >= G - 2 || (need_slide && vi > 0)) {
+            need_slide = false;
             if (ch.wbase + vi + G > nc) return RC_GENERAL;
             const int v0 = (gme - ch.gbase) & (G - 1);
             const int h = vi;
@@ -1318,7 +1321,7 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
                 const uint32_t ci = __shfl_sync(FULL, pinfo, lk);
                 if (!(ci & RC_PREP_OK)) break;
                 const int vk = v_of_lane(lk);
-                if (K > 0 && vk >= G / 2) break;
+                if (K > 0 && vk >= G - 2) break;
                 if (nrec + K >= cap) break;
                 const double tau = __shfl_sync(FULL, ptau, lk);
                 if (!(dbits(tau) < dbits(D))) break;  // a stall: the step below
@@ -1328,7 +1331,10 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
                 const float limk = __fadd_rn(d2f_trunc(D), sk.epsf);
                 int mst = 1;
                 while (mst < G - vk && !beyond_k(sk, mst, fxk, fxfk, limk, dbits(D))) ++mst;
-                if (mst >= G - vk) break;
+                if (mst >= G - vk) {
+                    need_slide = vk > 0;
+                    break;
+                }
                 const int pp = (int)(ci & 31u);
                 if (v_of_lane(pp) - vk >= mst) break;
                 unsigned sm = 0u;
@@ -1449,7 +1455,13 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
         const unsigned smask = rp_stop_mask(sk, ch.fx, fxf, dbits(ch.D), G - vi);
         const unsigned above = smask & ~1u;
         const int mstop = above ? __ffs(above) - 1 : G - vi;
-        if (mstop >= G - vi) return RC_GENERAL;
+        if (mstop >= G - vi) {
+            if (vi > 0) {  // slide first
+                need_slide = true;
+                continue;
+            }
+            return RC_GENERAL;
+        }
         const bool scanned = v >= vi && v < vi + mstop;
         if (__any_sync(FULL, scanned && !cok)) return RC_GENERAL;
         const int pp = nx;
