@@ -326,7 +326,7 @@ constexpr uint32_t RC_PREP_NX2OK = 1u << 30;
 template <int C>
 __device__ void rc_prep(const Dev &s, const RowChain &ch, const RowLane &w, int nxr, int rnk,
                         double &ptau, double &pxn, double &pfx, int &pR, unsigned &nsR,
-                        uint32_t &pinfo) {
+                        uint32_t &pinfo, float *thrf, float &pxf, float &ptf) {
     constexpr int G = 32 / C;
     const int lane = threadIdx.x & 31, g = lane / C;
     const int v = (g - ch.gbase) & (G - 1);
@@ -354,6 +354,16 @@ __device__ void rc_prep(const Dev &s, const RowChain &ch, const RowLane &w, int 
         ok = false;
     }
     pfx = __dsub_rn(w.x, w.colx);
+    // FP32 images: the stop rule's thr(m) = ((m a) - fx) - d for m = 1, 2, 3
+    // (as beyond_k forms it), x and t (truncated)
+    {
+        const float fxf = d2f_trunc(pfx);
+#pragma unroll
+        for (int m = 1; m <= 3; ++m)
+            thrf[m - 1] = __fsub_rn(__fsub_rn(__fmul_rn(__int2float_rn(m), s.af), fxf), s.df);
+        pxf = d2f_trunc(w.x);
+        ptf = d2f_trunc(w.t);
+    }
     bool nx2ok = true;
     const bool chk2 = ok && nx2 >= 0;
     if (__any_sync(FULL, chk2) && chk2) {
@@ -1274,10 +1284,11 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
     int pR;
     unsigned nsR, cokm;
     uint32_t pinfo;
+    float pthr[3], pxf, ptf;
     auto links = [&]() {
         int nxr, rnk;
         rp_links<C>(s, ch, w, &nxr, &rnk);
-        rc_prep<C>(s, ch, w, nxr, rnk, ptau, pxn, pfx, pR, nsR, pinfo);
+        rc_prep<C>(s, ch, w, nxr, rnk, ptau, pxn, pfx, pR, nsR, pinfo, pthr, pxf, ptf);
         cokm = __ballot_sync(FULL, cok);
     };
     links();
@@ -1325,21 +1336,35 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
                 if (nrec + K >= cap) break;
                 const double tau = __shfl_sync(FULL, ptau, lk);
                 if (!(dbits(tau) < dbits(D))) break;  // a stall: the step below
-                // the scan to D: its columns
-                const double fxk = __shfl_sync(FULL, pfx, lk);
-                const float fxfk = d2f_trunc(fxk);
-                const float limk = __fadd_rn(d2f_trunc(D), sk.epsf);
-                int mst = 1;
-                while (mst < G - vk && !beyond_k(sk, mst, fxk, fxfk, limk, dbits(D))) ++mst;
-                if (mst >= G - vk) {
-                    need_slide = vk > 0;
-                    break;
+                // the scan to D: its columns, from the active disk's FP32 image
+                // of thr(m) against trunc(D) + eps (decided where the images
+                // lie farther apart than their error bound; else the step
+                // below decides in FP64)
+                int mst = 0;
+                {
+                    const float limk = __fadd_rn(d2f_trunc(D), sk.epsf);
+                    bool doubt = !(sk.stop_e > 0.f);
+#pragma unroll
+                    for (int m = 1; m <= 3; ++m) {
+                        const float dfm = __fsub_rn(__shfl_sync(FULL, pthr[m - 1], lk), limk);
+                        if (mst == 0 && m < G - vk) {
+                            if (dfm > sk.stop_e)
+                                mst = m;
+                            else if (!(dfm < -sk.stop_e))
+                                doubt = true;
+                        }
+                    }
+                    if (doubt || mst == 0) {
+                        need_slide = mst == 0 && !doubt && vk > 0;
+                        break;
+                    }
                 }
                 const int pp = (int)(ci & 31u);
                 if (v_of_lane(pp) - vk >= mst) break;
-                unsigned sm = 0u;
-                for (int m = 0; m < mst; ++m)
-                    sm |= ((1u << C) - 1u) << (((ch.gbase + vk + m) & (G - 1)) * C);
+                // the scanned columns' lanes: mst groups from the active one's
+                const int gs = ((ch.gbase + vk) & (G - 1)) * C, nb = mst * C;
+                const unsigned run = nb >= 32 ? ~0u : ((1u << nb) - 1u);
+                const unsigned sm = gs == 0 ? run : ((run << gs) | (run >> (32 - gs)));
                 if (sm & ~cokm) break;
                 const int Rk = __shfl_sync(FULL, pR, lk);
                 {
@@ -1349,23 +1374,36 @@ __device__ int row_cont_member(const Dev &s, int c, int round, ChainReg &r, int3
                     if (nsR & inrange & after) break;
                 }
                 if ((int)((ci >> 8) & 31u) < vk + mst && !(ci & RC_PREP_NX2OK)) break;
-                // Eq. 2 on the scanned disks with t_j != 0 (the target by its tau)
+                const double tn = __dadd_rn(t, tau);
+                // Eq. 2 on the scanned disks with t_j != 0: the target by its
+                // tau (t_i + tau is the step's new time), the others from the
+                // FP32 image of t_i + (x_j - x_i - d) - t_j, decided where it lies
+                // above the image's error bound, else in FP64
                 const bool cz = w.id != EMPTY && pR > Rk && v < vk + mst && dbits(w.t) != 0ull;
                 if (__any_sync(FULL, cz)) {
-                    const double xk = __shfl_sync(FULL, w.x, lk);
-                    bool bad = false;
+                    const float xkf = __shfl_sync(FULL, pxf, lk);
+                    const float tkf = d2f_trunc(t);
+                    bool bad = false, doubt = false;
                     if (cz) {
-                        double sb = tau;
-                        if (lane != pp) {
+                        if (lane == pp) {
+                            bad = !(dbits(tn) > dbits(w.t));
+                        } else {
+                            const float sbf = __fsub_rn(__fsub_rn(pxf, xkf), sk.df);
+                            const float mf = __fsub_rn(__fadd_rn(tkf, sbf), ptf);
+                            doubt = !(sbf > sk.stop_e && mf > sk.stop_e);
+                        }
+                    }
+                    if (__any_sync(FULL, doubt)) {
+                        const double xk = __shfl_sync(FULL, w.x, lk);
+                        if (doubt) {
                             double dx = __dsub_rn(w.x, xk);
                             if (dneg(dx) && v > vk) dx = rp_add(dx, LL);
-                            sb = __dsub_rn(dx, dd);
+                            const double sb = __dsub_rn(dx, dd);
+                            bad = dneg(sb) || !(dbits(__dadd_rn(t, sb)) > dbits(w.t));
                         }
-                        bad = dneg(sb) || !(dbits(__dadd_rn(t, sb)) > dbits(w.t));
                     }
                     if (__any_sync(FULL, bad)) break;
                 }
-                const double tn = __dadd_rn(t, tau);
                 if (!(dbits(tn) < dbits(tend))) {  // pauses at the window end
                     pause = true;
                     break;
