@@ -351,9 +351,9 @@ __device__ bool grid_sync(unsigned int *bar, int32_t *err, int *sflag,
         __threadfence();
         *sflag = ok && *(volatile int32_t *)err == 0;
     }
+    // (thread 0's fence after the wait orders the block's later loads: the
+    // block barrier below passes that ordering on to its other threads)
     __syncthreads();
-    // every thread orders its later loads after the barrier (acquire)
-    __threadfence();
     return *sflag != 0;
 }
 
