@@ -2072,16 +2072,18 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
     // once per use): that block finishes a phase's serial tail without a grid
     // barrier before it; it sees every other block's writes of the phase
     auto last_block = [&]() -> bool {
-        __threadfence();
+        // (as in the grid barrier: the block barrier, then the master
+        // thread's fences, release before the count and acquire after it)
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             const int old = atomicAdd(b.g + G_UFDONE, 1);
             sflag = (old + 1) % (int)gridDim.x == 0;
+            if (sflag) __threadfence();
         }
         __syncthreads();
         const bool last = sflag != 0;
         __syncthreads();
-        if (last) __threadfence();
         return last;
     };
     // conflict components of replica r (one block): round 1 from the

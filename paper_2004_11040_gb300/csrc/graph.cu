@@ -1563,16 +1563,18 @@ __global__ void __launch_bounds__(GRUN_THREADS, GRUN_MIN_BLOCKS) k_run_graph_bat
     };
     // true in the last block to get here, of all blocks (each comes once per use)
     auto last_block = [&]() -> bool {
-        __threadfence();
+        // (as in the grid barrier: the block barrier, then the master
+        // thread's fences, release before the count and acquire after it)
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             const int old = atomicAdd(B.g + GB_DONE, 1);
             sflag = (old + 1) % (int)gridDim.x == 0;
+            if (sflag) __threadfence();
         }
         __syncthreads();
         const bool last = sflag != 0;
         __syncthreads();
-        if (last) __threadfence();
         return last;
     };
     for (int leg = 0; leg < B.max_legs; ++leg) {
