@@ -287,11 +287,32 @@ int ecmc_batch_run(ecmc_batch *b, ecmc_ctx *const *ctxs, int32_t n_ctx, int32_t 
 const char *ecmc_batch_last_error(const ecmc_batch *b);
 void ecmc_batch_destroy(ecmc_batch *b);
 
-/* ecmc_destroy -- frees every device allocation of ctx (NULL is a no-op) after
- * the work queued on its stream has finished; the configuration is lost
- * (read it first with ecmc_positions). The paper's programs keep their state
- * for the whole run; this is the end of a run (Alg. 1 after its last leg). */
+/* ecmc_destroy -- releases every device allocation of ctx (NULL is a no-op)
+ * after the work queued on its stream has finished: into the library's device
+ * memory cache (below), from which the next context of about the same size
+ * takes them. The configuration is lost (read it first with ecmc_positions).
+ * The paper's programs keep their state for the whole run; this is the end of
+ * a run (Alg. 1 after its last leg). */
 void ecmc_destroy(ecmc_ctx *ctx);
+
+/*
+ * Device memory cache. Contexts, batches and launches take their device
+ * arrays from a process-wide cache, one per device, instead of cudaMalloc, and
+ * give them back on destroy instead of cudaFree (each such driver call costs
+ * tens to hundreds of microseconds). A request takes the smallest cached block
+ * of at least its size and at most an eighth (plus 64 KiB) larger, else a new
+ * cudaMalloc; when that fails every cached block is freed and it is tried
+ * once more. The paper has no counterpart (its programs allocate once).
+ * ecmc_set_cache_limit -- bound on the bytes kept per device (default 4 GiB;
+ *   0 keeps nothing): cached blocks beyond it, least recently released
+ *   first, are freed at once. Errors: EINVAL (bytes < 0).
+ * ecmc_cache_info -- over all devices: the bytes held for reuse, the bytes
+ *   handed out and not yet released, and the requests served from the cache
+ *   (hits) or by cudaMalloc (misses). Any pointer may be NULL. Never fails.
+ */
+int ecmc_set_cache_limit(int64_t bytes);
+int ecmc_cache_info(int64_t *cached_bytes, int64_t *in_use_bytes, int64_t *hits,
+                    int64_t *misses);
 
 /* ecmc_last_error -- reason for the last failure on ctx ("" if none); the
    string belongs to ctx. With ctx == NULL, the last ecmc_create failure. */

@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "devmem.h"
 #include "ecmc.h"
 #include "graph.h"
 
@@ -2409,6 +2410,90 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
 
 // ------------------------------------------------------------------ host
 
+// ------------------------------------------------ device memory cache
+
+namespace {
+struct CudaBackend {
+    int alloc(void **p, size_t bytes) {
+        const cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) (void)cudaGetLastError();
+        return (int)e;
+    }
+    void free(void *p) { cudaFree(p); }
+};
+constexpr int DM_MAX_DEVICES = 64;
+constexpr size_t DM_DEFAULT_LIMIT = (size_t)4 << 30;  // cached bytes per device
+std::mutex g_dm_mu;
+BlockCache<CudaBackend> *g_dm[DM_MAX_DEVICES];
+size_t g_dm_limit = DM_DEFAULT_LIMIT;
+
+// The cache of device dev (created on first use, never destroyed: its blocks
+// would outlive the CUDA runtime at process exit).
+BlockCache<CudaBackend> *dm_cache(int dev) {
+    if (dev < 0 || dev >= DM_MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lock(g_dm_mu);
+    if (!g_dm[dev]) g_dm[dev] = new BlockCache<CudaBackend>(g_dm_limit);
+    return g_dm[dev];
+}
+}  // namespace
+
+int dm_alloc(void **p, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev = -1;
+    }
+    BlockCache<CudaBackend> *c = dm_cache(dev);
+    if (!c) return CudaBackend().alloc(p, bytes);
+    return c->acquire(p, bytes);
+}
+
+void dm_free(void *p) {
+    if (!p) return;
+    // the block goes back to the cache of the device that holds it
+    cudaPointerAttributes a;
+    int dev = -1;
+    if (cudaPointerGetAttributes(&a, p) == cudaSuccess)
+        dev = a.device;
+    else
+        (void)cudaGetLastError();
+    BlockCache<CudaBackend> *c = dm_cache(dev);
+    if (c)
+        c->release(p);
+    else
+        cudaFree(p);
+}
+
+extern "C" int ecmc_set_cache_limit(int64_t bytes) {
+    if (bytes < 0) return ECMC_EINVAL;
+    std::lock_guard<std::mutex> lock(g_dm_mu);
+    g_dm_limit = (size_t)bytes;
+    for (auto *c : g_dm)
+        if (c) c->set_limit(g_dm_limit);
+    return ECMC_OK;
+}
+
+extern "C" int ecmc_cache_info(int64_t *cached_bytes, int64_t *in_use_bytes, int64_t *hits,
+                               int64_t *misses) {
+    DevCacheInfo t = {0, 0, 0, 0};
+    {
+        std::lock_guard<std::mutex> lock(g_dm_mu);
+        for (auto *c : g_dm) {
+            if (!c) continue;
+            const DevCacheInfo i = c->info();
+            t.cached_bytes += i.cached_bytes;
+            t.in_use_bytes += i.in_use_bytes;
+            t.hits += i.hits;
+            t.misses += i.misses;
+        }
+    }
+    if (cached_bytes) *cached_bytes = t.cached_bytes;
+    if (in_use_bytes) *in_use_bytes = t.in_use_bytes;
+    if (hits) *hits = t.hits;
+    if (misses) *misses = t.misses;
+    return ECMC_OK;
+}
+
 // Launch scratch of the persistent kernel (reps, barrier, counters).
 struct Runner {
     int cap = 0;
@@ -2426,13 +2511,13 @@ struct Runner {
 static void runner_free(Runner &rn) {
     graph_batch_free(rn.gscratch);
     rn.gscratch = nullptr;
-    cudaFree(rn.d_reps);
-    cudaFree(rn.d_ctl);
-    cudaFree(rn.d_chain_base);
-    cudaFree(rn.d_comp_base);
-    cudaFree(rn.d_bar);
-    cudaFree(rn.d_g);
-    cudaFree(rn.d_phase);
+    dm_free(rn.d_reps);
+    dm_free(rn.d_ctl);
+    dm_free(rn.d_chain_base);
+    dm_free(rn.d_comp_base);
+    dm_free(rn.d_bar);
+    dm_free(rn.d_g);
+    dm_free(rn.d_phase);
     if (rn.ev0) cudaEventDestroy(rn.ev0);
     if (rn.ev1) cudaEventDestroy(rn.ev1);
     rn = Runner();
@@ -2453,8 +2538,6 @@ struct ecmc_ctx {
     // scratch of ecmc_positions, kept for the next call
     double *exp_x = nullptr, *exp_y = nullptr, *exp_t = nullptr;
     int32_t *exp_a = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     ecmc_profile_t prof = {};
     int n_sm = 1;
     int64_t legs_total = 0;
@@ -2501,18 +2584,18 @@ static int dalloc(ecmc_ctx *ctx, T **ptr, size_t count) {
     return 0;
 }
 
-// One cudaMalloc for every array requested since the last commit, each
-// starting on a 256-byte boundary.
+// One device block (from the device memory cache) for every array requested
+// since the last commit, each starting on a 256-byte boundary.
 static int pool_commit(ecmc_ctx *ctx) {
     size_t total = 0;
     for (auto &r : ctx->pending) total += (r.second + 255) & ~(size_t)255;
     void *base = nullptr;
     if (total) {
-        const cudaError_t e = cudaMalloc(&base, total);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
+        const int e = dm_alloc(&base, total);
+        if (e != 0) {
             ctx->pending.clear();
-            return fail(ctx, ECMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return fail(ctx, ECMC_ENOMEM,
+                        std::string("cudaMalloc: ") + cudaGetErrorString((cudaError_t)e));
         }
         ctx->allocs.push_back(base);
         ctx->device_bytes += (int64_t)total;
@@ -2598,8 +2681,7 @@ static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
     const size_t off_y = n * 8, off_a = 2 * n * 8, off_seen = (off_a + k * 4 + 15) & ~(size_t)15;
     const size_t off_bad = (off_seen + n * 4 + 15) & ~(size_t)15;
     char *scratch = nullptr;
-    if (cudaMalloc(&scratch, off_bad + 16) != cudaSuccess) {
-        (void)cudaGetLastError();
+    if (dm_alloc_t(&scratch, off_bad + 16) != 0) {
         g_create_err = "cudaMalloc failed (inputs)";
         return ECMC_ENOMEM;
     }
@@ -2609,7 +2691,11 @@ static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
     unsigned long long *bad = (unsigned long long *)(scratch + off_bad);
     const double *sx = x, *sy = y;
     const int32_t *sa = active;
-    auto release = [&]() { cudaFree(scratch); };
+    auto release = [&]() {
+        // (copies or the check may still read the scratch after a failure)
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) (void)cudaGetLastError();
+        dm_free(scratch);
+    };
     if (!dev_in) {
         if (cudaMemcpyAsync(dx, x, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
             cudaMemcpyAsync(dy, y, n * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
@@ -2940,46 +3026,72 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         return ECMC_ECAPACITY;
     }
     CU(cudaMemsetAsync(s.lc, 0, LC_N * sizeof(unsigned long long), st));
-    CU(cudaEventCreate(&ctx->ev0));
-    CU(cudaEventCreate(&ctx->ev1));
-    for (auto &e : ctx->kev) CU(cudaEventCreate(&e));
     *out = ctx;
     return ECMC_OK;
+}
+
+// Grids of the persistent launch on the current device (SMs x resident
+// blocks, for 4 and 8 slots per cell): queried once per device.
+static bool run_grids(int *grid4, int *grid8) {
+    static std::mutex mu;
+    static int g4[DM_MAX_DEVICES], g8[DM_MAX_DEVICES];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    const bool cached = dev >= 0 && dev < DM_MAX_DEVICES && g4[dev] > 0;
+    if (!cached) {
+        int n_sm = 1, b4 = 0, b8 = 0, coop = 0;
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, RUN_THREADS,
+                                                          UF_SMEM_BYTES) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, RUN_THREADS,
+                                                          UF_SMEM_BYTES) != cudaSuccess ||
+            !coop || b4 < 1 || b8 < 1) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (dev >= 0 && dev < DM_MAX_DEVICES) {
+            g4[dev] = n_sm * b4;
+            g8[dev] = n_sm * b8;
+        }
+        *grid4 = n_sm * b4;
+        *grid8 = n_sm * b8;
+        return true;
+    }
+    *grid4 = g4[dev];
+    *grid8 = g8[dev];
+    return true;
 }
 
 static int runner_reserve(Runner &rn, int R, std::string &err) {
     if (rn.cap >= R && rn.d_reps) return 0;
     runner_free(rn);
     const int cap = std::max(R, 1);
-    if (cudaMalloc(&rn.d_reps, cap * sizeof(Dev)) != cudaSuccess ||
-        cudaMalloc(&rn.d_ctl, cap * sizeof(RepCtl)) != cudaSuccess ||
-        cudaMalloc(&rn.d_chain_base, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&rn.d_comp_base, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&rn.d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc(&rn.d_g, G_N * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&rn.d_phase, PH_N * sizeof(unsigned long long)) != cudaSuccess ||
+    if (dm_alloc_t(&rn.d_reps, cap * sizeof(Dev)) != 0 ||
+        dm_alloc_t(&rn.d_ctl, cap * sizeof(RepCtl)) != 0 ||
+        dm_alloc_t(&rn.d_chain_base, (cap + 1) * sizeof(int32_t)) != 0 ||
+        dm_alloc_t(&rn.d_comp_base, (cap + 1) * sizeof(int32_t)) != 0 ||
+        dm_alloc_t(&rn.d_bar, 2 * sizeof(unsigned int)) != 0 ||
+        dm_alloc_t(&rn.d_g, G_N * sizeof(int32_t)) != 0 ||
+        dm_alloc_t(&rn.d_phase, PH_N * sizeof(unsigned long long)) != 0 ||
         cudaEventCreate(&rn.ev0) != cudaSuccess || cudaEventCreate(&rn.ev1) != cudaSuccess) {
         (void)cudaGetLastError();
         runner_free(rn);
         err = "runner allocation failed";
         return ECMC_ENOMEM;
     }
-    int dev = 0, n_sm = 1, b4 = 0, b8 = 0, coop = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_run<4>, RUN_THREADS, UF_SMEM_BYTES) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_run<8>, RUN_THREADS, UF_SMEM_BYTES) !=
-            cudaSuccess ||
-        !coop || b4 < 1 || b8 < 1) {
-        (void)cudaGetLastError();
+    int grid4 = 0, grid8 = 0;
+    if (!run_grids(&grid4, &grid8)) {
         runner_free(rn);
         err = "cooperative launch unavailable";
         return ECMC_ECUDA;
     }
-    rn.grid4 = n_sm * b4;
-    rn.grid8 = n_sm * b8;
+    rn.grid4 = grid4;
+    rn.grid8 = grid8;
     rn.cap = cap;
     return 0;
 }
@@ -3066,11 +3178,10 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
             return ECMC_ECUDA;
         }
         if (c->flags_cap < max_legs) {
-            cudaFree(c->d_flags);
+            dm_free(c->d_flags);
             c->d_flags = nullptr;
             c->flags_cap = 0;
-            if (cudaMalloc(&c->d_flags, (size_t)max_legs) != cudaSuccess) {
-                (void)cudaGetLastError();
+            if (dm_alloc_t(&c->d_flags, (size_t)max_legs) != 0) {
                 err = "flags allocation";
                 return ECMC_ENOMEM;
             }
@@ -3285,6 +3396,7 @@ extern "C" const char *ecmc_batch_last_error(const ecmc_batch *b) {
 
 extern "C" void ecmc_batch_destroy(ecmc_batch *b) {
     if (!b) return;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) (void)cudaGetLastError();
     runner_free(b->run);
     delete b;
 }
@@ -3431,14 +3543,13 @@ extern "C" int ecmc_liftings(ecmc_ctx *ctx, ecmc_lift_t *buf, int64_t cap, int64
 
 extern "C" void ecmc_destroy(ecmc_ctx *ctx) {
     if (!ctx) return;
+    // (every call on the context has synchronised its stream before
+    // returning; this one makes sure before its blocks go to the cache)
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) (void)cudaGetLastError();
     graph_destroy(ctx->graph);
     runner_free(ctx->run);
-    cudaFree(ctx->d_flags);
-    for (void *p : ctx->allocs) cudaFree(p);
-    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
-    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
-    for (auto e : ctx->kev)
-        if (e) cudaEventDestroy(e);
+    dm_free(ctx->d_flags);
+    for (void *p : ctx->allocs) dm_free(p);
     delete ctx;
 }
 

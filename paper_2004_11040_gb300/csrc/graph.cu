@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "devmem.h"
 #include "graph.h"
 
 namespace {
@@ -1790,8 +1791,7 @@ int gcommit(GraphCtx *g, std::string &err) {
     for (auto &r : g->pending) total += (r.second + 255) & ~(size_t)255;
     void *base = nullptr;
     if (total) {
-        if (cudaMalloc(&base, total) != cudaSuccess) {
-            (void)cudaGetLastError();
+        if (dm_alloc(&base, total) != 0) {
             g->pending.clear();
             err = "cudaMalloc failed (graph state)";
             return ECMC_ENOMEM;
@@ -1851,16 +1851,12 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     // scratch of the build, kept by the context for the next direction change
     void **tmp = g->build_tmp;
     if (!tmp[0]) {
-        if (cudaMalloc(&tmp[0], nslot * 4) != cudaSuccess ||
-            cudaMalloc(&tmp[1], nslot * 8) != cudaSuccess ||
-            cudaMalloc(&tmp[2], nslot * 8) != cudaSuccess ||
-            cudaMalloc(&tmp[3], ((size_t)b.nb + 1) * 4) != cudaSuccess ||
-            cudaMalloc(&tmp[4], 8) != cudaSuccess ||
-            cudaMalloc(&tmp[5], nslot * 4) != cudaSuccess ||
-            cudaMalloc(&tmp[6], (((size_t)b.nb + SCAN_TILE - 1) / SCAN_TILE) * 4) != cudaSuccess) {
-            (void)cudaGetLastError();
+        if (dm_alloc(&tmp[0], nslot * 4) != 0 || dm_alloc(&tmp[1], nslot * 8) != 0 ||
+            dm_alloc(&tmp[2], nslot * 8) != 0 || dm_alloc(&tmp[3], ((size_t)b.nb + 1) * 4) != 0 ||
+            dm_alloc(&tmp[4], 8) != 0 || dm_alloc(&tmp[5], nslot * 4) != 0 ||
+            dm_alloc(&tmp[6], (((size_t)b.nb + SCAN_TILE - 1) / SCAN_TILE) * 4) != 0) {
             for (int q = 0; q < 7; ++q) {
-                cudaFree(tmp[q]);
+                dm_free(tmp[q]);
                 tmp[q] = nullptr;
             }
             err = "cudaMalloc failed (graph build)";
@@ -2052,11 +2048,10 @@ int graph_run(GraphCtx *g, int32_t n_legs, uint64_t budget, uint8_t *flags_host,
     }
     cudaStream_t st = g->st;
     if (g->flags_cap < n_legs) {
-        cudaFree(g->d_flags);
+        dm_free(g->d_flags);
         g->d_flags = nullptr;
         g->flags_cap = 0;
-        if (cudaMalloc(&g->d_flags, (size_t)n_legs) != cudaSuccess) {
-            (void)cudaGetLastError();
+        if (dm_alloc_t(&g->d_flags, (size_t)n_legs) != 0) {
             err = "flags allocation";
             return ECMC_ENOMEM;
         }
@@ -2161,14 +2156,14 @@ struct GBatchScratch {
 
 void graph_batch_free(GBatchScratch *b) {
     if (!b) return;
-    cudaFree(b->d_S);
-    cudaFree(b->d_ctl);
-    cudaFree(b->d_chain_base);
-    cudaFree(b->d_comp_base);
-    cudaFree(b->d_g);
-    cudaFree(b->d_err);
-    cudaFree(b->d_bar);
-    cudaFree(b->d_phase);
+    dm_free(b->d_S);
+    dm_free(b->d_ctl);
+    dm_free(b->d_chain_base);
+    dm_free(b->d_comp_base);
+    dm_free(b->d_g);
+    dm_free(b->d_err);
+    dm_free(b->d_bar);
+    dm_free(b->d_phase);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -2209,20 +2204,19 @@ int graph_batch_run(GBatchScratch **scratch, GraphCtx *const *gs, int32_t n, int
         *scratch = b;
     }
     if (b->cap < n) {
-        cudaFree(b->d_S);
-        cudaFree(b->d_ctl);
-        cudaFree(b->d_chain_base);
-        cudaFree(b->d_comp_base);
+        const int cap = std::max(n, 2 * b->cap);
+        dm_free(b->d_S);
+        dm_free(b->d_ctl);
+        dm_free(b->d_chain_base);
+        dm_free(b->d_comp_base);
         b->d_S = nullptr;
         b->d_ctl = nullptr;
         b->d_chain_base = b->d_comp_base = nullptr;
         b->cap = 0;
-        const int cap = std::max(n, 2 * b->cap);
-        if (cudaMalloc(&b->d_S, (size_t)cap * sizeof(GDev)) != cudaSuccess ||
-            cudaMalloc(&b->d_ctl, (size_t)cap * sizeof(GCtl)) != cudaSuccess ||
-            cudaMalloc(&b->d_chain_base, (size_t)(cap + 1) * 4) != cudaSuccess ||
-            cudaMalloc(&b->d_comp_base, (size_t)(cap + 1) * 4) != cudaSuccess) {
-            (void)cudaGetLastError();
+        if (dm_alloc_t(&b->d_S, (size_t)cap * sizeof(GDev)) != 0 ||
+            dm_alloc_t(&b->d_ctl, (size_t)cap * sizeof(GCtl)) != 0 ||
+            dm_alloc_t(&b->d_chain_base, (size_t)(cap + 1) * 4) != 0 ||
+            dm_alloc_t(&b->d_comp_base, (size_t)(cap + 1) * 4) != 0) {
             err = "batch scratch";
             return ECMC_ENOMEM;
         }
@@ -2230,10 +2224,10 @@ int graph_batch_run(GBatchScratch **scratch, GraphCtx *const *gs, int32_t n, int
     }
     if (!b->d_g) {
         int dev = 0, n_sm = 1, blocks = 0;
-        if (cudaMalloc(&b->d_g, GB_N * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&b->d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
-            cudaMalloc(&b->d_phase, GPH_N * sizeof(unsigned long long)) != cudaSuccess ||
+        if (dm_alloc_t(&b->d_g, GB_N * sizeof(int32_t)) != 0 ||
+            dm_alloc_t(&b->d_err, sizeof(int32_t)) != 0 ||
+            dm_alloc_t(&b->d_bar, 2 * sizeof(unsigned int)) != 0 ||
+            dm_alloc_t(&b->d_phase, GPH_N * sizeof(unsigned long long)) != 0 ||
             cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
             cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -2262,11 +2256,10 @@ int graph_batch_run(GBatchScratch **scratch, GraphCtx *const *gs, int32_t n, int
         GraphCtx *g = gs[r];
         if (g->st != st) cu(cudaStreamSynchronize(g->st), "context stream");
         if (g->flags_cap < max_legs) {
-            cudaFree(g->d_flags);
+            dm_free(g->d_flags);
             g->d_flags = nullptr;
             g->flags_cap = 0;
-            if (cudaMalloc(&g->d_flags, (size_t)max_legs) != cudaSuccess) {
-                (void)cudaGetLastError();
+            if (dm_alloc_t(&g->d_flags, (size_t)max_legs) != 0) {
                 err = "flags allocation";
                 return ECMC_ENOMEM;
             }
@@ -2392,15 +2385,20 @@ int graph_arrows(GraphCtx *g, int32_t *a, double *b, std::string &err) {
 int graph_transpose(GraphCtx *g, std::string &err) {
     GDev &s = g->s;
     double *xnew = nullptr;
-    if (cudaMalloc(&xnew, (size_t)s.n * 8) != cudaSuccess) {
-        (void)cudaGetLastError();
+    if (dm_alloc_t(&xnew, (size_t)s.n * 8) != 0) {
         err = "transpose scratch";
         return ECMC_ENOMEM;
     }
     k_g_swap_xy<<<(unsigned)((s.n + 255) / 256), 256, 0, g->st>>>(s, xnew);
     k_g_reset_chains<<<(unsigned)((s.k + 127) / 128), 128, 0, g->st>>>(s);
     int rc = graph_build(g, xnew, s.y, err);  // x, t = 0 and arrows for the new frame
-    cudaFree(xnew);
+    // (the build's kernels read xnew: done before the block goes back)
+    if (cudaStreamSynchronize(g->st) != cudaSuccess && rc == 0) {
+        (void)cudaGetLastError();
+        err = "transpose";
+        rc = ECMC_ECUDA;
+    }
+    dm_free(xnew);
     return rc;
 }
 
@@ -2437,9 +2435,10 @@ int graph_liftings(GraphCtx *g, ecmc_lift_t *buf, int64_t cap, int64_t *n_out,
 
 void graph_destroy(GraphCtx *g) {
     if (!g) return;
-    for (void *p : g->allocs) cudaFree(p);
-    for (void *p : g->build_tmp) cudaFree(p);
-    cudaFree(g->d_flags);
+    if (cudaStreamSynchronize(g->st) != cudaSuccess) (void)cudaGetLastError();
+    for (void *p : g->allocs) dm_free(p);
+    for (void *p : g->build_tmp) dm_free(p);
+    dm_free(g->d_flags);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;

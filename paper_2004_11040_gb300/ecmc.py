@@ -30,7 +30,8 @@ EXPORTS = ("ecmc_create", "ecmc_run_to_breakpoint", "ecmc_positions", "ecmc_stat
            "ecmc_profile", "ecmc_liftings", "ecmc_destroy", "ecmc_last_error",
            "ecmc_batch_create", "ecmc_batch_run", "ecmc_batch_last_error",
            "ecmc_batch_destroy", "ecmc_leg_noalloc", "ecmc_set_direction",
-           "ecmc_graph_arrows", "ecmc_set_wait_limit", "ecmc_context_bytes")
+           "ecmc_graph_arrows", "ecmc_set_wait_limit", "ecmc_context_bytes",
+           "ecmc_set_cache_limit", "ecmc_cache_info")
 
 
 class ecmc_params(C.Structure):
@@ -97,6 +98,10 @@ def load(path: str | None = None):
     lib.ecmc_set_wait_limit.restype = C.c_int
     lib.ecmc_context_bytes.argtypes = [C.POINTER(ecmc_params), C.POINTER(C.c_int64)]
     lib.ecmc_context_bytes.restype = C.c_int
+    lib.ecmc_set_cache_limit.argtypes = [C.c_int64]
+    lib.ecmc_set_cache_limit.restype = C.c_int
+    lib.ecmc_cache_info.argtypes = [C.POINTER(C.c_int64)] * 4
+    lib.ecmc_cache_info.restype = C.c_int
     lib.ecmc_stats.argtypes = [vp, C.POINTER(ecmc_stats_t)]
     lib.ecmc_stats.restype = C.c_int
     lib.ecmc_profile.argtypes = [vp, C.POINTER(ecmc_profile_t)]
@@ -174,6 +179,18 @@ def ecmc_context_bytes(params) -> int:
     if rc != ECMC_OK:
         raise EcmcError(rc, "ecmc_context_bytes")
     return int(out.value)
+
+
+def ecmc_set_cache_limit(nbytes: int):
+    """Bound on the device bytes the library keeps for reuse per device (0: none)."""
+    _check(load().ecmc_set_cache_limit(int(nbytes)))
+
+
+def ecmc_cache_info() -> dict:
+    """The device memory cache: bytes cached and in use, hits and misses."""
+    v = [C.c_int64() for _ in range(4)]
+    _check(load().ecmc_cache_info(*[C.byref(x) for x in v]))
+    return dict(zip(("cached_bytes", "in_use_bytes", "hits", "misses"), (x.value for x in v)))
 
 
 def ecmc_set_wait_limit(ctx, ns: int):
