@@ -138,9 +138,17 @@ def test_server_poisson_arrivals_complete():
 def test_context_bytes_are_what_a_context_holds():
     """ecmc_context_bytes (nothing allocated) equals the device_bytes of the
     created context, and the device's free memory drops by that much (to the
-    allocator's granularity)."""
+    allocator's granularity) when the library's cache holds nothing."""
     import torch
     from paper_2004_11040_gb300 import synth
+    ecmc.ecmc_set_cache_limit(0)  # every block from cudaMalloc, back by cudaFree
+    try:
+        _context_bytes_cases(torch, synth)
+    finally:
+        ecmc.ecmc_set_cache_limit(4 << 30)
+
+
+def _context_bytes_cases(torch, synth):
     for m, k, cells, graph in ((64, 64, 64, False), (256, 512, 0, False), (512, 512, 512, False),
                                (64, 64, 0, True), (512, 512, 512, True)):
         s = synth.lattice_start(m, 0.70, k, seed=1)
