@@ -833,23 +833,52 @@ __device__ __forceinline__ void note_blocked(const Dev &s, int c, int32_t partne
 
 // ---------------------------------------------------------------- kernels
 
-// Cells from positions (slot order is irrelevant to every result).
+// Cells from positions, in two passes (slot order is irrelevant to every
+// result). k_place puts each disk's id into a free slot of its cell (a
+// compare-and-swap per disk, from slot 0; cid must hold EMPTY) and, with
+// bad_xy, counts coordinates outside [0, L). k_fill then writes every slot's
+// fields row by row -- whole 32-byte sectors, the slots of a cell by
+// consecutive threads -- and each disk's slot into loc_of. (Writing a disk's
+// fields from its own thread scattered partial-sector writes over the arrays,
+// one per field: about four times the time of both passes.)
 template <int C>
-__global__ void k_build_cells(Dev s, const double *x, const double *y) {
+__global__ void k_place(Dev s, const double *x, const double *y, unsigned long long *bad_xy) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= s.n) return;
-    const uint32_t cell = cell_of(x[q], y[q], s);
-    for (int sl = 0; sl < C; ++sl) {
-        const uint32_t loc = cell * C + sl;
-        if (atomicCAS(s.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
-            s.cx[loc] = x[q];
-            s.cy[loc] = y[q];
-            s.ct[loc] = 0.0;
-            s.cown[loc] = OWN_STATIC;
-            return;
-        }
-    }
+    const double xq = x[q], yq = y[q];
+    if (bad_xy && !(xq >= 0.0 && xq < s.L && yq >= 0.0 && yq < s.L)) atomicAdd(bad_xy, 1ull);
+    const uint32_t cell = cell_of(xq, yq, s);
+    for (int sl = 0; sl < C; ++sl)
+        if (atomicCAS(s.cid + cell * C + sl, EMPTY, (uint32_t)q) == EMPTY) return;
     atomicAdd(s.lc + LC_ERR_CAP, 1ull);
+}
+
+// One block per cell row (grid = nc). An empty slot's fields are never read;
+// they are written all the same, so that every sector is written whole.
+template <int C>
+__global__ void k_fill(Dev s, const double *x, const double *y, uint32_t *loc_of) {
+    const uint32_t nrow = (uint32_t)s.nc * C, base = (uint32_t)blockIdx.x * nrow;
+    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
+        const uint32_t q = base + o;
+        const uint32_t id = s.cid[q];
+        double xv = 0.0, yv = 0.0;
+        if (id != EMPTY) {
+            xv = x[id];
+            yv = y[id];
+            loc_of[id] = q;
+        }
+        s.cx[q] = xv;
+        s.cy[q] = yv;
+        s.ct[q] = 0.0;
+        s.cown[q] = OWN_STATIC;
+    }
+}
+
+template <int C>
+static void launch_cells(const Dev &s, const double *x, const double *y, uint32_t *loc_of,
+                         unsigned long long *bad_xy, cudaStream_t st) {
+    k_place<C><<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, x, y, bad_xy);
+    k_fill<C><<<(unsigned)s.nc, 256, 0, st>>>(s, x, y, loc_of);
 }
 
 // Least and largest y of each cell row, then the rows a disk's scan need not
@@ -862,38 +891,41 @@ __global__ void k_build_cells(Dev s, const double *x, const double *y) {
 // - It skips row R - 1 when RN(y - yhi(R - 1)) >= d, by the same argument.
 // An empty row is skipped. Moves along x never change a disk's row, so the
 // bits hold until the frame is transposed.
-__global__ void k_band_init(Dev s) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= s.nc) return;
-    s.rband[q] = INF_BITS;
-    s.rband[s.nc + q] = 0ull;
-}
-
-// A row is nc * C consecutive slots, so a warp's slots nearly always share
-// one: the warp reduces first and its lanes of each row issue one atomic pair.
-__global__ void k_bands(Dev s, int C) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const bool in = q < (int64_t)s.nc * s.nc * C;
-    const bool occ = in && s.cid[q] != EMPTY;
-    const int R = in ? (int)((q / C) / s.nc) : -1;
-    const unsigned long long y = occ ? dbits(s.cy[q]) : 0ull;  // y >= 0: bits order like values
-    unsigned long long lo = occ ? y : INF_BITS, hi = y;
-    const int R0 = __shfl_sync(FULL, R, 0);
-    if (__all_sync(FULL, R == R0)) {
+// One block per cell row (a row is nc * C consecutive slots; grid = nc,
+// 256 threads): the block reduces the row and thread 0 writes its band
+// (INF_BITS and 0 for an empty row). No atomics, no 64-bit division.
+constexpr int BAND_THREADS = 256;
+__global__ void __launch_bounds__(BAND_THREADS) k_bands(Dev s, int C) {
+    __shared__ unsigned long long wlo[BAND_THREADS / 32], whi[BAND_THREADS / 32];
+    const uint32_t nrow = (uint32_t)s.nc * (uint32_t)C, base = (uint32_t)blockIdx.x * nrow;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long lo = INF_BITS, hi = 0ull;
+    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
+        const uint32_t q = base + o;
+        if (s.cid[q] != EMPTY) {
+            const unsigned long long y = dbits(s.cy[q]);  // y >= 0: bits order like values
+            lo = y < lo ? y : lo;
+            hi = y > hi ? y : hi;
+        }
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long l2 = shfl_xor_u64(lo, o), h2 = shfl_xor_u64(hi, o);
-            lo = l2 < lo ? l2 : lo;
-            hi = h2 > hi ? h2 : hi;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = shfl_xor_u64(lo, o), h2 = shfl_xor_u64(hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if (lane == 0) {
+        wlo[w] = lo;
+        whi[w] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < BAND_THREADS / 32; ++q) {
+            lo = wlo[q] < lo ? wlo[q] : lo;
+            hi = whi[q] > hi ? whi[q] : hi;
         }
-        if (lane == 0 && R0 >= 0 && lo != INF_BITS) {
-            atomicMin(s.rband + R0, lo);
-            atomicMax(s.rband + s.nc + R0, hi);
-        }
-    } else if (occ) {
-        atomicMin(s.rband + R, y);
-        atomicMax(s.rband + s.nc + R, y);
+        s.rband[blockIdx.x] = lo;
+        s.rband[s.nc + blockIdx.x] = hi;
     }
 }
 
@@ -903,53 +935,53 @@ __global__ void k_bands(Dev s, int C) {
 // y_j falls, so RN(L - RN(yhi(nc - 1) - y)) >= d bounds the whole row; from row
 // nc - 1 towards row 0 it is RN(L - RN(y - y_j)), bounded by RN(L - RN(y -
 // ylo(0))). (The plain difference there is close to L, far above d.)
-__global__ void k_skip(Dev s, int C) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int nc = s.nc;
-    if (q >= (int64_t)nc * nc * C) return;
-    const int R = (int)((q / C) / nc);
-    uint8_t v = 0;
-    if (s.cid[q] != EMPTY && nc >= 5) {
-        const double y = s.cy[q];
-        const int Rdn = R == 0 ? nc - 1 : R - 1, Rup = R == nc - 1 ? 0 : R + 1;
-        const unsigned long long lo_dn = s.rband[Rdn], lo_up = s.rband[Rup];
-        const double hi_dn = __longlong_as_double((long long)s.rband[nc + Rdn]);
-        const double lo = __longlong_as_double((long long)lo_up);
-        if (lo_dn == INF_BITS) {
-            v |= 1;
-        } else if (R == 0) {
-            if (!(__dsub_rn(s.L, __dsub_rn(hi_dn, y)) < s.d)) v |= 1;
-        } else if (!(__dsub_rn(y, hi_dn) < s.d)) {
-            v |= 1;
+// One block per cell row (grid = nc), as k_bands.
+__global__ void __launch_bounds__(BAND_THREADS) k_skip(Dev s, int C) {
+    const int nc = s.nc, R = (int)blockIdx.x;
+    const uint32_t nrow = (uint32_t)nc * (uint32_t)C, base = (uint32_t)R * nrow;
+    const int Rdn = R == 0 ? nc - 1 : R - 1, Rup = R == nc - 1 ? 0 : R + 1;
+    const unsigned long long lo_dn = s.rband[Rdn], lo_up = s.rband[Rup];
+    const double hi_dn = __longlong_as_double((long long)s.rband[nc + Rdn]);
+    const double lo = __longlong_as_double((long long)lo_up);
+    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
+        const uint32_t q = base + o;
+        uint8_t v = 0;
+        if (s.cid[q] != EMPTY && nc >= 5) {
+            const double y = s.cy[q];
+            if (lo_dn == INF_BITS) {
+                v |= 1;
+            } else if (R == 0) {
+                if (!(__dsub_rn(s.L, __dsub_rn(hi_dn, y)) < s.d)) v |= 1;
+            } else if (!(__dsub_rn(y, hi_dn) < s.d)) {
+                v |= 1;
+            }
+            if (lo_up == INF_BITS) {
+                v |= 2;
+            } else if (R == nc - 1) {
+                if (!(__dsub_rn(s.L, __dsub_rn(y, lo)) < s.d)) v |= 2;
+            } else if (!(__dsub_rn(lo, y) < s.d)) {
+                v |= 2;
+            }
         }
-        if (lo_up == INF_BITS) {
-            v |= 2;
-        } else if (R == nc - 1) {
-            if (!(__dsub_rn(s.L, __dsub_rn(y, lo)) < s.d)) v |= 2;
-        } else if (!(__dsub_rn(lo, y) < s.d)) {
-            v |= 2;
-        }
+        s.cskp[q] = v;
     }
-    s.cskp[q] = v;
 }
 
 // Skip bits for the current frame (after the cells are built or transposed).
 static void launch_skip(const Dev &s, int C, cudaStream_t st) {
-    const size_t nslot = (size_t)s.nc * s.nc * C;
-    k_band_init<<<(unsigned)((s.nc + 255) / 256), 256, 0, st>>>(s);
-    k_bands<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C);
-    k_skip<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C);
+    k_bands<<<(unsigned)s.nc, BAND_THREADS, 0, st>>>(s, C);
+    k_skip<<<(unsigned)s.nc, BAND_THREADS, 0, st>>>(s, C);
 }
 
-// Coordinates in [0, L) (counted in *bad_xy) and distinct active ids in
-// [0, n) (*bad_id), checked on the device where the inputs already are.
-// seen[] must be zero.
+// Coordinates in [0, L) (counted in *bad_xy; not checked with x == null) and
+// distinct active ids in [0, n) (*bad_id), checked on the device where the
+// inputs already are. seen[] must be zero.
 __global__ void k_check_inputs(const double *x, const double *y, const int32_t *active,
                                int64_t n, int k, double L, uint32_t *seen,
                                unsigned long long *bad_xy, unsigned long long *bad_id) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t q = t0; q < n; q += stride)
+    for (int64_t q = t0; x && q < n; q += stride)
         if (!(x[q] >= 0.0 && x[q] < L && y[q] >= 0.0 && y[q] < L)) atomicAdd(bad_xy, 1ull);
     for (int64_t c = t0; c < k; c += stride) {
         const int32_t a = active[c];
@@ -960,16 +992,9 @@ __global__ void k_check_inputs(const double *x, const double *y, const int32_t *
 static void launch_check(const double *x, const double *y, const int32_t *active, int64_t n,
                          int k, double L, uint32_t *seen, unsigned long long *bad_xy,
                          unsigned long long *bad_id, cudaStream_t st) {
-    const int64_t work = std::max<int64_t>(n, k);
+    const int64_t work = x ? std::max<int64_t>(n, k) : (int64_t)k;
     const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
     k_check_inputs<<<blocks, 256, 0, st>>>(x, y, active, n, k, L, seen, bad_xy, bad_id);
-}
-
-__global__ void k_locate(Dev s, int C, uint32_t *loc_of) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)s.nc * s.nc * C) return;
-    const uint32_t id = s.cid[q];
-    if (id != EMPTY) loc_of[id] = (uint32_t)q;
 }
 
 __global__ void k_init_chains(Dev s, const int32_t *active, const uint32_t *loc_of) {
@@ -2739,11 +2764,6 @@ static int create_graph(ecmc_ctx *ctx, int nc, const double *x, const double *y,
     return rc;
 }
 
-template <int C>
-static void launch_build(ecmc_ctx *ctx, const double *x, const double *y) {
-    const int64_t n = ctx->s.n;
-    k_build_cells<C><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->s, x, y);
-}
 
 // Device arrays of a cell-scan context, set up but not allocated yet: the
 // scalar description in ctx->s and one request per array in ctx->pending
@@ -2992,18 +3012,18 @@ extern "C" int ecmc_create(const ecmc_params *p, const double *x, const double *
         s.colx = d_colx;
         s.xbound = d_xbound;
     }
-    // the inputs are checked on the device (loc_of holds the ids seen until
-    // k_locate fills it); nothing below indexes by an active id before
-    // k_init_chains, which does nothing if an id failed
+    // the inputs are checked on the device: the active ids here (loc_of holds
+    // the ids seen until k_fill writes the slots into it), the coordinates by
+    // k_place; nothing below indexes by an active id before k_init_chains,
+    // which does nothing if an id failed
     CU(cudaMemsetAsync(loc_of, 0, n * sizeof(uint32_t), st));
-    launch_check(sx, sy, sa, (int64_t)n, (int)k, s.L, loc_of, s.lc + LC_BADXY, s.lc + LC_BADID,
-                 st);
+    launch_check(nullptr, nullptr, sa, (int64_t)n, (int)k, s.L, loc_of, s.lc + LC_BADXY,
+                 s.lc + LC_BADID, st);
     if (C == 4)
-        launch_build<4>(ctx, sx, sy);
+        launch_cells<4>(s, sx, sy, loc_of, s.lc + LC_BADXY, st);
     else
-        launch_build<8>(ctx, sx, sy);
+        launch_cells<8>(s, sx, sy, loc_of, s.lc + LC_BADXY, st);
     launch_skip(s, C, st);
-    k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
     k_init_chains<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(s, sa, loc_of);
     CU(cudaGetLastError());
     {
@@ -3713,8 +3733,7 @@ static int noalloc_run(Dev &s, uint32_t *loc_of, double *x, const double *y, int
     CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
     CUN(cudaStreamSynchronize(st));
     if (lc[LC_ERR_CAP]) return ECMC_EINVAL;
-    k_build_cells<C><<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, x, y);
-    k_locate<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(s, C, loc_of);
+    launch_cells<C>(s, x, y, loc_of, nullptr, st);
     k_init_chains<<<(unsigned)((s.k + 255) / 256), 256, 0, st>>>(s, active, loc_of);
     CUN(cudaGetLastError());
     CUN(cudaMemcpyAsync(lc, s.lc, sizeof lc, cudaMemcpyDeviceToHost, st));
