@@ -1955,7 +1955,7 @@ struct RepCtl {
     int32_t incons;         // chain-table checks that failed (must stay 0)
     int32_t bad_where;      // first failure: leg * 65536 + window * 16 + phase
     int32_t bad_chain;
-    int32_t pad2;
+    int32_t dbg;            // an internal check recorded in Dev::dbg (set at the end)
 };
 
 enum { G_WORK = 0, G_ANY, G_ERR, G_REMAIN0, G_REMAIN1, G_UFDONE, G_N };
@@ -2429,6 +2429,11 @@ __global__ void __launch_bounds__(RUN_THREADS, RUN_MIN_BLOCKS) k_run(Batch b) {
         mark(PH_END);
         if (b.g[G_REMAIN0 + (leg & 1)] == 0) break;
     }
+    // the replicas whose internal checks recorded a failure (Dev::dbg[0]),
+    // for the host, which reads the details of those only
+    if (blockIdx.x == 0)
+        for (int r = threadIdx.x; r < R; r += blockDim.x)
+            if (b.reps[r].dbg && __ldcg(b.reps[r].dbg) != 0.0) b.ctl[r].dbg = 1;
 }
 
 }  // namespace
@@ -2522,6 +2527,13 @@ extern "C" int ecmc_cache_info(int64_t *cached_bytes, int64_t *in_use_bytes, int
 // Launch scratch of the persistent kernel (reps, barrier, counters).
 struct Runner {
     int cap = 0;
+    // one device block: [reps | chain_base | comp_base | ctl | bar | g | phase]
+    // (256-byte aligned parts), uploaded whole before a launch and read back
+    // from ctl on after it, through `host` (one copy each way)
+    unsigned char *block = nullptr;
+    size_t off_base = 0, off_comp = 0, off_ctl = 0, off_bar = 0, off_g = 0, off_phase = 0,
+           total = 0;
+    std::vector<unsigned char> host;
     Dev *d_reps = nullptr;
     RepCtl *d_ctl = nullptr;
     int32_t *d_chain_base = nullptr, *d_comp_base = nullptr;
@@ -2536,13 +2548,7 @@ struct Runner {
 static void runner_free(Runner &rn) {
     graph_batch_free(rn.gscratch);
     rn.gscratch = nullptr;
-    dm_free(rn.d_reps);
-    dm_free(rn.d_ctl);
-    dm_free(rn.d_chain_base);
-    dm_free(rn.d_comp_base);
-    dm_free(rn.d_bar);
-    dm_free(rn.d_g);
-    dm_free(rn.d_phase);
+    dm_free(rn.block);
     if (rn.ev0) cudaEventDestroy(rn.ev0);
     if (rn.ev1) cudaEventDestroy(rn.ev1);
     rn = Runner();
@@ -3091,13 +3097,22 @@ static int runner_reserve(Runner &rn, int R, std::string &err) {
     if (rn.cap >= R && rn.d_reps) return 0;
     runner_free(rn);
     const int cap = std::max(R, 1);
-    if (dm_alloc_t(&rn.d_reps, cap * sizeof(Dev)) != 0 ||
-        dm_alloc_t(&rn.d_ctl, cap * sizeof(RepCtl)) != 0 ||
-        dm_alloc_t(&rn.d_chain_base, (cap + 1) * sizeof(int32_t)) != 0 ||
-        dm_alloc_t(&rn.d_comp_base, (cap + 1) * sizeof(int32_t)) != 0 ||
-        dm_alloc_t(&rn.d_bar, 2 * sizeof(unsigned int)) != 0 ||
-        dm_alloc_t(&rn.d_g, G_N * sizeof(int32_t)) != 0 ||
-        dm_alloc_t(&rn.d_phase, PH_N * sizeof(unsigned long long)) != 0 ||
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    (void)take(cap * sizeof(Dev));
+    rn.off_base = take((cap + 1) * sizeof(int32_t));
+    rn.off_comp = take((cap + 1) * sizeof(int32_t));
+    rn.off_ctl = take(cap * sizeof(RepCtl));
+    rn.off_bar = take(2 * sizeof(unsigned int));
+    rn.off_g = take(G_N * sizeof(int32_t));
+    rn.off_phase = take(PH_N * sizeof(unsigned long long));
+    rn.total = off;
+    rn.host.assign(rn.total, 0);
+    if (dm_alloc_t(&rn.block, rn.total) != 0 ||
         cudaEventCreate(&rn.ev0) != cudaSuccess || cudaEventCreate(&rn.ev1) != cudaSuccess) {
         (void)cudaGetLastError();
         runner_free(rn);
@@ -3112,6 +3127,13 @@ static int runner_reserve(Runner &rn, int R, std::string &err) {
     }
     rn.grid4 = grid4;
     rn.grid8 = grid8;
+    rn.d_reps = (Dev *)rn.block;
+    rn.d_chain_base = (int32_t *)(rn.block + rn.off_base);
+    rn.d_comp_base = (int32_t *)(rn.block + rn.off_comp);
+    rn.d_ctl = (RepCtl *)(rn.block + rn.off_ctl);
+    rn.d_bar = (unsigned int *)(rn.block + rn.off_bar);
+    rn.d_g = (int32_t *)(rn.block + rn.off_g);
+    rn.d_phase = (unsigned long long *)(rn.block + rn.off_phase);
     rn.cap = cap;
     return 0;
 }
@@ -3223,13 +3245,13 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
             rc = ECMC_ECUDA;
         }
     };
-    cu(cudaMemcpyAsync(rn.d_reps, reps.data(), R * sizeof(Dev), cudaMemcpyHostToDevice, st), "reps");
-    cu(cudaMemcpyAsync(rn.d_ctl, ctl.data(), R * sizeof(RepCtl), cudaMemcpyHostToDevice, st), "ctl");
-    cu(cudaMemcpyAsync(rn.d_chain_base, base.data(), (R + 1) * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, st), "base");
-    cu(cudaMemsetAsync(rn.d_bar, 0, 2 * sizeof(unsigned int), st), "bar");
-    cu(cudaMemsetAsync(rn.d_g, 0, G_N * sizeof(int32_t), st), "g");
-    cu(cudaMemsetAsync(rn.d_phase, 0, PH_N * sizeof(unsigned long long), st), "phase");
+    // the tables and zeroed barrier, counters and phase times: one copy
+    unsigned char *h = rn.host.data();
+    memcpy(h, reps.data(), R * sizeof(Dev));
+    memcpy(h + rn.off_base, base.data(), (R + 1) * sizeof(int32_t));
+    memcpy(h + rn.off_ctl, ctl.data(), R * sizeof(RepCtl));
+    memset(h + rn.off_bar, 0, rn.total - rn.off_bar);
+    cu(cudaMemcpyAsync(rn.block, h, rn.total, cudaMemcpyHostToDevice, st), "tables");
     if (rc) return rc;
     Batch b;
     b.reps = rn.d_reps;
@@ -3256,11 +3278,14 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     cu(cudaEventRecord(rn.ev1, st), "event");
     int32_t g[G_N];
     unsigned long long ph[PH_N];
-    cu(cudaMemcpyAsync(ctl.data(), rn.d_ctl, R * sizeof(RepCtl), cudaMemcpyDeviceToHost, st), "ctl");
-    cu(cudaMemcpyAsync(g, rn.d_g, sizeof g, cudaMemcpyDeviceToHost, st), "g");
-    cu(cudaMemcpyAsync(ph, rn.d_phase, sizeof ph, cudaMemcpyDeviceToHost, st), "phase");
+    // control blocks, counters and phase times back: one copy
+    cu(cudaMemcpyAsync(h + rn.off_ctl, rn.block + rn.off_ctl, rn.total - rn.off_ctl,
+                       cudaMemcpyDeviceToHost, st), "tables");
     cu(cudaStreamSynchronize(st), "run");
     if (rc) return rc;
+    memcpy(ctl.data(), h + rn.off_ctl, R * sizeof(RepCtl));
+    memcpy(g, h + rn.off_g, sizeof g);
+    memcpy(ph, h + rn.off_phase, sizeof ph);
     float ms = 0.f;
     cu(cudaEventElapsedTime(&ms, rn.ev0, rn.ev1), "elapsed");
     if (ms_out) *ms_out = ms;
@@ -3316,7 +3341,9 @@ static int runner_run(Runner &rn, cudaStream_t st, ecmc_ctx *const *ctxs, int R,
     }
     for (int r = 0; r < R; ++r) {
         double dg[7];
-        if (ctxs[r]->s.dbg &&
+        // (the launch flagged the replicas whose internal checks recorded
+        // something; only those are read)
+        if (ctl[r].dbg && ctxs[r]->s.dbg &&
             cudaMemcpy(dg, ctxs[r]->s.dbg, sizeof dg, cudaMemcpyDeviceToHost) == cudaSuccess &&
             dg[0] != 0.0) {
             char buf[240];
