@@ -155,12 +155,8 @@ __device__ __forceinline__ int cell_coord(double v, double inv_a, int nc) {
     return c;
 }
 
-// The build's cells in two passes, as the cell-scan context builds its own:
-// k_gb_place puts each disk's id into a free slot of its cell (and counts it
-// in its y bin), k_gb_fill writes the slots' fields row by row, whole sectors
-// at a time (an empty slot's fields are never read).
 template <int C>
-__global__ void k_gb_place(GBuild b) {
+__global__ void k_gb_cells(GBuild b) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= b.n) return;
     const double x = b.x[q], y = b.y[q];
@@ -171,27 +167,16 @@ __global__ void k_gb_place(GBuild b) {
     if (bin >= b.nb) bin = b.nb - 1;
     if (bin < 0) bin = 0;
     atomicAdd(b.bins + bin, 1);
-    for (int sl = 0; sl < C; ++sl)
-        if (atomicCAS(b.cid + cell * C + sl, EMPTY, (uint32_t)q) == EMPTY) return;
-    atomicAdd(b.err, 1ull);
-}
-
-// One block per cell row (grid = nc).
-template <int C>
-__global__ void k_gb_fill(GBuild b) {
-    const uint32_t nrow = (uint32_t)b.nc * C, base = (uint32_t)blockIdx.x * nrow;
-    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
-        const uint32_t q = base + o;
-        const uint32_t id = b.cid[q];
-        double xv = 0.0, yv = 0.0;
-        if (id != EMPTY) {
-            xv = b.x[id];
-            yv = b.y[id];
+    for (int sl = 0; sl < C; ++sl) {
+        const uint32_t loc = cell * C + sl;
+        if (atomicCAS(b.cid + loc, EMPTY, (uint32_t)q) == EMPTY) {
+            b.cx[loc] = x;
+            b.cy[loc] = y;
+            b.cyf[loc] = __double2float_rn(y);
+            return;
         }
-        b.cx[q] = xv;
-        b.cy[q] = yv;
-        b.cyf[q] = __double2float_rn(yv);
     }
+    atomicAdd(b.err, 1ull);
 }
 
 // Exclusive prefix of the y-bin counts, in tiles of SCAN_TILE bins (one block
@@ -1890,13 +1875,10 @@ int graph_build(GraphCtx *g, const double *x, const double *y, std::string &err)
     cudaMemsetAsync(b.bins, 0, ((size_t)b.nb + 1) * 4, st);
     cudaMemsetAsync(b.err, 0, 8, st);
     const unsigned nblk = (unsigned)((s.n + 255) / 256);
-    if (C == 4) {
-        k_gb_place<4><<<nblk, 256, 0, st>>>(b);
-        k_gb_fill<4><<<(unsigned)nc, 256, 0, st>>>(b);
-    } else {
-        k_gb_place<8><<<nblk, 256, 0, st>>>(b);
-        k_gb_fill<8><<<(unsigned)nc, 256, 0, st>>>(b);
-    }
+    if (C == 4)
+        k_gb_cells<4><<<nblk, 256, 0, st>>>(b);
+    else
+        k_gb_cells<8><<<nblk, 256, 0, st>>>(b);
     {
         const unsigned tiles = (unsigned)((b.nb + SCAN_TILE - 1) / SCAN_TILE);
         int32_t *part = (int32_t *)tmp[6];
