@@ -853,32 +853,41 @@ __global__ void k_place(Dev s, const double *x, const double *y, unsigned long l
     atomicAdd(s.lc + LC_ERR_CAP, 1ull);
 }
 
-// One block per cell row (grid = nc). An empty slot's fields are never read;
-// they are written all the same, so that every sector is written whole.
+// Kernels over the slots of every cell row take a 2D grid (rows_grid): y the
+// cell row, x the 256-slot chunk of the row, one thread per slot -- the row
+// without a 64-bit division, and every slot's loads in flight at once.
+constexpr int ROW_THREADS = 256;
+static dim3 rows_grid(int nc, int C) {
+    return dim3((unsigned)(((int64_t)nc * C + ROW_THREADS - 1) / ROW_THREADS), (unsigned)nc);
+}
+
+// An empty slot's fields are never read; they are written all the same, so
+// that every sector is written whole.
 template <int C>
-__global__ void k_fill(Dev s, const double *x, const double *y, uint32_t *loc_of) {
-    const uint32_t nrow = (uint32_t)s.nc * C, base = (uint32_t)blockIdx.x * nrow;
-    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
-        const uint32_t q = base + o;
-        const uint32_t id = s.cid[q];
-        double xv = 0.0, yv = 0.0;
-        if (id != EMPTY) {
-            xv = x[id];
-            yv = y[id];
-            loc_of[id] = q;
-        }
-        s.cx[q] = xv;
-        s.cy[q] = yv;
-        s.ct[q] = 0.0;
-        s.cown[q] = OWN_STATIC;
+__global__ void __launch_bounds__(ROW_THREADS)
+k_fill(Dev s, const double *x, const double *y, uint32_t *loc_of) {
+    const uint32_t nrow = (uint32_t)s.nc * C;
+    const uint32_t o = blockIdx.x * ROW_THREADS + threadIdx.x;
+    if (o >= nrow) return;
+    const uint32_t q = blockIdx.y * nrow + o;
+    const uint32_t id = s.cid[q];
+    double xv = 0.0, yv = 0.0;
+    if (id != EMPTY) {
+        xv = x[id];
+        yv = y[id];
+        loc_of[id] = q;
     }
+    s.cx[q] = xv;
+    s.cy[q] = yv;
+    s.ct[q] = 0.0;
+    s.cown[q] = OWN_STATIC;
 }
 
 template <int C>
 static void launch_cells(const Dev &s, const double *x, const double *y, uint32_t *loc_of,
                          unsigned long long *bad_xy, cudaStream_t st) {
     k_place<C><<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, x, y, bad_xy);
-    k_fill<C><<<(unsigned)s.nc, 256, 0, st>>>(s, x, y, loc_of);
+    k_fill<C><<<rows_grid(s.nc, C), ROW_THREADS, 0, st>>>(s, x, y, loc_of);
 }
 
 // Least and largest y of each cell row, then the rows a disk's scan need not
@@ -891,26 +900,32 @@ static void launch_cells(const Dev &s, const double *x, const double *y, uint32_
 // - It skips row R - 1 when RN(y - yhi(R - 1)) >= d, by the same argument.
 // An empty row is skipped. Moves along x never change a disk's row, so the
 // bits hold until the frame is transposed.
-// One block per cell row (a row is nc * C consecutive slots; grid = nc,
-// 256 threads): the block reduces the row and thread 0 writes its band
-// (INF_BITS and 0 for an empty row). No atomics, no 64-bit division.
-constexpr int BAND_THREADS = 256;
-__global__ void __launch_bounds__(BAND_THREADS) k_bands(Dev s, int C) {
-    __shared__ unsigned long long wlo[BAND_THREADS / 32], whi[BAND_THREADS / 32];
-    const uint32_t nrow = (uint32_t)s.nc * (uint32_t)C, base = (uint32_t)blockIdx.x * nrow;
+__global__ void k_band_init(Dev s) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= s.nc) return;
+    s.rband[q] = INF_BITS;
+    s.rband[s.nc + q] = 0ull;
+}
+
+// Over rows_grid: each block reduces its chunk of one row and its thread 0
+// folds that into the row's band (a few atomics per row, after k_band_init).
+__global__ void __launch_bounds__(ROW_THREADS) k_bands(Dev s, int C) {
+    __shared__ unsigned long long wlo[ROW_THREADS / 32], whi[ROW_THREADS / 32];
+    const uint32_t nrow = (uint32_t)s.nc * (uint32_t)C;
+    const uint32_t o = blockIdx.x * ROW_THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long lo = INF_BITS, hi = 0ull;
-    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
-        const uint32_t q = base + o;
+    if (o < nrow) {
+        const uint32_t q = blockIdx.y * nrow + o;
         if (s.cid[q] != EMPTY) {
             const unsigned long long y = dbits(s.cy[q]);  // y >= 0: bits order like values
-            lo = y < lo ? y : lo;
-            hi = y > hi ? y : hi;
+            lo = y;
+            hi = y;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long l2 = shfl_xor_u64(lo, o), h2 = shfl_xor_u64(hi, o);
+    for (int k2 = 16; k2 > 0; k2 >>= 1) {
+        const unsigned long long l2 = shfl_xor_u64(lo, k2), h2 = shfl_xor_u64(hi, k2);
         lo = l2 < lo ? l2 : lo;
         hi = h2 > hi ? h2 : hi;
     }
@@ -920,12 +935,14 @@ __global__ void __launch_bounds__(BAND_THREADS) k_bands(Dev s, int C) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int q = 1; q < BAND_THREADS / 32; ++q) {
+        for (int q = 1; q < ROW_THREADS / 32; ++q) {
             lo = wlo[q] < lo ? wlo[q] : lo;
             hi = whi[q] > hi ? whi[q] : hi;
         }
-        s.rband[blockIdx.x] = lo;
-        s.rband[s.nc + blockIdx.x] = hi;
+        if (lo != INF_BITS) {
+            atomicMin(s.rband + blockIdx.y, lo);
+            atomicMax(s.rband + s.nc + blockIdx.y, hi);
+        }
     }
 }
 
@@ -935,16 +952,17 @@ __global__ void __launch_bounds__(BAND_THREADS) k_bands(Dev s, int C) {
 // y_j falls, so RN(L - RN(yhi(nc - 1) - y)) >= d bounds the whole row; from row
 // nc - 1 towards row 0 it is RN(L - RN(y - y_j)), bounded by RN(L - RN(y -
 // ylo(0))). (The plain difference there is close to L, far above d.)
-// One block per cell row (grid = nc), as k_bands.
-__global__ void __launch_bounds__(BAND_THREADS) k_skip(Dev s, int C) {
-    const int nc = s.nc, R = (int)blockIdx.x;
-    const uint32_t nrow = (uint32_t)nc * (uint32_t)C, base = (uint32_t)R * nrow;
+// Over rows_grid, one thread per slot.
+__global__ void __launch_bounds__(ROW_THREADS) k_skip(Dev s, int C) {
+    const int nc = s.nc, R = (int)blockIdx.y;
+    const uint32_t nrow = (uint32_t)nc * (uint32_t)C;
     const int Rdn = R == 0 ? nc - 1 : R - 1, Rup = R == nc - 1 ? 0 : R + 1;
     const unsigned long long lo_dn = s.rband[Rdn], lo_up = s.rband[Rup];
     const double hi_dn = __longlong_as_double((long long)s.rband[nc + Rdn]);
     const double lo = __longlong_as_double((long long)lo_up);
-    for (uint32_t o = threadIdx.x; o < nrow; o += blockDim.x) {
-        const uint32_t q = base + o;
+    const uint32_t o = blockIdx.x * ROW_THREADS + threadIdx.x;
+    if (o < nrow) {
+        const uint32_t q = (uint32_t)R * nrow + o;
         uint8_t v = 0;
         if (s.cid[q] != EMPTY && nc >= 5) {
             const double y = s.cy[q];
@@ -969,8 +987,9 @@ __global__ void __launch_bounds__(BAND_THREADS) k_skip(Dev s, int C) {
 
 // Skip bits for the current frame (after the cells are built or transposed).
 static void launch_skip(const Dev &s, int C, cudaStream_t st) {
-    k_bands<<<(unsigned)s.nc, BAND_THREADS, 0, st>>>(s, C);
-    k_skip<<<(unsigned)s.nc, BAND_THREADS, 0, st>>>(s, C);
+    k_band_init<<<(unsigned)((s.nc + 255) / 256), 256, 0, st>>>(s);
+    k_bands<<<rows_grid(s.nc, C), ROW_THREADS, 0, st>>>(s, C);
+    k_skip<<<rows_grid(s.nc, C), ROW_THREADS, 0, st>>>(s, C);
 }
 
 // Coordinates in [0, L) (counted in *bad_xy; not checked with x == null) and
