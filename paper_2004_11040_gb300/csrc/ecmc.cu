@@ -952,8 +952,13 @@ __global__ void __launch_bounds__(ROW_THREADS) k_bands(Dev s, int C) {
 // y_j falls, so RN(L - RN(yhi(nc - 1) - y)) >= d bounds the whole row; from row
 // nc - 1 towards row 0 it is RN(L - RN(y - y_j)), bounded by RN(L - RN(y -
 // ylo(0))). (The plain difference there is close to L, far above d.)
-// Over rows_grid, one thread per slot.
+// Over rows_grid, one thread per slot. The occupied slots of the block are
+// packed first, so that the FP64 tests run on full warps (an FP64 warp
+// instruction occupies the unit as long whatever its lane mask, and most
+// slots are empty: one disk per cell of four slots on a lattice).
 __global__ void __launch_bounds__(ROW_THREADS) k_skip(Dev s, int C) {
+    __shared__ uint32_t occ_q[ROW_THREADS];
+    __shared__ int n_occ;
     const int nc = s.nc, R = (int)blockIdx.y;
     const uint32_t nrow = (uint32_t)nc * (uint32_t)C;
     const int Rdn = R == 0 ? nc - 1 : R - 1, Rup = R == nc - 1 ? 0 : R + 1;
@@ -961,10 +966,20 @@ __global__ void __launch_bounds__(ROW_THREADS) k_skip(Dev s, int C) {
     const double hi_dn = __longlong_as_double((long long)s.rband[nc + Rdn]);
     const double lo = __longlong_as_double((long long)lo_up);
     const uint32_t o = blockIdx.x * ROW_THREADS + threadIdx.x;
+    if (threadIdx.x == 0) n_occ = 0;
+    __syncthreads();
     if (o < nrow) {
         const uint32_t q = (uint32_t)R * nrow + o;
+        if (s.cid[q] != EMPTY && nc >= 5)
+            occ_q[atomicAdd(&n_occ, 1)] = q;
+        else
+            s.cskp[q] = 0;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n_occ) {
+        const uint32_t q = occ_q[threadIdx.x];
         uint8_t v = 0;
-        if (s.cid[q] != EMPTY && nc >= 5) {
+        {
             const double y = s.cy[q];
             if (lo_dn == INF_BITS) {
                 v |= 1;
