@@ -1728,25 +1728,58 @@ __device__ int continue_component(const Dev &s, const int32_t *mem, int m, int r
     // all first keeps the slot operations in last-in first-out order.
     const int nm = m <= 32 ? -m : 0;
     const int my_member = lane < m ? mem[lane] : -1;
+    // up to 32 members: their status and chain state in one round of loads,
+    // one member per lane; the first member continued starts from them (its
+    // state is read once instead of after its status)
+    int my_st = ST_RUNNING;
+    uint32_t my_aloc = 0u, my_ci = 0u;
+    double my_tc = 0.0, my_D = 0.0;
+    int32_t my_nrec = 0;
+    if (nm != 0 && my_member >= 0) {
+        my_st = s.status[my_member];
+        my_aloc = s.aloc[my_member];
+        my_ci = s.ci[my_member];
+        my_tc = s.tc[my_member];
+        my_D = s.D[my_member];
+        my_nrec = s.nrec[my_member];
+    }
+    bool first = nm != 0;
     uint32_t cnt = 0;
     int e = 0, cur = -1, switches = 0;
     for (;;) {
         if (cur < 0) {  // the next member still blocked
-            while (e < m && s.status[mem[e]] != ST_BLOCKED) ++e;
-            if (e >= m) break;
-            cur = mem[e];
+            if (first) {
+                const unsigned bm = __ballot_sync(FULL, my_member >= 0 && my_st == ST_BLOCKED);
+                if (!bm) break;
+                e = __ffs(bm) - 1;
+                cur = __shfl_sync(FULL, my_member, e);
+            } else {
+                while (e < m && s.status[mem[e]] != ST_BLOCKED) ++e;
+                if (e >= m) break;
+                cur = mem[e];
+            }
         }
         const int c = cur;
         int next = -1;
         ChainReg r;
-        r.iloc = s.aloc[c];
-        r.i = s.ci[c];
+        int32_t nrec;
+        if (first) {  // c is the member of lane e
+            r.iloc = __shfl_sync(FULL, my_aloc, e);
+            r.i = __shfl_sync(FULL, my_ci, e);
+            r.ti = __shfl_sync(FULL, my_tc, e);
+            r.D = __shfl_sync(FULL, my_D, e);
+            nrec = __shfl_sync(FULL, my_nrec, e);
+        } else {
+            r.iloc = s.aloc[c];
+            r.i = s.ci[c];
+            r.ti = s.tc[c];
+            r.D = s.D[c];
+            nrec = s.nrec[c];
+        }
+        first = false;
         r.xi = s.cx[r.iloc];
         r.yi = s.cy[r.iloc];
         r.skip = skip_of(s, r.iloc);
-        r.ti = s.tc[c];
-        r.D = s.D[c];
-        int32_t nrec = s.nrec[c];
         int st = ST_RUNNING;
         // members along rows out of reach of their neighbours: the row
         // window while it applies (rowpass.cuh), the general step after
@@ -1820,15 +1853,23 @@ __device__ void repair_component(const Dev &s, int q, int round, double tw, doub
     const int root = s.comp_root[q];
     const int off = s.comp_off[q], m = s.comp_off[q + 1] - off;
     const int32_t *mem = s.comp_mem + off;
+    // T*, the members' earliest time: loaded now, before any member moves, and
+    // reduced where it is needed (after the continuation in the first round),
+    // so that its loads overlap the continuation's own
     double Ts = INFINITY;
-    for (int e = lane; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
+    if (lane < m) Ts = s.vt[mem[lane]];  // (nothing waits on this load yet)
+    for (int e = lane + 32; e < m; e += 32) Ts = fmin(Ts, s.vt[mem[e]]);
+    auto t_star = [&]() {
+        double T = Ts;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) Ts = fmin(Ts, __shfl_xor_sync(FULL, Ts, o));
-    Ts = fmax(Ts, tw);  // earlier windows are final
+        for (int o = 16; o > 0; o >>= 1) T = fmin(T, __shfl_xor_sync(FULL, T, o));
+        return fmax(T, tw);  // earlier windows are final
+    };
     if (lane == 0) atomicAdd(s.lc + LC_REPAIRED, (unsigned long long)m);
     if (round == 1) {
         int met = -1;
         const int how = continue_component<C>(s, mem, m, root, round, tw, tend, &met);
+        Ts = t_star();
         if (how == CONT_DONE) {
             if (lane == 0) atomicAdd(s.lc + LC_CONTINUED, (unsigned long long)m);
             // a later merge must undo all continued events (they were applied
@@ -1842,6 +1883,8 @@ __device__ void repair_component(const Dev &s, int q, int round, double tw, doub
             finish_component(s, mem, m, root, true, met, Ts);
             return;
         }
+    } else {
+        Ts = t_star();
     }
     rollback_members(s, mem, m, Ts);
     if (m <= 32)
