@@ -63,6 +63,9 @@ def create(reps: list[Replica], cells="lattice", undo_cap: int = 256, stream=Non
 # scan), or the constraint graph
 SEARCHES = {"row": dict(rowpass=True, graph=False), "general": dict(rowpass=False, graph=False),
             "graph": dict(rowpass=False, graph=True)}
+# chains a warp advances in each search: one (the warp's lanes share a chain's
+# scan) or 32 (graph mode: a chain per thread)
+CHAINS_PER_WARP = {"row": 1, "general": 1, "graph": 32}
 
 
 def run_batched(systems, budget: int, legs_per_launch: int, stream=None):
@@ -166,6 +169,7 @@ def autotune(reps: list[Replica], trial_budget: int = 20_000,
                 rate = lifts / (ms / 1e3) if ms > 0 else 0.0
                 rows = sum(q.stats()["row_windows"] for q in systems)
                 trials.append({"cells": cells, "search": search, "legs_per_launch": legs,
+                               "chains_per_warp": CHAINS_PER_WARP[search],
                                "liftings_per_s": rate, "row_windows": rows})
                 if best is None or rate > best["liftings_per_s"]:
                     best = dict(trials[-1])

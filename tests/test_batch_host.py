@@ -117,6 +117,9 @@ def test_autotune_keeps_the_fastest_and_records_every_trial(fake, tmp_path, monk
     want = [(c, s, l) for s in ("row", "general", "graph") for c in ("lattice", "default")
             if s != "graph" or c == "lattice" for l in (4, 16, 64)]
     assert sorted(settings) == sorted(want) and len(settings) == len(set(settings))
+    # the chains a warp advances: one in the cell scans, one per thread in graph mode
+    assert {(t["search"], t["chains_per_warp"]) for t in got["trials"]} == \
+           {("row", 1), ("general", 1), ("graph", 32)}
     best = max(got["trials"], key=lambda t: t["liftings_per_s"])
     assert (got["cells"], got["search"], got["legs_per_launch"]) == \
            (best["cells"], best["search"], best["legs_per_launch"]) == ("lattice", "graph", 16)
