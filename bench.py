@@ -386,8 +386,9 @@ def measure(a, search, start, stream, flush, barrier, ws, nc, e2e=True):
         # host x, y, active; run one step; read x, t, active back
         nx = start.n
         e2e_lifts, e2e_s = 0, 0.0
-        h2d = 2 * nx * 8 + 4 * k
-        d2h = 2 * nx * 8 + 4 * k
+        # (bytes of the whole job's step: every rank copies its own system)
+        h2d = ws * (2 * nx * 8 + 4 * k)
+        d2h = ws * (2 * nx * 8 + 4 * k)
         hx = torch.from_numpy(start.x).pin_memory().numpy()
         hy = torch.from_numpy(start.y).pin_memory().numpy()
         ha = torch.from_numpy(start.active.astype(np.int32)).pin_memory().numpy()
@@ -408,6 +409,10 @@ def measure(a, search, start, stream, flush, barrier, ws, nc, e2e=True):
             if s > 0:
                 e2e_lifts += n_l
                 e2e_s += el
+        # whole job over the ranks, as the device value: all ranks' liftings
+        # over the slowest rank's time (the rank's own with one GPU)
+        e2e_ms, e2e_lifts = aggregate(e2e_s * 1000.0, e2e_lifts, ws, device="cuda")
+        e2e_s = e2e_ms / 1000.0
         out["e2e"] = {"value": e2e_lifts / e2e_s, "unit": "liftings/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "includes": "context creation from host positions (cell build), "
