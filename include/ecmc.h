@@ -277,7 +277,9 @@ int ecmc_profile(ecmc_ctx *ctx, ecmc_profile_t *out);
  *   Errors: EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT (a grid barrier wait
  *   passed its 60 s limit; the launch returned instead of waiting).
  * ecmc_batch_last_error -- reason of the last failure of b.
- * ecmc_batch_destroy    -- frees the scratch (the contexts stay valid).
+ * ecmc_batch_destroy    -- releases the scratch to the device memory cache after
+ *                         the batch's stream has finished (the contexts stay
+ *                         valid).
  */
 typedef struct ecmc_batch ecmc_batch;
 int ecmc_batch_create(void *stream, ecmc_batch **out);
